@@ -1,0 +1,358 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself
+(brute force on tiny inputs written independently here, the paper's worked
+example, closed-form relations of Table 1 / Algorithm 3, the LF-decode
+certificate).  CPU only."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CODE = {"$": 0, "A": 1, "C": 2, "G": 3, "T": 4, "N": 5}
+LETTER = "$ACGTN"
+
+
+def enc(s):
+    return np.array([CODE[c] for c in s], dtype=np.uint8)
+
+
+def dec(a):
+    return "".join(LETTER[int(c)] for c in a)
+
+
+def golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            rows[k] = v
+    return rows
+
+
+# ---- independent brute-force pieces (Python, tiny inputs) -------------------
+
+def py_sa(T):
+    """Sort suffixes as explicit tuples: a letter c is (1, c); the j-th sentinel
+    of T is (0, j); a suffix's key runs up to and including its first sentinel."""
+    T = [int(c) for c in T]
+    elem, j = [], 0
+    for c in T:
+        if c == 0:
+            elem.append((0, j))
+            j += 1
+        else:
+            elem.append((1, c))
+    keys = []
+    for p in range(len(T)):
+        k = []
+        for t in range(p, len(T)):
+            k.append(elem[t])
+            if T[t] == 0:
+                break
+        keys.append(tuple(k))
+    return sorted(range(len(T)), key=lambda p: keys[p])
+
+
+def py_concat(strings, both=True):
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A", "N": "N"}
+    out = ""
+    for s in strings:
+        out += s + "$"
+        if both:
+            out += "".join(comp[c] for c in reversed(s)) + "$"
+    return out
+
+
+def rand_list(g, n_str, max_len, n_frac=0.0, allow_empty=True):
+    S = synth.random_strings(g, n_str, max_len, n_frac=n_frac, allow_empty=allow_empty)
+    return S, ["".join(LETTER[c] for c in S.seq[o:o + l]) for o, l in zip(S.offsets[:-1], S.lens)]
+
+
+# ---- concatenation ------------------------------------------------------------
+
+def test_ds_concat_golden():
+    gd = golden("ds_concat_worked_example.txt")
+    s = gd["input"][0]
+    T = oracle.concat(enc(s), np.array([len(s)]), both=True)
+    assert dec(T) == gd["ds"][0]
+
+
+def test_concat_matches_python():
+    g = synth.rng(11)
+    for both in (True, False):
+        for _ in range(20):
+            S, strs = rand_list(g, int(g.integers(1, 6)), 9, n_frac=0.1)
+            assert dec(oracle.concat(S.seq, S.lens, both)) == py_concat(strs, both)
+
+
+# ---- O1 suffix array / BWT --------------------------------------------------------
+
+@pytest.mark.parametrize("both", [True, False])
+def test_suffix_array_vs_python_sort(both):
+    g = synth.rng(12 + both)
+    for _ in range(60):
+        S, strs = rand_list(g, int(g.integers(1, 5)), 10, n_frac=0.15)
+        T = oracle.concat(S.seq, S.lens, both)
+        assert list(oracle.suffix_array(T)) == py_sa(T)
+
+
+def test_all_short_lists_exhaustive():
+    """Every list of <= 2 strings of length <= 3 over {A,C,N} (plus empty)."""
+    import itertools
+    words = [""] + ["".join(w) for L in range(1, 4) for w in itertools.product("ACN", repeat=L)]
+    cnt = 0
+    for a in words:
+        for b in [None] + words[::5]:
+            strs = [a] if b is None else [a, b]
+            seq = enc("".join(strs))
+            T = oracle.concat(seq, np.array([len(s) for s in strs]), True)
+            SA = py_sa(T)
+            B = np.array([T[p - 1] if p > 0 else T[-1] for p in SA], dtype=np.uint8)
+            assert np.array_equal(oracle.bwt(T), B)
+            cnt += 1
+    assert cnt > 300
+
+
+def test_bwt_lf_closed_form():
+    """Table 1: pi(k) = S^{-1}(S(k)-1) = pi_B(B[k],k) whenever B[k] != $; the $
+    rows map onto rows 0..m-1 (Section "Locating with FM-index": LF does not
+    follow the text at a sentinel)."""
+    g = synth.rng(13)
+    for _ in range(30):
+        S, _ = rand_list(g, int(g.integers(1, 6)), 30, n_frac=0.05)
+        T = oracle.concat(S.seq, S.lens, True)
+        SA = oracle.suffix_array(T)
+        B = oracle.bwt_from_sa(T, SA)
+        n = len(T)
+        inv = np.empty(n, dtype=np.int64)
+        inv[SA] = np.arange(n)
+        C = np.array([np.sum(B < a) for a in range(6)])
+        seen = np.zeros(6, dtype=np.int64)
+        dollar_targets = []
+        for k in range(n):
+            a = int(B[k])
+            pik = C[a] + seen[a]
+            seen[a] += 1
+            if a != 0:
+                assert pik == inv[(SA[k] - 1) % n]
+            else:
+                dollar_targets.append(pik)
+        assert sorted(dollar_targets) == list(range(int(np.sum(T == 0))))
+
+
+def test_counts_and_occ_table():
+    g = synth.rng(14)
+    S, _ = rand_list(g, 7, 200, n_frac=0.02)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    C = oracle.counts(B)
+    for a in range(6):
+        assert C[a + 1] - C[a] == np.sum(T == a)
+    for D in (1, 7, 64, 128):
+        occ = oracle.occ_table(B, D)
+        ref = np.zeros((len(B) // D + 1, 6), dtype=np.int64)
+        cum = np.zeros((len(B) + 1, 6), dtype=np.int64)
+        for a in range(6):
+            cum[1:, a] = np.cumsum(B == a)
+        ref[:] = cum[np.arange(len(B) // D + 1) * D]
+        assert np.array_equal(occ, ref)
+
+
+# ---- O2 certificate / Retrieve ------------------------------------------------------
+
+def test_retrieve_decodes_every_string():
+    g = synth.rng(15)
+    S, strs = rand_list(g, 6, 40, n_frac=0.05)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    ds = py_concat(strs, True).split("$")[:-1]
+    for i, s in enumerate(ds):
+        assert dec(oracle.retrieve(B, i)) == s
+
+
+def test_certificate_accepts_true_bwt_and_rejects_plants():
+    g = synth.rng(16)
+    for trial in range(40):
+        S, _ = rand_list(g, int(g.integers(1, 6)), 25, n_frac=0.05)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        assert oracle.certify(B, T) == 0
+        # plant: swap two different symbols
+        diff = np.flatnonzero(B != B[0])
+        if len(diff):
+            Bb = B.copy()
+            j = int(diff[g.integers(0, len(diff))])
+            Bb[0], Bb[j] = Bb[j], Bb[0]
+            assert oracle.certify(Bb, T) != 0
+        # plant: BWT of the list in another order
+        if len(S.lens) > 1 and len(set(map(tuple, np.split(S.seq, S.offsets[1:-1])))) > 1:
+            perm = np.arange(len(S.lens))[::-1]
+            off = S.offsets
+            seq2 = np.concatenate([S.seq[off[i]:off[i + 1]] for i in perm])
+            T2 = oracle.concat(seq2, S.lens[perm], True)
+            B2 = oracle.bwt(T2)
+            if not np.array_equal(B2, B):
+                assert oracle.certify(B2, T) != 0
+        # plant: a symbol changed (counts break)
+        Bc = B.copy()
+        Bc[len(B) // 2] = (Bc[len(B) // 2] % 5) + 1 if Bc[len(B) // 2] != 0 else 1
+        assert oracle.certify(Bc, T) != 0
+
+
+# ---- O3 Algorithm 1 ---------------------------------------------------------------
+
+@pytest.mark.parametrize("both", [True, False])
+def test_merge_equals_build_of_concatenation(both):
+    g = synth.rng(17 + both)
+    for trial in range(80):
+        S, _ = rand_list(g, int(g.integers(1, 7)), 30, n_frac=0.05)
+        cut = int(g.integers(0, len(S.lens) + 1))
+        A, Bl = S.subset(0, cut), S.subset(cut, len(S.lens))
+        TA = oracle.concat(A.seq, A.lens, both)
+        TB = oracle.concat(Bl.seq, Bl.lens, both)
+        Tall = oracle.concat(S.seq, S.lens, both)
+        M, pos = oracle.merge(oracle.bwt(TA), oracle.bwt(TB), want_pos=True)
+        assert np.array_equal(M, oracle.bwt(Tall))
+        assert np.all(np.diff(pos) > 0)
+
+
+def test_merge_into_empty_and_of_empty():
+    g = synth.rng(19)
+    S, _ = rand_list(g, 4, 30)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    assert np.array_equal(oracle.merge(np.zeros(0, np.uint8), B), B)
+    assert np.array_equal(oracle.merge(B, np.zeros(0, np.uint8)), B)
+
+
+def test_build_incremental_groups():
+    g = synth.rng(20)
+    S, _ = rand_list(g, 9, 60, n_frac=0.02)
+    ref = oracle.bwt(oracle.concat(S.seq, S.lens, True))
+    for grp in (1, 2, 4, 9):
+        assert np.array_equal(oracle.build_incremental(S.seq, S.lens, True, grp, nthreads=2), ref)
+
+
+def test_pangenome_incremental_certified():
+    """A small pangenome (near-identical haplotypes): incremental build passes the
+    certificate and equals the one-shot O1 build."""
+    S = synth.pangenome(seed=99, founder_len=3000, n_hap=6, batch=2)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.build_incremental(S.seq, S.lens, True, 2, nthreads=2)
+    assert oracle.certify(B, T) == 0
+    assert np.array_equal(B, oracle.bwt(T))
+
+
+# ---- backward search / Algorithm 3 ------------------------------------------------
+
+def test_backward_search_vs_brute():
+    g = synth.rng(21)
+    for both in (True, False):
+        S, _ = rand_list(g, 5, 60, n_frac=0.05)
+        T = oracle.concat(S.seq, S.lens, both)
+        B = oracle.bwt(T)
+        pats = []
+        for _ in range(80):
+            L = int(g.integers(1, 7))
+            if g.random() < 0.6 and len(S.seq) > L:
+                s = int(g.integers(0, len(S.seq) - L))
+                pats.append(S.seq[s:s + L].copy())
+            else:
+                pats.append(synth.random_bases(g, L))
+        q = np.concatenate(pats)
+        qoff = np.concatenate([[0], np.cumsum([len(p) for p in pats])])
+        lohi = oracle.backward_search(B, q, qoff)
+        for (lo, hi), p in zip(lohi, pats):
+            assert lo == oracle.lo_brute(T, p)
+            assert hi - lo == oracle.occ_brute(T, p)
+
+
+def test_occ_strand_symmetry():
+    """Section "Double-strand BWT": occ(P) = occ(rc(P)) in a DS text."""
+    g = synth.rng(22)
+    S, _ = rand_list(g, 4, 80)
+    T = oracle.concat(S.seq, S.lens, True)
+    comp = np.array([0, 4, 3, 2, 1, 5], dtype=np.uint8)
+    for _ in range(100):
+        L = int(g.integers(1, 6))
+        p = synth.random_bases(g, L)
+        assert oracle.occ_brute(T, p) == oracle.occ_brute(T, comp[p[::-1]])
+
+
+def test_extension_bi_intervals():
+    """Algorithm 3 against the bi-interval definition (lo(P), lo(rc P), occ(P))."""
+    g = synth.rng(23)
+    comp = np.array([0, 4, 3, 2, 1, 5], dtype=np.uint8)
+    S, _ = rand_list(g, 4, 50, n_frac=0.05)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+
+    def bi(p):
+        return (oracle.lo_brute(T, p), oracle.lo_brute(T, comp[p[::-1]]), oracle.occ_brute(T, p))
+
+    for _ in range(150):
+        L = int(g.integers(0, 5))
+        if L and g.random() < 0.7:
+            s = int(g.integers(0, len(S.seq) - L))
+            p = S.seq[s:s + L].copy()
+        else:
+            p = synth.random_bases(g, L)
+        x = bi(p) if L else (0, 0, len(T))
+        a = int(g.integers(1, 6))
+        assert oracle.ext(B, x, a, forward=False) == bi(np.concatenate([[a], p]).astype(np.uint8))
+        assert oracle.ext(B, x, a, forward=True) == bi(np.concatenate([p, [a]]).astype(np.uint8))
+
+
+# ---- O4 Algorithm 4 vs O5 definition ----------------------------------------------
+
+def test_smem_paper_worked_example():
+    gd = golden("smem_worked_example.txt")
+    text, query = gd["text"][0], gd["query"][0]
+    T = oracle.concat(enc(text), np.array([len(text)]), True)
+    B = oracle.bwt(T)
+    q = enc(query)
+    qoff = np.array([0, len(q)])
+    got = oracle.smem(B, q, qoff, 1, 1)
+    want = np.array([[int(v) for v in gd["smem"]]])
+    assert np.array_equal(got, want)
+    assert np.array_equal(oracle.smem_brute(T, q, qoff, 1, 1), want)
+    # the contained MEM (5,1,2): text offset 5, pattern offset 1, length 2 matches
+    t_off, p_off, L = (int(v) for v in gd["contained_mem"])
+    assert text[t_off:t_off + L] == query[p_off:p_off + L]
+    assert not any(r[1] == p_off for r in got)
+
+
+@pytest.mark.parametrize("ell,smin", [(1, 1), (2, 1), (3, 2), (4, 1), (2, 3), (6, 1)])
+def test_smem_alg4_equals_definition(ell, smin):
+    g = synth.rng(100 + 10 * ell + smin)
+    comp = np.array([0, 4, 3, 2, 1, 5], dtype=np.uint8)
+    for trial in range(12):
+        S, _ = rand_list(g, int(g.integers(1, 5)), 40, n_frac=0.03, allow_empty=True)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        qs = []
+        for _ in range(8):
+            L = int(g.integers(0, 25))
+            if g.random() < 0.7 and len(S.seq) > L + 1:
+                s = int(g.integers(0, len(S.seq) - L))
+                p = S.seq[s:s + L].copy()
+                m = g.random(L) < 0.08
+                p[m] = synth.random_bases(g, int(m.sum()))
+                if g.random() < 0.5:
+                    p = comp[p[::-1]]
+            else:
+                p = synth.random_bases(g, L)
+            qs.append(p.astype(np.uint8))
+        q = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
+        qoff = np.concatenate([[0], np.cumsum([len(p) for p in qs])]).astype(np.int64)
+        a = oracle.smem(B, q, qoff, ell, smin)
+        b = oracle.smem_brute(T, q, qoff, ell, smin)
+        assert np.array_equal(a, b), (ell, smin, trial)
+        a_mt = oracle.smem(B, q, qoff, ell, smin, nthreads=3)
+        assert np.array_equal(a, a_mt)
