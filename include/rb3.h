@@ -1,0 +1,172 @@
+/*
+ * rb3.h -- C ABI of librb3.so: GB300 (sm_103a) multi-string double-strand BWT
+ * construction by batch build + merge, and backward / SMEM search on the
+ * result.  The method is H. Li, "BWT construction and search at the terabase
+ * scale" (arXiv 2409.00613); each call cites the passage that defines what it
+ * computes.  All arithmetic is integer and exact.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Symbols.  uint8 codes $=0 A=1 C=2 G=3 T=4 N=5, ordered
+ *    $_0 < ... < $_{m-1} < A < C < G < T < N   (Section "BWT construction").
+ *    Input strings and queries hold letters 1..5 only.  N is an ordinary
+ *    symbol: it matches N and is its own complement (Section "Double-strand
+ *    BWT": the complements of $,A,C,G,T,N are $,T,G,C,A,N).
+ *  Integers.  Every count, rank and position is int64 (a BWT may exceed 2^32
+ *    symbols; one index holds at most 2^40).
+ *  Pointers.  Any array argument may be a device pointer or a host pointer;
+ *    the library tells them apart with cudaPointerGetAttributes.  Host inputs
+ *    are copied to the device inside the call; host outputs are filled before
+ *    the call returns.
+ *  Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    Every device operation is enqueued on it.  Calls whose result size is
+ *    data dependent (build, merge, mem_search) synchronize that stream before
+ *    they return; the others return once the work is enqueued when all their
+ *    outputs are device memory.
+ *  Ownership.  The library owns every rb3_index and its scratch memory
+ *    (stream-ordered cudaMallocAsync); callers own every output buffer.
+ *  Errors.  Every int-returning call returns RB3_OK or an RB3_E_* code and
+ *    sets a per-thread message readable with rb3_last_error().  There is no
+ *    CPU fallback: without a usable CUDA device every compute call returns
+ *    RB3_E_CUDA.
+ */
+#ifndef RB3_H
+#define RB3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RB3_OK 0
+#define RB3_E_INVAL 1    /* bad argument: NULL, negative size, symbol out of range, wrong index kind */
+#define RB3_E_NOMEM 2    /* a device or host allocation failed */
+#define RB3_E_CUDA 3     /* a CUDA call failed (no device, launch error, ...) */
+#define RB3_E_TIMEOUT 4  /* a bounded device-side wait gave up; the context is still usable */
+#define RB3_E_CAPACITY 5 /* caller's output buffer too small; the needed size is returned */
+#define RB3_E_IO 6       /* file read / write / format error */
+
+#define RB3_SYM_SENTINEL 0
+#define RB3_SYM_A 1
+#define RB3_SYM_C 2
+#define RB3_SYM_G 3
+#define RB3_SYM_T 4
+#define RB3_SYM_N 5
+
+/* Opaque, device-resident index: a 4-bit packed BWT B with interleaved Occ
+ * checkpoints, C_B(a) for every symbol, n = |B|, m = number of sentinels.
+ * Layout in HBM: blocks of D symbols; block b is 32 header bytes (for each
+ * symbol a, rank_B(a, b*D) as uint32 low words at bytes 0..23 and uint8 high
+ * bytes at 24..29) followed by D/2 payload bytes (symbol b*D+o in byte o/2,
+ * low nibble when o is even).  An index returned by rb3_build_batch also keeps
+ * the batch's text and inverse suffix array, which rb3_merge uses to walk the
+ * new strings in segments; rb3_drop_build_data frees them. */
+typedef struct rb3_index rb3_index;
+
+/* Tuning knobs.  Zero in any field means "default / autotuned". */
+typedef struct {
+    int32_t occ_interval;  /* D, symbols per Occ block: 64, 128 or 256 (default 64) */
+    int32_t single_strand; /* 0: index both strands (the paper's default, Section "Methods"); 1: forward only */
+    int64_t seg_len;       /* merge: walk segment length L (default: autotuned) */
+    int64_t seed_cap;      /* merge: most ForwardExt steps spent on one segment seed (default 4*L) */
+    int32_t merge_form;    /* 0: segmented batched walk; 1: plain Algorithm 1, one walk per string */
+    int32_t search_form;   /* 0: chunked work-stealing SMEM search; 1: plain, one query per thread */
+    int64_t chunk_len;     /* SMEM: query chunk length (default 256) */
+    int32_t reserved[8];
+} rb3_opts;
+
+/* One SMEM: query qid, query interval [start, end), and the SA bi-interval
+ * (k, k', s) = (lo(X), lo(rc X), occ(X)) of X = query[start, end)
+ * (Section "Double-strand BWT", SA bi-interval). 40 bytes. */
+typedef struct {
+    int64_t qid;
+    int32_t start, end;
+    int64_t k, kp, s;
+} rb3_smem;
+
+/* Fills *o with defaults (all zero). */
+void rb3_opts_default(rb3_opts *o);
+
+/* Partial BWT of one batch (Section "BWT construction": the BWT of a batch is
+ * computed on its own and then merged; Section "Basic concepts" and Table 1
+ * define T, S and B[i] = T[S(i)-1]).
+ * seq: the n_seq strings back to back, codes 1..5 (device or host), of total
+ *   length sum(len); len: n_seq lengths >= 0 (host or device).
+ * The indexed text is T = P0 $ rc(P0) $ P1 $ rc(P1) $ ... (Section
+ * "Double-strand BWT"), or P0 $ P1 $ ... with single_strand; sentinels are
+ * ordered by position.  The batch's text must hold fewer than 2^31 symbols.
+ * *out receives a new index owned by the caller (free with rb3_index_free).
+ * RB3_E_INVAL on a symbol outside 1..5 or a negative length. */
+int rb3_build_batch(const uint8_t *seq, const int64_t *len, int64_t n_seq, const rb3_opts *o,
+                    void *stream, rb3_index **out);
+
+/* An index of zero strings (n = m = 0); merging a batch into it yields the batch. */
+int rb3_index_empty(const rb3_opts *o, rb3_index **out);
+
+/* Algorithm 1 (AppendBWT): dst := BWT(strings of dst, then strings of src).
+ * The sentinels of src rank after those of dst (the walk starts at l = m1).
+ * src is unchanged.  With src's build data the new strings are walked in
+ * exact segments (seeded by ForwardExt of Algorithm 3); without it, or with
+ * merge_form = 1, one walk per string as in the paper.  The result is the same
+ * bit for bit.  rb3_merge uses default options. */
+int rb3_merge(rb3_index *dst, const rb3_index *src, void *stream);
+int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_opts *o, void *stream);
+
+/* Backward search (Section "Suffix array interval and backward search"):
+ * for query i = q[qoff[i] .. qoff[i+1]) writes lo_hi[2i] = lo(P) (the number of
+ * suffixes smaller than P) and lo_hi[2i+1] = hi(P) = lo(P) + occ(P).
+ * qoff: nq+1 non-decreasing offsets; lo_hi: 2*nq int64, caller-owned. */
+int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
+                        int64_t *lo_hi, void *stream);
+
+/* SMEMs of length >= min_len occurring >= min_occ times (Section "Finding
+ * supermaximal exact matches", Algorithm 4 with Algorithm 3), for every query.
+ * Needs a double-strand index.  Records are sorted by (qid, start).  If more
+ * than cap records exist, nothing is written, *n_out holds the number needed
+ * and RB3_E_CAPACITY is returned; call again with a larger buffer. */
+int rb3_mem_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
+                   int64_t min_occ, rb3_smem *out, int64_t cap, int64_t *n_out, void *stream);
+int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
+                        int32_t min_len, int64_t min_occ, const rb3_opts *o, rb3_smem *out, int64_t cap,
+                        int64_t *n_out, void *stream);
+
+/* Unpacks B into codes (n bytes, one symbol per byte) and, when occ != NULL,
+ * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */
+int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);
+
+/* n, m, C[0..6] (C[a] = C_B(a), C[6] = n), D and flags (bit0: single strand,
+ * bit1: holds build data).  Any output pointer may be NULL. */
+int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int32_t *occ_interval,
+                   int32_t *flags);
+
+/* Frees the batch text and inverse suffix array kept by rb3_build_batch. */
+int rb3_drop_build_data(rb3_index *idx);
+
+/* Static on-disk image (header + the packed blocks, which already hold the
+ * Occ checkpoints), in the spirit of the paper's static, memory-mappable BWT
+ * (Section "BWT construction").  Appending after a load continues the build. */
+int rb3_index_save(const rb3_index *idx, const char *path);
+int rb3_index_load(const char *path, void *stream, rb3_index **out);
+
+void rb3_index_free(rb3_index *idx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rb3_last_error(void);
+
+/* Host helper: ACGT/acgt -> 1..4, every other byte -> N (5). */
+int rb3_encode_ascii(const char *ascii, int64_t n, uint8_t *codes);
+
+/* Per-phase device timing.  When enabled, every phase of build / merge /
+ * search is bracketed by CUDA events on the caller's stream and its duration
+ * accumulated; launches of the library's kernels are counted always.
+ * names[i] (static strings), ms[i], calls[i] for i < *n (at most cap). */
+int rb3_profile_enable(int on);
+int rb3_profile_reset(void);
+int rb3_profile_read(const char **names, double *ms, int64_t *calls, int32_t cap, int32_t *n);
+int64_t rb3_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB3_H */

@@ -1,0 +1,574 @@
+// The C ABI of librb3 (declared in include/rb3.h): argument checks, host/device
+// pointer handling, index lifetime, export / save / load, profiling and errors.
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace rb3 {
+
+std::atomic<int64_t> g_launches{0};
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    cudaGetLastError();  // clear a sticky-free error so later calls start clean
+    set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+    return e == cudaErrorMemoryAllocation ? RB3_E_NOMEM : RB3_E_CUDA;
+}
+
+static void ensure_pool() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        // keep up to 64 GiB of freed scratch in the pool between calls
+        uint64_t thr = 64ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = true;
+}
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+    ensure_pool();
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RB3_E_NOMEM : RB3_E_CUDA;
+    }
+    return RB3_OK;
+}
+
+void dev_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+int DevBuf::alloc(size_t nbytes, cudaStream_t s) {
+    release();
+    st = s;
+    int r = dev_alloc(&p, nbytes, s);
+    if (r == RB3_OK) bytes = nbytes;
+    return r;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- profiling ---------------------------------------------------------------
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+struct Pending {
+    const char *name;
+    cudaEvent_t a, b;
+};
+static std::vector<Pending> g_pending;
+static std::map<std::string, std::pair<double, int64_t>> g_acc;
+static std::vector<std::string> g_names;  // stable storage for names handed out
+
+bool profile_on() { return g_prof.load(std::memory_order_relaxed); }
+
+void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back({name, a, b});
+}
+
+static void profile_drain() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &e = g_acc[p.name];
+            e.first += ms;
+            e.second += 1;
+        }
+        cudaGetLastError();
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_pending.clear();
+}
+
+// ---- index utilities ----------------------------------------------------------
+__global__ void k_counts_at_n(OccView V, int64_t *__restrict__ out) {
+    int64_t r[SIGMA];
+    rank_all(V, V.n, r);
+    for (int a = 0; a < SIGMA; ++a) out[a] = r[a];
+}
+
+int finalize_counts(rb3_index *x, cudaStream_t st) {
+    DevBuf b;
+    RB3_TRY(b.alloc(sizeof(int64_t) * SIGMA, st));
+    RB3_LAUNCH(k_counts_at_n, 1, 1, 0, st, occ_view(x), b.as<int64_t>());
+    int64_t h[SIGMA];
+    RB3_CUDA_TRY(cudaMemcpyAsync(h, b.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    x->C[0] = 0;
+    for (int a = 0; a < SIGMA; ++a) x->C[a + 1] = x->C[a] + h[a];
+    if (x->C[SIGMA] != x->n || h[0] != x->m) {
+        set_error("index counts inconsistent: sum %lld n %lld, sentinels %lld m %lld", (long long)x->C[SIGMA],
+                  (long long)x->n, (long long)h[0], (long long)x->m);
+        return RB3_E_CUDA;
+    }
+    return RB3_OK;
+}
+
+// one thread per 8 symbols
+__global__ void k_unpack(OccView V, uint8_t *__restrict__ codes) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t q0 = t * 8;
+    if (q0 >= V.n) return;
+    const uint8_t *blk = V.blocks + (q0 >> V.log2D) * (int64_t)V.bb;
+    int o = (int)(q0 & ((1 << V.log2D) - 1));
+    uint32_t w = *reinterpret_cast<const uint32_t *>(blk + HEADER_BYTES + (o >> 1));
+    for (int j = 0; j < 8 && q0 + j < V.n; ++j) codes[q0 + j] = (uint8_t)((w >> (4 * j)) & 15u);
+}
+
+__global__ void k_occ_export(OccView V, int64_t nblocks, int64_t *__restrict__ occ) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const uint8_t *h = V.blocks + b * (int64_t)V.bb;
+    for (int a = 0; a < SIGMA; ++a)
+        occ[b * SIGMA + a] = (int64_t)(*reinterpret_cast<const uint32_t *>(h + 4 * a)) | ((int64_t)h[24 + a] << 32);
+}
+
+int export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st) {
+    OccView V = occ_view(x);
+    if (codes && x->n > 0) {
+        int64_t th = (x->n + 7) / 8;
+        RB3_LAUNCH(k_unpack, (unsigned)((th + 255) / 256), 256, 0, st, V, codes);
+    }
+    if (occ) RB3_LAUNCH(k_occ_export, (unsigned)((x->nblocks + 255) / 256), 256, 0, st, V, x->nblocks, occ);
+    return RB3_OK;
+}
+
+static int make_empty(const rb3_opts *o, cudaStream_t st, rb3_index **out) {
+    int D = (o && o->occ_interval) ? o->occ_interval : 64;
+    RB3_CHECK_ARG(D == 64 || D == 128 || D == 256, "occ_interval must be 64, 128 or 256");
+    rb3_index *x = new rb3_index();
+    x->D = D;
+    x->log2D = ilog2(D);
+    x->block_bytes = HEADER_BYTES + D / 2;
+    x->single_strand = (o && o->single_strand) ? 1 : 0;
+    x->nblocks = 1;
+    cudaGetDevice(&x->device);
+    int r = dev_alloc((void **)&x->blocks, x->block_bytes, st);
+    if (r != RB3_OK) {
+        delete x;
+        return r;
+    }
+    cudaError_t e = cudaMemsetAsync(x->blocks, 0, x->block_bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(x->blocks, st);
+        delete x;
+        return cuda_fail(e, "make_empty", __FILE__, __LINE__);
+    }
+    *out = x;
+    return RB3_OK;
+}
+
+static void free_index(rb3_index *x) {
+    if (!x) return;
+    cudaStream_t st = 0;
+    dev_free(x->blocks, st);
+    dev_free(x->text, st);
+    dev_free(x->isa, st);
+    cudaStreamSynchronize(st);
+    delete x;
+}
+
+// Copies a caller array to the device when it is host memory.
+struct InArg {
+    const void *dev = nullptr;
+    DevBuf buf;
+    int set(const void *p, size_t bytes, cudaStream_t st) {
+        if (is_device_ptr(p) || bytes == 0) {
+            dev = p;
+            return RB3_OK;
+        }
+        RB3_TRY(buf.alloc(bytes, st));
+        RB3_CUDA_TRY(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, st));
+        dev = buf.p;
+        return RB3_OK;
+    }
+};
+
+static int read_i64(const int64_t *p, int64_t n, std::vector<int64_t> &v, cudaStream_t st) {
+    v.resize(n);
+    if (n == 0) return RB3_OK;
+    if (is_device_ptr(p)) {
+        RB3_CUDA_TRY(cudaMemcpyAsync(v.data(), p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
+        RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        memcpy(v.data(), p, sizeof(int64_t) * n);
+    }
+    return RB3_OK;
+}
+
+static int check_qoff(const std::vector<int64_t> &qo) {
+    if (qo.empty()) return RB3_OK;
+    RB3_CHECK_ARG(qo[0] >= 0, "qoff[0] < 0");
+    for (size_t i = 1; i < qo.size(); ++i) RB3_CHECK_ARG(qo[i] >= qo[i - 1], "qoff must be non-decreasing");
+    return RB3_OK;
+}
+
+}  // namespace rb3
+
+using namespace rb3;
+
+// ---------------------------------------------------------------------------
+RB3_EXPORT void rb3_opts_default(rb3_opts *o) {
+    if (o) memset(o, 0, sizeof(*o));
+}
+
+RB3_EXPORT const char *rb3_last_error(void) { return g_err.c_str(); }
+
+RB3_EXPORT int rb3_build_batch(const uint8_t *seq, const int64_t *len, int64_t n_seq, const rb3_opts *o, void *stream,
+                               rb3_index **out) {
+    g_err.clear();
+    RB3_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    RB3_CHECK_ARG(n_seq >= 0, "n_seq < 0");
+    RB3_CHECK_ARG(n_seq == 0 || len != nullptr, "len is NULL");
+    rb3_opts opts;
+    rb3_opts_default(&opts);
+    if (o) opts = *o;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> lens;
+    RB3_TRY(read_i64(len, n_seq, lens, st));
+    int64_t total = 0;
+    for (int64_t i = 0; i < n_seq; ++i) {
+        RB3_CHECK_ARG(lens[i] >= 0, "negative string length");
+        total += lens[i];
+    }
+    RB3_CHECK_ARG(total == 0 || seq != nullptr, "seq is NULL");
+    InArg s;
+    RB3_TRY(s.set(seq, (size_t)total, st));
+    rb3_index *x = new rb3_index();
+    cudaGetDevice(&x->device);
+    int r = build_batch_impl(static_cast<const uint8_t *>(s.dev), lens.data(), n_seq, opts, st, x);
+    if (r == RB3_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "rb3_build_batch", __FILE__, __LINE__);
+    }
+    if (r != RB3_OK) {
+        free_index(x);
+        return r;
+    }
+    *out = x;
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_index_empty(const rb3_opts *o, rb3_index **out) {
+    g_err.clear();
+    RB3_CHECK_ARG(out != nullptr, "out is NULL");
+    return make_empty(o, 0, out);
+}
+
+RB3_EXPORT int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_opts *o, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(dst && src, "NULL index");
+    rb3_opts opts;
+    rb3_opts_default(&opts);
+    if (o) opts = *o;
+    cudaStream_t st = (cudaStream_t)stream;
+    RB3_TRY(merge_impl(dst, src, opts, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_merge(rb3_index *dst, const rb3_index *src, void *stream) {
+    return rb3_merge_opts(dst, src, nullptr, stream);
+}
+
+RB3_EXPORT int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
+                                   int64_t *lo_hi, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    RB3_CHECK_ARG(nq >= 0, "nq < 0");
+    if (nq == 0) return RB3_OK;
+    RB3_CHECK_ARG(qoff && lo_hi, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> qo;
+    RB3_TRY(read_i64(qoff, nq + 1, qo, st));
+    RB3_TRY(check_qoff(qo));
+    RB3_CHECK_ARG(qo[nq] == 0 || q != nullptr, "q is NULL");
+    InArg dq, doff;
+    RB3_TRY(dq.set(q, (size_t)qo[nq], st));
+    RB3_TRY(doff.set(qoff, sizeof(int64_t) * (nq + 1), st));
+    bool dev_out = is_device_ptr(lo_hi);
+    DevBuf ob;
+    int64_t *o = lo_hi;
+    if (!dev_out) {
+        RB3_TRY(ob.alloc(sizeof(int64_t) * 2 * nq, st));
+        o = ob.as<int64_t>();
+    }
+    RB3_TRY(backward_search_impl(idx, static_cast<const uint8_t *>(dq.dev), static_cast<const int64_t *>(doff.dev), nq,
+                                 qo[nq], o, st));
+    if (!dev_out) RB3_CUDA_TRY(cudaMemcpyAsync(lo_hi, o, sizeof(int64_t) * 2 * nq, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
+                                   int32_t min_len, int64_t min_occ, const rb3_opts *o, rb3_smem *out, int64_t cap,
+                                   int64_t *n_out, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr && n_out != nullptr, "NULL argument");
+    *n_out = 0;
+    RB3_CHECK_ARG(nq >= 0 && cap >= 0, "negative size");
+    RB3_CHECK_ARG(min_len >= 1, "min_len must be >= 1");
+    RB3_CHECK_ARG(min_occ >= 1, "min_occ must be >= 1");
+    RB3_CHECK_ARG(!idx->single_strand, "SMEM search needs a double-strand index");
+    if (nq == 0) return RB3_OK;
+    RB3_CHECK_ARG(qoff != nullptr, "qoff is NULL");
+    RB3_CHECK_ARG(cap == 0 || out != nullptr, "out is NULL");
+    rb3_opts opts;
+    rb3_opts_default(&opts);
+    if (o) opts = *o;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> qo;
+    RB3_TRY(read_i64(qoff, nq + 1, qo, st));
+    RB3_TRY(check_qoff(qo));
+    for (int64_t i = 0; i < nq; ++i)
+        RB3_CHECK_ARG(qo[i + 1] - qo[i] < (int64_t(1) << 31), "query longer than 2^31 - 1");
+    RB3_CHECK_ARG(qo[nq] == 0 || q != nullptr, "q is NULL");
+    InArg dq, doff;
+    RB3_TRY(dq.set(q, (size_t)qo[nq], st));
+    RB3_TRY(doff.set(qoff, sizeof(int64_t) * (nq + 1), st));
+    bool dev_out = cap == 0 || is_device_ptr(out);
+    DevBuf ob;
+    rb3_smem *od = out;
+    if (!dev_out) {
+        RB3_TRY(ob.alloc(sizeof(rb3_smem) * cap, st));
+        od = ob.as<rb3_smem>();
+    }
+    int64_t cnt = 0;
+    int r = mem_search_impl(idx, static_cast<const uint8_t *>(dq.dev), static_cast<const int64_t *>(doff.dev),
+                            qo.data(), nq, qo[nq], min_len, min_occ, opts, od, cap, &cnt, st);
+    *n_out = cnt;
+    if (r != RB3_OK) return r;
+    if (!dev_out && cnt > 0)
+        RB3_CUDA_TRY(cudaMemcpyAsync(out, od, sizeof(rb3_smem) * cnt, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_mem_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
+                              int64_t min_occ, rb3_smem *out, int64_t cap, int64_t *n_out, void *stream) {
+    return rb3_mem_search_opts(idx, q, qoff, nq, min_len, min_occ, nullptr, out, cap, n_out, stream);
+}
+
+RB3_EXPORT int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    cudaStream_t st = (cudaStream_t)stream;
+    bool dc = !codes || is_device_ptr(codes), doc = !occ || is_device_ptr(occ);
+    DevBuf cb, obuf;
+    uint8_t *c = codes;
+    int64_t *oc = occ;
+    if (!dc) {
+        RB3_TRY(cb.alloc((size_t)idx->n, st));
+        c = cb.as<uint8_t>();
+    }
+    if (!doc) {
+        RB3_TRY(obuf.alloc(sizeof(int64_t) * SIGMA * idx->nblocks, st));
+        oc = obuf.as<int64_t>();
+    }
+    RB3_TRY(export_impl(idx, c, oc, st));
+    if (!dc && idx->n) RB3_CUDA_TRY(cudaMemcpyAsync(codes, c, (size_t)idx->n, cudaMemcpyDeviceToHost, st));
+    if (!doc)
+        RB3_CUDA_TRY(cudaMemcpyAsync(occ, oc, sizeof(int64_t) * SIGMA * idx->nblocks, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int32_t *occ_interval,
+                              int32_t *flags) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    if (n) *n = idx->n;
+    if (m) *m = idx->m;
+    if (C)
+        for (int a = 0; a <= SIGMA; ++a) C[a] = idx->C[a];
+    if (occ_interval) *occ_interval = idx->D;
+    if (flags) *flags = (idx->single_strand ? 1 : 0) | ((idx->text && idx->isa) ? 2 : 0);
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_drop_build_data(rb3_index *idx) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    dev_free(idx->text, 0);
+    dev_free(idx->isa, 0);
+    idx->text = nullptr;
+    idx->isa = nullptr;
+    idx->str_end.clear();
+    RB3_CUDA_TRY(cudaStreamSynchronize(0));
+    return RB3_OK;
+}
+
+static const char k_magic[8] = {'R', 'B', '3', 'I', 'D', 'X', 0, 1};
+
+RB3_EXPORT int rb3_index_save(const rb3_index *idx, const char *path) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx && path, "NULL argument");
+    size_t bytes = (size_t)idx->nblocks * idx->block_bytes;
+    std::vector<uint8_t> host(bytes);
+    RB3_CUDA_TRY(cudaMemcpy(host.data(), idx->blocks, bytes, cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        set_error("cannot open %s for writing", path);
+        return RB3_E_IO;
+    }
+    int64_t hdr[12] = {1, idx->n, idx->m, idx->C[0], idx->C[1], idx->C[2], idx->C[3], idx->C[4], idx->C[5],
+                       idx->C[6], idx->nblocks, ((int64_t)idx->D << 8) | (idx->single_strand ? 1 : 0)};
+    bool ok = fwrite(k_magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(host.data(), 1, bytes, f) == bytes;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("write to %s failed", path);
+        return RB3_E_IO;
+    }
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
+    g_err.clear();
+    RB3_CHECK_ARG(path && out, "NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        set_error("cannot open %s", path);
+        return RB3_E_IO;
+    }
+    char mg[8];
+    int64_t hdr[12];
+    if (fread(mg, 1, 8, f) != 8 || memcmp(mg, k_magic, 8) != 0 || fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 1) {
+        fclose(f);
+        set_error("%s: not an rb3 index image", path);
+        return RB3_E_IO;
+    }
+    int D = (int)(hdr[11] >> 8);
+    int64_t n = hdr[1], nblocks = hdr[10];
+    if (!(D == 64 || D == 128 || D == 256) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
+        fclose(f);
+        set_error("%s: inconsistent header", path);
+        return RB3_E_IO;
+    }
+    rb3_index *x = new rb3_index();
+    x->n = n;
+    x->m = hdr[2];
+    for (int a = 0; a < 7; ++a) x->C[a] = hdr[3 + a];
+    x->D = D;
+    x->log2D = ilog2(D);
+    x->block_bytes = HEADER_BYTES + D / 2;
+    x->single_strand = (int)(hdr[11] & 1);
+    x->nblocks = nblocks;
+    cudaGetDevice(&x->device);
+    size_t bytes = (size_t)nblocks * x->block_bytes;
+    std::vector<uint8_t> host(bytes);
+    bool ok = fread(host.data(), 1, bytes, f) == bytes;
+    fclose(f);
+    if (!ok) {
+        delete x;
+        set_error("%s: truncated", path);
+        return RB3_E_IO;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = dev_alloc((void **)&x->blocks, bytes, st);
+    if (r == RB3_OK) {
+        cudaError_t e = cudaMemcpyAsync(x->blocks, host.data(), bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+    }
+    if (r == RB3_OK) {
+        int64_t C0[7];
+        memcpy(C0, x->C, sizeof(C0));
+        r = finalize_counts(x, st);
+        if (r == RB3_OK && memcmp(C0, x->C, sizeof(C0)) != 0) {
+            set_error("%s: counts do not match the blocks", path);
+            r = RB3_E_IO;
+        }
+    }
+    if (r != RB3_OK) {
+        free_index(x);
+        return r;
+    }
+    *out = x;
+    return RB3_OK;
+}
+
+RB3_EXPORT void rb3_index_free(rb3_index *idx) { free_index(idx); }
+
+RB3_EXPORT int rb3_encode_ascii(const char *ascii, int64_t n, uint8_t *codes) {
+    g_err.clear();
+    RB3_CHECK_ARG(n >= 0 && (n == 0 || (ascii && codes)), "bad argument");
+    for (int64_t i = 0; i < n; ++i) {
+        switch (ascii[i]) {
+            case 'A': case 'a': codes[i] = 1; break;
+            case 'C': case 'c': codes[i] = 2; break;
+            case 'G': case 'g': codes[i] = 3; break;
+            case 'T': case 't': codes[i] = 4; break;
+            default: codes[i] = 5;
+        }
+    }
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_profile_enable(int on) {
+    g_prof.store(on != 0);
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_profile_reset(void) {
+    profile_drain();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_acc.clear();
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_profile_read(const char **names, double *ms, int64_t *calls, int32_t cap, int32_t *n) {
+    profile_drain();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int32_t i = 0;
+    g_names.clear();
+    g_names.reserve(g_acc.size());
+    for (auto &kv : g_acc) g_names.push_back(kv.first);
+    for (auto &kv : g_acc) {
+        if (i < cap) {
+            if (names) names[i] = g_names[i].c_str();
+            if (ms) ms[i] = kv.second.first;
+            if (calls) calls[i] = kv.second.second;
+        }
+        ++i;
+    }
+    if (n) *n = i;
+    return RB3_OK;
+}
+
+RB3_EXPORT int64_t rb3_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,605 @@
+// Batch BWT builder: S0 encode (both strands), S1 prefix-doubling suffix sort,
+// S2 BWT extraction, 4-bit packing and Occ checkpoints.
+//
+// What is computed (Section "Basic concepts", Table 1; Section "BWT
+// construction" for the sentinel order; Section "Double-strand BWT" for the
+// text): T = P0 $ rc(P0) $ P1 $ ..., S its suffix array under
+// $_0 < ... < $_{m-1} < A < C < G < T < N, B[i] = T[S(i)-1] with T[-1] = T[n-1].
+// The paper runs libsais on the integer alphabet; here the suffix array comes
+// from prefix doubling with radix passes (how), which reaches the same S.
+//
+// Prefix doubling, Larsson-Sadakane style:
+//   round 0   key(p) = T[p..p+21) packed 3 bits per symbol, cut after the
+//             first sentinel.  A window holding a sentinel makes its suffix's
+//             order final (sentinels are distinct and ordered by position, and
+//             the stable sort by key keeps position order among equal keys).
+//             Stable radix sort of (key, p); ranks = group start positions.
+//   round h   for every suffix still in a group of >= 2, key = rank[p + h];
+//             sort inside the group; split; new rank = start of the sub-group.
+// Rank writes of a round are applied only after every key of that round has
+// been read, so all keys of a round see the same (h-level) ranks.
+#include "common.cuh"
+
+namespace rb3 {
+
+constexpr int H0 = 21;            // symbols in the round-0 key (3 bits each)
+constexpr int SMALL_MAX = 1024;   // groups up to this size are sorted in shared memory
+constexpr int RT_TILE = 2048;     // round-kernel tile (entries)
+constexpr int RT_THREADS = 256;
+constexpr int RT_MAXR = RT_TILE + SMALL_MAX;
+constexpr uint32_t SURV = 0x80000000u;
+
+// ---- S0: encode ------------------------------------------------------------
+__global__ void k_encode(const uint8_t *__restrict__ seq, const int64_t *__restrict__ in_off,
+                         const int64_t *__restrict__ out_off, int64_t n_seq, int64_t total_in, int both,
+                         uint8_t *__restrict__ T, int *__restrict__ bad) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total_in;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        // string s with in_off[s] <= g < in_off[s+1]
+        int64_t lo = 0, hi = n_seq;  // count of in_off[1..] <= g
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (in_off[mid + 1] <= g) lo = mid + 1;
+            else hi = mid;
+        }
+        int64_t s = lo;
+        int64_t o = g - in_off[s], L = in_off[s + 1] - in_off[s];
+        int x = seq[g];
+        if (x < 1 || x > 5) {
+            atomicOr(bad, 1);
+            x = 5;
+        }
+        int64_t base = out_off[s];
+        T[base + o] = (uint8_t)x;
+        if (both) T[base + L + 1 + (L - 1 - o)] = (uint8_t)comp_sym(x);
+    }
+}
+
+__global__ void k_sentinels(const int64_t *__restrict__ in_off, const int64_t *__restrict__ out_off, int64_t n_seq,
+                            int both, uint8_t *__restrict__ T) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n_seq) return;
+    int64_t L = in_off[s + 1] - in_off[s], base = out_off[s];
+    T[base + L] = 0;
+    if (both) T[base + 2 * L + 1] = 0;
+}
+
+// ---- S1: round 0 ------------------------------------------------------------
+__global__ void k_init_keys(const uint8_t *__restrict__ T, int64_t n, uint64_t *__restrict__ key,
+                            uint32_t *__restrict__ val) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint64_t k = 0;
+    bool stop = false;
+#pragma unroll
+    for (int j = 0; j < H0; ++j) {
+        uint32_t c = stop ? 0u : (uint32_t)T[p + j];  // T ends with a sentinel: reads stop at n-1
+        stop = stop || c == 0;
+        k = (k << 3) | c;
+    }
+    key[p] = k;
+    val[p] = (uint32_t)p;
+}
+
+// A group starts at i if its key differs from the previous one, or if its
+// window holds a sentinel (then its order is final: singleton).  A window
+// holds a sentinel iff its last 3-bit field is 0.
+__global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__restrict__ hv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool head = i == 0 || K[i] != K[i - 1] || (K[i] & 7u) == 0;
+    hv[i] = head ? (uint32_t)i : 0u;
+}
+
+__global__ void k_init_rank(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart, int64_t n,
+                            int32_t *__restrict__ rank, uint32_t *__restrict__ gsize) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t g = gstart[i];
+    rank[SA[i]] = (int32_t)g;
+    atomicAdd(&gsize[g], 1u);
+}
+
+__global__ void k_init_flags(const uint32_t *__restrict__ gstart, const uint32_t *__restrict__ gsize, int64_t n,
+                             uint32_t *__restrict__ fs, uint32_t *__restrict__ fl) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t sz = gsize[gstart[i]];
+    fs[i] = (sz >= 2 && sz <= (uint32_t)SMALL_MAX) ? 1u : 0u;
+    fl[i] = sz > (uint32_t)SMALL_MAX ? 1u : 0u;
+}
+
+__global__ void k_init_lists(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart,
+                             const uint32_t *__restrict__ fs, const uint32_t *__restrict__ fl,
+                             const uint32_t *__restrict__ ps, const uint32_t *__restrict__ pl, int64_t n,
+                             uint32_t *__restrict__ sp, uint32_t *__restrict__ sg, uint32_t *__restrict__ lp,
+                             uint32_t *__restrict__ lg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (fs[i]) {
+        sp[ps[i]] = SA[i];
+        sg[ps[i]] = gstart[i];
+    } else if (fl[i]) {
+        lp[pl[i]] = SA[i];
+        lg[pl[i]] = gstart[i];
+    }
+}
+
+// out[0] = excl[n-1] + flag[n-1] (+ out[0] when accumulate)
+__global__ void k_tally(const uint32_t *__restrict__ excl, const uint32_t *__restrict__ flag, int64_t n,
+                        uint32_t *__restrict__ out, int accumulate) {
+    uint32_t v = n > 0 ? excl[n - 1] + flag[n - 1] : 0u;
+    out[0] = accumulate ? out[0] + v : v;
+}
+
+// ---- S1: doubling rounds, groups of <= SMALL_MAX -----------------------------
+// Tiles of RT_TILE list entries, moved to group boundaries.  Keys are gathered
+// into shared memory; each entry counts the keys of its group that are smaller
+// (less) and equal before it (eqb): its new place is group start + less + eqb,
+// its new rank group start + less.
+__device__ __forceinline__ int64_t run_start_at(const uint32_t *__restrict__ wg, int64_t x, int64_t N) {
+    while (x > 0 && x < N && wg[x] == wg[x - 1]) ++x;
+    return x;
+}
+
+__global__ void __launch_bounds__(RT_THREADS) k_round_small(const uint32_t *__restrict__ wp,
+                                                            const uint32_t *__restrict__ wg, int64_t N,
+                                                            const int32_t *__restrict__ rank, uint32_t h, int64_t n,
+                                                            uint32_t *__restrict__ err,
+                                                            int32_t *__restrict__ SA, uint32_t *__restrict__ tp,
+                                                            uint32_t *__restrict__ tg,
+                                                            uint32_t *__restrict__ tile_surv,
+                                                            uint32_t *__restrict__ tile_begin) {
+    __shared__ uint32_t sp[RT_MAXR], sg[RT_MAXR], sk[RT_MAXR];
+    __shared__ int64_t rb, re;
+    __shared__ uint32_t wtot[32];
+    int64_t b0 = (int64_t)blockIdx.x * RT_TILE;
+    int64_t e0 = b0 + RT_TILE < N ? b0 + RT_TILE : N;
+    if (threadIdx.x == 0) {
+        rb = run_start_at(wg, b0, N);
+        tile_begin[blockIdx.x] = (uint32_t)rb;
+    }
+    if (threadIdx.x == 32) re = run_start_at(wg, e0, N);
+    __syncthreads();
+    int64_t b = rb;
+    int cnt = (int)(re - rb);
+    for (int i = threadIdx.x; i < cnt; i += RT_THREADS) {
+        uint32_t p = wp[b + i];
+        sp[i] = p;
+        sg[i] = wg[b + i];
+        int64_t ph = (int64_t)p + h;
+        if (ph < n) {
+            sk[i] = (uint32_t)rank[ph];
+        } else {  // cannot happen for a sentinel-terminated text; recorded, never read
+            atomicOr(err, 1u);
+            sk[i] = 0u;
+        }
+    }
+    __syncthreads();
+    uint32_t surv = 0;
+    for (int i = threadIdx.x; i < cnt; i += RT_THREADS) {
+        uint32_t g = sg[i], k = sk[i];
+        int rs = i;
+        while (rs > 0 && sg[rs - 1] == g) --rs;
+        int rend = i + 1;
+        while (rend < cnt && sg[rend] == g) ++rend;
+        int less = 0, eqb = 0, eqt = 0;
+        for (int j = rs; j < rend; ++j) {
+            uint32_t kj = sk[j];
+            less += kj < k;
+            int e = kj == k;
+            eqt += e;
+            eqb += e & (j < i);
+        }
+        int off = less + eqb;
+        SA[g + off] = (int32_t)sp[i];
+        uint32_t gn = g + (uint32_t)less;
+        bool sv = eqt >= 2;
+        tp[b + rs + off] = sp[i];
+        tg[b + rs + off] = gn | (sv ? SURV : 0u);
+        surv += sv;
+    }
+    // block sum of survivors
+    uint32_t ex = block_excl<uint32_t>(surv, 0, wtot);
+    if (threadIdx.x == RT_THREADS - 1) tile_surv[blockIdx.x] = ex + surv;
+}
+
+// Applies the new ranks of a tile and compacts its survivors (order kept, so
+// every group stays contiguous).
+__global__ void __launch_bounds__(RT_THREADS) k_compact_small(const uint32_t *__restrict__ tp,
+                                                              const uint32_t *__restrict__ tg,
+                                                              const uint32_t *__restrict__ tile_begin,
+                                                              const uint32_t *__restrict__ tile_off, int64_t ntiles,
+                                                              int64_t N, int32_t *__restrict__ rank,
+                                                              uint32_t *__restrict__ op,
+                                                              uint32_t *__restrict__ og) {
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t tot;
+    int64_t b = tile_begin[blockIdx.x];
+    int64_t e = blockIdx.x + 1 < ntiles ? (int64_t)tile_begin[blockIdx.x + 1] : N;
+    uint32_t base = tile_off[blockIdx.x];
+    uint32_t running = 0;
+    for (int64_t c0 = b; c0 < e; c0 += RT_THREADS) {
+        int64_t i = c0 + threadIdx.x;
+        uint32_t p = 0, g = 0, sv = 0;
+        if (i < e) {
+            p = tp[i];
+            g = tg[i];
+            rank[p] = (int32_t)(g & ~SURV);
+            sv = g >> 31;
+        }
+        uint32_t ex = block_excl<uint32_t>(sv, 0, wtot);
+        if (sv) {
+            op[base + running + ex] = p;
+            og[base + running + ex] = g & ~SURV;
+        }
+        if (threadIdx.x == RT_THREADS - 1) tot = ex + sv;
+        __syncthreads();
+        running += tot;
+        __syncthreads();
+    }
+}
+
+// ---- S1: doubling rounds, groups > SMALL_MAX (radix sort by (group, key)) ----
+__global__ void k_large_keys(const uint32_t *__restrict__ lp, const uint32_t *__restrict__ lg, int64_t NL,
+                             const int32_t *__restrict__ rank, uint32_t h, int64_t n, uint32_t *__restrict__ err,
+                             uint64_t *__restrict__ ck, uint32_t *__restrict__ cv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= NL) return;
+    int64_t ph = (int64_t)lp[i] + h;
+    uint32_t r = 0;
+    if (ph < n) r = (uint32_t)rank[ph];
+    else atomicOr(err, 1u);
+    ck[i] = ((uint64_t)lg[i] << 32) | r;
+    cv[i] = (uint32_t)i;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *__restrict__ a, int64_t n, uint64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_large_assign(const uint64_t *__restrict__ ck, const uint32_t *__restrict__ cv, int64_t NL,
+                               const uint32_t *__restrict__ lp, int32_t *__restrict__ SA,
+                               uint32_t *__restrict__ tp, uint32_t *__restrict__ tg,
+                               uint32_t *__restrict__ gsize) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= NL) return;
+    uint64_t c = ck[j];
+    uint32_t g = (uint32_t)(c >> 32);
+    uint32_t p = lp[cv[j]];
+    int64_t fg = lower_bound_u64(ck, NL, (uint64_t)g << 32);
+    int64_t fe = lower_bound_u64(ck, NL, c);
+    int64_t ee = lower_bound_u64(ck, NL, c + 1);
+    SA[g + (j - fg)] = (int32_t)p;
+    uint32_t gn = g + (uint32_t)(fe - fg);
+    int64_t eqt = ee - fe;
+    tp[j] = p;
+    tg[j] = gn | (eqt >= 2 ? SURV : 0u);
+    if (j == fe) gsize[gn] = (uint32_t)eqt;
+}
+
+__global__ void k_large_flags(const uint32_t *__restrict__ tp, const uint32_t *__restrict__ tg, int64_t NL,
+                              int32_t *__restrict__ rank, const uint32_t *__restrict__ gsize,
+                              uint32_t *__restrict__ fs, uint32_t *__restrict__ fl) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= NL) return;
+    uint32_t g = tg[j], gn = g & ~SURV;
+    rank[tp[j]] = (int32_t)gn;
+    uint32_t sz = (g & SURV) ? gsize[gn] : 0u;
+    fs[j] = (sz >= 2 && sz <= (uint32_t)SMALL_MAX) ? 1u : 0u;
+    fl[j] = sz > (uint32_t)SMALL_MAX ? 1u : 0u;
+}
+
+__global__ void k_large_scatter(const uint32_t *__restrict__ tp, const uint32_t *__restrict__ tg,
+                                const uint32_t *__restrict__ fs, const uint32_t *__restrict__ fl,
+                                const uint32_t *__restrict__ ps, const uint32_t *__restrict__ pl, int64_t NL,
+                                const uint32_t *__restrict__ small_base, uint32_t *__restrict__ sp,
+                                uint32_t *__restrict__ sg, uint32_t *__restrict__ lp2, uint32_t *__restrict__ lg2) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= NL) return;
+    uint32_t gn = tg[j] & ~SURV;
+    if (fs[j]) {
+        uint32_t o = small_base[0] + ps[j];
+        sp[o] = tp[j];
+        sg[o] = gn;
+    } else if (fl[j]) {
+        lp2[pl[j]] = tp[j];
+        lg2[pl[j]] = gn;
+    }
+}
+
+// ---- S2: BWT extraction, packing, Occ ------------------------------------------
+// One thread packs 8 consecutive BWT symbols into a 32-bit payload word and
+// counts them; the D/8 threads of a block reduce their counts with shuffles.
+__global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict__ SA, int64_t n, int log2D, int bb,
+                       int64_t nblocks, uint8_t *__restrict__ blocks, uint32_t *__restrict__ cnt) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = nblocks << (log2D - 3);
+    if (t >= total) return;  // total is a multiple of 32 when D >= 256 ... guarded reduce below
+    int64_t q0 = t << 3;
+    int64_t b = q0 >> log2D;
+    uint32_t word = 0;
+    uint32_t c[SIGMA] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int64_t i = q0 + j;
+        if (i < n) {
+            int32_t s = SA[i];
+            uint32_t sym = s ? T[s - 1] : T[n - 1];
+            word |= sym << (4 * j);
+            c[sym]++;
+        }
+    }
+    int o = (int)(q0 & ((1 << log2D) - 1));
+    *reinterpret_cast<uint32_t *>(blocks + b * bb + HEADER_BYTES + (o >> 1)) = word;
+    // segmented reduce over the D/8 lanes of this block (D/8 in {8,16,32})
+    int seg = 1 << (log2D - 3);
+    unsigned full = __activemask();
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a) {
+        uint32_t v = c[a];
+        for (int d = seg >> 1; d >= 1; d >>= 1) v += __shfl_down_sync(full, v, d, seg);
+        c[a] = v;
+    }
+    if ((t & (seg - 1)) == 0)
+        for (int a = 0; a < SIGMA; ++a) cnt[(int64_t)a * nblocks + b] = c[a];
+}
+
+// Header of block b: rank(a, b*D) = (exclusive prefix of row a at b).  The
+// scan ran over the whole [6][nblocks] array, so subtract the row's start.
+__global__ void k_headers(const uint32_t *__restrict__ ex, int64_t nblocks, int bb, uint8_t *__restrict__ blocks) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    uint8_t *h = blocks + b * bb;
+    uint32_t *h32 = reinterpret_cast<uint32_t *>(h);
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a) h32[a] = ex[(int64_t)a * nblocks + b] - ex[(int64_t)a * nblocks];
+    *reinterpret_cast<uint32_t *>(h + 24) = 0;  // high bytes 0..3
+    *reinterpret_cast<uint32_t *>(h + 28) = 0;  // high bytes 4..5, reserved
+}
+
+static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq, const rb3_opts &o,
+                     cudaStream_t st, rb3_index *out) {
+    const int both = o.single_strand ? 0 : 1;
+    const int mult = both ? 2 : 1;
+    int D = o.occ_interval ? o.occ_interval : 64;
+    RB3_CHECK_ARG(D == 64 || D == 128 || D == 256, "occ_interval must be 64, 128 or 256");
+    std::vector<int64_t> in_off(n_seq + 1, 0), out_off(n_seq + 1, 0);
+    for (int64_t s = 0; s < n_seq; ++s) {
+        RB3_CHECK_ARG(lens[s] >= 0, "negative string length");
+        in_off[s + 1] = in_off[s] + lens[s];
+        out_off[s + 1] = out_off[s] + mult * (lens[s] + 1);
+    }
+    const int64_t total_in = in_off[n_seq], n = out_off[n_seq];
+    if (n >= (int64_t(1) << 31) - 64) {
+        set_error("batch too large: %lld symbols (limit 2^31 - 64 per batch)", (long long)n);
+        return RB3_E_INVAL;
+    }
+    out->D = D;
+    out->log2D = ilog2(D);
+    out->block_bytes = HEADER_BYTES + D / 2;
+    out->single_strand = !both;
+    out->n = n;
+    out->m = n_seq * mult;
+    out->nblocks = n / D + 1;
+    out->str_end.clear();
+    for (int64_t s = 0; s < n_seq; ++s) {
+        out->str_end.push_back(out_off[s] + lens[s]);
+        if (both) out->str_end.push_back(out_off[s] + 2 * lens[s] + 1);
+    }
+    DevBuf blocks_buf;
+    RB3_TRY(blocks_buf.alloc((size_t)out->nblocks * out->block_bytes, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(blocks_buf.p, 0, (size_t)out->nblocks * out->block_bytes, st));
+    DevBuf Tb, isab;
+    RB3_TRY(Tb.alloc((size_t)n + 64, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(Tb.p, 0, (size_t)n + 64, st));
+    RB3_TRY(isab.alloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), st));
+    uint8_t *T = Tb.as<uint8_t>();
+    int32_t *rank = isab.as<int32_t>();
+
+    if (n > 0) {
+        // ---- S0 ----
+        {
+            Phase ph("build.encode", st);
+            DevBuf offs, bad;
+            RB3_TRY(offs.alloc(sizeof(int64_t) * 2 * (n_seq + 1), st));
+            RB3_TRY(bad.alloc(sizeof(int), st));
+            int64_t *d_in = offs.as<int64_t>(), *d_out = d_in + (n_seq + 1);
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_in, in_off.data(), sizeof(int64_t) * (n_seq + 1), cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_out, out_off.data(), sizeof(int64_t) * (n_seq + 1), cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            if (total_in > 0) {
+                unsigned grid = nb_for(total_in, 256);
+                if (grid > 65535u * 16) grid = 65535u * 16;
+                RB3_LAUNCH(k_encode, grid, 256, 0, st, seq_dev, d_in, d_out, n_seq, total_in, both, T, bad.as<int>());
+            }
+            RB3_LAUNCH(k_sentinels, nb_for(n_seq, 256), 256, 0, st, d_in, d_out, n_seq, both, T);
+            int hbad = 0;
+            RB3_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hbad) {
+                set_error("input symbol outside 1..5 (A,C,G,T,N codes)");
+                return RB3_E_INVAL;
+            }
+        }
+        // ---- S1 round 0 ----
+        DevBuf SAb, gsizeb;
+        RB3_TRY(SAb.alloc(sizeof(int32_t) * n, st));
+        RB3_TRY(gsizeb.alloc(sizeof(uint32_t) * n, st));
+        int32_t *SA = SAb.as<int32_t>();
+        uint32_t *gsize = gsizeb.as<uint32_t>();
+        DevBuf sp, sg, sp2, sg2, tp, tg, lp, lg;
+        int64_t NS = 0, NL = 0;
+        DevBuf counters;
+        RB3_TRY(counters.alloc(sizeof(uint32_t) * 4, st));
+        RB3_CUDA_TRY(cudaMemsetAsync(counters.p, 0, sizeof(uint32_t) * 4, st));
+        uint32_t *d_cnt = counters.as<uint32_t>();
+        uint32_t *d_err = d_cnt + 2;
+        {
+            Phase ph("build.sort0", st);
+            DevBuf k0, k1, v1;
+            RB3_TRY(k0.alloc(sizeof(uint64_t) * n, st));
+            RB3_TRY(k1.alloc(sizeof(uint64_t) * n, st));
+            RB3_TRY(v1.alloc(sizeof(uint32_t) * n, st));
+            uint32_t *v0 = reinterpret_cast<uint32_t *>(SA);
+            RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, k0.as<uint64_t>(), v0);
+            bool alt = false;
+            RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0, k1.as<uint64_t>(), v1.as<uint32_t>(), n, 0, 3 * H0, st,
+                                     &alt));
+            const uint64_t *K = alt ? k1.as<uint64_t>() : k0.as<uint64_t>();
+            if (alt) RB3_CUDA_TRY(cudaMemcpyAsync(SA, v1.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+            DevBuf hv, fs, fl, ps, pl;
+            RB3_TRY(hv.alloc(sizeof(uint32_t) * n, st));
+            RB3_LAUNCH(k_heads, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
+            RB3_TRY(scan_u32(hv.as<uint32_t>(), hv.as<uint32_t>(), n, true, 1, st));  // gstart
+            RB3_CUDA_TRY(cudaMemsetAsync(gsize, 0, sizeof(uint32_t) * n, st));
+            RB3_LAUNCH(k_init_rank, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
+                       n, rank, gsize);
+            k0.release();
+            k1.release();
+            v1.release();
+            RB3_TRY(fs.alloc(sizeof(uint32_t) * n, st));
+            RB3_TRY(fl.alloc(sizeof(uint32_t) * n, st));
+            RB3_TRY(ps.alloc(sizeof(uint32_t) * n, st));
+            RB3_TRY(pl.alloc(sizeof(uint32_t) * n, st));
+            RB3_LAUNCH(k_init_flags, nb_for(n, 256), 256, 0, st, hv.as<uint32_t>(), gsize, n, fs.as<uint32_t>(),
+                       fl.as<uint32_t>());
+            RB3_TRY(scan_u32(fs.as<uint32_t>(), ps.as<uint32_t>(), n, false, 0, st));
+            RB3_TRY(scan_u32(fl.as<uint32_t>(), pl.as<uint32_t>(), n, false, 0, st));
+            RB3_LAUNCH(k_tally, 1, 1, 0, st, ps.as<uint32_t>(), fs.as<uint32_t>(), n, d_cnt, 0);
+            RB3_LAUNCH(k_tally, 1, 1, 0, st, pl.as<uint32_t>(), fl.as<uint32_t>(), n, d_cnt + 1, 0);
+            uint32_t hc[2];
+            RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            NS = hc[0];
+            NL = hc[1];
+            RB3_TRY(sp.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(sg.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(sp2.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(sg2.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(tp.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(tg.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
+            RB3_TRY(lp.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lg.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_LAUNCH(k_init_lists, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
+                       fs.as<uint32_t>(), fl.as<uint32_t>(), ps.as<uint32_t>(), pl.as<uint32_t>(), n,
+                       sp.as<uint32_t>(), sg.as<uint32_t>(), lp.as<uint32_t>(), lg.as<uint32_t>());
+        }
+        // ---- S1 doubling rounds ----
+        const int64_t capS = NS + NL + 1;
+        DevBuf lp2, lg2, ltp, ltg, lck0, lck1, lcv0, lcv1, lfs, lfl, lps, lpl;
+        if (NL > 0) {
+            RB3_TRY(lp2.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lg2.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(ltp.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(ltg.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lck0.alloc(sizeof(uint64_t) * (NL + 1), st));
+            RB3_TRY(lck1.alloc(sizeof(uint64_t) * (NL + 1), st));
+            RB3_TRY(lcv0.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lcv1.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lfs.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lfl.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lps.alloc(sizeof(uint32_t) * (NL + 1), st));
+            RB3_TRY(lpl.alloc(sizeof(uint32_t) * (NL + 1), st));
+        }
+        const int64_t max_tiles = (capS + RT_TILE - 1) / RT_TILE + 1;
+        DevBuf tsurv, tbeg, toff;
+        RB3_TRY(tsurv.alloc(sizeof(uint32_t) * max_tiles, st));
+        RB3_TRY(tbeg.alloc(sizeof(uint32_t) * max_tiles, st));
+        RB3_TRY(toff.alloc(sizeof(uint32_t) * max_tiles, st));
+        int gbits = ilog2(n) + 1;
+        uint32_t h = H0;
+        int round = 0;
+        while (NS + NL > 0) {
+            Phase ph("build.round", st);
+            if (++round > 40 || h >= (uint32_t)n) {
+                set_error("prefix doubling did not converge (round %d, h=%u)", round, h);
+                return RB3_E_CUDA;
+            }
+            int64_t ntiles = (NS + RT_TILE - 1) / RT_TILE;
+            if (NS > 0)
+                RB3_LAUNCH(k_round_small, (unsigned)ntiles, RT_THREADS, 0, st, sp.as<uint32_t>(), sg.as<uint32_t>(), NS,
+                           rank, h, n, d_err, SA, tp.as<uint32_t>(), tg.as<uint32_t>(), tsurv.as<uint32_t>(),
+                           tbeg.as<uint32_t>());
+            if (NL > 0) {
+                RB3_LAUNCH(k_large_keys, nb_for(NL, 256), 256, 0, st, lp.as<uint32_t>(), lg.as<uint32_t>(), NL, rank, h, n,
+                           d_err, lck0.as<uint64_t>(), lcv0.as<uint32_t>());
+                bool alt = false;
+                RB3_TRY(radix_sort_pairs(lck0.as<uint64_t>(), lcv0.as<uint32_t>(), lck1.as<uint64_t>(),
+                                         lcv1.as<uint32_t>(), NL, 0, 32 + gbits, st, &alt));
+                const uint64_t *ck = alt ? lck1.as<uint64_t>() : lck0.as<uint64_t>();
+                const uint32_t *cv = alt ? lcv1.as<uint32_t>() : lcv0.as<uint32_t>();
+                RB3_LAUNCH(k_large_assign, nb_for(NL, 256), 256, 0, st, ck, cv, NL, lp.as<uint32_t>(), SA,
+                           ltp.as<uint32_t>(), ltg.as<uint32_t>(), gsize);
+            }
+            // all keys of this round are read; now apply ranks and compact
+            if (NS > 0) {
+                RB3_TRY(scan_u32(tsurv.as<uint32_t>(), toff.as<uint32_t>(), ntiles, false, 0, st));
+                RB3_LAUNCH(k_tally, 1, 1, 0, st, toff.as<uint32_t>(), tsurv.as<uint32_t>(), ntiles, d_cnt, 0);
+                RB3_LAUNCH(k_compact_small, (unsigned)ntiles, RT_THREADS, 0, st, tp.as<uint32_t>(), tg.as<uint32_t>(),
+                           tbeg.as<uint32_t>(), toff.as<uint32_t>(), ntiles, NS, rank, sp2.as<uint32_t>(),
+                           sg2.as<uint32_t>());
+            } else {
+                RB3_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t), st));
+            }
+            RB3_CUDA_TRY(cudaMemsetAsync(d_cnt + 1, 0, sizeof(uint32_t), st));
+            if (NL > 0) {
+                RB3_LAUNCH(k_large_flags, nb_for(NL, 256), 256, 0, st, ltp.as<uint32_t>(), ltg.as<uint32_t>(), NL,
+                           rank, gsize, lfs.as<uint32_t>(), lfl.as<uint32_t>());
+                RB3_TRY(scan_u32(lfs.as<uint32_t>(), lps.as<uint32_t>(), NL, false, 0, st));
+                RB3_TRY(scan_u32(lfl.as<uint32_t>(), lpl.as<uint32_t>(), NL, false, 0, st));
+                RB3_LAUNCH(k_large_scatter, nb_for(NL, 256), 256, 0, st, ltp.as<uint32_t>(), ltg.as<uint32_t>(),
+                           lfs.as<uint32_t>(), lfl.as<uint32_t>(), lps.as<uint32_t>(), lpl.as<uint32_t>(), NL,
+                           d_cnt, sp2.as<uint32_t>(), sg2.as<uint32_t>(), lp2.as<uint32_t>(), lg2.as<uint32_t>());
+                RB3_LAUNCH(k_tally, 1, 1, 0, st, lps.as<uint32_t>(), lfs.as<uint32_t>(), NL, d_cnt, 1);
+                RB3_LAUNCH(k_tally, 1, 1, 0, st, lpl.as<uint32_t>(), lfl.as<uint32_t>(), NL, d_cnt + 1, 0);
+            }
+            uint32_t hc[3];
+            RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            NS = hc[0];
+            NL = hc[1];
+            if (hc[2]) {
+                set_error("prefix doubling: internal error (rank gather past the text end)");
+                return RB3_E_CUDA;
+            }
+            if (NS > capS) {
+                set_error("prefix doubling list overflow");
+                return RB3_E_CUDA;
+            }
+            std::swap(sp.p, sp2.p);
+            std::swap(sg.p, sg2.p);
+            std::swap(lp.p, lp2.p);
+            std::swap(lg.p, lg2.p);
+            h *= 2;
+        }
+        // ---- S2 ----
+        {
+            Phase ph("build.pack", st);
+            int64_t nb = out->nblocks;
+            DevBuf cnt;
+            RB3_TRY(cnt.alloc(sizeof(uint32_t) * SIGMA * nb, st));
+            int64_t threads = nb << (out->log2D - 3);
+            RB3_LAUNCH(k_pack, nb_for(threads, 256), 256, 0, st, T, SA, n, out->log2D, out->block_bytes, nb,
+                       blocks_buf.as<uint8_t>(), cnt.as<uint32_t>());
+            RB3_TRY(scan_u32(cnt.as<uint32_t>(), cnt.as<uint32_t>(), SIGMA * nb, false, 0, st));
+            RB3_LAUNCH(k_headers, nb_for(nb, 256), 256, 0, st, cnt.as<uint32_t>(), nb, out->block_bytes,
+                       blocks_buf.as<uint8_t>());
+        }
+    }
+    out->blocks = static_cast<uint8_t *>(blocks_buf.detach());
+    out->text = static_cast<uint8_t *>(Tb.detach());
+    out->isa = static_cast<int32_t *>(isab.detach());
+    RB3_TRY(finalize_counts(out, st));
+    return RB3_OK;
+}
+
+}  // namespace rb3

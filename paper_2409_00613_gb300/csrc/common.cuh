@@ -1,0 +1,321 @@
+// Shared internals of librb3: the index object, error / launch / profiling
+// plumbing, stream-ordered scratch buffers and the device-side rank core.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rb3.h"
+
+#define RB3_EXPORT extern "C" __attribute__((visibility("default")))
+
+// ---------------------------------------------------------------------------
+// The index.  Blocks of D symbols: 32-byte header (rank of each symbol at the
+// block start: uint32 low words at bytes 0..23, uint8 high bytes at 24..29)
+// then D/2 payload bytes (4-bit codes, low nibble first).  nblocks = n/D + 1
+// so that rank(a, n) reads a header that exists.
+// ---------------------------------------------------------------------------
+struct rb3_index {
+    int64_t n = 0, m = 0;
+    int64_t C[7] = {0, 0, 0, 0, 0, 0, 0};
+    int32_t D = 64, log2D = 6, block_bytes = 64;
+    int32_t single_strand = 0;
+    int64_t nblocks = 0;
+    uint8_t *blocks = nullptr;  // device
+    // build data of a batch (optional): its text and inverse suffix array
+    uint8_t *text = nullptr;   // device, n codes (0 = sentinel)
+    int32_t *isa = nullptr;    // device, n entries
+    std::vector<int64_t> str_end;  // host: position of the sentinel ending DS string i
+    int device = 0;
+};
+
+namespace rb3 {
+
+constexpr int SIGMA = 6;
+constexpr int HEADER_BYTES = 32;
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define RB3_CUDA_TRY(expr)                                                       \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess) return rb3::cuda_fail(e_, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#define RB3_TRY(expr)                 \
+    do {                              \
+        int s_ = (expr);              \
+        if (s_ != RB3_OK) return s_;  \
+    } while (0)
+
+#define RB3_CHECK_ARG(cond, msg)                          \
+    do {                                                  \
+        if (!(cond)) {                                    \
+            rb3::set_error("invalid argument: %s", msg);  \
+            return RB3_E_INVAL;                           \
+        }                                                 \
+    } while (0)
+
+// ---- launches -------------------------------------------------------------
+extern std::atomic<int64_t> g_launches;
+
+#define RB3_LAUNCH(kern, grid, block, smem, stream, ...)                                  \
+    do {                                                                                  \
+        kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                         \
+        rb3::g_launches.fetch_add(1, std::memory_order_relaxed);                          \
+        cudaError_t e_ = cudaPeekAtLastError();                                           \
+        if (e_ != cudaSuccess) return rb3::cuda_fail(e_, #kern, __FILE__, __LINE__);      \
+    } while (0)
+
+// ---- profiling: per-phase CUDA events on the caller's stream ---------------
+bool profile_on();
+void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b);
+
+struct Phase {
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Phase(const char *nm, cudaStream_t s) : name(nm), st(s) {
+        if (profile_on() && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, st);
+        else
+            a = b = nullptr;
+    }
+    ~Phase() {
+        if (a) {
+            cudaEventRecord(b, st);
+            profile_push(name, a, b);
+        }
+    }
+};
+
+// ---- stream-ordered device buffers ------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t nbytes, cudaStream_t s);
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    void *detach() {
+        void *q = p;
+        p = nullptr;
+        bytes = 0;
+        return q;
+    }
+};
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+// Pointer kind: true if the CUDA runtime knows it as device (or managed) memory.
+bool is_device_ptr(const void *p);
+
+// ---- device helpers -------------------------------------------------------
+__host__ __device__ __forceinline__ int comp_sym(int a) {
+    // Watson-Crick complement of $,A,C,G,T,N = $,T,G,C,A,N
+    return (a >= 1 && a <= 4) ? 5 - a : a;
+}
+
+// Read-only view of an index for kernels (passed by value).
+struct OccView {
+    const uint8_t *__restrict__ blocks;
+    int64_t n;
+    int64_t C[7];
+    int32_t log2D;
+    int32_t bb;  // bytes per block
+};
+
+inline OccView occ_view(const rb3_index *x) {
+    OccView v;
+    v.blocks = x->blocks;
+    v.n = x->n;
+    for (int i = 0; i < 7; ++i) v.C[i] = x->C[i];
+    v.log2D = x->log2D;
+    v.bb = x->block_bytes;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ldg_u64(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const unsigned long long *>(p));
+}
+
+// Number of nibbles equal to c among the nibbles selected by mask (one bit 0
+// of each selected nibble set, i.e. a sub-mask of 0x1111...).  Codes are 3-bit,
+// so a nibble equals c iff its xor with c has bits 0..2 clear.
+__device__ __forceinline__ int nib_eq(uint64_t w, int c, uint64_t mask) {
+    uint64_t x = w ^ (0x1111111111111111ull * (uint64_t)c);
+    uint64_t nz = (x | (x >> 1) | (x >> 2)) & 0x1111111111111111ull;
+    return __popcll(~nz & mask);
+}
+
+__device__ __forceinline__ uint64_t nib_mask(int k) {  // first k nibbles of a word, k in 0..16
+    return k >= 16 ? 0x1111111111111111ull : (((1ull << (4 * k)) - 1) & 0x1111111111111111ull);
+}
+
+// rank_B(c, l) = |{i < l : B[i] = c}|  (Table 1), from the Occ header of
+// l's block plus the nibbles before l inside the block.
+__device__ __forceinline__ int64_t rank1(const OccView &v, int c, int64_t l) {
+    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
+    int o = (int)(l & ((1 << v.log2D) - 1));
+    uint32_t lo = __ldg(reinterpret_cast<const unsigned int *>(blk) + c);
+    uint32_t hi = __ldg(blk + 24 + c);
+    int64_t r = (int64_t)lo | ((int64_t)hi << 32);
+    const uint8_t *pay = blk + HEADER_BYTES;
+    int w = 0;
+    for (; (w + 1) * 16 <= o; ++w) r += nib_eq(ldg_u64(pay + 8 * w), c, 0x1111111111111111ull);
+    int rem = o - w * 16;
+    if (rem) r += nib_eq(ldg_u64(pay + 8 * w), c, nib_mask(rem));
+    return r;
+}
+
+// rank_B(a, l) for every symbol a.
+__device__ __forceinline__ void rank_all(const OccView &v, int64_t l, int64_t r[SIGMA]) {
+    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
+    int o = (int)(l & ((1 << v.log2D) - 1));
+    const unsigned int *h32 = reinterpret_cast<const unsigned int *>(blk);
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a) r[a] = (int64_t)__ldg(h32 + a) | ((int64_t)__ldg(blk + 24 + a) << 32);
+    const uint8_t *pay = blk + HEADER_BYTES;
+    int nw = (o + 15) >> 4;
+    for (int w = 0; w < nw; ++w) {
+        uint64_t word = ldg_u64(pay + 8 * w);
+        uint64_t mask = nib_mask(o - w * 16);
+#pragma unroll
+        for (int a = 0; a < SIGMA; ++a) r[a] += nib_eq(word, a, mask);
+    }
+}
+
+// Symbol B[i].
+__device__ __forceinline__ int sym_at(const OccView &v, int64_t i) {
+    const uint8_t *blk = v.blocks + (i >> v.log2D) * (int64_t)v.bb;
+    int o = (int)(i & ((1 << v.log2D) - 1));
+    uint8_t byte = __ldg(blk + HEADER_BYTES + (o >> 1));
+    return (o & 1) ? (byte >> 4) : (byte & 15);
+}
+
+// SA bi-interval (k, k', s) of Section "Double-strand BWT".
+struct BiInt {
+    int64_t k, kp, s;
+};
+
+// Algorithm 3, BackwardExt: for b < comp(a): k' += pi(comp b, k+s) - pi(comp b, k);
+// s <- pi(a,k+s) - pi(a,k); k <- pi(a,k).  (C_B cancels in the differences.)
+__device__ __forceinline__ BiInt backward_ext(const OccView &v, BiInt x, int a) {
+    int64_t r0[SIGMA], r1[SIGMA];
+    rank_all(v, x.k, r0);
+    rank_all(v, x.k + x.s, r1);
+    int ac = comp_sym(a);
+    int64_t add = 0;
+#pragma unroll
+    for (int b = 0; b < SIGMA; ++b)
+        if (b < ac) {
+            int bc = comp_sym(b);
+            add += r1[bc] - r0[bc];
+        }
+    BiInt y;
+    y.kp = x.kp + add;
+    y.s = r1[a] - r0[a];
+    y.k = v.C[a] + r0[a];
+    return y;
+}
+
+// Algorithm 3, ForwardExt = swap(BackwardExt(swap(x), comp(a))).
+__device__ __forceinline__ BiInt forward_ext(const OccView &v, BiInt x, int a) {
+    BiInt y = {x.kp, x.k, x.s};
+    y = backward_ext(v, y, comp_sym(a));
+    BiInt z = {y.kp, y.k, y.s};
+    return z;
+}
+
+// ---- block-level scans (256-thread blocks) -------------------------------
+constexpr int SC_THREADS = 256;
+
+template <class T> __device__ __forceinline__ T op2(T a, T b, int op) { return op == 0 ? a + b : (a > b ? a : b); }
+
+template <class T> __device__ __forceinline__ T warp_incl(T v, int op) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v = op2(v, u, op);
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread across a 256-thread block.
+template <class T> __device__ __forceinline__ T block_excl(T v, int op, T *wtot) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = warp_incl(v, op);
+    if (lane == 31) wtot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < SC_THREADS / 32 ? wtot[lane] : T(0);
+        T ti = warp_incl(t, op);
+        if (lane < SC_THREADS / 32) wtot[lane] = ti;  // inclusive over warps
+    }
+    __syncthreads();
+    T before = w ? wtot[w - 1] : T(0);
+    T up = __shfl_up_sync(0xffffffffu, inc, 1);
+    T excl = lane ? up : T(0);
+    T r = op2(before, excl, op);
+    __syncthreads();
+    return r;
+}
+
+// ---- primitives (sort.cu) --------------------------------------------------
+// Device-wide scans.  op: 0 = sum, 1 = max.
+int scan_u32(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, int op, cudaStream_t st);
+int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, bool inclusive, cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit).
+// The result ends in (k0, v0) if *in_alt comes back false, else in (k1, v1).
+int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, int begin_bit,
+                     int end_bit, cudaStream_t st, bool *in_alt);
+
+// ---- phases (build.cu / merge.cu / search.cu) -------------------------------
+int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n_seq, const rb3_opts &o,
+                     cudaStream_t st, rb3_index *out);
+int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
+int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
+                         int64_t *lohi, cudaStream_t st);
+int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
+                    int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
+                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);
+int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
+// Fills idx->C from its blocks (rank of every symbol at n).
+int finalize_counts(rb3_index *idx, cudaStream_t st);
+
+inline int ilog2(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << (r + 1)) <= x) ++r;
+    return r;
+}
+
+inline int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace rb3

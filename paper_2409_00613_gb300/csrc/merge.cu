@@ -1,0 +1,372 @@
+// Merge of a batch BWT B2 into B1: Algorithm 1 (AppendBWT).
+//
+// For every B2 row k the merged row is pos[k] = k + l(k), where l(k) is the
+// number of B1 suffixes smaller than the suffix of row k (the walk of
+// Algorithm 1: l starts at m1 at each new string's sentinel and becomes
+// pi_{B1}(a, l) one symbol back).  pos increases with k, so the inserts of
+// Algorithm 1 are a stable merge: row q of the result takes the next B2
+// symbol when q is the next pos, else the next B1 symbol.
+//
+// Forms of the walk (equal results):
+//  * plain     -- one thread per new string, exactly as Algorithm 1: rows of
+//                 B2 are followed by LF on B2 (pi_{B2}), l by pi_{B1}.
+//  * segmented -- uses the batch's text T2 and inverse suffix array: the rows
+//                 visited by Algorithm 1's walk for string i are ISA2 of the
+//                 positions of P_i read right to left, and the symbol at each
+//                 step is the text symbol.  Each string is cut into segments of
+//                 L symbols; the exact l at a segment's right end is found with
+//                 ForwardExt (Algorithm 3) over B1 along the suffix X that starts
+//                 there: extend until the count s drops to 0 (l = the k field
+//                 after that failing extension, = the number of B1 suffixes below
+//                 X) or until X's sentinel (l = k + occ(Q$), the B1 suffixes equal
+//                 to Q and ending at a sentinel, all older than X's).  Seeds give
+//                 up after seed_cap steps; the walk from the segment above then
+//                 continues through that segment.  Walks run independently under
+//                 warp-aggregated work stealing, ordered so that homologous
+//                 segments of the batch's strings run together and share B1
+//                 blocks in L2.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rb3 {
+
+// ---- plain Algorithm 1 walk --------------------------------------------------
+__global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int64_t *__restrict__ pos,
+                             unsigned int *__restrict__ err) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m2) return;
+    int64_t k = i, l = m1;
+    for (int64_t steps = 0;; ++steps) {
+        int a = sym_at(B2, k);
+        pos[k] = k + l;
+        if (a == 0) break;
+        if (steps >= B2.n) {  // a BWT walk ends within n steps; guards a corrupt input
+            atomicOr(err, 1u);
+            break;
+        }
+        int64_t kn = B2.C[a] + rank1(B2, a, k);
+        l = B1.C[a] + rank1(B1, a, l);
+        k = kn;
+    }
+}
+
+// ---- segment seeds ---------------------------------------------------------------
+// One thread per segment boundary x (a text position inside a string; the
+// string's sentinel is at send).  seed[w] = l(x) or -1 when capped.
+__global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
+                        const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    int64_t x = w_hi[w], send = w_send[w];
+    if (x == send) {  // a walk starting at the sentinel needs no seed
+        seed[w] = -2;
+        return;
+    }
+    BiInt q = {0, 0, B1.n};
+    int64_t res = -1;
+    for (int64_t t = 0;; ++t) {
+        int64_t p = x + t;
+        if (p == send) {
+            // X = Q$: every B1 suffix equal to Q up to a sentinel is older, hence smaller
+            int64_t occ_end = rank1(B1, 0, q.kp + q.s) - rank1(B1, 0, q.kp);
+            res = q.k + occ_end;
+            break;
+        }
+        if (t >= cap) break;
+        BiInt y = forward_ext(B1, q, T2[p]);
+        if (y.s == 0) {
+            res = y.k;
+            break;
+        }
+        q = y;
+    }
+    seed[w] = res;
+}
+
+// Walk w covers positions [lo, hi) of its string, right to left; its lower end
+// is the next walk below with a usable seed (or the string start).  One thread
+// per string fixes the lower ends (walks of a string are stored top down).
+__global__ void k_walk_bounds(const int64_t *__restrict__ s_first, const int64_t *__restrict__ s_start, int64_t ns,
+                              const int64_t *__restrict__ w_hi, const int64_t *__restrict__ seed,
+                              int64_t *__restrict__ w_lo) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    int64_t lo = s_start[s];
+    for (int64_t w = s_first[s + 1] - 1; w >= s_first[s]; --w) {
+        w_lo[w] = lo;
+        if (seed[w] != -1) lo = w_hi[w];
+    }
+}
+
+// Segmented walk.  The work list order[] lists walks by (segment rank from the
+// string end, string); threads take walks with a warp-aggregated atomic.
+__global__ void __launch_bounds__(256) k_walk_seg(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
+                                                  const int32_t *__restrict__ isa2, const int64_t *__restrict__ w_hi,
+                                                  const int64_t *__restrict__ w_lo, const int64_t *__restrict__ w_send,
+                                                  const int64_t *__restrict__ seed,
+                                                  const int32_t *__restrict__ order, int64_t nw,
+                                                  unsigned long long *__restrict__ next,
+                                                  int64_t *__restrict__ pos) {
+    for (;;) {
+        // warp-aggregated grab of one walk per active lane
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        int64_t idx = (int64_t)base + grp.thread_rank();
+        if (idx >= nw) break;
+        int64_t w = order[idx];
+        int64_t sd = seed[w];
+        if (sd == -1) continue;  // covered by the walk above
+        int64_t hi = w_hi[w], lo = w_lo[w];
+        int64_t l;
+        if (sd == -2) {  // starts at the string's sentinel: row isa2[hi], l = m1
+            l = m1;
+            int64_t k = isa2[hi];
+            pos[k] = k + l;
+        } else {
+            l = sd;
+        }
+        for (int64_t p = hi - 1; p >= lo; --p) {
+            int a = T2[p];
+            l = B1.C[a] + rank1(B1, a, l);
+            int64_t k = isa2[p];
+            pos[k] = k + l;
+        }
+    }
+}
+
+// ---- scatter-merge (S4) + Occ rebuild ---------------------------------------------
+// Tiles of MT output symbols.  kstart[t] = number of B2 rows with pos < t*MT.
+constexpr int MT = 2048;
+constexpr int MT_THREADS = MT / 8;
+
+__global__ void k_tile_starts(const int64_t *__restrict__ pos, int64_t n2, int64_t ntiles,
+                              int64_t *__restrict__ kstart) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k > n2) return;
+    int64_t tk = k < n2 ? pos[k] / MT : ntiles;           // tile of row k (ntiles past the end)
+    int64_t tp = k > 0 ? pos[k - 1] / MT : -1;           // tile of row k-1
+    for (int64_t t = tp + 1; t <= tk && t < ntiles + 1; ++t) kstart[t] = k;
+}
+
+__device__ __forceinline__ int nib_get(const OccView &v, int64_t i) { return sym_at(v, i); }
+
+__global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, const int64_t *__restrict__ pos,
+                                                        const int64_t *__restrict__ kstart, int64_t nM, int64_t nbM,
+                                                        int log2D, int bb, uint8_t *__restrict__ M) {
+    __shared__ uint32_t flags[MT / 32];
+    __shared__ uint32_t wtot[32];
+    __shared__ int64_t base6[SIGMA];
+    __shared__ uint32_t bcnt[MT / 64][SIGMA];  // per 64-symbol group counts
+    const int64_t t = blockIdx.x;
+    const int64_t q0 = t * MT;
+    const int64_t k0 = kstart[t], k1 = kstart[t + 1];
+    const int64_t j0 = q0 - k0;
+    for (int i = threadIdx.x; i < MT / 32; i += MT_THREADS) flags[i] = 0;
+    if (threadIdx.x < SIGMA) base6[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < (MT / 64) * SIGMA; i += MT_THREADS) (&bcnt[0][0])[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t r1[SIGMA], r2[SIGMA];
+        rank_all(B1, j0, r1);
+        rank_all(B2, k0, r2);
+        for (int a = 0; a < SIGMA; ++a) base6[a] = r1[a] + r2[a];
+    }
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += MT_THREADS) {
+        int d = (int)(pos[k] - q0);
+        atomicOr(&flags[d >> 5], 1u << (d & 31));
+    }
+    __syncthreads();
+    // thread owns output symbols [q0 + 8*tid, +8)
+    const int o8 = threadIdx.x * 8;
+    uint32_t fw = (flags[o8 >> 5] >> (o8 & 31)) & 0xFFu;
+    uint32_t nf = __popc(fw);
+    uint32_t before = block_excl<uint32_t>(nf, 0, wtot);
+    int64_t kb = k0 + before;              // next B2 row
+    int64_t jb = j0 + (o8 - (int64_t)before);  // next B1 row
+    uint32_t word = 0;
+    uint32_t c[SIGMA] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int64_t q = q0 + o8 + j;
+        if (q < nM) {
+            int s = ((fw >> j) & 1u) ? nib_get(B2, kb++) : nib_get(B1, jb++);
+            word |= (uint32_t)s << (4 * j);
+            c[s]++;
+        }
+    }
+    // counts per 64-symbol group (8 threads)
+    const int grp = o8 >> 6;
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a)
+        if (c[a]) atomicAdd(&bcnt[grp][a], c[a]);
+    __syncthreads();
+    // write payload word; headers at block starts
+    const int D = 1 << log2D;
+    const int64_t q = q0 + o8;
+    if ((q >> log2D) >= nbM) return;  // past the last output block (no barrier follows)
+    uint8_t *blk = M + (q >> log2D) * (int64_t)bb;
+    const int o = (int)(q & (D - 1));
+    *reinterpret_cast<uint32_t *>(blk + HEADER_BYTES + (o >> 1)) = word;
+    if (o == 0) {
+        // rank at q = base + counts of the groups of this tile before q
+        int ng = o8 >> 6;
+        uint32_t *h32 = reinterpret_cast<uint32_t *>(blk);
+        uint8_t hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < SIGMA; ++a) {
+            int64_t r = base6[a];
+            for (int g = 0; g < ng; ++g) r += bcnt[g][a];
+            h32[a] = (uint32_t)r;
+            hb[a] = (uint8_t)(r >> 32);
+        }
+        *reinterpret_cast<uint2 *>(blk + 24) =
+            make_uint2((uint32_t)hb[0] | ((uint32_t)hb[1] << 8) | ((uint32_t)hb[2] << 16) | ((uint32_t)hb[3] << 24),
+                       (uint32_t)hb[4] | ((uint32_t)hb[5] << 8));
+    }
+}
+
+static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+__global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) pos[k] = k;
+}
+
+int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
+    RB3_CHECK_ARG(dst != src, "dst and src must differ");
+    RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
+                  "cannot merge a single-strand index with a double-strand one");
+    if (src->n == 0) return RB3_OK;
+    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
+    if (nM >= (int64_t(1) << 40)) {
+        set_error("merged index would exceed 2^40 symbols");
+        return RB3_E_INVAL;
+    }
+    // output layout: D of dst (or of src when dst is empty)
+    int D = n1 ? dst->D : src->D;
+    int log2D = ilog2(D), bb = HEADER_BYTES + D / 2;
+    int64_t nbM = nM / D + 1;
+    int64_t ntiles = (nbM * D + MT - 1) / MT;
+    DevBuf posb, kst, Mb;
+    RB3_TRY(posb.alloc(sizeof(int64_t) * n2, st));
+    RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
+    RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
+    int64_t *pos = posb.as<int64_t>();
+    OccView V1 = occ_view(dst), V2 = occ_view(src);
+    const int64_t m1 = dst->m, m2 = src->m;
+    {
+        Phase ph("merge.walk", st);
+        bool segmented = o.merge_form == 0 && src->text && src->isa;
+        if (n1 == 0) {
+            // empty B1: every l is 0 (there are no older suffixes), pos[k] = k
+            RB3_LAUNCH(k_iota, nb_for(n2, 256), 256, 0, st, pos, n2);
+        } else if (!segmented) {
+            DevBuf err;
+            RB3_TRY(err.alloc(sizeof(unsigned int), st));
+            RB3_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(unsigned int), st));
+            RB3_LAUNCH(k_walk_plain, nb_for(m2, 32), 32, 0, st, V1, V2, m1, m2, pos, err.as<unsigned int>());
+            unsigned int herr = 0;
+            RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            if (herr) {
+                set_error("merge: a walk over the batch BWT did not reach a sentinel (corrupt batch index)");
+                return RB3_E_INVAL;
+            }
+        } else {
+            // segment plan (host): strings of src from its sentinel positions
+            int64_t L = o.seg_len;
+            if (L <= 0) {
+                // about 512 walks per SM, segment length clamped to [512, 16384]
+                int64_t target = (int64_t)num_sms() * 512;
+                L = n2 / (target > 0 ? target : 1);
+                if (L < 512) L = 512;
+                if (L > 16384) L = 16384;
+            }
+            int64_t cap = o.seed_cap > 0 ? o.seed_cap : 4 * L;
+            const int64_t ns = (int64_t)src->str_end.size();
+            std::vector<int64_t> s_first(ns + 1, 0), s_start(ns), w_hi, w_send;
+            std::vector<int32_t> w_rank;  // segment rank from the string end
+            int64_t maxr = 0;
+            for (int64_t s = 0; s < ns; ++s) {
+                int64_t start = s == 0 ? 0 : src->str_end[s - 1] + 1;
+                int64_t end = src->str_end[s];
+                s_start[s] = start;
+                s_first[s] = (int64_t)w_hi.size();
+                // walk 0 starts at the sentinel; walk r at end - r*L while > start
+                int64_t r = 0;
+                for (int64_t x = end;; x -= L, ++r) {
+                    w_hi.push_back(x);
+                    w_send.push_back(end);
+                    w_rank.push_back((int32_t)r);
+                    if (x - L <= start) break;
+                }
+                if (r > maxr) maxr = r;
+            }
+            s_first[ns] = (int64_t)w_hi.size();
+            const int64_t nw = (int64_t)w_hi.size();
+            // processing order: by rank from the end, then string
+            std::vector<int32_t> order(nw);
+            {
+                std::vector<int64_t> cnt(maxr + 2, 0);
+                for (int64_t w = 0; w < nw; ++w) cnt[w_rank[w] + 1]++;
+                for (int64_t r = 0; r <= maxr; ++r) cnt[r + 1] += cnt[r];
+                for (int64_t w = 0; w < nw; ++w) order[cnt[w_rank[w]]++] = (int32_t)w;
+            }
+            DevBuf plan;
+            size_t bytes = sizeof(int64_t) * (4 * nw + 2 * (ns + 1)) + sizeof(unsigned long long) +
+                           sizeof(int32_t) * nw + 64;
+            RB3_TRY(plan.alloc(bytes, st));
+            int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_seed = d_send + nw, *d_lo = d_seed + nw;
+            int64_t *d_sfirst = d_lo + nw, *d_sstart = d_sfirst + (ns + 1);
+            unsigned long long *d_next = reinterpret_cast<unsigned long long *>(d_sstart + (ns + 1));
+            int32_t *d_order = reinterpret_cast<int32_t *>(d_next + 1);
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_hi, w_hi.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_send, w_send.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_sfirst, s_first.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_sstart, s_start.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
+            {
+                Phase ps("merge.seed", st);
+                RB3_LAUNCH(k_seeds, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi, d_send, nw, cap, d_seed);
+                RB3_LAUNCH(k_walk_bounds, nb_for(ns, 128), 128, 0, st, d_sfirst, d_sstart, ns, d_hi, d_seed, d_lo);
+            }
+            {
+                Phase pw("merge.lfwalk", st);
+                int64_t resident = (int64_t)num_sms() * 2048;
+                int64_t threads = nw < resident ? nw : resident;
+                RB3_LAUNCH(k_walk_seg, nb_for(threads, 256), 256, 0, st, V1, m1, src->text, src->isa, d_hi, d_lo,
+                           d_send, d_seed, d_order, nw, d_next, pos);
+            }
+        }
+    }
+    {
+        Phase ph("merge.scatter", st);
+        RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst.as<int64_t>());
+        RB3_LAUNCH(k_scatter, (unsigned)ntiles, MT_THREADS, 0, st, V1, V2, pos, kst.as<int64_t>(), nM, nbM, log2D, bb,
+                   Mb.as<uint8_t>());
+    }
+    // install
+    if (dst->blocks) dev_free(dst->blocks, st);
+    if (dst->text) dev_free(dst->text, st);
+    if (dst->isa) dev_free(dst->isa, st);
+    dst->text = nullptr;
+    dst->isa = nullptr;
+    dst->str_end.clear();
+    dst->blocks = static_cast<uint8_t *>(Mb.detach());
+    dst->n = nM;
+    dst->m = m1 + m2;
+    for (int a = 0; a <= SIGMA; ++a) dst->C[a] = dst->C[a] + src->C[a];
+    dst->D = D;
+    dst->log2D = log2D;
+    dst->block_bytes = bb;
+    dst->nblocks = nbM;
+    dst->single_strand = src->single_strand;
+    return RB3_OK;
+}
+
+}  // namespace rb3

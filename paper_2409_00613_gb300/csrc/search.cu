@@ -1,0 +1,278 @@
+// Searches on a resident index: backward search (S5) and SMEM finding (S6).
+//
+// Backward search, Section "Suffix array interval and backward search":
+// [lo, hi) starts at [0, n) and becomes [pi(a,lo), pi(a,hi)) for the query's
+// symbols from last to first.
+//
+// SMEMs, Section "Finding supermaximal exact matches", Algorithm 4 over the
+// bi-interval extensions of Algorithm 3, with these readings: after the
+// forward loop e = |P| if it ran out and e = j if it broke at j, and the
+// SMEM's bi-interval is the one before the failing ForwardExt; when e = |P|
+// FindSMEM1 returns |P|; when the last backward loop runs out it returns i+1.
+//
+// Chunked form: a long query is cut at multiples of chunk_len; chunk c runs
+// the same loop from x0 = c*chunk_len and keeps SMEMs that start in
+// [x0, x0 + chunk_len).  Every start FindSMEM1 returns (other than the one it
+// was started from) is an SMEM candidate whatever the loop started from, and
+// no SMEM start is ever skipped, so the chunks together give exactly the
+// unchunked set; the one start that may be spurious is x0 itself, kept only
+// if P[x0-1, e) occurs fewer than s_min times (then f(x0) > f(x0-1)).
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rb3 {
+
+__global__ void k_check_codes(const uint8_t *__restrict__ q, int64_t n, int *__restrict__ bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t c = q[i];
+        if (c < 1 || c > 5) atomicOr(bad, 1);
+    }
+}
+
+__global__ void k_bsearch(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq,
+                          int64_t *__restrict__ lohi) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    int64_t lo = 0, hi = V.n;
+    for (int64_t j = qoff[i + 1] - 1; j >= qoff[i]; --j) {
+        int a = q[j];
+        if (lo == hi) {  // empty interval: lo and hi move together
+            lo = hi = V.C[a] + rank1(V, a, lo);
+        } else {
+            lo = V.C[a] + rank1(V, a, lo);
+            hi = V.C[a] + rank1(V, a, hi);
+        }
+    }
+    lohi[2 * i] = lo;
+    lohi[2 * i + 1] = hi;
+}
+
+__device__ __forceinline__ void emit(rb3_smem *__restrict__ out, int64_t cap, unsigned long long *__restrict__ count,
+                                     int64_t qid, int64_t st, int64_t en, const BiInt &x) {
+    unsigned long long at = atomicAdd(count, 1ull);
+    if ((int64_t)at < cap) {
+        rb3_smem r;
+        r.qid = qid;
+        r.start = (int32_t)st;
+        r.end = (int32_t)en;
+        r.k = x.k;
+        r.kp = x.kp;
+        r.s = x.s;
+        out[at] = r;
+    }
+}
+
+// FindSMEM loop over starts in [x0, x1) of one query.
+__device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int64_t len, int64_t qid, int64_t x0,
+                           int64_t x1, int ell, int64_t smin, rb3_smem *__restrict__ out, int64_t cap,
+                           unsigned long long *__restrict__ count) {
+    int64_t i = x0;
+    bool first = x0 > 0;
+    while (i < x1) {
+        if (i + ell > len) break;
+        BiInt x = {0, 0, V.n};
+        int64_t j;
+        bool fail = false;
+        for (j = i + ell - 1; j >= i; --j) {
+            x = backward_ext(V, x, P[j]);
+            if (x.s < smin) {
+                fail = true;
+                break;
+            }
+        }
+        if (fail) {
+            i = j + 1;
+            first = false;
+            continue;
+        }
+        for (j = i + ell; j < len; ++j) {
+            BiInt y = forward_ext(V, x, P[j]);
+            if (y.s < smin) break;
+            x = y;
+        }
+        const int64_t e = j;
+        bool keep = true;
+        if (first) {  // i == x0 > 0: spurious if P[x0-1, e) still occurs >= smin times
+            BiInt y = backward_ext(V, x, P[x0 - 1]);
+            if (y.s >= smin) keep = false;
+        }
+        first = false;
+        if (keep) emit(out, cap, count, qid, i, e, x);
+        if (e == len) break;
+        BiInt z = {0, 0, V.n};
+        int64_t nxt = i + 1;
+        for (j = e; j >= i + 1; --j) {
+            z = backward_ext(V, z, P[j]);
+            if (z.s < smin) {
+                nxt = j + 1;
+                break;
+            }
+        }
+        i = nxt;
+    }
+}
+
+// Plain form: one thread per query, the whole query.
+__global__ void k_smem_plain(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq,
+                             int ell, int64_t smin, rb3_smem *__restrict__ out, int64_t cap,
+                             unsigned long long *__restrict__ count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    int64_t len = qoff[i + 1] - qoff[i];
+    smem_range(V, q + qoff[i], len, i, 0, len, ell, smin, out, cap, count);
+}
+
+// Chunked form: items are (query, chunk); item_off[i] = first item of query i.
+// Persistent threads take items with a warp-aggregated atomic counter.
+__global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *__restrict__ q,
+                                                      const int64_t *__restrict__ qoff, int64_t nq,
+                                                      const int64_t *__restrict__ item_off, int64_t nitems,
+                                                      int64_t chunk, int ell, int64_t smin,
+                                                      unsigned long long *__restrict__ next,
+                                                      rb3_smem *__restrict__ out, int64_t cap,
+                                                      unsigned long long *__restrict__ count) {
+    for (;;) {
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        int64_t it = (int64_t)base + grp.thread_rank();
+        if (it >= nitems) break;
+        // query of item it: largest i with item_off[i] <= it
+        int64_t lo = 0, hi = nq;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        int64_t qi = lo;
+        int64_t len = qoff[qi + 1] - qoff[qi];
+        int64_t x0 = (it - item_off[qi]) * chunk;
+        int64_t x1 = x0 + chunk < len ? x0 + chunk : len;
+        smem_range(V, q + qoff[qi], len, qi, x0, x1, ell, smin, out, cap, count);
+    }
+}
+
+__global__ void k_smem_keys(const rb3_smem *__restrict__ r, int64_t n, uint64_t *__restrict__ key,
+                            uint32_t *__restrict__ val) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = ((uint64_t)r[i].qid << 32) | (uint32_t)r[i].start;
+    val[i] = (uint32_t)i;
+}
+
+__global__ void k_smem_gather(const rb3_smem *__restrict__ in, const uint32_t *__restrict__ idx, int64_t n,
+                              rb3_smem *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[idx[i]];
+}
+
+static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+static int check_codes(const uint8_t *q, int64_t n, cudaStream_t st) {
+    if (n <= 0) return RB3_OK;
+    DevBuf bad;
+    RB3_TRY(bad.alloc(sizeof(int), st));
+    RB3_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    unsigned grid = nb_for(n, 256);
+    if (grid > (unsigned)num_sms() * 8) grid = (unsigned)num_sms() * 8;
+    RB3_LAUNCH(k_check_codes, grid, 256, 0, st, q, n, bad.as<int>());
+    int h = 0;
+    RB3_CUDA_TRY(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("query symbol outside 1..5 (A,C,G,T,N codes)");
+        return RB3_E_INVAL;
+    }
+    return RB3_OK;
+}
+
+int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
+                         int64_t *lohi, cudaStream_t st) {
+    RB3_TRY(check_codes(q, total_q, st));
+    Phase ph("search.backward", st);
+    if (nq > 0) RB3_LAUNCH(k_bsearch, nb_for(nq, 128), 128, 0, st, occ_view(idx), q, qoff, nq, lohi);
+    return RB3_OK;
+}
+
+int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
+                    int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
+                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st) {
+    RB3_TRY(check_codes(q, total_q, st));
+    *n_out = 0;
+    if (nq == 0) return RB3_OK;
+    OccView V = occ_view(idx);
+    int64_t chunk = o.chunk_len > 0 ? o.chunk_len : 256;
+    const bool plain = o.search_form == 1;
+    std::vector<int64_t> item_off;
+    int64_t nitems = nq;
+    if (!plain) {
+        item_off.resize(nq + 1);
+        item_off[0] = 0;
+        for (int64_t i = 0; i < nq; ++i) {
+            int64_t len = qoff_host[i + 1] - qoff_host[i];
+            int64_t c = len <= chunk ? 1 : (len + chunk - 1) / chunk;
+            item_off[i + 1] = item_off[i] + c;
+        }
+        nitems = item_off[nq];
+    }
+    DevBuf items, ctr;
+    RB3_TRY(ctr.alloc(2 * sizeof(unsigned long long), st));
+    if (!plain) {
+        RB3_TRY(items.alloc(sizeof(int64_t) * (nq + 1), st));
+        RB3_CUDA_TRY(cudaMemcpyAsync(items.p, item_off.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
+    }
+    // scratch for unsorted records: grows once if the first guess is short
+    int64_t guess = total_q / 32 + 4096;
+    int64_t scap = guess < cap ? guess : cap;
+    if (scap < 1) scap = 1;
+    DevBuf raw;
+    unsigned long long count = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        raw.release();
+        RB3_TRY(raw.alloc(sizeof(rb3_smem) * scap, st));
+        RB3_CUDA_TRY(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), st));
+        unsigned long long *d_next = ctr.as<unsigned long long>(), *d_count = d_next + 1;
+        {
+            Phase ph(plain ? "search.smem_plain" : "search.smem", st);
+            if (plain) {
+                RB3_LAUNCH(k_smem_plain, nb_for(nq, 128), 128, 0, st, V, q, qoff, nq, (int)min_len, min_occ,
+                           raw.as<rb3_smem>(), scap, d_count);
+            } else {
+                int64_t resident = (int64_t)num_sms() * 2048;
+                int64_t threads = nitems < resident ? nitems : resident;
+                RB3_LAUNCH(k_smem_chunked, nb_for(threads, 256), 256, 0, st, V, q, qoff, nq, items.as<int64_t>(),
+                           nitems, chunk, (int)min_len, min_occ, d_next, raw.as<rb3_smem>(), scap, d_count);
+            }
+        }
+        RB3_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));
+        RB3_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((int64_t)count <= scap || (int64_t)count > cap) break;
+        scap = (int64_t)count;  // rerun with room for every record
+    }
+    *n_out = (int64_t)count;
+    if ((int64_t)count > cap) {
+        set_error("mem_search: %lld SMEMs found, output capacity %lld", (long long)count, (long long)cap);
+        return RB3_E_CAPACITY;
+    }
+    if (count == 0) return RB3_OK;
+    Phase ph("search.smem_sort", st);
+    int64_t R = (int64_t)count;
+    DevBuf k0, k1, v0, v1;
+    RB3_TRY(k0.alloc(sizeof(uint64_t) * R, st));
+    RB3_TRY(k1.alloc(sizeof(uint64_t) * R, st));
+    RB3_TRY(v0.alloc(sizeof(uint32_t) * R, st));
+    RB3_TRY(v1.alloc(sizeof(uint32_t) * R, st));
+    RB3_LAUNCH(k_smem_keys, nb_for(R, 256), 256, 0, st, raw.as<rb3_smem>(), R, k0.as<uint64_t>(), v0.as<uint32_t>());
+    bool alt = false;
+    RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0.as<uint32_t>(), k1.as<uint64_t>(), v1.as<uint32_t>(), R, 0,
+                             32 + ilog2(nq) + 1, st, &alt));
+    RB3_LAUNCH(k_smem_gather, nb_for(R, 256), 256, 0, st, raw.as<rb3_smem>(),
+               alt ? v1.as<uint32_t>() : v0.as<uint32_t>(), R, out_dev);
+    return RB3_OK;
+}
+
+}  // namespace rb3

@@ -1,0 +1,282 @@
+"""ctypes binding of librb3 (include/rb3.h).  Argument marshalling only: every
+step of the computation runs in the library's CUDA kernels.  Function names
+are the C ABI's.  Array arguments may be torch tensors (CUDA or CPU), numpy
+arrays or raw integer addresses; streams are torch streams, raw cudaStream_t
+integers or None (legacy default stream)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RB3_OK, RB3_E_INVAL, RB3_E_NOMEM, RB3_E_CUDA, RB3_E_TIMEOUT, RB3_E_CAPACITY, RB3_E_IO = range(7)
+_NAMES = {0: "RB3_OK", 1: "RB3_E_INVAL", 2: "RB3_E_NOMEM", 3: "RB3_E_CUDA", 4: "RB3_E_TIMEOUT",
+          5: "RB3_E_CAPACITY", 6: "RB3_E_IO"}
+
+
+class RB3Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rb3_opts(ctypes.Structure):
+    _fields_ = [("occ_interval", ctypes.c_int32), ("single_strand", ctypes.c_int32),
+                ("seg_len", ctypes.c_int64), ("seed_cap", ctypes.c_int64),
+                ("merge_form", ctypes.c_int32), ("search_form", ctypes.c_int32),
+                ("chunk_len", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+SMEM_DTYPE = np.dtype([("qid", "<i8"), ("start", "<i4"), ("end", "<i4"), ("k", "<i8"), ("kp", "<i8"),
+                       ("s", "<i8")])
+assert SMEM_DTYPE.itemsize == 40
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_lib = None
+
+
+def lib():
+    """Loads librb3.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "rb3_opts_default": (None, [_vp]),
+            "rb3_build_batch": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_vp)]),
+            "rb3_index_empty": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+            "rb3_merge": (ctypes.c_int, [_vp, _vp, _vp]),
+            "rb3_merge_opts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rb3_backward_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+            "rb3_mem_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
+                                              ctypes.POINTER(_i64), _vp]),
+            "rb3_mem_search_opts": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp, _i64,
+                                                   ctypes.POINTER(_i64), _vp]),
+            "rb3_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rb3_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                              ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+            "rb3_drop_build_data": (ctypes.c_int, [_vp]),
+            "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+            "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
+            "rb3_index_free": (None, [_vp]),
+            "rb3_last_error": (ctypes.c_char_p, []),
+            "rb3_encode_ascii": (ctypes.c_int, [ctypes.c_char_p, _i64, _vp]),
+            "rb3_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+            "rb3_profile_reset": (ctypes.c_int, []),
+            "rb3_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
+            "rb3_launch_count": (_i64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != RB3_OK:
+        raise RB3Error(code, lib().rb3_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Address of a tensor / array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() if x.numel() else None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data if x.size else None
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _len(x) -> int:
+    return int(x.numel()) if hasattr(x, "numel") else int(len(x))
+
+
+def _opts(o):
+    if o is None:
+        return None
+    if isinstance(o, rb3_opts):
+        return o
+    r = rb3_opts()
+    for k, v in dict(o).items():
+        setattr(r, k, int(v))
+    return r
+
+
+class Index:
+    """Owns one rb3_index handle; freed with rb3_index_free."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            lib().rb3_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+
+def rb3_opts_default() -> rb3_opts:
+    o = rb3_opts()
+    lib().rb3_opts_default(ctypes.byref(o))
+    return o
+
+
+def rb3_build_batch(seq, lens, n_seq=None, opts=None, stream=None) -> Index:
+    n_seq = _len(lens) if n_seq is None else n_seq
+    out = _vp()
+    o = _opts(opts)
+    _check(lib().rb3_build_batch(_ptr(seq), _ptr(lens), n_seq, ctypes.byref(o) if o else None, _stream(stream),
+                                 ctypes.byref(out)))
+    return Index(out.value)
+
+
+def rb3_index_empty(opts=None) -> Index:
+    out = _vp()
+    o = _opts(opts)
+    _check(lib().rb3_index_empty(ctypes.byref(o) if o else None, ctypes.byref(out)))
+    return Index(out.value)
+
+
+def rb3_merge(dst: Index, src: Index, stream=None):
+    _check(lib().rb3_merge(dst.handle, src.handle, _stream(stream)))
+
+
+def rb3_merge_opts(dst: Index, src: Index, opts=None, stream=None):
+    o = _opts(opts)
+    _check(lib().rb3_merge_opts(dst.handle, src.handle, ctypes.byref(o) if o else None, _stream(stream)))
+
+
+def rb3_backward_search(idx: Index, q, qoff, nq=None, lo_hi=None, stream=None):
+    nq = _len(qoff) - 1 if nq is None else nq
+    if lo_hi is None:
+        lo_hi = np.empty((nq, 2), dtype=np.int64)
+    _check(lib().rb3_backward_search(idx.handle, _ptr(q), _ptr(qoff), nq, _ptr(lo_hi), _stream(stream)))
+    return lo_hi
+
+
+def rb3_mem_search_opts(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opts=None, out=None, cap=None,
+                        nq=None, stream=None):
+    """Returns (records, n).  Without `out` a host array is allocated and grown
+    once on RB3_E_CAPACITY."""
+    nq = _len(qoff) - 1 if nq is None else nq
+    o = _opts(opts)
+    n_out = _i64(0)
+    auto = out is None
+    if auto:
+        cap = 1 << 16 if cap is None else cap
+        out = np.empty(cap, dtype=SMEM_DTYPE)
+    elif cap is None:
+        cap = _len(out) if not hasattr(out, "element_size") else out.numel() * out.element_size() // 40
+    r = lib().rb3_mem_search_opts(idx.handle, _ptr(q), _ptr(qoff), nq, int(min_len), int(min_occ),
+                                  ctypes.byref(o) if o else None, _ptr(out), cap, ctypes.byref(n_out),
+                                  _stream(stream))
+    if r == RB3_E_CAPACITY and auto:
+        cap = int(n_out.value)
+        out = np.empty(cap, dtype=SMEM_DTYPE)
+        r = lib().rb3_mem_search_opts(idx.handle, _ptr(q), _ptr(qoff), nq, int(min_len), int(min_occ),
+                                      ctypes.byref(o) if o else None, _ptr(out), cap, ctypes.byref(n_out),
+                                      _stream(stream))
+    _check(r)
+    n = int(n_out.value)
+    return (out[:n] if auto else out), n
+
+
+def rb3_mem_search(idx: Index, q, qoff, min_len: int, min_occ: int = 1, out=None, cap=None, nq=None, stream=None):
+    return rb3_mem_search_opts(idx, q, qoff, min_len, min_occ, None, out, cap, nq, stream)
+
+
+def rb3_index_info(idx: Index) -> dict:
+    n, m, D, fl = _i64(), _i64(), _i32(), _i32()
+    C = (_i64 * 7)()
+    _check(lib().rb3_index_info(idx.handle, ctypes.byref(n), ctypes.byref(m), C, ctypes.byref(D), ctypes.byref(fl)))
+    return {"n": n.value, "m": m.value, "C": list(C), "occ_interval": D.value,
+            "single_strand": bool(fl.value & 1), "has_build_data": bool(fl.value & 2)}
+
+
+def rb3_export(idx: Index, codes=None, occ=None, stream=None, want_occ: bool = False):
+    info = rb3_index_info(idx)
+    if codes is None:
+        codes = np.empty(info["n"], dtype=np.uint8)
+    if occ is None and want_occ:
+        occ = np.empty((info["n"] // info["occ_interval"] + 1, 6), dtype=np.int64)
+    _check(lib().rb3_export(idx.handle, _ptr(codes), _ptr(occ), _stream(stream)))
+    return (codes, occ) if want_occ else codes
+
+
+def rb3_drop_build_data(idx: Index):
+    _check(lib().rb3_drop_build_data(idx.handle))
+
+
+def rb3_index_save(idx: Index, path: str):
+    _check(lib().rb3_index_save(idx.handle, os.fsencode(path)))
+
+
+def rb3_index_load(path: str, stream=None) -> Index:
+    out = _vp()
+    _check(lib().rb3_index_load(os.fsencode(path), _stream(stream), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def rb3_index_free(idx: Index):
+    idx.free()
+
+
+def rb3_last_error() -> str:
+    return lib().rb3_last_error().decode(errors="replace")
+
+
+def rb3_encode_ascii(s) -> np.ndarray:
+    b = s.encode() if isinstance(s, str) else bytes(s)
+    out = np.empty(len(b), dtype=np.uint8)
+    _check(lib().rb3_encode_ascii(b, len(b), out.ctypes.data if len(b) else None))
+    return out
+
+
+def rb3_profile_enable(on: bool = True):
+    _check(lib().rb3_profile_enable(int(on)))
+
+
+def rb3_profile_reset():
+    _check(lib().rb3_profile_reset())
+
+
+def rb3_profile_read() -> dict:
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    calls = (_i64 * cap)()
+    n = _i32()
+    _check(lib().rb3_profile_read(names, ms, calls, cap, ctypes.byref(n)))
+    return {names[i].decode(): (ms[i], calls[i]) for i in range(min(n.value, cap))}
+
+
+def rb3_launch_count() -> int:
+    return int(lib().rb3_launch_count())

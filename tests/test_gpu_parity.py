@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element
+by element (bit-exact: every output is integer)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2409_00613_gb300 as rb
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+FIELDS = ("qid", "start", "end", "k", "kp", "s")
+
+
+def build(S, s0=0, s1=None, host=False, **opts):
+    s1 = len(S.lens) if s1 is None else s1
+    off = S.offsets
+    seq = S.seq[off[s0]:off[s1]].copy()
+    lens = S.lens[s0:s1].copy()
+    if not host:
+        seq = torch.from_numpy(seq).to(DEV)
+    return rb.rb3_build_batch(seq, lens, opts=opts or None)
+
+
+def ref_bwt(S, s0=0, s1=None, both=True):
+    s1 = len(S.lens) if s1 is None else s1
+    sub = S.subset(s0, s1)
+    return oracle.bwt(oracle.concat(sub.seq, sub.lens, both))
+
+
+def smem_rows(recs, n):
+    if n == 0:
+        return np.zeros((0, 6), dtype=np.int64)
+    return np.stack([recs[f].astype(np.int64) for f in FIELDS], axis=1)
+
+
+def check_index(idx, B, D=64):
+    codes, occ = rb.rb3_export(idx, want_occ=True)
+    assert np.array_equal(codes, B)
+    assert np.array_equal(occ, oracle.occ_table(B, D))
+    info = rb.rb3_index_info(idx)
+    assert info["n"] == len(B)
+    assert info["C"] == list(oracle.counts(B))
+
+
+def test_config0_tiny_build_merge_search():
+    S, Q = synth.tiny()
+    B_all = ref_bwt(S)
+    A = build(S, 0, 32)
+    B = build(S, 32, 64)
+    check_index(A, ref_bwt(S, 0, 32))
+    check_index(B, ref_bwt(S, 32, 64))
+    rb.rb3_merge(A, B)
+    check_index(A, B_all)
+    assert rb.rb3_index_info(A)["m"] == 128
+    direct = build(S, 0, 64)
+    check_index(direct, B_all)
+    # plain Algorithm 1 form gives the same bits
+    A2 = build(S, 0, 32)
+    rb.rb3_merge_opts(A2, B, {"merge_form": 1})
+    check_index(A2, B_all)
+    # backward search: 1,000 queries of 20 bp, device and host buffers
+    want = oracle.backward_search(B_all, Q.q, Q.qoff)
+    got = rb.rb3_backward_search(A, torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV))
+    assert np.array_equal(got, want)
+    assert np.array_equal(rb.rb3_backward_search(A, Q.q, Q.qoff), want)
+    assert np.all(want[:, 1] > want[:, 0])  # every query was sampled from the text
+
+
+@pytest.mark.parametrize("D", [64, 128, 256])
+@pytest.mark.parametrize("both", [True, False])
+def test_random_lists_batches(D, both):
+    g = synth.rng(1000 + D + both)
+    for trial in range(5):
+        n_str = int(g.integers(3, 40))
+        S = synth.random_strings(g, n_str, int(g.integers(5, 700)), n_frac=0.03, allow_empty=True)
+        cuts = sorted(set([0, n_str] + list(g.integers(0, n_str, size=2))))
+        opts = {"occ_interval": D, "single_strand": int(not both)}
+        idx = None
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            part = build(S, a, b, host=bool(trial & 1), **opts)
+            check_index(part, ref_bwt(S, a, b, both), D)
+            if idx is None:
+                idx = part
+            else:
+                mopts = dict(opts, seg_len=int(g.integers(3, 64)), seed_cap=int(g.integers(1, 20)))
+                rb.rb3_merge_opts(idx, part, mopts)
+        check_index(idx, ref_bwt(S, 0, n_str, both), D)
+
+
+def test_merge_into_empty_and_empty_batches():
+    g = synth.rng(77)
+    S = synth.random_strings(g, 9, 300, n_frac=0.02)
+    idx = rb.rb3_index_empty()
+    assert rb.rb3_index_info(idx)["n"] == 0
+    for a, b in [(0, 0), (0, 4), (4, 4), (4, 9)]:
+        part = build(S, a, b)
+        rb.rb3_merge(idx, part)
+    check_index(idx, ref_bwt(S))
+    # merging an empty batch leaves the index unchanged
+    rb.rb3_merge(idx, build(S, 0, 0))
+    check_index(idx, ref_bwt(S))
+
+
+def test_all_empty_strings_and_single_symbols():
+    S = synth.Strings(np.array([1, 5], dtype=np.uint8), np.array([0, 1, 0, 0, 1, 0], dtype=np.int64))
+    check_index(build(S), ref_bwt(S))
+
+
+def test_large_groups_low_complexity():
+    """Long single-symbol runs make suffix groups far larger than the shared-memory
+    path handles (the radix path of the builder)."""
+    g = synth.rng(5)
+    parts = [np.full(3000, 5, np.uint8), synth.random_bases(g, 500), np.full(2500, 1, np.uint8),
+             np.tile(np.array([1, 2], np.uint8), 1500), synth.random_bases(g, 100)]
+    seq = np.concatenate(parts)
+    S = synth.Strings(seq, np.array([3000, 500, 2500, 3000, 100], dtype=np.int64))
+    check_index(build(S), ref_bwt(S))
+    A = build(S, 0, 2)
+    rb.rb3_merge_opts(A, build(S, 2, 5), {"seg_len": 100})
+    check_index(A, ref_bwt(S))
+
+
+def test_backward_search_edges():
+    g = synth.rng(9)
+    S = synth.random_strings(g, 12, 200, n_frac=0.05)
+    B = ref_bwt(S)
+    idx = build(S)
+    pats = [np.zeros(0, np.uint8), np.array([5], np.uint8), np.array([5, 5, 5], np.uint8)]
+    for _ in range(200):
+        L = int(g.integers(1, 15))
+        s = int(g.integers(0, len(S.seq) - L))
+        pats.append(S.seq[s:s + L].copy() if g.random() < 0.7 else synth.random_bases(g, L))
+    q = np.concatenate(pats)
+    qoff = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.int64)
+    assert np.array_equal(rb.rb3_backward_search(idx, q, qoff), oracle.backward_search(B, q, qoff))
+
+
+@pytest.mark.parametrize("chunk", [0, 5, 17, 64])
+@pytest.mark.parametrize("ell,smin", [(1, 1), (4, 1), (12, 2), (19, 1)])
+def test_smem_vs_oracle(chunk, ell, smin):
+    S = synth.pangenome(seed=31, founder_len=3000, n_hap=6, batch=3)
+    B = ref_bwt(S)
+    idx = build(S, 0, 3)
+    rb.rb3_merge(idx, build(S, 3, 6))
+    Q = synth.mem_queries(S, seed=32, nq=300, median=80, lo=1, hi=600, sub=0.02)
+    want = oracle.smem(B, Q.q, Q.qoff, ell, smin)
+    for form in (0, 1):
+        recs, n = rb.rb3_mem_search_opts(idx, torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV),
+                                         ell, smin, {"chunk_len": chunk, "search_form": form})
+        assert np.array_equal(smem_rows(recs, n), want), (form, chunk, ell, smin)
+
+
+def test_smem_capacity_and_single_strand_rejected():
+    S = synth.pangenome(seed=33, founder_len=2000, n_hap=3, batch=3)
+    idx = build(S)
+    Q = synth.mem_queries(S, seed=34, nq=50, median=100, lo=40, hi=200, sub=0.0)
+    want = oracle.smem(ref_bwt(S), Q.q, Q.qoff, 10, 1)
+    assert len(want) > 3
+    out = np.empty(2, dtype=rb.SMEM_DTYPE)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_mem_search(idx, Q.q, Q.qoff, 10, 1, out=out, cap=2)
+    assert e.value.code == rb.RB3_E_CAPACITY
+    ss = build(S, single_strand=1)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_mem_search(ss, Q.q, Q.qoff, 10, 1)
+    assert e.value.code == rb.RB3_E_INVAL
+
+
+def test_invalid_symbols_rejected():
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_build_batch(np.array([1, 2, 7], np.uint8), np.array([3], np.int64))
+    assert e.value.code == rb.RB3_E_INVAL
+    S = synth.pangenome(seed=35, founder_len=500, n_hap=2, batch=2)
+    idx = build(S)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_backward_search(idx, np.array([1, 0, 2], np.uint8), np.array([0, 3], np.int64))
+    assert e.value.code == rb.RB3_E_INVAL
+
+
+def test_pangenome_medium_incremental():
+    """Near-identical haplotypes (long exact matches, both strands): batch builds
+    and segmented merges against the oracle's own incremental build."""
+    S = synth.pangenome(seed=41, founder_len=60_000, n_hap=12, batch=4)
+    T = oracle.concat(S.seq, S.lens, True)
+    want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=4)
+    assert oracle.certify(want, T) == 0
+    idx = build(S, 0, 4)
+    for b0, b1 in [(4, 8), (8, 12)]:
+        rb.rb3_merge_opts(idx, build(S, b0, b1), {"seg_len": 997})
+    check_index(idx, want)
+    # plain Algorithm 1 form of the same merges
+    idx2 = build(S, 0, 4)
+    for b0, b1 in [(4, 8), (8, 12)]:
+        rb.rb3_merge_opts(idx2, build(S, b0, b1), {"merge_form": 1})
+    check_index(idx2, want)
+
+
+def test_save_load_resume(tmp_path):
+    S = synth.pangenome(seed=51, founder_len=5000, n_hap=6, batch=2)
+    idx = build(S, 0, 2)
+    rb.rb3_merge(idx, build(S, 2, 4))
+    p = str(tmp_path / "x.rb3")
+    rb.rb3_index_save(idx, p)
+    back = rb.rb3_index_load(p)
+    assert rb.rb3_index_info(back)["has_build_data"] is False
+    rb.rb3_merge(back, build(S, 4, 6))  # resume: load + further merge
+    rb.rb3_merge(idx, build(S, 4, 6))
+    check_index(back, ref_bwt(S))
+    check_index(idx, ref_bwt(S))
