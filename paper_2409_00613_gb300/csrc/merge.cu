@@ -21,7 +21,10 @@
 //                 X) or until X's sentinel (l = k + occ(Q$), the B1 suffixes equal
 //                 to Q and ending at a sentinel, all older than X's).  Seeds give
 //                 up after seed_cap steps; the walk from the segment above then
-//                 continues through that segment.  Walks run independently under
+//                 continues through that segment.  A single-strand B1 has no
+//                 ForwardExt; there the seed is a backward search from up to
+//                 seed_cap symbols to the right, exact once its interval is
+//                 empty (or from the sentinel).  Walks run independently under
 //                 warp-aggregated work stealing, ordered so that homologous
 //                 segments of the batch's strings run together and share B1
 //                 blocks in L2.
@@ -84,6 +87,37 @@ __global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_
         q = y;
     }
     seed[w] = res;
+}
+
+// Seed for any BWT (used for single-strand indexes, where ForwardExt is not
+// available): backward search over P[x, y) with y = min(x + cap, send).  When
+// y is the sentinel the walk is exact from the start (l = m1).  Otherwise the
+// SA interval [lo, hi) of P[p, y) is kept; once it is empty (P[p, y) does not
+// occur in B1) every B1 suffix compares with P[p..]$ as it does with P[p, y),
+// so l(p) = lo exactly, and the steps continue exactly down to x.
+__global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
+                            const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    int64_t x = w_hi[w], send = w_send[w];
+    if (x == send) {
+        seed[w] = -2;
+        return;
+    }
+    int64_t y = x + cap < send ? x + cap : send;
+    bool exact = y == send;
+    int64_t lo = exact ? m1 : 0, hi = exact ? m1 : B1.n;
+    for (int64_t p = y - 1; p >= x; --p) {
+        int a = T2[p];
+        lo = B1.C[a] + rank1(B1, a, lo);
+        if (exact) {
+            hi = lo;
+        } else {
+            hi = B1.C[a] + rank1(B1, a, hi);
+            exact = lo == hi;
+        }
+    }
+    seed[w] = exact ? lo : -1;
 }
 
 // Walk w covers positions [lo, hi) of its string, right to left; its lower end
@@ -332,7 +366,11 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             RB3_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
             {
                 Phase ps("merge.seed", st);
-                RB3_LAUNCH(k_seeds, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi, d_send, nw, cap, d_seed);
+                if (dst->single_strand)
+                    RB3_LAUNCH(k_seeds_bwd, nb_for(nw, 128), 128, 0, st, V1, m1, src->text, d_hi, d_send, nw, cap,
+                               d_seed);
+                else
+                    RB3_LAUNCH(k_seeds, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi, d_send, nw, cap, d_seed);
                 RB3_LAUNCH(k_walk_bounds, nb_for(ns, 128), 128, 0, st, d_sfirst, d_sstart, ns, d_hi, d_seed, d_lo);
             }
             {
