@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 BWT build + merge path (and MEM search on its result).
+
+Workload (default): the pangenome merge -- a 5 Mb uniform-random founder, 50
+haplotypes with 0.1% SNPs and 0.01% indels, both strands (~500 M symbols),
+built incrementally in batches of 10 haplotypes.  Batch 0 is built before the
+timed region; each timed step builds the next batch's BWT on the device and
+merges it into the running index (step k uses batch 1 + (k mod 4)).  value =
+new symbols per second (Msym/s) over the K timed steps, inputs resident in HBM.
+After the timed steps the index holds all 50 haplotypes (for K = 4) and is
+searched for SMEMs (>= 31 bp) of 1 M queries (lognormal lengths, median 150 bp;
+90% from the haplotypes with 1% substitutions, 10% random) -- reported as
+`mem_search` (Mbp/s) beside the plain one-query-per-thread form.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rb3|reference]
+
+With torchrun (N > 1) every rank runs its own independent pangenome (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (plain Algorithm 1 on naive-sort batch
+BWTs) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = ("pangenome merge: 5 Mb uniform founder, 50 haplotypes (0.1% SNPs, 0.01% indels 1-10 bp), "
+            "both strands (~500 Msym), batches of 10 haplotypes; step = device batch-BWT build + merge into "
+            "the running index")
+METRIC = "BWT-merge Msymbols/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["rb3", "reference"], default="rb3")
+    p.add_argument("--scale", type=float, default=1.0, help="founder length / 5 Mb (1.0 = the workload)")
+    p.add_argument("--queries", type=int, default=1_000_000)
+    p.add_argument("--no-search", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--seg-len", type=int, default=0)
+    p.add_argument("--occ", type=int, default=64)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_hint: str | None):
+        self.bus = (bus_hint or "").lower()
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rb3_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.bus and self.bus not in parts[0].lower():
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def bus_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the rb3 arm
+# ---------------------------------------------------------------------------
+def run_rb3(args, rank, world, local_rank):
+    import torch
+    import paper_2409_00613_gb300 as rb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    st = torch.cuda.current_stream()
+    founder = int(5_000_000 * args.scale)
+    S = synth.pangenome(seed=synth.SEED_BASE + 1 + 1000 * rank, founder_len=founder, n_hap=50, batch=10)
+    off = S.offsets
+    batches = S.batches
+    dev_batches, host_batches = [], []
+    for (a, b) in batches:
+        seq = S.seq[off[a]:off[b]]
+        lens = S.lens[a:b].copy()
+        dev_batches.append((torch.from_numpy(seq.copy()).to(dev), lens))
+        pinned = torch.empty(len(seq), dtype=torch.uint8, pin_memory=True)
+        pinned.numpy()[:] = seq
+        host_batches.append((pinned, lens))
+    ds = [int(2 * (lens.sum() + len(lens))) for (_, lens) in dev_batches]
+    opts = {"occ_interval": args.occ, "seg_len": args.seg_len}
+    step_batch = [1 + (k % (len(batches) - 1)) for k in range(args.steps)]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- warm-up: build batch 0, then W steps merging into it ----
+    idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    for w in range(args.warmup):
+        src = rb.rb3_build_batch(*dev_batches[1 + w % (len(batches) - 1)], opts=opts, stream=st)
+        rb.rb3_merge_opts(idx, src, opts, stream=st)
+        src.free()
+    idx.free()
+    # ---- timed: fresh batch-0 index (untimed), then K steps ----
+    idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    barrier()
+    rb.rb3_profile_reset()
+    rb.rb3_profile_enable(True)
+    clocks = ClockSampler(bus_id(torch, local_rank))
+    clocks.start()
+    launches0 = rb.rb3_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(st)
+    new_syms = 0
+    for k in range(args.steps):
+        b = step_batch[k]
+        src = rb.rb3_build_batch(dev_batches[b][0], dev_batches[b][1], opts=opts, stream=st)
+        rb.rb3_merge_opts(idx, src, opts, stream=st)
+        src.free()
+        new_syms += ds[b]
+    t1.record(st)
+    barrier()
+    ms = t0.elapsed_time(t1)
+    launches = rb.rb3_launch_count() - launches0
+    clk = clocks.stop()
+    rb.rb3_profile_enable(False)
+    prof = rb.rb3_profile_read()
+    info = rb.rb3_index_info(idx)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        s = torch.tensor([new_syms], device=dev, dtype=torch.float64)
+        dist.all_reduce(s)
+        total_syms = float(s.item())
+    else:
+        total_syms = float(new_syms)
+    value = total_syms / (ms * 1e3)
+
+    # ---- e2e: same steps through the public API from pinned host buffers ----
+    e2e_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    barrier()
+    h2d = 0
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        b = step_batch[k]
+        src = rb.rb3_build_batch(host_batches[b][0], host_batches[b][1], opts=opts, stream=st)
+        rb.rb3_merge_opts(e2e_idx, src, opts, stream=st)  # reads the merged counts back (2 x 48 B)
+        src.free()
+        h2d += host_batches[b][0].numel() + 8 * len(host_batches[b][1])
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - e0) * 1e3
+    e2e_idx.free()
+    e2e = {"value": round(new_syms / (e_ms * 1e3), 3), "unit": "Msym/s",
+           "h2d_bytes_per_step": int(h2d // max(1, args.steps)), "d2h_bytes_per_step": 96}
+
+    # ---- roofline of the dominant kernel (live CUDA events of the timed region) ----
+    hbm, peak_kind = peaks()
+    kern = {k: v for k, v in prof.items() if k.startswith("k.") and v[2] > 0}
+    roof = None
+    if kern:
+        top = max(kern, key=lambda k: kern[k][0])
+        kms, kcalls, kbytes = kern[top]
+        achieved = kbytes / (kms * 1e-3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),
+                "launches": kcalls, "share_of_step": round(kms / ms, 4)}
+    phases = {k: round(v[0], 3) for k, v in sorted(prof.items())}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "Msym/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "founder_bp": founder, "haplotypes": 50, "batch_haplotypes": 10,
+                      "new_symbols_per_gpu": new_syms, "final_index_symbols": info["n"],
+                      "occ_interval": info["occ_interval"], "seg_len": args.seg_len or "auto",
+                      "l2": "inputs larger than L2 (batch ~100 Msym text + 100-500 MB index per step)",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases}
+
+    # ---- comparison with the plain one-walk-per-string form on one merge ----
+    if not args.no_plain and rank == 0:
+        out["merge_vs_plain"] = plain_vs_segmented(rb, torch, dev_batches, opts, st, ds)
+
+    # ---- MEM search on the finished index ----
+    if not args.no_search and rank == 0:
+        out["mem_search"] = mem_search(rb, torch, S, idx, args, st, dev)
+    idx.free()
+    if rank == 0 and not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_sample(S)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def plain_vs_segmented(rb, torch, dev_batches, opts, st, ds):
+    """Times the merge of batch 1 into batch 0 both ways (builds excluded)."""
+    res = {}
+    for form in (0, 1):
+        base = rb.rb3_build_batch(*dev_batches[0], opts=opts, stream=st)
+        src = rb.rb3_build_batch(*dev_batches[1], opts=opts, stream=st)
+        o = dict(opts, merge_form=form)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rb.rb3_merge_opts(base, src, o, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        res["plain_ms" if form else "segmented_ms"] = round(a.elapsed_time(b), 3)
+        if form == 0:
+            ref = rb.rb3_export(base)
+        else:
+            res["equal_output"] = bool(np.array_equal(ref, rb.rb3_export(base)))
+        base.free()
+        src.free()
+    res["speedup"] = round(res["plain_ms"] / res["segmented_ms"], 2)
+    res["batch"] = "batch 1 (10 haplotypes, both strands) into batch 0"
+    res["new_symbols"] = ds[1]
+    return res
+
+
+def mem_search(rb, torch, S, idx, args, st, dev):
+    Q = synth.mem_queries(S, nq=args.queries)
+    q = torch.from_numpy(Q.q).to(dev)
+    qoff = torch.from_numpy(Q.qoff).to(dev)
+    bp = int(Q.qoff[-1])
+    res = {"workload": f"{Q.nq} queries (lognormal len, median 150, sigma 1, clipped [31, 10000]; 90% haplotype "
+                       "windows with 1% substitutions, 10% random), SMEMs >= 31 bp, min_occ 1, on the finished index",
+           "query_bp": bp, "unit": "Mbp/s"}
+    cap = max(1 << 20, bp // 16)
+    out = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
+    for form, key in ((0, "value"), (1, "plain_value")):
+        o = {"search_form": form}
+        reps = 2 if form == 0 else 1
+        _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[key] = round(bp / (ms * 1e3), 2)
+        res[key.replace("value", "ms")] = round(ms, 3)
+        res["smems"] = int(n)
+    res["speedup_vs_plain"] = round(res["value"] / res["plain_value"], 2)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample_inputs(S, window: int):
+    """Windows of haplotype 0 (batch 0) and haplotype 10 (batch 1)."""
+    off = S.offsets
+    a = S.seq[off[0]:off[0] + min(window, S.lens[0])]
+    b = S.seq[off[10]:off[10] + min(window, S.lens[10])]
+    return a.copy(), b.copy()
+
+
+def oracle_step(oracle, B1, b):
+    """One oracle step: naive-sort BWT of the new batch (both strands) + Algorithm 1 merge."""
+    T2 = oracle.concat(b, np.array([len(b)]), True)
+    t = time.perf_counter()
+    B2 = oracle.bwt(T2)
+    M = oracle.merge(B1, B2, nthreads=2)
+    dt = time.perf_counter() - t
+    return len(T2), dt, M
+
+
+def cpu_sample(S, window: int = 5_000_000):
+    import oracle
+    a, b = oracle_sample_inputs(S, window)
+    B1 = oracle.bwt(oracle.concat(a, np.array([len(a)]), True))
+    n2, dt, _ = oracle_step(oracle, B1, b)
+    return {"value": round(n2 / dt / 1e6, 4), "unit": "Msym/s", "cores": 2, "kind": "oracle",
+            "host_cores": os.cpu_count(),
+            "sample": f"build (naive suffix sort, 1 thread) of the double-strand BWT of a {len(b)} bp window of "
+                      f"haplotype 10 and Algorithm 1 merge (2 walks, 2 threads) into that of haplotype 0's window: "
+                      f"{n2} new symbols in {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    S = synth.pangenome(founder_len=int(5_000_000 * args.scale), n_hap=50, batch=10)
+    a, b = oracle_sample_inputs(S, 5_000_000)
+    B1 = oracle.bwt(oracle.concat(a, np.array([len(a)]), True))
+    for _ in range(args.warmup):
+        oracle_step(oracle, B1, b)
+    tot_n, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        n2, dt, _ = oracle_step(oracle, B1, b)
+        tot_n += n2
+        tot_t += dt
+    v = tot_n / tot_t / 1e6
+    sample = (f"each step: naive-sort double-strand BWT of a {len(b)} bp window of haplotype 10 + Algorithm 1 "
+              f"merge into haplotype 0's window ({tot_n // args.steps} new symbols)")
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Msym/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "parallelism": "CPU oracle, host cores"},
+           "cpu_baseline": {"value": round(v, 4), "unit": "Msym/s", "cores": 2, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(v, 4), "unit": "Msym/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_rb3(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

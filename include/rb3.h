@@ -158,12 +158,14 @@ const char *rb3_last_error(void);
 int rb3_encode_ascii(const char *ascii, int64_t n, uint8_t *codes);
 
 /* Per-phase device timing.  When enabled, every phase of build / merge /
- * search is bracketed by CUDA events on the caller's stream and its duration
- * accumulated; launches of the library's kernels are counted always.
- * names[i] (static strings), ms[i], calls[i] for i < *n (at most cap). */
+ * search, and each hot kernel on its own, is bracketed by CUDA events on the
+ * caller's stream; durations, call counts and the algorithmic bytes the
+ * kernels moved are accumulated per name.  Launches of the library's kernels
+ * are counted always.  Fills names[i] (valid until the next read), ms[i],
+ * calls[i], bytes[i] for i < min(*n, cap); any output array may be NULL. */
 int rb3_profile_enable(int on);
 int rb3_profile_reset(void);
-int rb3_profile_read(const char **names, double *ms, int64_t *calls, int32_t cap, int32_t *n);
+int rb3_profile_read(const char **names, double *ms, int64_t *calls, double *bytes, int32_t cap, int32_t *n);
 int64_t rb3_launch_count(void);
 
 #ifdef __cplusplus

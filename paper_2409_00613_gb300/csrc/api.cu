@@ -84,16 +84,21 @@ static std::mutex g_prof_mu;
 struct Pending {
     const char *name;
     cudaEvent_t a, b;
+    double bytes;
+};
+struct Acc {
+    double ms = 0.0, bytes = 0.0;
+    int64_t calls = 0;
 };
 static std::vector<Pending> g_pending;
-static std::map<std::string, std::pair<double, int64_t>> g_acc;
+static std::map<std::string, Acc> g_acc;
 static std::vector<std::string> g_names;  // stable storage for names handed out
 
 bool profile_on() { return g_prof.load(std::memory_order_relaxed); }
 
-void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b) {
+void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b, double bytes) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_pending.push_back({name, a, b});
+    g_pending.push_back({name, a, b, bytes});
 }
 
 static void profile_drain() {
@@ -101,9 +106,10 @@ static void profile_drain() {
     for (auto &p : g_pending) {
         float ms = 0.f;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            auto &e = g_acc[p.name];
-            e.first += ms;
-            e.second += 1;
+            Acc &e = g_acc[p.name];
+            e.ms += ms;
+            e.bytes += p.bytes;
+            e.calls += 1;
         }
         cudaGetLastError();
         cudaEventDestroy(p.a);
@@ -552,7 +558,8 @@ RB3_EXPORT int rb3_profile_reset(void) {
     return RB3_OK;
 }
 
-RB3_EXPORT int rb3_profile_read(const char **names, double *ms, int64_t *calls, int32_t cap, int32_t *n) {
+RB3_EXPORT int rb3_profile_read(const char **names, double *ms, int64_t *calls, double *bytes, int32_t cap,
+                                int32_t *n) {
     profile_drain();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     int32_t i = 0;
@@ -562,8 +569,9 @@ RB3_EXPORT int rb3_profile_read(const char **names, double *ms, int64_t *calls, 
     for (auto &kv : g_acc) {
         if (i < cap) {
             if (names) names[i] = g_names[i].c_str();
-            if (ms) ms[i] = kv.second.first;
-            if (calls) calls[i] = kv.second.second;
+            if (ms) ms[i] = kv.second.ms;
+            if (calls) calls[i] = kv.second.calls;
+            if (bytes) bytes[i] = kv.second.bytes;
         }
         ++i;
     }

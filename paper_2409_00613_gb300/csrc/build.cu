@@ -450,7 +450,10 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(k1.alloc(sizeof(uint64_t) * n, st));
             RB3_TRY(v1.alloc(sizeof(uint32_t) * n, st));
             uint32_t *v0 = reinterpret_cast<uint32_t *>(SA);
-            RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, k0.as<uint64_t>(), v0);
+            {
+                Phase pk("k.init_keys", st, 13.0 * n);  // 1 text byte in, 8-byte key + 4-byte value out
+                RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, k0.as<uint64_t>(), v0);
+            }
             bool alt = false;
             RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0, k1.as<uint64_t>(), v1.as<uint32_t>(), n, 0, 3 * H0, st,
                                      &alt));
@@ -525,10 +528,13 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
                 return RB3_E_CUDA;
             }
             int64_t ntiles = (NS + RT_TILE - 1) / RT_TILE;
-            if (NS > 0)
+            if (NS > 0) {
+                // per entry: 8 B list in, 4 B rank gather, 4 B SA out, 8 B (p, rank) out
+                Phase pr("k.round_small", st, 24.0 * NS);
                 RB3_LAUNCH(k_round_small, (unsigned)ntiles, RT_THREADS, 0, st, sp.as<uint32_t>(), sg.as<uint32_t>(), NS,
                            rank, h, n, d_err, SA, tp.as<uint32_t>(), tg.as<uint32_t>(), tsurv.as<uint32_t>(),
                            tbeg.as<uint32_t>());
+            }
             if (NL > 0) {
                 RB3_LAUNCH(k_large_keys, nb_for(NL, 256), 256, 0, st, lp.as<uint32_t>(), lg.as<uint32_t>(), NL, rank, h, n,
                            d_err, lck0.as<uint64_t>(), lcv0.as<uint32_t>());
@@ -544,6 +550,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             if (NS > 0) {
                 RB3_TRY(scan_u32(tsurv.as<uint32_t>(), toff.as<uint32_t>(), ntiles, false, 0, st));
                 RB3_LAUNCH(k_tally, 1, 1, 0, st, toff.as<uint32_t>(), tsurv.as<uint32_t>(), ntiles, d_cnt, 0);
+                Phase pc("k.compact_small", st, 12.0 * NS);  // 8 B in, 4 B rank out (survivor writes not counted)
                 RB3_LAUNCH(k_compact_small, (unsigned)ntiles, RT_THREADS, 0, st, tp.as<uint32_t>(), tg.as<uint32_t>(),
                            tbeg.as<uint32_t>(), toff.as<uint32_t>(), ntiles, NS, rank, sp2.as<uint32_t>(),
                            sg2.as<uint32_t>());
@@ -588,8 +595,12 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             DevBuf cnt;
             RB3_TRY(cnt.alloc(sizeof(uint32_t) * SIGMA * nb, st));
             int64_t threads = nb << (out->log2D - 3);
-            RB3_LAUNCH(k_pack, nb_for(threads, 256), 256, 0, st, T, SA, n, out->log2D, out->block_bytes, nb,
-                       blocks_buf.as<uint8_t>(), cnt.as<uint32_t>());
+            {
+                // per symbol: 4 B SA in, 1 B text gather, payload out; per block 24 B of counts
+                Phase pp("k.pack", st, n * (5.0 + 0.5) + 24.0 * nb);
+                RB3_LAUNCH(k_pack, nb_for(threads, 256), 256, 0, st, T, SA, n, out->log2D, out->block_bytes, nb,
+                           blocks_buf.as<uint8_t>(), cnt.as<uint32_t>());
+            }
             RB3_TRY(scan_u32(cnt.as<uint32_t>(), cnt.as<uint32_t>(), SIGMA * nb, false, 0, st));
             RB3_LAUNCH(k_headers, nb_for(nb, 256), 256, 0, st, cnt.as<uint32_t>(), nb, out->block_bytes,
                        blocks_buf.as<uint8_t>());

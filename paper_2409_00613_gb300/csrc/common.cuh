@@ -76,14 +76,16 @@ extern std::atomic<int64_t> g_launches;
     } while (0)
 
 // ---- profiling: per-phase CUDA events on the caller's stream ---------------
+// A phase may carry the algorithmic bytes its kernel moves (for the roofline).
 bool profile_on();
-void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b);
+void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b, double bytes);
 
 struct Phase {
     const char *name;
     cudaStream_t st;
+    double bytes;
     cudaEvent_t a = nullptr, b = nullptr;
-    Phase(const char *nm, cudaStream_t s) : name(nm), st(s) {
+    Phase(const char *nm, cudaStream_t s, double algo_bytes = 0.0) : name(nm), st(s), bytes(algo_bytes) {
         if (profile_on() && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, st);
         else
@@ -92,7 +94,7 @@ struct Phase {
     ~Phase() {
         if (a) {
             cudaEventRecord(b, st);
-            profile_push(name, a, b);
+            profile_push(name, a, b, bytes);
         }
     }
 };

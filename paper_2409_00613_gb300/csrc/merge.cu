@@ -302,7 +302,11 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             DevBuf err;
             RB3_TRY(err.alloc(sizeof(unsigned int), st));
             RB3_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(unsigned int), st));
-            RB3_LAUNCH(k_walk_plain, nb_for(m2, 32), 32, 0, st, V1, V2, m1, m2, pos, err.as<unsigned int>());
+            {
+                // per new symbol: two ranks (B2 row, B1 l) of 5 + D/4 B each and an 8 B pos
+                Phase pk("k.walk_plain", st, (double)n2 * (2.0 * (5.0 + dst->D / 4.0) + 8.0));
+                RB3_LAUNCH(k_walk_plain, nb_for(m2, 32), 32, 0, st, V1, V2, m1, m2, pos, err.as<unsigned int>());
+            }
             unsigned int herr = 0;
             RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
@@ -377,6 +381,8 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                 Phase pw("merge.lfwalk", st);
                 int64_t resident = (int64_t)num_sms() * 2048;
                 int64_t threads = nw < resident ? nw : resident;
+                // per new symbol: 1 B text, 4 B ISA, 4+1 B Occ count, D/4 B payload on average, 8 B pos
+                Phase pk("k.walk_seg", st, (double)n2 * (18.0 + dst->D / 4.0));
                 RB3_LAUNCH(k_walk_seg, nb_for(threads, 256), 256, 0, st, V1, m1, src->text, src->isa, d_hi, d_lo,
                            d_send, d_seed, d_order, nw, d_next, pos);
             }
@@ -385,8 +391,14 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
     {
         Phase ph("merge.scatter", st);
         RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst.as<int64_t>());
-        RB3_LAUNCH(k_scatter, (unsigned)ntiles, MT_THREADS, 0, st, V1, V2, pos, kst.as<int64_t>(), nM, nbM, log2D, bb,
-                   Mb.as<uint8_t>());
+        {
+            // every input block read once, every output block written once, 8 B pos per new symbol
+            double bytes = (double)dst->nblocks * dst->block_bytes + (double)src->nblocks * src->block_bytes +
+                           (double)nbM * bb + 8.0 * n2;
+            Phase pk("k.scatter", st, bytes);
+            RB3_LAUNCH(k_scatter, (unsigned)ntiles, MT_THREADS, 0, st, V1, V2, pos, kst.as<int64_t>(), nM, nbM, log2D,
+                       bb, Mb.as<uint8_t>());
+        }
     }
     // install
     if (dst->blocks) dev_free(dst->blocks, st);
@@ -399,11 +411,20 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
     dst->n = nM;
     dst->m = m1 + m2;
     for (int a = 0; a <= SIGMA; ++a) dst->C[a] = dst->C[a] + src->C[a];
+    // the merged blocks must hold exactly the symbols of both inputs (read back from the device)
+    int64_t Cw[SIGMA + 1];
+    for (int a = 0; a <= SIGMA; ++a) Cw[a] = dst->C[a];
     dst->D = D;
     dst->log2D = log2D;
     dst->block_bytes = bb;
     dst->nblocks = nbM;
     dst->single_strand = src->single_strand;
+    RB3_TRY(finalize_counts(dst, st));
+    for (int a = 0; a <= SIGMA; ++a)
+        if (dst->C[a] != Cw[a]) {
+            set_error("merge: merged counts differ from the inputs' (symbol %d)", a);
+            return RB3_E_CUDA;
+        }
     return RB3_OK;
 }
 

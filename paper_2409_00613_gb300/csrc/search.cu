@@ -237,7 +237,7 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
         RB3_CUDA_TRY(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), st));
         unsigned long long *d_next = ctr.as<unsigned long long>(), *d_count = d_next + 1;
         {
-            Phase ph(plain ? "search.smem_plain" : "search.smem", st);
+            Phase ph(plain ? "k.smem_plain" : "k.smem_chunked", st, (double)total_q);  // bytes = query bases
             if (plain) {
                 RB3_LAUNCH(k_smem_plain, nb_for(nq, 128), 128, 0, st, V, q, qoff, nq, (int)min_len, min_occ,
                            raw.as<rb3_smem>(), scap, d_count);

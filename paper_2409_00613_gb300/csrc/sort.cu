@@ -225,10 +225,17 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         int nb = end_bit - shift < 8 ? end_bit - shift : 8;
         uint32_t mask = (1u << nb) - 1u;
-        RB3_LAUNCH(k_rs_hist, (unsigned)ntiles, RS_THREADS, 0, st, ka, n, shift, mask, counts.as<uint32_t>(), ntiles);
+        {
+            Phase ph("k.rs_hist", st, 8.0 * n);  // reads the keys
+            RB3_LAUNCH(k_rs_hist, (unsigned)ntiles, RS_THREADS, 0, st, ka, n, shift, mask, counts.as<uint32_t>(),
+                       ntiles);
+        }
         RB3_TRY(scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), RS_BINS * ntiles, false, 0, st));
-        RB3_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem), st, ka, va, kb, vb, n, shift, mask,
-                   counts.as<uint32_t>(), ntiles);
+        {
+            Phase ph("k.rs_scatter", st, 24.0 * n);  // reads and writes (8-byte key, 4-byte value)
+            RB3_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem), st, ka, va, kb, vb, n, shift,
+                       mask, counts.as<uint32_t>(), ntiles);
+        }
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
         alt = !alt;

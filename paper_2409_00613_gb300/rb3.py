@@ -69,7 +69,8 @@ def lib():
             "rb3_profile_enable": (ctypes.c_int, [ctypes.c_int]),
             "rb3_profile_reset": (ctypes.c_int, []),
             "rb3_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
-                                                ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
+                                                ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _i32,
+                                                ctypes.POINTER(_i32)]),
             "rb3_launch_count": (_i64, []),
         }
         for name, (res, args) in sig.items():
@@ -269,13 +270,15 @@ def rb3_profile_reset():
 
 
 def rb3_profile_read() -> dict:
-    cap = 64
+    """{name: (ms, calls, algorithmic bytes)} accumulated since the last reset."""
+    cap = 128
     names = (ctypes.c_char_p * cap)()
     ms = (ctypes.c_double * cap)()
     calls = (_i64 * cap)()
+    byts = (ctypes.c_double * cap)()
     n = _i32()
-    _check(lib().rb3_profile_read(names, ms, calls, cap, ctypes.byref(n)))
-    return {names[i].decode(): (ms[i], calls[i]) for i in range(min(n.value, cap))}
+    _check(lib().rb3_profile_read(names, ms, calls, byts, cap, ctypes.byref(n)))
+    return {names[i].decode(): (ms[i], calls[i], byts[i]) for i in range(min(n.value, cap))}
 
 
 def rb3_launch_count() -> int:
