@@ -121,7 +121,7 @@ static void profile_drain() {
 // ---- index utilities ----------------------------------------------------------
 __global__ void k_counts_at_n(OccView V, int64_t *__restrict__ out) {
     int64_t r[SIGMA];
-    rank_all(V, V.n, r);
+    rank_all_any(V, V.n, r);
     for (int a = 0; a < SIGMA; ++a) out[a] = r[a];
 }
 

@@ -91,22 +91,19 @@ __global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__r
     hv[i] = head ? (uint32_t)i : 0u;
 }
 
-__global__ void k_init_rank(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart, int64_t n,
-                            int32_t *__restrict__ rank, uint32_t *__restrict__ gsize) {
+// rank[SA[i]] = start of i's group; flags route entries of groups of 2..SMALL_MAX
+// (fs) and of larger groups (fl).  A group starting at g has more than SMALL_MAX
+// members iff the entry SMALL_MAX places after g still has group start g.
+__global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart, int64_t n,
+                                  int32_t *__restrict__ rank, uint32_t *__restrict__ fs, uint32_t *__restrict__ fl) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t g = gstart[i];
     rank[SA[i]] = (int32_t)g;
-    atomicAdd(&gsize[g], 1u);
-}
-
-__global__ void k_init_flags(const uint32_t *__restrict__ gstart, const uint32_t *__restrict__ gsize, int64_t n,
-                             uint32_t *__restrict__ fs, uint32_t *__restrict__ fl) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t sz = gsize[gstart[i]];
-    fs[i] = (sz >= 2 && sz <= (uint32_t)SMALL_MAX) ? 1u : 0u;
-    fl[i] = sz > (uint32_t)SMALL_MAX ? 1u : 0u;
+    bool single = g == (uint32_t)i && (i + 1 == n || gstart[i + 1] == (uint32_t)(i + 1));
+    bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
+    fs[i] = (!single && !large) ? 1u : 0u;
+    fl[i] = large ? 1u : 0u;
 }
 
 __global__ void k_init_lists(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart,
@@ -192,7 +189,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_round_small(const uint32_t *__re
             eqb += e & (j < i);
         }
         int off = less + eqb;
-        SA[g + off] = (int32_t)sp[i];
+        if (off != i - rs) SA[g + off] = (int32_t)sp[i];  // unchanged places are not rewritten
         uint32_t gn = g + (uint32_t)less;
         bool sv = eqt >= 2;
         tp[b + rs + off] = sp[i];
@@ -208,6 +205,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_round_small(const uint32_t *__re
 // every group stays contiguous).
 __global__ void __launch_bounds__(RT_THREADS) k_compact_small(const uint32_t *__restrict__ tp,
                                                               const uint32_t *__restrict__ tg,
+                                                              const uint32_t *__restrict__ wg_old,
                                                               const uint32_t *__restrict__ tile_begin,
                                                               const uint32_t *__restrict__ tile_off, int64_t ntiles,
                                                               int64_t N, int32_t *__restrict__ rank,
@@ -225,7 +223,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_compact_small(const uint32_t *__
         if (i < e) {
             p = tp[i];
             g = tg[i];
-            rank[p] = (int32_t)(g & ~SURV);
+            // entry i of the new order lies in the same old group as entry i of the
+            // old list; its rank changes only if its sub-group does not start there
+            if ((g & ~SURV) != wg_old[i]) rank[p] = (int32_t)(g & ~SURV);
             sv = g >> 31;
         }
         uint32_t ex = block_excl<uint32_t>(sv, 0, wtot);
@@ -463,9 +463,6 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(hv.alloc(sizeof(uint32_t) * n, st));
             RB3_LAUNCH(k_heads, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
             RB3_TRY(scan_u32(hv.as<uint32_t>(), hv.as<uint32_t>(), n, true, 1, st));  // gstart
-            RB3_CUDA_TRY(cudaMemsetAsync(gsize, 0, sizeof(uint32_t) * n, st));
-            RB3_LAUNCH(k_init_rank, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
-                       n, rank, gsize);
             k0.release();
             k1.release();
             v1.release();
@@ -473,8 +470,8 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(fl.alloc(sizeof(uint32_t) * n, st));
             RB3_TRY(ps.alloc(sizeof(uint32_t) * n, st));
             RB3_TRY(pl.alloc(sizeof(uint32_t) * n, st));
-            RB3_LAUNCH(k_init_flags, nb_for(n, 256), 256, 0, st, hv.as<uint32_t>(), gsize, n, fs.as<uint32_t>(),
-                       fl.as<uint32_t>());
+            RB3_LAUNCH(k_init_rank_flags, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA),
+                       hv.as<uint32_t>(), n, rank, fs.as<uint32_t>(), fl.as<uint32_t>());
             RB3_TRY(scan_u32(fs.as<uint32_t>(), ps.as<uint32_t>(), n, false, 0, st));
             RB3_TRY(scan_u32(fl.as<uint32_t>(), pl.as<uint32_t>(), n, false, 0, st));
             RB3_LAUNCH(k_tally, 1, 1, 0, st, ps.as<uint32_t>(), fs.as<uint32_t>(), n, d_cnt, 0);
@@ -521,8 +518,17 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
         int gbits = ilog2(n) + 1;
         uint32_t h = H0;
         int round = 0;
+        static const char *kRoundNames[] = {
+            "round.00", "round.01", "round.02", "round.03", "round.04", "round.05", "round.06", "round.07",
+            "round.08", "round.09", "round.10", "round.11", "round.12", "round.13", "round.14", "round.15",
+            "round.16", "round.17", "round.18", "round.19", "round.20", "round.21", "round.22", "round.23",
+            "round.24", "round.25", "round.26", "round.27", "round.28", "round.29", "round.30", "round.31",
+            "round.32", "round.33", "round.34", "round.35", "round.36", "round.37", "round.38", "round.39",
+            "round.40"};
         while (NS + NL > 0) {
             Phase ph("build.round", st);
+            // "bytes" of a per-round record = entries still unresolved at its start
+            Phase pr_(kRoundNames[round < 40 ? round : 40], st, (double)(NS + NL));
             if (++round > 40 || h >= (uint32_t)n) {
                 set_error("prefix doubling did not converge (round %d, h=%u)", round, h);
                 return RB3_E_CUDA;
@@ -552,7 +558,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
                 RB3_LAUNCH(k_tally, 1, 1, 0, st, toff.as<uint32_t>(), tsurv.as<uint32_t>(), ntiles, d_cnt, 0);
                 Phase pc("k.compact_small", st, 12.0 * NS);  // 8 B in, 4 B rank out (survivor writes not counted)
                 RB3_LAUNCH(k_compact_small, (unsigned)ntiles, RT_THREADS, 0, st, tp.as<uint32_t>(), tg.as<uint32_t>(),
-                           tbeg.as<uint32_t>(), toff.as<uint32_t>(), ntiles, NS, rank, sp2.as<uint32_t>(),
+                           sg.as<uint32_t>(), tbeg.as<uint32_t>(), toff.as<uint32_t>(), ntiles, NS, rank, sp2.as<uint32_t>(),
                            sg2.as<uint32_t>());
             } else {
                 RB3_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t), st));

@@ -158,50 +158,131 @@ __device__ __forceinline__ uint64_t ldg_u64(const uint8_t *p) {
     return __ldg(reinterpret_cast<const unsigned long long *>(p));
 }
 
-// Number of nibbles equal to c among the nibbles selected by mask (one bit 0
-// of each selected nibble set, i.e. a sub-mask of 0x1111...).  Codes are 3-bit,
-// so a nibble equals c iff its xor with c has bits 0..2 clear.
-__device__ __forceinline__ int nib_eq(uint64_t w, int c, uint64_t mask) {
-    uint64_t x = w ^ (0x1111111111111111ull * (uint64_t)c);
-    uint64_t nz = (x | (x >> 1) | (x >> 2)) & 0x1111111111111111ull;
-    return __popcll(~nz & mask);
+// One 32-byte sector in a single 256-bit load (read-only path).  Occ blocks are
+// 32-byte aligned: block sizes are 64, 96 or 160 bytes from a 256-aligned base.
+struct Sec {
+    uint32_t w[8];
+};
+__device__ __forceinline__ Sec ld_sec(const uint8_t *p) {
+    Sec s;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(s.w[0]), "=r"(s.w[1]), "=r"(s.w[2]), "=r"(s.w[3]), "=r"(s.w[4]), "=r"(s.w[5]), "=r"(s.w[6]),
+          "=r"(s.w[7])
+        : "l"(p));
+    return s;
 }
 
-__device__ __forceinline__ uint64_t nib_mask(int k) {  // first k nibbles of a word, k in 0..16
-    return k >= 16 ? 0x1111111111111111ull : (((1ull << (4 * k)) - 1) & 0x1111111111111111ull);
+// Mask of bit 0 of the first k nibbles of a 32-bit word (k may be <= 0 or >= 8).
+__device__ __forceinline__ uint32_t nmask32(int k) {
+    return k >= 8 ? 0x11111111u : (k <= 0 ? 0u : (((1u << (4 * k)) - 1u) & 0x11111111u));
 }
 
-// rank_B(c, l) = |{i < l : B[i] = c}|  (Table 1), from the Occ header of
-// l's block plus the nibbles before l inside the block.
-__device__ __forceinline__ int64_t rank1(const OccView &v, int c, int64_t l) {
-    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
-    int o = (int)(l & ((1 << v.log2D) - 1));
-    uint32_t lo = __ldg(reinterpret_cast<const unsigned int *>(blk) + c);
-    uint32_t hi = __ldg(blk + 24 + c);
-    int64_t r = (int64_t)lo | ((int64_t)hi << 32);
-    const uint8_t *pay = blk + HEADER_BYTES;
-    int w = 0;
-    for (; (w + 1) * 16 <= o; ++w) r += nib_eq(ldg_u64(pay + 8 * w), c, 0x1111111111111111ull);
-    int rem = o - w * 16;
-    if (rem) r += nib_eq(ldg_u64(pay + 8 * w), c, nib_mask(rem));
+// Number of nibbles equal to c among the first k nibbles (0..64) of a sector.
+// Codes are 3-bit, so a nibble equals c iff its xor with c has bits 0..2 clear.
+__device__ __forceinline__ int sec_count(const Sec &s, int c, int k) {
+    int r = 0;
+    const uint32_t cc = 0x11111111u * (uint32_t)c;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t x = s.w[i] ^ cc;
+        uint32_t nz = (x | (x >> 1) | (x >> 2)) & 0x11111111u;
+        r += __popc(~nz & nmask32(k - 8 * i));
+    }
     return r;
 }
 
-// rank_B(a, l) for every symbol a.
-__device__ __forceinline__ void rank_all(const OccView &v, int64_t l, int64_t r[SIGMA]) {
-    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
-    int o = (int)(l & ((1 << v.log2D) - 1));
-    const unsigned int *h32 = reinterpret_cast<const unsigned int *>(blk);
+// Counts of every symbol among the first k nibbles of a sector, added to r[].
+// Bit planes: b0, b1, b2 of each nibble; symbol codes 0..5 = 000 .. 101.
+__device__ __forceinline__ void sec_count_all(const Sec &s, int k, int64_t r[6]) {
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
 #pragma unroll
-    for (int a = 0; a < SIGMA; ++a) r[a] = (int64_t)__ldg(h32 + a) | ((int64_t)__ldg(blk + 24 + a) << 32);
-    const uint8_t *pay = blk + HEADER_BYTES;
-    int nw = (o + 15) >> 4;
-    for (int w = 0; w < nw; ++w) {
-        uint64_t word = ldg_u64(pay + 8 * w);
-        uint64_t mask = nib_mask(o - w * 16);
-#pragma unroll
-        for (int a = 0; a < SIGMA; ++a) r[a] += nib_eq(word, a, mask);
+    for (int i = 0; i < 8; ++i) {
+        uint32_t m = nmask32(k - 8 * i);
+        uint32_t w = s.w[i];
+        uint32_t b0 = w & m, b1 = (w >> 1) & m, b2 = (w >> 2) & m;
+        uint32_t n0 = ~w & m, n1 = ~(w >> 1) & m, n2 = ~(w >> 2) & m;
+        uint32_t t00 = n1 & n2, t10 = b1 & n2, t01 = n1 & b2;
+        c0 += __popc(n0 & t00);
+        c1 += __popc(b0 & t00);
+        c2 += __popc(n0 & t10);
+        c3 += __popc(b0 & t10);
+        c4 += __popc(n0 & t01);
+        c5 += __popc(b0 & t01);
     }
+    r[0] += c0; r[1] += c1; r[2] += c2; r[3] += c3; r[4] += c4; r[5] += c5;
+}
+
+// Header value of symbol c (registers only: the select is unrolled).
+__device__ __forceinline__ int64_t hdr_get(const Sec &h, int c) {
+    uint32_t lo = h.w[0], hib = h.w[6] & 0xFFu;
+#pragma unroll
+    for (int a = 1; a < 6; ++a)
+        if (c == a) {
+            lo = h.w[a];
+            hib = (a < 4 ? (h.w[6] >> (8 * a)) : (h.w[7] >> (8 * (a - 4)))) & 0xFFu;
+        }
+    return (int64_t)lo | ((int64_t)hib << 32);
+}
+
+__device__ __forceinline__ void hdr_all(const Sec &h, int64_t r[6]) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        uint32_t hib = (a < 4 ? (h.w[6] >> (8 * a)) : (h.w[7] >> (8 * (a - 4)))) & 0xFFu;
+        r[a] = (int64_t)h.w[a] | ((int64_t)hib << 32);
+    }
+}
+
+// Loads of one rank: the header sector and the payload sectors that hold the
+// nibbles before offset o, all issued before any is used.  NS = D/64 payload
+// sectors per block (1, 2 or 4); sectors past o are not loaded.
+template <int NS> struct BlockLd {
+    Sec h, p[NS];
+    int o;
+};
+template <int NS> __device__ __forceinline__ BlockLd<NS> block_load(const OccView &v, int64_t l) {
+    BlockLd<NS> b;
+    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
+    b.o = (int)(l & (64 * NS - 1));
+    b.h = ld_sec(blk);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        if (NS == 1 || b.o > 64 * j) b.p[j] = ld_sec(blk + HEADER_BYTES + 32 * j);
+    return b;
+}
+
+template <int NS> __device__ __forceinline__ int64_t block_rank(const BlockLd<NS> &b, int c) {
+    int64_t r = hdr_get(b.h, c);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        if (NS == 1 || b.o > 64 * j) r += sec_count(b.p[j], c, b.o - 64 * j);
+    return r;
+}
+
+template <int NS> __device__ __forceinline__ void block_rank_all(const BlockLd<NS> &b, int64_t r[6]) {
+    hdr_all(b.h, r);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        if (NS == 1 || b.o > 64 * j) sec_count_all(b.p[j], b.o - 64 * j, r);
+}
+
+// rank_B(c, l) = |{i < l : B[i] = c}|  (Table 1).
+template <int NS> __device__ __forceinline__ int64_t rank1(const OccView &v, int c, int64_t l) {
+    BlockLd<NS> b = block_load<NS>(v, l);
+    return block_rank<NS>(b, c);
+}
+
+// rank_B(a, l) for every symbol a.
+template <int NS> __device__ __forceinline__ void rank_all(const OccView &v, int64_t l, int64_t r[SIGMA]) {
+    BlockLd<NS> b = block_load<NS>(v, l);
+    block_rank_all<NS>(b, r);
+}
+
+// Any D (tile-level lookups outside the hot loops).
+__device__ __forceinline__ void rank_all_any(const OccView &v, int64_t l, int64_t r[SIGMA]) {
+    const int ns = (1 << v.log2D) >> 6;
+    if (ns == 1) rank_all<1>(v, l, r);
+    else if (ns == 2) rank_all<2>(v, l, r);
+    else rank_all<4>(v, l, r);
 }
 
 // Symbol B[i].
@@ -219,31 +300,52 @@ struct BiInt {
 
 // Algorithm 3, BackwardExt: for b < comp(a): k' += pi(comp b, k+s) - pi(comp b, k);
 // s <- pi(a,k+s) - pi(a,k); k <- pi(a,k).  (C_B cancels in the differences.)
-__device__ __forceinline__ BiInt backward_ext(const OccView &v, BiInt x, int a) {
+// Both blocks are loaded before either is counted.
+template <int NS> __device__ __forceinline__ BiInt backward_ext(const OccView &v, BiInt x, int a) {
     int64_t r0[SIGMA], r1[SIGMA];
-    rank_all(v, x.k, r0);
-    rank_all(v, x.k + x.s, r1);
-    int ac = comp_sym(a);
+    {
+        BlockLd<NS> b0 = block_load<NS>(v, x.k);
+        BlockLd<NS> b1 = block_load<NS>(v, x.k + x.s);
+        block_rank_all<NS>(b0, r0);
+        block_rank_all<NS>(b1, r1);
+    }
+    int64_t d[SIGMA];
+#pragma unroll
+    for (int i = 0; i < SIGMA; ++i) d[i] = r1[i] - r0[i];
+    const int ac = comp_sym(a);
     int64_t add = 0;
 #pragma unroll
     for (int b = 0; b < SIGMA; ++b)
-        if (b < ac) {
-            int bc = comp_sym(b);
-            add += r1[bc] - r0[bc];
+        if (b < ac) add += d[(b >= 1 && b <= 4) ? 5 - b : b];
+    int64_t s = d[0], k = v.C[0] + r0[0];
+#pragma unroll
+    for (int i = 1; i < SIGMA; ++i)
+        if (a == i) {
+            s = d[i];
+            k = v.C[i] + r0[i];
         }
     BiInt y;
     y.kp = x.kp + add;
-    y.s = r1[a] - r0[a];
-    y.k = v.C[a] + r0[a];
+    y.s = s;
+    y.k = k;
     return y;
 }
 
 // Algorithm 3, ForwardExt = swap(BackwardExt(swap(x), comp(a))).
-__device__ __forceinline__ BiInt forward_ext(const OccView &v, BiInt x, int a) {
+template <int NS> __device__ __forceinline__ BiInt forward_ext(const OccView &v, BiInt x, int a) {
     BiInt y = {x.kp, x.k, x.s};
-    y = backward_ext(v, y, comp_sym(a));
+    y = backward_ext<NS>(v, y, comp_sym(a));
     BiInt z = {y.kp, y.k, y.s};
     return z;
+}
+
+// C_B(a) by register select.
+__device__ __forceinline__ int64_t C_of(const OccView &v, int a) {
+    int64_t c = v.C[0];
+#pragma unroll
+    for (int i = 1; i < SIGMA; ++i)
+        if (a == i) c = v.C[i];
+    return c;
 }
 
 // ---- block-level scans (256-thread blocks) -------------------------------
@@ -302,6 +404,21 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
 // Fills idx->C from its blocks (rank of every symbol at n).
 int finalize_counts(rb3_index *idx, cudaStream_t st);
+
+// Calls body with a compile-time NS = D/64 for D in {64, 128, 256}.
+#define RB3_WITH_NS(D, ...)                      \
+    do {                                         \
+        if ((D) == 64) {                         \
+            constexpr int NS = 1;                \
+            __VA_ARGS__;                         \
+        } else if ((D) == 128) {                 \
+            constexpr int NS = 2;                \
+            __VA_ARGS__;                         \
+        } else {                                 \
+            constexpr int NS = 4;                \
+            __VA_ARGS__;                         \
+        }                                        \
+    } while (0)
 
 inline int ilog2(int64_t x) {
     int r = 0;

@@ -37,6 +37,7 @@ namespace cg = cooperative_groups;
 namespace rb3 {
 
 // ---- plain Algorithm 1 walk --------------------------------------------------
+template <int NS1, int NS2>
 __global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int64_t *__restrict__ pos,
                              unsigned int *__restrict__ err) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -50,8 +51,10 @@ __global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int
             atomicOr(err, 1u);
             break;
         }
-        int64_t kn = B2.C[a] + rank1(B2, a, k);
-        l = B1.C[a] + rank1(B1, a, l);
+        BlockLd<NS2> b2 = block_load<NS2>(B2, k);  // both blocks issued before use
+        BlockLd<NS1> b1 = block_load<NS1>(B1, l);
+        int64_t kn = C_of(B2, a) + block_rank<NS2>(b2, a);
+        l = C_of(B1, a) + block_rank<NS1>(b1, a);
         k = kn;
     }
 }
@@ -59,6 +62,7 @@ __global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int
 // ---- segment seeds ---------------------------------------------------------------
 // One thread per segment boundary x (a text position inside a string; the
 // string's sentinel is at send).  seed[w] = l(x) or -1 when capped.
+template <int NS>
 __global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
                         const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
     int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -70,16 +74,19 @@ __global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_
     }
     BiInt q = {0, 0, B1.n};
     int64_t res = -1;
+    int a = T2[x];
     for (int64_t t = 0;; ++t) {
         int64_t p = x + t;
         if (p == send) {
             // X = Q$: every B1 suffix equal to Q up to a sentinel is older, hence smaller
-            int64_t occ_end = rank1(B1, 0, q.kp + q.s) - rank1(B1, 0, q.kp);
+            int64_t occ_end = rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp);
             res = q.k + occ_end;
             break;
         }
         if (t >= cap) break;
-        BiInt y = forward_ext(B1, q, T2[p]);
+        int an = T2[p + 1];  // next symbol (the sentinel at most), loaded ahead
+        BiInt y = forward_ext<NS>(B1, q, a);
+        a = an;
         if (y.s == 0) {
             res = y.k;
             break;
@@ -95,6 +102,7 @@ __global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_
 // SA interval [lo, hi) of P[p, y) is kept; once it is empty (P[p, y) does not
 // occur in B1) every B1 suffix compares with P[p..]$ as it does with P[p, y),
 // so l(p) = lo exactly, and the steps continue exactly down to x.
+template <int NS>
 __global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
                             const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
     int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -109,11 +117,13 @@ __global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ 
     int64_t lo = exact ? m1 : 0, hi = exact ? m1 : B1.n;
     for (int64_t p = y - 1; p >= x; --p) {
         int a = T2[p];
-        lo = B1.C[a] + rank1(B1, a, lo);
         if (exact) {
+            lo = C_of(B1, a) + rank1<NS>(B1, a, lo);
             hi = lo;
         } else {
-            hi = B1.C[a] + rank1(B1, a, hi);
+            BlockLd<NS> bl = block_load<NS>(B1, lo), bh = block_load<NS>(B1, hi);
+            lo = C_of(B1, a) + block_rank<NS>(bl, a);
+            hi = C_of(B1, a) + block_rank<NS>(bh, a);
             exact = lo == hi;
         }
     }
@@ -121,22 +131,27 @@ __global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ 
 }
 
 // Walk w covers positions [lo, hi) of its string, right to left; its lower end
-// is the next walk below with a usable seed (or the string start).  One thread
-// per string fixes the lower ends (walks of a string are stored top down).
-__global__ void k_walk_bounds(const int64_t *__restrict__ s_first, const int64_t *__restrict__ s_start, int64_t ns,
-                              const int64_t *__restrict__ w_hi, const int64_t *__restrict__ seed,
+// is the right end of the next walk below with a usable seed, or the string
+// start.  Walks of a string are stored top down and share w_send; one thread
+// per walk looks downward (usually one step).
+__global__ void k_walk_bounds(const int64_t *__restrict__ w_send, const int64_t *__restrict__ w_sstart,
+                              const int64_t *__restrict__ w_hi, const int64_t *__restrict__ seed, int64_t nw,
                               int64_t *__restrict__ w_lo) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= ns) return;
-    int64_t lo = s_start[s];
-    for (int64_t w = s_first[s + 1] - 1; w >= s_first[s]; --w) {
-        w_lo[w] = lo;
-        if (seed[w] != -1) lo = w_hi[w];
-    }
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int64_t send = w_send[w];
+    int64_t lo = w_sstart[w];
+    for (int64_t v = w + 1; v < nw && w_send[v] == send; ++v)
+        if (seed[v] != -1) {
+            lo = w_hi[v];
+            break;
+        }
+    w_lo[w] = lo;
 }
 
 // Segmented walk.  The work list order[] lists walks by (segment rank from the
 // string end, string); threads take walks with a warp-aggregated atomic.
+template <int NS>
 __global__ void __launch_bounds__(256) k_walk_seg(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
                                                   const int32_t *__restrict__ isa2, const int64_t *__restrict__ w_hi,
                                                   const int64_t *__restrict__ w_lo, const int64_t *__restrict__ w_send,
@@ -164,11 +179,24 @@ __global__ void __launch_bounds__(256) k_walk_seg(OccView B1, int64_t m1, const 
         } else {
             l = sd;
         }
-        for (int64_t p = hi - 1; p >= lo; --p) {
+        int64_t p = hi - 1;
+        if (p >= lo) {
             int a = T2[p];
-            l = B1.C[a] + rank1(B1, a, l);
             int64_t k = isa2[p];
-            pos[k] = k + l;
+            for (;;) {
+                // next position's symbol and row, loaded while this step's block is in flight
+                int an = 0;
+                int64_t kn = 0;
+                if (p > lo) {
+                    an = T2[p - 1];
+                    kn = isa2[p - 1];
+                }
+                l = C_of(B1, a) + rank1<NS>(B1, a, l);
+                pos[k] = k + l;
+                if (--p < lo) break;
+                a = an;
+                k = kn;
+            }
         }
     }
 }
@@ -206,8 +234,8 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     __syncthreads();
     if (threadIdx.x == 0) {
         int64_t r1[SIGMA], r2[SIGMA];
-        rank_all(B1, j0, r1);
-        rank_all(B2, k0, r2);
+        rank_all_any(B1, j0, r1);
+        rank_all_any(B2, k0, r2);
         for (int a = 0; a < SIGMA; ++a) base6[a] = r1[a] + r2[a];
     }
     for (int64_t k = k0 + threadIdx.x; k < k1; k += MT_THREADS) {
@@ -265,6 +293,30 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+template <int NS1>
+static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
+                               unsigned int *err, cudaStream_t st) {
+    unsigned grid = nb_for(m2, 32);
+    if (D2 == 64) {
+        auto kern = k_walk_plain<NS1, 1>;
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+    } else if (D2 == 128) {
+        auto kern = k_walk_plain<NS1, 2>;
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+    } else {
+        auto kern = k_walk_plain<NS1, 4>;
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+    }
+    return RB3_OK;
+}
+
+static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
+                             unsigned int *err, cudaStream_t st) {
+    if (D1 == 64) return launch_walk_plain_1<1>(D2, V1, V2, m1, m2, pos, err, st);
+    if (D1 == 128) return launch_walk_plain_1<2>(D2, V1, V2, m1, m2, pos, err, st);
+    return launch_walk_plain_1<4>(D2, V1, V2, m1, m2, pos, err, st);
+}
+
 __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < n) pos[k] = k;
@@ -305,7 +357,7 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             {
                 // per new symbol: two ranks (B2 row, B1 l) of 5 + D/4 B each and an 8 B pos
                 Phase pk("k.walk_plain", st, (double)n2 * (2.0 * (5.0 + dst->D / 4.0) + 8.0));
-                RB3_LAUNCH(k_walk_plain, nb_for(m2, 32), 32, 0, st, V1, V2, m1, m2, pos, err.as<unsigned int>());
+                RB3_TRY(launch_walk_plain(dst->D, src->D, V1, V2, m1, m2, pos, err.as<unsigned int>(), st));
             }
             unsigned int herr = 0;
             RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
@@ -326,7 +378,7 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             }
             int64_t cap = o.seed_cap > 0 ? o.seed_cap : 4 * L;
             const int64_t ns = (int64_t)src->str_end.size();
-            std::vector<int64_t> s_first(ns + 1, 0), s_start(ns), w_hi, w_send;
+            std::vector<int64_t> s_first(ns + 1, 0), s_start(ns), w_hi, w_send, w_sstart;
             std::vector<int32_t> w_rank;  // segment rank from the string end
             int64_t maxr = 0;
             for (int64_t s = 0; s < ns; ++s) {
@@ -339,6 +391,7 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                 for (int64_t x = end;; x -= L, ++r) {
                     w_hi.push_back(x);
                     w_send.push_back(end);
+                    w_sstart.push_back(start);
                     w_rank.push_back((int32_t)r);
                     if (x - L <= start) break;
                 }
@@ -355,27 +408,27 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                 for (int64_t w = 0; w < nw; ++w) order[cnt[w_rank[w]]++] = (int32_t)w;
             }
             DevBuf plan;
-            size_t bytes = sizeof(int64_t) * (4 * nw + 2 * (ns + 1)) + sizeof(unsigned long long) +
-                           sizeof(int32_t) * nw + 64;
+            size_t bytes = sizeof(int64_t) * (5 * nw) + sizeof(unsigned long long) + sizeof(int32_t) * nw + 64;
             RB3_TRY(plan.alloc(bytes, st));
             int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_seed = d_send + nw, *d_lo = d_seed + nw;
-            int64_t *d_sfirst = d_lo + nw, *d_sstart = d_sfirst + (ns + 1);
-            unsigned long long *d_next = reinterpret_cast<unsigned long long *>(d_sstart + (ns + 1));
+            int64_t *d_wss = d_lo + nw;
+            unsigned long long *d_next = reinterpret_cast<unsigned long long *>(d_wss + nw);
             int32_t *d_order = reinterpret_cast<int32_t *>(d_next + 1);
             RB3_CUDA_TRY(cudaMemcpyAsync(d_hi, w_hi.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_send, w_send.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_sfirst, s_first.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_sstart, s_start.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_wss, w_sstart.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
             {
                 Phase ps("merge.seed", st);
+                Phase pk("k.seeds", st);
                 if (dst->single_strand)
-                    RB3_LAUNCH(k_seeds_bwd, nb_for(nw, 128), 128, 0, st, V1, m1, src->text, d_hi, d_send, nw, cap,
-                               d_seed);
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH(k_seeds_bwd<NS>, nb_for(nw, 128), 128, 0, st, V1, m1, src->text,
+                                                   d_hi, d_send, nw, cap, d_seed));
                 else
-                    RB3_LAUNCH(k_seeds, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi, d_send, nw, cap, d_seed);
-                RB3_LAUNCH(k_walk_bounds, nb_for(ns, 128), 128, 0, st, d_sfirst, d_sstart, ns, d_hi, d_seed, d_lo);
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH(k_seeds<NS>, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi,
+                                                   d_send, nw, cap, d_seed));
+                RB3_LAUNCH(k_walk_bounds, nb_for(nw, 256), 256, 0, st, d_send, d_wss, d_hi, d_seed, nw, d_lo);
             }
             {
                 Phase pw("merge.lfwalk", st);
@@ -383,8 +436,8 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                 int64_t threads = nw < resident ? nw : resident;
                 // per new symbol: 1 B text, 4 B ISA, 4+1 B Occ count, D/4 B payload on average, 8 B pos
                 Phase pk("k.walk_seg", st, (double)n2 * (18.0 + dst->D / 4.0));
-                RB3_LAUNCH(k_walk_seg, nb_for(threads, 256), 256, 0, st, V1, m1, src->text, src->isa, d_hi, d_lo,
-                           d_send, d_seed, d_order, nw, d_next, pos);
+                RB3_WITH_NS(dst->D, RB3_LAUNCH(k_walk_seg<NS>, nb_for(threads, 256), 256, 0, st, V1, m1, src->text,
+                                               src->isa, d_hi, d_lo, d_send, d_seed, d_order, nw, d_next, pos));
             }
         }
     }

@@ -32,6 +32,7 @@ __global__ void k_check_codes(const uint8_t *__restrict__ q, int64_t n, int *__r
     }
 }
 
+template <int NS>
 __global__ void k_bsearch(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq,
                           int64_t *__restrict__ lohi) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -40,10 +41,11 @@ __global__ void k_bsearch(OccView V, const uint8_t *__restrict__ q, const int64_
     for (int64_t j = qoff[i + 1] - 1; j >= qoff[i]; --j) {
         int a = q[j];
         if (lo == hi) {  // empty interval: lo and hi move together
-            lo = hi = V.C[a] + rank1(V, a, lo);
+            lo = hi = C_of(V, a) + rank1<NS>(V, a, lo);
         } else {
-            lo = V.C[a] + rank1(V, a, lo);
-            hi = V.C[a] + rank1(V, a, hi);
+            BlockLd<NS> bl = block_load<NS>(V, lo), bh = block_load<NS>(V, hi);
+            lo = C_of(V, a) + block_rank<NS>(bl, a);
+            hi = C_of(V, a) + block_rank<NS>(bh, a);
         }
     }
     lohi[2 * i] = lo;
@@ -66,6 +68,7 @@ __device__ __forceinline__ void emit(rb3_smem *__restrict__ out, int64_t cap, un
 }
 
 // FindSMEM loop over starts in [x0, x1) of one query.
+template <int NS>
 __device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int64_t len, int64_t qid, int64_t x0,
                            int64_t x1, int ell, int64_t smin, rb3_smem *__restrict__ out, int64_t cap,
                            unsigned long long *__restrict__ count) {
@@ -77,7 +80,7 @@ __device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int6
         int64_t j;
         bool fail = false;
         for (j = i + ell - 1; j >= i; --j) {
-            x = backward_ext(V, x, P[j]);
+            x = backward_ext<NS>(V, x, P[j]);
             if (x.s < smin) {
                 fail = true;
                 break;
@@ -89,14 +92,14 @@ __device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int6
             continue;
         }
         for (j = i + ell; j < len; ++j) {
-            BiInt y = forward_ext(V, x, P[j]);
+            BiInt y = forward_ext<NS>(V, x, P[j]);
             if (y.s < smin) break;
             x = y;
         }
         const int64_t e = j;
         bool keep = true;
         if (first) {  // i == x0 > 0: spurious if P[x0-1, e) still occurs >= smin times
-            BiInt y = backward_ext(V, x, P[x0 - 1]);
+            BiInt y = backward_ext<NS>(V, x, P[x0 - 1]);
             if (y.s >= smin) keep = false;
         }
         first = false;
@@ -105,7 +108,7 @@ __device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int6
         BiInt z = {0, 0, V.n};
         int64_t nxt = i + 1;
         for (j = e; j >= i + 1; --j) {
-            z = backward_ext(V, z, P[j]);
+            z = backward_ext<NS>(V, z, P[j]);
             if (z.s < smin) {
                 nxt = j + 1;
                 break;
@@ -116,17 +119,19 @@ __device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int6
 }
 
 // Plain form: one thread per query, the whole query.
+template <int NS>
 __global__ void k_smem_plain(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq,
                              int ell, int64_t smin, rb3_smem *__restrict__ out, int64_t cap,
                              unsigned long long *__restrict__ count) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq) return;
     int64_t len = qoff[i + 1] - qoff[i];
-    smem_range(V, q + qoff[i], len, i, 0, len, ell, smin, out, cap, count);
+    smem_range<NS>(V, q + qoff[i], len, i, 0, len, ell, smin, out, cap, count);
 }
 
 // Chunked form: items are (query, chunk); item_off[i] = first item of query i.
 // Persistent threads take items with a warp-aggregated atomic counter.
+template <int NS>
 __global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *__restrict__ q,
                                                       const int64_t *__restrict__ qoff, int64_t nq,
                                                       const int64_t *__restrict__ item_off, int64_t nitems,
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *
         int64_t len = qoff[qi + 1] - qoff[qi];
         int64_t x0 = (it - item_off[qi]) * chunk;
         int64_t x1 = x0 + chunk < len ? x0 + chunk : len;
-        smem_range(V, q + qoff[qi], len, qi, x0, x1, ell, smin, out, cap, count);
+        smem_range<NS>(V, q + qoff[qi], len, qi, x0, x1, ell, smin, out, cap, count);
     }
 }
 
@@ -194,7 +199,8 @@ int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *
                          int64_t *lohi, cudaStream_t st) {
     RB3_TRY(check_codes(q, total_q, st));
     Phase ph("search.backward", st);
-    if (nq > 0) RB3_LAUNCH(k_bsearch, nb_for(nq, 128), 128, 0, st, occ_view(idx), q, qoff, nq, lohi);
+    if (nq > 0)
+        RB3_WITH_NS(idx->D, RB3_LAUNCH(k_bsearch<NS>, nb_for(nq, 128), 128, 0, st, occ_view(idx), q, qoff, nq, lohi));
     return RB3_OK;
 }
 
@@ -239,13 +245,14 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
         {
             Phase ph(plain ? "k.smem_plain" : "k.smem_chunked", st, (double)total_q);  // bytes = query bases
             if (plain) {
-                RB3_LAUNCH(k_smem_plain, nb_for(nq, 128), 128, 0, st, V, q, qoff, nq, (int)min_len, min_occ,
-                           raw.as<rb3_smem>(), scap, d_count);
+                RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_plain<NS>, nb_for(nq, 128), 128, 0, st, V, q, qoff, nq,
+                                               (int)min_len, min_occ, raw.as<rb3_smem>(), scap, d_count));
             } else {
                 int64_t resident = (int64_t)num_sms() * 2048;
                 int64_t threads = nitems < resident ? nitems : resident;
-                RB3_LAUNCH(k_smem_chunked, nb_for(threads, 256), 256, 0, st, V, q, qoff, nq, items.as<int64_t>(),
-                           nitems, chunk, (int)min_len, min_occ, d_next, raw.as<rb3_smem>(), scap, d_count);
+                RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_chunked<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff, nq,
+                                               items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ, d_next,
+                                               raw.as<rb3_smem>(), scap, d_count));
             }
         }
         RB3_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));
