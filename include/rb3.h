@@ -168,6 +168,16 @@ int rb3_profile_reset(void);
 int rb3_profile_read(const char **names, double *ms, int64_t *calls, double *bytes, int32_t cap, int32_t *n);
 int64_t rb3_launch_count(void);
 
+/* Random-access roofline probe (measurement only; touches no index).  Times
+ * random reads of bytes_per_access (32, 64 or 128) bytes at 32-byte-aligned
+ * random addresses of a device buffer of buffer_bytes (>= 64 MiB; use one much
+ * larger than L2), with threads_per_sm threads on every SM.  dependent = 0:
+ * each thread keeps 4 independent reads in flight; dependent = 1: each thread
+ * follows a chain whose next address depends on the data read (the pattern of
+ * an LF walk).  Writes the delivered GB/s and millions of reads per second. */
+int rb3_probe_random_gather(int32_t bytes_per_access, int32_t dependent, int32_t threads_per_sm, int64_t buffer_bytes,
+                            double *gbs, double *maccess_per_s, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,8 @@ def lib():
                                                 ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _i32,
                                                 ctypes.POINTER(_i32)]),
             "rb3_launch_count": (_i64, []),
+            "rb3_probe_random_gather": (ctypes.c_int, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double),
+                                                       ctypes.POINTER(ctypes.c_double), _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -283,3 +285,12 @@ def rb3_profile_read() -> dict:
 
 def rb3_launch_count() -> int:
     return int(lib().rb3_launch_count())
+
+
+def rb3_probe_random_gather(bytes_per_access: int, dependent: bool, threads_per_sm: int,
+                            buffer_bytes: int = 8 << 30, stream=None):
+    """(GB/s, M reads/s) of random reads; see include/rb3.h."""
+    g, m = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rb3_probe_random_gather(int(bytes_per_access), int(dependent), int(threads_per_sm),
+                                         int(buffer_bytes), ctypes.byref(g), ctypes.byref(m), _stream(stream)))
+    return g.value, m.value
