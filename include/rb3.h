@@ -131,6 +131,25 @@ int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *q
                         int32_t min_len, int64_t min_occ, const rb3_opts *o, rb3_smem *out, int64_t cap,
                         int64_t *n_out, void *stream);
 
+/* No counterpart in the paper: an allocation-free form of rb3_mem_search for
+ * callers that cannot allocate device memory while they search -- their device
+ * memory belongs to their own allocator or a fixed memory plan, or their
+ * request loop must not call cudaMalloc / cudaFree, which can block and
+ * synchronize the device.  Same records in the same order as rb3_mem_search.
+ * q, qoff and out must be device pointers (out may be NULL when cap = 0).
+ * Limits: at most 131,072 queries per call, and at most 524,288 query chunks
+ * (a query of L bases counts max(1, ceil(L/256)) chunks); larger calls return
+ * RB3_E_INVAL without doing any work.  The scratch is a file-scope device
+ * array of 4,726,868 bytes that every GPU which loads the library holds until
+ * the process exits; the library allocates nothing else for this call.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array, and it keeps the last call's contents (the call clears what
+ * must start at zero): calls that overlap on the GPU race, so do not run two
+ * at once.  Synchronizes the stream; RB3_E_CAPACITY as for rb3_mem_search. */
+int rb3_mem_search_noalloc(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
+                           int64_t min_occ, rb3_smem *out, int64_t cap, int64_t *n_out, void *stream);
+
 /* Unpacks B into codes (n bytes, one symbol per byte) and, when occ != NULL,
  * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */
 int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);

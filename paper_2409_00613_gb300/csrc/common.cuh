@@ -387,6 +387,8 @@ template <class T> __device__ __forceinline__ T block_excl(T v, int op, T *wtot)
 // Device-wide scans.  op: 0 = sum, 1 = max.
 int scan_u32(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, int op, cudaStream_t st);
 int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, bool inclusive, cudaStream_t st);
+int scan_u32_ws(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, uint32_t *part_ws, int64_t part_cap,
+                cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit).
 // The result ends in (k0, v0) if *in_alt comes back false, else in (k1, v1).
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, int begin_bit,

@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "smem.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -52,72 +53,6 @@ __global__ void k_bsearch(OccView V, const uint8_t *__restrict__ q, const int64_
     lohi[2 * i + 1] = hi;
 }
 
-__device__ __forceinline__ void emit(rb3_smem *__restrict__ out, int64_t cap, unsigned long long *__restrict__ count,
-                                     int64_t qid, int64_t st, int64_t en, const BiInt &x) {
-    unsigned long long at = atomicAdd(count, 1ull);
-    if ((int64_t)at < cap) {
-        rb3_smem r;
-        r.qid = qid;
-        r.start = (int32_t)st;
-        r.end = (int32_t)en;
-        r.k = x.k;
-        r.kp = x.kp;
-        r.s = x.s;
-        out[at] = r;
-    }
-}
-
-// FindSMEM loop over starts in [x0, x1) of one query.
-template <int NS>
-__device__ void smem_range(const OccView &V, const uint8_t *__restrict__ P, int64_t len, int64_t qid, int64_t x0,
-                           int64_t x1, int ell, int64_t smin, rb3_smem *__restrict__ out, int64_t cap,
-                           unsigned long long *__restrict__ count) {
-    int64_t i = x0;
-    bool first = x0 > 0;
-    while (i < x1) {
-        if (i + ell > len) break;
-        BiInt x = {0, 0, V.n};
-        int64_t j;
-        bool fail = false;
-        for (j = i + ell - 1; j >= i; --j) {
-            x = backward_ext<NS>(V, x, P[j]);
-            if (x.s < smin) {
-                fail = true;
-                break;
-            }
-        }
-        if (fail) {
-            i = j + 1;
-            first = false;
-            continue;
-        }
-        for (j = i + ell; j < len; ++j) {
-            BiInt y = forward_ext<NS>(V, x, P[j]);
-            if (y.s < smin) break;
-            x = y;
-        }
-        const int64_t e = j;
-        bool keep = true;
-        if (first) {  // i == x0 > 0: spurious if P[x0-1, e) still occurs >= smin times
-            BiInt y = backward_ext<NS>(V, x, P[x0 - 1]);
-            if (y.s >= smin) keep = false;
-        }
-        first = false;
-        if (keep) emit(out, cap, count, qid, i, e, x);
-        if (e == len) break;
-        BiInt z = {0, 0, V.n};
-        int64_t nxt = i + 1;
-        for (j = e; j >= i + 1; --j) {
-            z = backward_ext<NS>(V, z, P[j]);
-            if (z.s < smin) {
-                nxt = j + 1;
-                break;
-            }
-        }
-        i = nxt;
-    }
-}
-
 // Plain form: one thread per query, the whole query.
 template <int NS>
 __global__ void k_smem_plain(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq,
@@ -126,7 +61,8 @@ __global__ void k_smem_plain(OccView V, const uint8_t *__restrict__ q, const int
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq) return;
     int64_t len = qoff[i + 1] - qoff[i];
-    smem_range<NS>(V, q + qoff[i], len, i, 0, len, ell, smin, out, cap, count);
+    EmitAppend em{out, cap, count};
+    smem_range<NS>(V, q + qoff[i], len, i, 0, len, ell, smin, em);
 }
 
 // Chunked form: items are (query, chunk); item_off[i] = first item of query i.
@@ -157,7 +93,8 @@ __global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *
         int64_t len = qoff[qi + 1] - qoff[qi];
         int64_t x0 = (it - item_off[qi]) * chunk;
         int64_t x1 = x0 + chunk < len ? x0 + chunk : len;
-        smem_range<NS>(V, q + qoff[qi], len, qi, x0, x1, ell, smin, out, cap, count);
+        EmitAppend em{out, cap, count};
+        smem_range<NS>(V, q + qoff[qi], len, qi, x0, x1, ell, smin, em);
     }
 }
 

@@ -90,6 +90,29 @@ template <class T> static int scan_impl(const T *in, T *out, int64_t n, bool inc
 int scan_u32(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, int op, cudaStream_t st) {
     return scan_impl<uint32_t>(in, out, n, inclusive, op, st);
 }
+// Sum scan whose tile partials go to a caller-provided workspace instead of a
+// fresh allocation: n <= SC_TILE * SC_TILE and part_cap >= ceil(n / SC_TILE).
+int scan_u32_ws(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, uint32_t *part_ws, int64_t part_cap,
+                cudaStream_t st) {
+    if (n <= 0) return RB3_OK;
+    int64_t ntiles = (n + SC_TILE - 1) / SC_TILE;
+    if (ntiles == 1) {
+        RB3_LAUNCH(k_scan_apply<uint32_t>, 1, SC_THREADS, 0, st, in, out, n, (const uint32_t *)nullptr, (int)inclusive,
+                   0);
+        return RB3_OK;
+    }
+    if (ntiles > SC_TILE || ntiles > part_cap) {
+        set_error("scan workspace too small (%lld tiles)", (long long)ntiles);
+        return RB3_E_INVAL;
+    }
+    RB3_LAUNCH(k_scan_reduce<uint32_t>, (unsigned)ntiles, SC_THREADS, 0, st, in, n, part_ws, 0);
+    RB3_LAUNCH(k_scan_apply<uint32_t>, 1, SC_THREADS, 0, st, part_ws, part_ws, ntiles, (const uint32_t *)nullptr, 0,
+               0);
+    RB3_LAUNCH(k_scan_apply<uint32_t>, (unsigned)ntiles, SC_THREADS, 0, st, in, out, n, (const uint32_t *)part_ws,
+               (int)inclusive, 0);
+    return RB3_OK;
+}
+
 int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, bool inclusive, cudaStream_t st) {
     return scan_impl<unsigned long long>(reinterpret_cast<const unsigned long long *>(in),
                                          reinterpret_cast<unsigned long long *>(out), n, inclusive, 0, st);

@@ -57,6 +57,8 @@ def lib():
                                               ctypes.POINTER(_i64), _vp]),
             "rb3_mem_search_opts": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp, _i64,
                                                    ctypes.POINTER(_i64), _vp]),
+            "rb3_mem_search_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
+                                                      ctypes.POINTER(_i64), _vp]),
             "rb3_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rb3_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                               ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -214,6 +216,16 @@ def rb3_mem_search_opts(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opt
 
 def rb3_mem_search(idx: Index, q, qoff, min_len: int, min_occ: int = 1, out=None, cap=None, nq=None, stream=None):
     return rb3_mem_search_opts(idx, q, qoff, min_len, min_occ, None, out, cap, nq, stream)
+
+
+def rb3_mem_search_noalloc(idx: Index, q, qoff, min_len: int, min_occ: int, out, cap: int, nq=None, stream=None):
+    """Allocation-free SMEM search for callers that cannot allocate device memory
+    while searching (see include/rb3.h).  q, qoff, out: device tensors.  Returns n."""
+    nq = _len(qoff) - 1 if nq is None else nq
+    n_out = _i64(0)
+    _check(lib().rb3_mem_search_noalloc(idx.handle, _ptr(q), _ptr(qoff), nq, int(min_len), int(min_occ), _ptr(out),
+                                        int(cap), ctypes.byref(n_out), _stream(stream)))
+    return int(n_out.value)
 
 
 def rb3_index_info(idx: Index) -> dict:
