@@ -58,8 +58,10 @@ extern "C" {
  * checkpoints, C_B(a) for every symbol, n = |B|, m = number of sentinels.
  * Layout in HBM: blocks of D symbols; block b is 32 header bytes (for each
  * symbol a, rank_B(a, b*D) as uint32 low words at bytes 0..23 and uint8 high
- * bytes at 24..29) followed by D/2 payload bytes (symbol b*D+o in byte o/2,
- * low nibble when o is even).  An index returned by rb3_build_batch also keeps
+ * bytes at 24..29) followed by D/2 payload bytes: every 64 symbols form one
+ * 32-byte sector holding their 4-bit codes bit-sliced, as four 64-bit planes
+ * (plane j, bytes 8j..8j+7, has bit o set iff bit j of the code of symbol o is
+ * set; plane 3 is zero since codes are 0..5).  An index returned by rb3_build_batch also keeps
  * the batch's text and inverse suffix array, which rb3_merge uses to walk the
  * new strings in segments; rb3_drop_build_data frees them. */
 typedef struct rb3_index rb3_index;

@@ -149,8 +149,9 @@ __global__ void k_unpack(OccView V, uint8_t *__restrict__ codes) {
     if (q0 >= V.n) return;
     const uint8_t *blk = V.blocks + (q0 >> V.log2D) * (int64_t)V.bb;
     int o = (int)(q0 & ((1 << V.log2D) - 1));
-    uint32_t w = *reinterpret_cast<const uint32_t *>(blk + HEADER_BYTES + (o >> 1));
-    for (int j = 0; j < 8 && q0 + j < V.n; ++j) codes[q0 + j] = (uint8_t)((w >> (4 * j)) & 15u);
+    uint32_t p0 = blk[plane_byte(o, 0)], p1 = blk[plane_byte(o, 1)], p2 = blk[plane_byte(o, 2)];
+    for (int j = 0; j < 8 && q0 + j < V.n; ++j)
+        codes[q0 + j] = (uint8_t)(((p0 >> j) & 1u) | (((p1 >> j) & 1u) << 1) | (((p2 >> j) & 1u) << 2));
 }
 
 __global__ void k_occ_export(OccView V, int64_t nblocks, int64_t *__restrict__ occ) {

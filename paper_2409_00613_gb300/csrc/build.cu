@@ -324,7 +324,7 @@ __global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict_
     if (t >= total) return;  // total is a multiple of 32 when D >= 256 ... guarded reduce below
     int64_t q0 = t << 3;
     int64_t b = q0 >> log2D;
-    uint32_t word = 0;
+    uint32_t pl[3] = {0, 0, 0};  // plane bytes of these 8 symbols
     uint32_t c[SIGMA] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -332,12 +332,16 @@ __global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict_
         if (i < n) {
             int32_t s = SA[i];
             uint32_t sym = s ? T[s - 1] : T[n - 1];
-            word |= sym << (4 * j);
+            pl[0] |= (sym & 1u) << j;
+            pl[1] |= ((sym >> 1) & 1u) << j;
+            pl[2] |= ((sym >> 2) & 1u) << j;
             c[sym]++;
         }
     }
     int o = (int)(q0 & ((1 << log2D) - 1));
-    *reinterpret_cast<uint32_t *>(blocks + b * bb + HEADER_BYTES + (o >> 1)) = word;
+    uint8_t *blk = blocks + b * bb;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) blk[plane_byte(o, p)] = (uint8_t)pl[p];  // plane 3 stays zero (memset)
     // segmented reduce over the D/8 lanes of this block (D/8 in {8,16,32})
     int seg = 1 << (log2D - 3);
     unsigned full = __activemask();

@@ -18,8 +18,9 @@
 // ---------------------------------------------------------------------------
 // The index.  Blocks of D symbols: 32-byte header (rank of each symbol at the
 // block start: uint32 low words at bytes 0..23, uint8 high bytes at 24..29)
-// then D/2 payload bytes (4-bit codes, low nibble first).  nblocks = n/D + 1
-// so that rank(a, n) reads a header that exists.
+// then D/2 payload bytes: one 32-byte sector per 64 symbols holding their 4-bit
+// codes as four 64-bit bit-planes.  nblocks = n/D + 1 so that rank(a, n) reads
+// a header that exists.
 // ---------------------------------------------------------------------------
 struct rb3_index {
     int64_t n = 0, m = 0;
@@ -172,44 +173,38 @@ __device__ __forceinline__ Sec ld_sec(const uint8_t *p) {
     return s;
 }
 
-// Mask of bit 0 of the first k nibbles of a 32-bit word (k may be <= 0 or >= 8).
-__device__ __forceinline__ uint32_t nmask32(int k) {
-    return k >= 8 ? 0x11111111u : (k <= 0 ? 0u : (((1u << (4 * k)) - 1u) & 0x11111111u));
+// Payload layout: every 64 symbols of a block form one 32-byte sector holding
+// their 4-bit codes as four 64-bit bit-planes: plane b (bytes 8b..8b+7) has bit
+// o set iff bit b of the code of symbol o is set.  Codes are 0..5, so plane 3
+// is always zero.  A symbol's rank inside a sector is then a popcount of the
+// AND of three (possibly complemented) planes under a prefix mask.
+__device__ __forceinline__ uint64_t sec_plane(const Sec &s, int b) {
+    return (uint64_t)s.w[2 * b] | ((uint64_t)s.w[2 * b + 1] << 32);
 }
 
-// Number of nibbles equal to c among the first k nibbles (0..64) of a sector.
-// Codes are 3-bit, so a nibble equals c iff its xor with c has bits 0..2 clear.
+__device__ __forceinline__ uint64_t prefix_mask(int k) {  // bits [0, k), k may be <= 0 or >= 64
+    return k >= 64 ? ~0ull : (k <= 0 ? 0ull : ((1ull << k) - 1ull));
+}
+
+// Number of symbols equal to c among the first k symbols (0..64) of a sector.
 __device__ __forceinline__ int sec_count(const Sec &s, int c, int k) {
-    int r = 0;
-    const uint32_t cc = 0x11111111u * (uint32_t)c;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        uint32_t x = s.w[i] ^ cc;
-        uint32_t nz = (x | (x >> 1) | (x >> 2)) & 0x11111111u;
-        r += __popc(~nz & nmask32(k - 8 * i));
-    }
-    return r;
+    const uint64_t p0 = sec_plane(s, 0), p1 = sec_plane(s, 1), p2 = sec_plane(s, 2);
+    const uint64_t m = ((c & 1) ? p0 : ~p0) & ((c & 2) ? p1 : ~p1) & ((c & 4) ? p2 : ~p2);
+    return __popcll(m & prefix_mask(k));
 }
 
-// Counts of every symbol among the first k nibbles of a sector, added to r[].
-// Bit planes: b0, b1, b2 of each nibble; symbol codes 0..5 = 000 .. 101.
+// Counts of every symbol among the first k symbols of a sector, added to r[].
 __device__ __forceinline__ void sec_count_all(const Sec &s, int k, int64_t r[6]) {
-    int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        uint32_t m = nmask32(k - 8 * i);
-        uint32_t w = s.w[i];
-        uint32_t b0 = w & m, b1 = (w >> 1) & m, b2 = (w >> 2) & m;
-        uint32_t n0 = ~w & m, n1 = ~(w >> 1) & m, n2 = ~(w >> 2) & m;
-        uint32_t t00 = n1 & n2, t10 = b1 & n2, t01 = n1 & b2;
-        c0 += __popc(n0 & t00);
-        c1 += __popc(b0 & t00);
-        c2 += __popc(n0 & t10);
-        c3 += __popc(b0 & t10);
-        c4 += __popc(n0 & t01);
-        c5 += __popc(b0 & t01);
-    }
-    r[0] += c0; r[1] += c1; r[2] += c2; r[3] += c3; r[4] += c4; r[5] += c5;
+    const uint64_t mk = prefix_mask(k);
+    const uint64_t p0 = sec_plane(s, 0), p1 = sec_plane(s, 1), p2 = sec_plane(s, 2);
+    const uint64_t b0 = p0 & mk, n0 = ~p0 & mk;
+    const uint64_t t00 = ~p1 & ~p2, t10 = p1 & ~p2, t01 = ~p1 & p2;
+    r[0] += __popcll(n0 & t00);
+    r[1] += __popcll(b0 & t00);
+    r[2] += __popcll(n0 & t10);
+    r[3] += __popcll(b0 & t10);
+    r[4] += __popcll(n0 & t01);
+    r[5] += __popcll(b0 & t01);
 }
 
 // Header value of symbol c (registers only: the select is unrolled).
@@ -285,12 +280,19 @@ __device__ __forceinline__ void rank_all_any(const OccView &v, int64_t l, int64_
     else rank_all<4>(v, l, r);
 }
 
-// Symbol B[i].
+// Symbol B[i]: bit o&63 of the three planes of its sector.
 __device__ __forceinline__ int sym_at(const OccView &v, int64_t i) {
     const uint8_t *blk = v.blocks + (i >> v.log2D) * (int64_t)v.bb;
     int o = (int)(i & ((1 << v.log2D) - 1));
-    uint8_t byte = __ldg(blk + HEADER_BYTES + (o >> 1));
-    return (o & 1) ? (byte >> 4) : (byte & 15);
+    const uint8_t *sec = blk + HEADER_BYTES + 32 * (o >> 6);
+    int bit = o & 63;
+    uint64_t p0 = ldg_u64(sec), p1 = ldg_u64(sec + 8), p2 = ldg_u64(sec + 16);
+    return (int)(((p0 >> bit) & 1u) | (((p1 >> bit) & 1u) << 1) | (((p2 >> bit) & 1u) << 2));
+}
+
+// Writer side: byte of plane b that holds symbols [8j, 8j+8) of a sector.
+__device__ __forceinline__ int plane_byte(int o_in_block, int b) {
+    return HEADER_BYTES + 32 * (o_in_block >> 6) + 8 * b + ((o_in_block & 63) >> 3);
 }
 
 // SA bi-interval (k, k', s) of Section "Double-strand BWT".

@@ -14,20 +14,14 @@
 //                 visited by Algorithm 1's walk for string i are ISA2 of the
 //                 positions of P_i read right to left, and the symbol at each
 //                 step is the text symbol.  Each string is cut into segments of
-//                 L symbols; the exact l at a segment's right end is found with
-//                 ForwardExt (Algorithm 3) over B1 along the suffix X that starts
-//                 there: extend until the count s drops to 0 (l = the k field
-//                 after that failing extension, = the number of B1 suffixes below
-//                 X) or until X's sentinel (l = k + occ(Q$), the B1 suffixes equal
-//                 to Q and ending at a sentinel, all older than X's).  Seeds give
-//                 up after seed_cap steps; the walk from the segment above then
-//                 continues through that segment.  A single-strand B1 has no
-//                 ForwardExt; there the seed is a backward search from up to
-//                 seed_cap symbols to the right, exact once its interval is
-//                 empty (or from the sentinel).  Walks run independently under
-//                 warp-aggregated work stealing, ordered so that homologous
-//                 segments of the batch's strings run together and share B1
-//                 blocks in L2.
+//                 L symbols; the exact l at a segment's right end (its seed) is
+//                 found with ForwardExt (Algorithm 3) over B1 along the suffix
+//                 that starts there, in the same persistent kernel that walks
+//                 the segment; a walk that reaches a segment whose seed is not
+//                 in yet takes that segment over (see k_merge_walk).  Segments
+//                 are taken under warp-aggregated work stealing, ordered so that
+//                 homologous segments of the batch's strings run together and
+//                 share B1 blocks in L2.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -59,64 +53,57 @@ __global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int
     }
 }
 
-// ---- segment seeds ---------------------------------------------------------------
-// One thread per segment boundary x (a text position inside a string; the
-// string's sentinel is at send).  seed[w] = l(x) or -1 when capped.
+// ---- segmented walk with in-kernel seeds ------------------------------------------
+// Segment w of a string covers positions [hi(w+1), hi(w)) (hi(w+1) = string
+// start for its lowest segment); the top segment of a string starts at its
+// sentinel, where l = m1 is known.  Every other segment first computes the exact
+// l at hi(w) (its seed), then walks down.  A walk that has written position
+// hi(w+1) either stops there, if segment w+1 has already resolved its seed, or
+// claims segment w+1 and walks on through it.  state[w] goes 0 -> 1 when w's
+// seed resolves and 0 -> 2 when the walk from above claims w; both moves are
+// compare-and-swap, so exactly one walk covers every segment.  A seed whose
+// segment was claimed stops at its next check.  No thread ever waits.
+constexpr int ST_PENDING = 0, ST_RESOLVED = 1, ST_CLAIMED = 2;
+
+__device__ __forceinline__ int load_state(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// Seed by ForwardExt (Algorithm 3) along X = T2[x, send)$ over a double-strand
+// B1: extend until the count s is 0 (l = the k field of that failing extension:
+// the B1 suffixes below X), or to X's sentinel (l = k + occ(Q$): the B1
+// suffixes equal to Q up to a sentinel are older, hence smaller).  Returns -1
+// if claimed from above or after cap steps.
 template <int NS>
-__global__ void k_seeds(OccView B1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
-                        const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
-    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    int64_t x = w_hi[w], send = w_send[w];
-    if (x == send) {  // a walk starting at the sentinel needs no seed
-        seed[w] = -2;
-        return;
-    }
+__device__ __forceinline__ int64_t seed_forward(const OccView &B1, const uint8_t *__restrict__ T2, int64_t x,
+                                                int64_t send, int64_t cap, const int *state_w) {
     BiInt q = {0, 0, B1.n};
-    int64_t res = -1;
     int a = T2[x];
     for (int64_t t = 0;; ++t) {
-        int64_t p = x + t;
-        if (p == send) {
-            // X = Q$: every B1 suffix equal to Q up to a sentinel is older, hence smaller
-            int64_t occ_end = rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp);
-            res = q.k + occ_end;
-            break;
-        }
-        if (t >= cap) break;
-        int an = T2[p + 1];  // next symbol (the sentinel at most), loaded ahead
-        BiInt y = forward_ext<NS>(B1, q, a);
-        a = an;
-        if (y.s == 0) {
-            res = y.k;
-            break;
-        }
+        const int64_t p = x + t;
+        if (p == send) return q.k + (rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp));
+        if (t >= cap) return -1;
+        if ((t & 15) == 15 && load_state(state_w) == ST_CLAIMED) return -1;
+        const int an = T2[p + 1];  // next symbol (the sentinel at most), loaded ahead
+        const BiInt y = forward_ext<NS>(B1, q, a);
+        if (y.s == 0) return y.k;
         q = y;
+        a = an;
     }
-    seed[w] = res;
 }
 
-// Seed for any BWT (used for single-strand indexes, where ForwardExt is not
-// available): backward search over P[x, y) with y = min(x + cap, send).  When
-// y is the sentinel the walk is exact from the start (l = m1).  Otherwise the
-// SA interval [lo, hi) of P[p, y) is kept; once it is empty (P[p, y) does not
-// occur in B1) every B1 suffix compares with P[p..]$ as it does with P[p, y),
-// so l(p) = lo exactly, and the steps continue exactly down to x.
+// Seed for any B1 (single strand has no ForwardExt): backward search over
+// T2[x, y), y = min(x + cap, send).  From the sentinel the walk is exact at
+// once (l = m1); otherwise the SA interval [lo, hi) of T2[p, y) is kept, and
+// once it is empty every B1 suffix compares with T2[p..]$ as with T2[p, y), so
+// l(p) = lo exactly.  Returns -1 if it never becomes exact or is claimed.
 template <int NS>
-__global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ T2, const int64_t *__restrict__ w_hi,
-                            const int64_t *__restrict__ w_send, int64_t nw, int64_t cap, int64_t *__restrict__ seed) {
-    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    int64_t x = w_hi[w], send = w_send[w];
-    if (x == send) {
-        seed[w] = -2;
-        return;
-    }
-    int64_t y = x + cap < send ? x + cap : send;
+__device__ __forceinline__ int64_t seed_backward(const OccView &B1, int64_t m1, const uint8_t *__restrict__ T2,
+                                                 int64_t x, int64_t send, int64_t cap, const int *state_w) {
+    const int64_t y = x + cap < send ? x + cap : send;
     bool exact = y == send;
     int64_t lo = exact ? m1 : 0, hi = exact ? m1 : B1.n;
     for (int64_t p = y - 1; p >= x; --p) {
-        int a = T2[p];
+        if (((y - p) & 15) == 0 && load_state(state_w) == ST_CLAIMED) return -1;
+        const int a = T2[p];
         if (exact) {
             lo = C_of(B1, a) + rank1<NS>(B1, a, lo);
             hi = lo;
@@ -127,76 +114,67 @@ __global__ void k_seeds_bwd(OccView B1, int64_t m1, const uint8_t *__restrict__ 
             exact = lo == hi;
         }
     }
-    seed[w] = exact ? lo : -1;
+    return exact ? lo : -1;
 }
 
-// Walk w covers positions [lo, hi) of its string, right to left; its lower end
-// is the right end of the next walk below with a usable seed, or the string
-// start.  Walks of a string are stored top down and share w_send; one thread
-// per walk looks downward (usually one step).
-__global__ void k_walk_bounds(const int64_t *__restrict__ w_send, const int64_t *__restrict__ w_sstart,
-                              const int64_t *__restrict__ w_hi, const int64_t *__restrict__ seed, int64_t nw,
-                              int64_t *__restrict__ w_lo) {
-    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    const int64_t send = w_send[w];
-    int64_t lo = w_sstart[w];
-    for (int64_t v = w + 1; v < nw && w_send[v] == send; ++v)
-        if (seed[v] != -1) {
-            lo = w_hi[v];
-            break;
-        }
-    w_lo[w] = lo;
-}
-
-// Segmented walk.  The work list order[] lists walks by (segment rank from the
-// string end, string); threads take walks with a warp-aggregated atomic.
-template <int NS>
-__global__ void __launch_bounds__(256) k_walk_seg(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
-                                                  const int32_t *__restrict__ isa2, const int64_t *__restrict__ w_hi,
-                                                  const int64_t *__restrict__ w_lo, const int64_t *__restrict__ w_send,
-                                                  const int64_t *__restrict__ seed,
-                                                  const int32_t *__restrict__ order, int64_t nw,
-                                                  unsigned long long *__restrict__ next,
-                                                  int64_t *__restrict__ pos) {
+template <int NS, bool DS>
+__global__ void __launch_bounds__(256) k_merge_walk(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
+                                                    const int32_t *__restrict__ isa2,
+                                                    const int64_t *__restrict__ w_hi,
+                                                    const int64_t *__restrict__ w_send,
+                                                    const int64_t *__restrict__ w_sstart,
+                                                    const int32_t *__restrict__ w_next, int *__restrict__ state,
+                                                    const int32_t *__restrict__ order, int64_t nw, int64_t cap,
+                                                    unsigned long long *__restrict__ next,
+                                                    int64_t *__restrict__ pos) {
     for (;;) {
-        // warp-aggregated grab of one walk per active lane
+        // warp-aggregated grab of one segment per active lane
         cg::coalesced_group grp = cg::coalesced_threads();
         unsigned long long base = 0;
         if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
         base = grp.shfl(base, 0);
-        int64_t idx = (int64_t)base + grp.thread_rank();
+        const int64_t idx = (int64_t)base + grp.thread_rank();
         if (idx >= nw) break;
-        int64_t w = order[idx];
-        int64_t sd = seed[w];
-        if (sd == -1) continue;  // covered by the walk above
-        int64_t hi = w_hi[w], lo = w_lo[w];
+        const int32_t w = order[idx];
+        const int64_t hi = w_hi[w], send = w_send[w];
         int64_t l;
-        if (sd == -2) {  // starts at the string's sentinel: row isa2[hi], l = m1
+        if (hi == send) {  // top segment: starts at the string's sentinel, row isa2[hi]
             l = m1;
-            int64_t k = isa2[hi];
+            const int64_t k = isa2[hi];
             pos[k] = k + l;
         } else {
-            l = sd;
+            if (load_state(&state[w]) == ST_CLAIMED) continue;
+            l = DS ? seed_forward<NS>(B1, T2, hi, send, cap, &state[w])
+                   : seed_backward<NS>(B1, m1, T2, hi, send, cap, &state[w]);
+            if (l < 0) continue;
+            if (atomicCAS(&state[w], ST_PENDING, ST_RESOLVED) == ST_CLAIMED) continue;
         }
+        const int64_t lo = w_sstart[w];
+        int32_t nx = w_next[w];
+        int64_t bnd = nx >= 0 ? w_hi[nx] : lo;
         int64_t p = hi - 1;
-        if (p >= lo) {
-            int a = T2[p];
-            int64_t k = isa2[p];
-            for (;;) {
-                // next position's symbol and row, loaded while this step's block is in flight
-                int an = 0;
-                int64_t kn = 0;
-                if (p > lo) {
-                    an = T2[p - 1];
-                    kn = isa2[p - 1];
-                }
-                l = C_of(B1, a) + rank1<NS>(B1, a, l);
-                pos[k] = k + l;
-                if (--p < lo) break;
-                a = an;
-                k = kn;
+        if (p < lo) continue;
+        int a = T2[p];
+        int64_t k = isa2[p];
+        for (;;) {
+            // next position's symbol and row, loaded while this step's block is in flight
+            int an = 0;
+            int64_t kn = 0;
+            if (p > lo) {
+                an = T2[p - 1];
+                kn = isa2[p - 1];
             }
+            l = C_of(B1, a) + rank1<NS>(B1, a, l);
+            pos[k] = k + l;
+            if (p == bnd && nx >= 0) {
+                // reached the top of segment nx: stop if its seed is in, else take it over
+                if (atomicCAS(&state[nx], ST_PENDING, ST_CLAIMED) == ST_RESOLVED) break;
+                nx = w_next[nx];
+                bnd = nx >= 0 ? w_hi[nx] : lo;
+            }
+            if (--p < lo) break;
+            a = an;
+            k = kn;
         }
     }
 }
@@ -250,14 +228,16 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     uint32_t before = block_excl<uint32_t>(nf, 0, wtot);
     int64_t kb = k0 + before;              // next B2 row
     int64_t jb = j0 + (o8 - (int64_t)before);  // next B1 row
-    uint32_t word = 0;
+    uint32_t pl[3] = {0, 0, 0};  // plane bytes of these 8 output symbols
     uint32_t c[SIGMA] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int64_t q = q0 + o8 + j;
         if (q < nM) {
             int s = ((fw >> j) & 1u) ? nib_get(B2, kb++) : nib_get(B1, jb++);
-            word |= (uint32_t)s << (4 * j);
+            pl[0] |= ((uint32_t)s & 1u) << j;
+            pl[1] |= (((uint32_t)s >> 1) & 1u) << j;
+            pl[2] |= (((uint32_t)s >> 2) & 1u) << j;
             c[s]++;
         }
     }
@@ -273,7 +253,9 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     if ((q >> log2D) >= nbM) return;  // past the last output block (no barrier follows)
     uint8_t *blk = M + (q >> log2D) * (int64_t)bb;
     const int o = (int)(q & (D - 1));
-    *reinterpret_cast<uint32_t *>(blk + HEADER_BYTES + (o >> 1)) = word;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) blk[plane_byte(o, p)] = (uint8_t)pl[p];
+    blk[plane_byte(o, 3)] = 0;  // plane 3: codes are 3-bit
     if (o == 0) {
         // rank at q = base + counts of the groups of this tile before q
         int ng = o8 >> 6;
@@ -370,36 +352,42 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             // segment plan (host): strings of src from its sentinel positions
             int64_t L = o.seg_len;
             if (L <= 0) {
-                // about 512 walks per SM, segment length clamped to [512, 16384]
+                // about 512 segments per SM, length clamped to [512, 16384]
                 int64_t target = (int64_t)num_sms() * 512;
                 L = n2 / (target > 0 ? target : 1);
                 if (L < 512) L = 512;
                 if (L > 16384) L = 16384;
             }
-            int64_t cap = o.seed_cap > 0 ? o.seed_cap : 4 * L;
+            // double strand: seeds are self-limiting (claimed from above), so no cap
+            // unless asked; single strand: the backward seed looks cap symbols ahead
+            int64_t cap = o.seed_cap > 0 ? o.seed_cap : (dst->single_strand ? 4 * L : (int64_t)1 << 62);
             const int64_t ns = (int64_t)src->str_end.size();
-            std::vector<int64_t> s_first(ns + 1, 0), s_start(ns), w_hi, w_send, w_sstart;
-            std::vector<int32_t> w_rank;  // segment rank from the string end
+            std::vector<int64_t> w_hi, w_send, w_sstart;
+            std::vector<int32_t> w_next, w_rank;
             int64_t maxr = 0;
             for (int64_t s = 0; s < ns; ++s) {
-                int64_t start = s == 0 ? 0 : src->str_end[s - 1] + 1;
-                int64_t end = src->str_end[s];
-                s_start[s] = start;
-                s_first[s] = (int64_t)w_hi.size();
-                // walk 0 starts at the sentinel; walk r at end - r*L while > start
+                const int64_t start = s == 0 ? 0 : src->str_end[s - 1] + 1;
+                const int64_t end = src->str_end[s];
+                // segment r starts at end - r*L (r = 0 at the sentinel) while > start
                 int64_t r = 0;
                 for (int64_t x = end;; x -= L, ++r) {
                     w_hi.push_back(x);
                     w_send.push_back(end);
                     w_sstart.push_back(start);
                     w_rank.push_back((int32_t)r);
-                    if (x - L <= start) break;
+                    const bool last = x - L <= start;
+                    w_next.push_back(last ? -1 : (int32_t)w_hi.size());
+                    if (last) break;
                 }
                 if (r > maxr) maxr = r;
             }
-            s_first[ns] = (int64_t)w_hi.size();
             const int64_t nw = (int64_t)w_hi.size();
-            // processing order: by rank from the end, then string
+            if (nw >= (int64_t(1) << 31)) {
+                set_error("merge: too many segments");
+                return RB3_E_INVAL;
+            }
+            // processing order: by rank from the string end, then string, so the
+            // homologous segments of a batch's strings run side by side
             std::vector<int32_t> order(nw);
             {
                 std::vector<int64_t> cnt(maxr + 2, 0);
@@ -408,36 +396,34 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                 for (int64_t w = 0; w < nw; ++w) order[cnt[w_rank[w]]++] = (int32_t)w;
             }
             DevBuf plan;
-            size_t bytes = sizeof(int64_t) * (5 * nw) + sizeof(unsigned long long) + sizeof(int32_t) * nw + 64;
+            size_t bytes = sizeof(int64_t) * (3 * nw) + sizeof(int32_t) * (3 * nw) + sizeof(unsigned long long) + 64;
             RB3_TRY(plan.alloc(bytes, st));
-            int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_seed = d_send + nw, *d_lo = d_seed + nw;
-            int64_t *d_wss = d_lo + nw;
-            unsigned long long *d_next = reinterpret_cast<unsigned long long *>(d_wss + nw);
-            int32_t *d_order = reinterpret_cast<int32_t *>(d_next + 1);
+            int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_sstart = d_send + nw;
+            int32_t *d_next = reinterpret_cast<int32_t *>(d_sstart + nw), *d_state = d_next + nw, *d_order = d_state + nw;
+            unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(
+                (reinterpret_cast<uintptr_t>(d_order + nw) + 15) & ~uintptr_t(15));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_hi, w_hi.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_send, w_send.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_wss, w_sstart.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_sstart, w_sstart.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_next, w_next.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
+            RB3_CUDA_TRY(cudaMemsetAsync(d_state, 0, sizeof(int32_t) * nw, st));
+            RB3_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st));
             {
-                Phase ps("merge.seed", st);
-                Phase pk("k.seeds", st);
-                if (dst->single_strand)
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH(k_seeds_bwd<NS>, nb_for(nw, 128), 128, 0, st, V1, m1, src->text,
-                                                   d_hi, d_send, nw, cap, d_seed));
-                else
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH(k_seeds<NS>, nb_for(nw, 128), 128, 0, st, V1, src->text, d_hi,
-                                                   d_send, nw, cap, d_seed));
-                RB3_LAUNCH(k_walk_bounds, nb_for(nw, 256), 256, 0, st, d_send, d_wss, d_hi, d_seed, nw, d_lo);
-            }
-            {
-                Phase pw("merge.lfwalk", st);
+                // per new symbol: 1 B text, 4 B ISA, 4+1 B Occ count, D/4 B payload on average,
+                // 8 B pos (seed steps not counted)
+                Phase pw("k.merge_walk", st, (double)n2 * (18.0 + dst->D / 4.0));
                 int64_t resident = (int64_t)num_sms() * 2048;
                 int64_t threads = nw < resident ? nw : resident;
-                // per new symbol: 1 B text, 4 B ISA, 4+1 B Occ count, D/4 B payload on average, 8 B pos
-                Phase pk("k.walk_seg", st, (double)n2 * (18.0 + dst->D / 4.0));
-                RB3_WITH_NS(dst->D, RB3_LAUNCH(k_walk_seg<NS>, nb_for(threads, 256), 256, 0, st, V1, m1, src->text,
-                                               src->isa, d_hi, d_lo, d_send, d_seed, d_order, nw, d_next, pos));
+                unsigned grid = nb_for(threads, 256);
+                if (dst->single_strand)
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, 256, 0, st, V1, m1, src->text,
+                                                   src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
+                                                   cap, d_ctr, pos));
+                else
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, 256, 0, st, V1, m1, src->text,
+                                                   src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
+                                                   cap, d_ctr, pos));
             }
         }
     }
