@@ -16,6 +16,8 @@
 //             Stable radix sort of (key, p); ranks = group start positions.
 //   round h   for every suffix still in a group of >= 2, key = rank[p + h];
 //             sort inside the group; split; new rank = start of the sub-group.
+//             Groups are processed in the order of their first member's text
+//             position (locality of the rank reads and writes).
 // Rank writes of a round are applied only after every key of that round has
 // been read, so all keys of a round see the same (h-level) ranks.
 #include "common.cuh"
@@ -102,8 +104,44 @@ __global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_
     rank[SA[i]] = (int32_t)g;
     bool single = g == (uint32_t)i && (i + 1 == n || gstart[i + 1] == (uint32_t)(i + 1));
     bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
-    fs[i] = (!single && !large) ? 1u : 0u;
+    fs[i] = (g == (uint32_t)i && !single && !large) ? 1u : 0u;  // head of a group of 2..SMALL_MAX
     fl[i] = large ? 1u : 0u;
+}
+
+// The groups of 2..SMALL_MAX members are listed in the order of their first
+// member's text position (the stable sort keeps members in position order, so
+// that is the head's SA value).  A pangenome's groups are mostly homologous
+// copies of one locus, so neighbouring groups are neighbouring loci and the
+// rank[p + h] reads and rank writes of a round touch nearby addresses.
+__global__ void k_head_pairs(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ fs,
+                             const uint32_t *__restrict__ ps, int64_t n, uint64_t *__restrict__ hkey,
+                             uint32_t *__restrict__ hval) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !fs[i]) return;
+    hkey[ps[i]] = SA[i];
+    hval[ps[i]] = (uint32_t)i;
+}
+
+__global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, const uint32_t *__restrict__ gstart,
+                              int64_t n, uint32_t *__restrict__ gsz) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= G) return;
+    uint32_t h = hval[j];
+    int64_t t = 1;
+    while (h + t < n && gstart[h + t] == h) ++t;
+    gsz[j] = (uint32_t)t;
+}
+
+__global__ void k_expand_groups(const uint32_t *__restrict__ hval, const uint32_t *__restrict__ gsz,
+                                const uint32_t *__restrict__ goff, int64_t G, const uint32_t *__restrict__ SA,
+                                uint32_t *__restrict__ sp, uint32_t *__restrict__ sg) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= G) return;
+    uint32_t h = hval[j], o = goff[j], z = gsz[j];
+    for (uint32_t t = 0; t < z; ++t) {
+        sp[o + t] = SA[h + t];
+        sg[o + t] = h;
+    }
 }
 
 __global__ void k_init_lists(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart,
@@ -113,10 +151,7 @@ __global__ void k_init_lists(const uint32_t *__restrict__ SA, const uint32_t *__
                              uint32_t *__restrict__ lg) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (fs[i]) {
-        sp[ps[i]] = SA[i];
-        sg[ps[i]] = gstart[i];
-    } else if (fl[i]) {
+    if (fl[i]) {
         lp[pl[i]] = SA[i];
         lg[pl[i]] = gstart[i];
     }
@@ -340,8 +375,7 @@ __global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict_
     }
     int o = (int)(q0 & ((1 << log2D) - 1));
     uint8_t *blk = blocks + b * bb;
-#pragma unroll
-    for (int p = 0; p < 3; ++p) blk[plane_byte(o, p)] = (uint8_t)pl[p];  // plane 3 stays zero (memset)
+    store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], __activemask(), true);
     // segmented reduce over the D/8 lanes of this block (D/8 in {8,16,32})
     int seg = 1 << (log2D - 3);
     unsigned full = __activemask();
@@ -483,8 +517,29 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             uint32_t hc[2];
             RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
-            NS = hc[0];
+            const int64_t G = hc[0];  // groups of 2..SMALL_MAX
             NL = hc[1];
+            // small groups in order of their first member's text position
+            DevBuf hk0, hk1, hv0, hv1, gsz, goff;
+            RB3_TRY(hk0.alloc(sizeof(uint64_t) * (G + 1), st));
+            RB3_TRY(hk1.alloc(sizeof(uint64_t) * (G + 1), st));
+            RB3_TRY(hv0.alloc(sizeof(uint32_t) * (G + 1), st));
+            RB3_TRY(hv1.alloc(sizeof(uint32_t) * (G + 1), st));
+            RB3_TRY(gsz.alloc(sizeof(uint32_t) * (G + 1), st));
+            RB3_TRY(goff.alloc(sizeof(uint32_t) * (G + 1), st));
+            RB3_LAUNCH(k_head_pairs, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), fs.as<uint32_t>(),
+                       ps.as<uint32_t>(), n, hk0.as<uint64_t>(), hv0.as<uint32_t>());
+            bool halt = false;
+            RB3_TRY(radix_sort_pairs(hk0.as<uint64_t>(), hv0.as<uint32_t>(), hk1.as<uint64_t>(), hv1.as<uint32_t>(), G,
+                                     0, ilog2(n) + 1, st, &halt));
+            const uint32_t *hval = halt ? hv1.as<uint32_t>() : hv0.as<uint32_t>();
+            if (G > 0)
+                RB3_LAUNCH(k_group_sizes, nb_for(G, 256), 256, 0, st, hval, G, hv.as<uint32_t>(), n, gsz.as<uint32_t>());
+            RB3_TRY(scan_u32(gsz.as<uint32_t>(), goff.as<uint32_t>(), G, false, 0, st));
+            RB3_LAUNCH(k_tally, 1, 1, 0, st, goff.as<uint32_t>(), gsz.as<uint32_t>(), G, d_cnt, 0);
+            RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            NS = hc[0];
             RB3_TRY(sp.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
             RB3_TRY(sg.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
             RB3_TRY(sp2.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
@@ -493,6 +548,9 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(tg.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
             RB3_TRY(lp.alloc(sizeof(uint32_t) * (NL + 1), st));
             RB3_TRY(lg.alloc(sizeof(uint32_t) * (NL + 1), st));
+            if (G > 0)
+                RB3_LAUNCH(k_expand_groups, nb_for(G, 256), 256, 0, st, hval, gsz.as<uint32_t>(), goff.as<uint32_t>(),
+                           G, reinterpret_cast<uint32_t *>(SA), sp.as<uint32_t>(), sg.as<uint32_t>());
             RB3_LAUNCH(k_init_lists, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
                        fs.as<uint32_t>(), fl.as<uint32_t>(), ps.as<uint32_t>(), pl.as<uint32_t>(), n,
                        sp.as<uint32_t>(), sg.as<uint32_t>(), lp.as<uint32_t>(), lg.as<uint32_t>());

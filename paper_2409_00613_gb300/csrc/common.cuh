@@ -290,6 +290,23 @@ __device__ __forceinline__ int sym_at(const OccView &v, int64_t i) {
     return (int)(((p0 >> bit) & 1u) | (((p1 >> bit) & 1u) << 1) | (((p2 >> bit) & 1u) << 2));
 }
 
+// Writer side: the 8 lanes 8g..8g+7 of a warp hold the plane bytes of the 8
+// consecutive 8-symbol groups of one 64-symbol sector; an xor butterfly inside
+// the 8 lanes builds each 64-bit plane and lanes 0..3 of the group store planes
+// 0..3 (plane 3 zero).  mask: the active lanes (whole 8-lane groups).
+__device__ __forceinline__ void store_planes(uint8_t *sec, uint32_t b0, uint32_t b1, uint32_t b2, unsigned mask,
+                                             bool do_store) {
+    const int j = threadIdx.x & 7;
+    uint64_t v0 = (uint64_t)b0 << (8 * j), v1 = (uint64_t)b1 << (8 * j), v2 = (uint64_t)b2 << (8 * j);
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        v0 |= __shfl_xor_sync(mask, v0, d);
+        v1 |= __shfl_xor_sync(mask, v1, d);
+        v2 |= __shfl_xor_sync(mask, v2, d);
+    }
+    if (do_store && j < 4) *reinterpret_cast<uint64_t *>(sec + 8 * j) = j == 0 ? v0 : (j == 1 ? v1 : (j == 2 ? v2 : 0ull));
+}
+
 // Writer side: byte of plane b that holds symbols [8j, 8j+8) of a sector.
 __device__ __forceinline__ int plane_byte(int o_in_block, int b) {
     return HEADER_BYTES + 32 * (o_in_block >> 6) + 8 * b + ((o_in_block & 63) >> 3);

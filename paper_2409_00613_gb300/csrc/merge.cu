@@ -250,12 +250,11 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     // write payload word; headers at block starts
     const int D = 1 << log2D;
     const int64_t q = q0 + o8;
-    if ((q >> log2D) >= nbM) return;  // past the last output block (no barrier follows)
+    const bool live = (q >> log2D) < nbM;  // past the last output block nothing is stored
     uint8_t *blk = M + (q >> log2D) * (int64_t)bb;
     const int o = (int)(q & (D - 1));
-#pragma unroll
-    for (int p = 0; p < 3; ++p) blk[plane_byte(o, p)] = (uint8_t)pl[p];
-    blk[plane_byte(o, 3)] = 0;  // plane 3: codes are 3-bit
+    store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], 0xffffffffu, live);
+    if (!live) return;  // no barrier follows
     if (o == 0) {
         // rank at q = base + counts of the groups of this tile before q
         int ng = o8 >> 6;

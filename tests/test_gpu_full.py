@@ -1,0 +1,85 @@
+"""Full-size GPU parity on the benchmark workload (pangenome merge: 5 Mb founder,
+50 haplotypes, batches of 10, both strands, ~500 Msym), in the configuration
+bench.py times (default options), against the oracle's own incremental build
+(naive sort per haplotype + Algorithm 1 merges), plus the LF-decode certificate;
+MEM search on the finished index checked on a sample of the 1 M queries; and a
+reduced instance of the uneven-genome workload (clusters, N-runs)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2409_00613_gb300 as rb
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+DEV = torch.device("cuda:0")
+FIELDS = ("qid", "start", "end", "k", "kp", "s")
+NTH = os.cpu_count() or 4
+
+
+def gpu_incremental(S, opts=None):
+    off = S.offsets
+    idx = None
+    for a, b in S.batches:
+        part = rb.rb3_build_batch(torch.from_numpy(S.seq[off[a]:off[b]].copy()).to(DEV), S.lens[a:b].copy(),
+                                  opts=opts)
+        if idx is None:
+            idx = part
+        else:
+            rb.rb3_merge_opts(idx, part, opts)
+            part.free()
+    return idx
+
+
+@pytest.fixture(scope="module")
+def pangenome_full():
+    S = synth.pangenome()
+    idx = gpu_incremental(S)
+    want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=NTH)
+    return S, idx, want
+
+
+def test_pangenome_full_bwt_equals_oracle(pangenome_full):
+    S, idx, want = pangenome_full
+    codes, occ = rb.rb3_export(idx, want_occ=True)
+    assert len(codes) == len(want) == S.ds_symbols()
+    assert np.array_equal(codes, want)
+    T = oracle.concat(S.seq, S.lens, True)
+    assert oracle.certify(codes, T, nthreads=NTH) == 0
+    assert np.array_equal(occ, oracle.occ_table(want, 64))
+    info = rb.rb3_index_info(idx)
+    assert info["m"] == 100 and info["C"] == list(oracle.counts(want))
+
+
+def test_pangenome_full_mem_search_sample(pangenome_full):
+    S, idx, want = pangenome_full
+    Q = synth.mem_queries(S)  # the 1 M benchmark queries
+    recs, n = rb.rb3_mem_search(idx, torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV), 31, 1,
+                                cap=Q.nq * 8)
+    got = np.stack([recs[f].astype(np.int64) for f in FIELDS], axis=1)
+    g = synth.rng(7)
+    sample = np.sort(g.choice(Q.nq, size=10_000, replace=False))
+    sub = Q.subset(sample)
+    ref = oracle.smem(want, sub.q, sub.qoff, 31, 1, nthreads=NTH)
+    # map the sample's records back to their global query ids
+    ref[:, 0] = sample[ref[:, 0]]
+    mask = np.isin(got[:, 0], sample)
+    assert np.array_equal(got[mask], ref)
+    # backward search on the same sample
+    lohi = rb.rb3_backward_search(idx, sub.q, sub.qoff)
+    assert np.array_equal(lohi, oracle.backward_search(want, sub.q, sub.qoff))
+
+
+def test_uneven_genomes_reduced():
+    """Uneven-genome shape at reduced size: 6 clusters, lognormal lengths, 1%
+    substitutions, 0.5% N-runs of 10-100, batches of 16 genomes."""
+    S = synth.uneven(n_founders=6, founder_len=300_000, n_genomes=60, per_cluster=10, median=150_000, sigma=0.35,
+                     lo=50_000, hi=300_000, batch=16)
+    idx = gpu_incremental(S)
+    codes = rb.rb3_export(idx)
+    want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=NTH)
+    assert np.array_equal(codes, want)
+    assert oracle.certify(codes, oracle.concat(S.seq, S.lens, True), nthreads=NTH) == 0
