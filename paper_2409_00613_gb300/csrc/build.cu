@@ -9,10 +9,11 @@
 // from prefix doubling with radix passes (how), which reaches the same S.
 //
 // Prefix doubling, Larsson-Sadakane style:
-//   round 0   key(p) = T[p..p+21) packed 3 bits per symbol, cut after the
-//             first sentinel.  A window holding a sentinel makes its suffix's
+//   round 0   key(p) = T[p..p+18) as an 18-digit base-6 number (47 bits),
+//             cut after the first sentinel.  A window holding a sentinel makes its suffix's
 //             order final (sentinels are distinct and ordered by position, and
 //             the stable sort by key keeps position order among equal keys).
+//             A window holds a sentinel iff its last digit is 0.
 //             Stable radix sort of (key, p); ranks = group start positions.
 //   round h   for every suffix still in a group of >= 2, key = rank[p + h];
 //             sort inside the group; split; new rank = start of the sub-group.
@@ -24,7 +25,8 @@
 
 namespace rb3 {
 
-constexpr int H0 = 21;            // symbols in the round-0 key (3 bits each)
+constexpr int H0 = 18;            // symbols in the round-0 key (base-6 digits; 6^18 < 2^47)
+constexpr int H0_BITS = 47;
 constexpr int SMALL_MAX = 1024;   // groups up to this size are sorted in shared memory
 constexpr int RT_TILE = 2048;     // round-kernel tile (entries)
 constexpr int RT_THREADS = 256;
@@ -77,7 +79,7 @@ __global__ void k_init_keys(const uint8_t *__restrict__ T, int64_t n, uint64_t *
     for (int j = 0; j < H0; ++j) {
         uint32_t c = stop ? 0u : (uint32_t)T[p + j];  // T ends with a sentinel: reads stop at n-1
         stop = stop || c == 0;
-        k = (k << 3) | c;
+        k = k * 6u + c;
     }
     key[p] = k;
     val[p] = (uint32_t)p;
@@ -85,11 +87,11 @@ __global__ void k_init_keys(const uint8_t *__restrict__ T, int64_t n, uint64_t *
 
 // A group starts at i if its key differs from the previous one, or if its
 // window holds a sentinel (then its order is final: singleton).  A window
-// holds a sentinel iff its last 3-bit field is 0.
+// holds a sentinel iff its last base-6 digit is 0.
 __global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__restrict__ hv) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool head = i == 0 || K[i] != K[i - 1] || (K[i] & 7u) == 0;
+    bool head = i == 0 || K[i] != K[i - 1] || (K[i] % 6u) == 0;
     hv[i] = head ? (uint32_t)i : 0u;
 }
 
@@ -101,9 +103,10 @@ __global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t g = gstart[i];
-    rank[SA[i]] = (int32_t)g;
     bool single = g == (uint32_t)i && (i + 1 == n || gstart[i + 1] == (uint32_t)(i + 1));
     bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
+    // members of small groups get their rank from k_expand_groups, in locus order
+    if (single || large) rank[SA[i]] = (int32_t)g;
     fs[i] = (g == (uint32_t)i && !single && !large) ? 1u : 0u;  // head of a group of 2..SMALL_MAX
     fl[i] = large ? 1u : 0u;
 }
@@ -134,13 +137,15 @@ __global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, cons
 
 __global__ void k_expand_groups(const uint32_t *__restrict__ hval, const uint32_t *__restrict__ gsz,
                                 const uint32_t *__restrict__ goff, int64_t G, const uint32_t *__restrict__ SA,
-                                uint32_t *__restrict__ sp, uint32_t *__restrict__ sg) {
+                                uint32_t *__restrict__ sp, uint32_t *__restrict__ sg, int32_t *__restrict__ rank) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= G) return;
     uint32_t h = hval[j], o = goff[j], z = gsz[j];
     for (uint32_t t = 0; t < z; ++t) {
-        sp[o + t] = SA[h + t];
+        uint32_t p = SA[h + t];
+        sp[o + t] = p;
         sg[o + t] = h;
+        rank[p] = (int32_t)h;
     }
 }
 
@@ -493,7 +498,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
                 RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, k0.as<uint64_t>(), v0);
             }
             bool alt = false;
-            RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0, k1.as<uint64_t>(), v1.as<uint32_t>(), n, 0, 3 * H0, st,
+            RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0, k1.as<uint64_t>(), v1.as<uint32_t>(), n, 0, H0_BITS, st,
                                      &alt));
             const uint64_t *K = alt ? k1.as<uint64_t>() : k0.as<uint64_t>();
             if (alt) RB3_CUDA_TRY(cudaMemcpyAsync(SA, v1.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
@@ -550,7 +555,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(lg.alloc(sizeof(uint32_t) * (NL + 1), st));
             if (G > 0)
                 RB3_LAUNCH(k_expand_groups, nb_for(G, 256), 256, 0, st, hval, gsz.as<uint32_t>(), goff.as<uint32_t>(),
-                           G, reinterpret_cast<uint32_t *>(SA), sp.as<uint32_t>(), sg.as<uint32_t>());
+                           G, reinterpret_cast<uint32_t *>(SA), sp.as<uint32_t>(), sg.as<uint32_t>(), rank);
             RB3_LAUNCH(k_init_lists, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
                        fs.as<uint32_t>(), fl.as<uint32_t>(), ps.as<uint32_t>(), pl.as<uint32_t>(), n,
                        sp.as<uint32_t>(), sg.as<uint32_t>(), lp.as<uint32_t>(), lg.as<uint32_t>());

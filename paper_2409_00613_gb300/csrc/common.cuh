@@ -323,8 +323,23 @@ struct BiInt {
 template <int NS> __device__ __forceinline__ BiInt backward_ext(const OccView &v, BiInt x, int a) {
     int64_t r0[SIGMA], r1[SIGMA];
     {
+        // both ends' blocks are requested before either is counted; when both
+        // ends fall in one block it is read once
+        const int64_t e = x.k + x.s;
+        const bool same = (e >> v.log2D) == (x.k >> v.log2D);
         BlockLd<NS> b0 = block_load<NS>(v, x.k);
-        BlockLd<NS> b1 = block_load<NS>(v, x.k + x.s);
+        BlockLd<NS> b1;
+        if (!same) {
+            b1 = block_load<NS>(v, e);
+        } else {
+            b1 = b0;
+            b1.o = (int)(e & (64 * NS - 1));
+            if (NS > 1)  // payload sectors the first offset did not need (block_load skips them)
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    if (b1.o > 64 * j && !(b0.o > 64 * j))
+                        b1.p[j] = ld_sec(v.blocks + (e >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * j);
+        }
         block_rank_all<NS>(b0, r0);
         block_rank_all<NS>(b1, r1);
     }

@@ -193,10 +193,45 @@ __global__ void k_tile_starts(const int64_t *__restrict__ pos, int64_t n2, int64
     for (int64_t t = tp + 1; t <= tk && t < ntiles + 1; ++t) kstart[t] = k;
 }
 
-__device__ __forceinline__ int nib_get(const OccView &v, int64_t i) { return sym_at(v, i); }
+// Plane bits of the cnt (<= 8) consecutive symbols starting at row `start`:
+// out[b] bit j = bit b of the code of symbol start + j.  The run may cross
+// into the next sector (of the same block or the next block).
+__device__ __forceinline__ void plane_bits(const OccView &v, int64_t start, int cnt, uint32_t out[3]) {
+    out[0] = out[1] = out[2] = 0u;
+    if (cnt <= 0) return;
+    const int D = 1 << v.log2D;
+    const int o = (int)(start & (D - 1));
+    const uint8_t *sec = v.blocks + (start >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * (o >> 6);
+    const int bit = o & 63;
+    const uint32_t m = (1u << cnt) - 1u;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) out[b] = (uint32_t)(ldg_u64(sec + 8 * b) >> bit) & m;
+    if (bit + cnt > 64) {
+        const int64_t nxt = (start | 63) + 1;  // first row of the next sector
+        const int on = (int)(nxt & (D - 1));
+        const uint8_t *sec2 = v.blocks + (nxt >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * (on >> 6);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) out[b] |= (uint32_t)(ldg_u64(sec2 + 8 * b) << (64 - bit)) & m;
+    }
+}
 
-__global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, const int64_t *__restrict__ pos,
-                                                        const int64_t *__restrict__ kstart, int64_t nM, int64_t nbM,
+// Rank of every symbol at each tile start of the merged BWT: rank_B1 at the
+// number of B1 rows before it plus rank_B2 at the number of B2 rows before it.
+__global__ void k_tile_bases(OccView B1, OccView B2, const int64_t *__restrict__ kstart, int64_t ntiles,
+                             int64_t *__restrict__ base6) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int64_t k0 = kstart[t], j0 = t * MT - k0;
+    int64_t r1[SIGMA], r2[SIGMA];
+    rank_all_any(B1, j0, r1);
+    rank_all_any(B2, k0, r2);
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a) base6[t * SIGMA + a] = r1[a] + r2[a];
+}
+
+__global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B2, const int64_t *__restrict__ pos,
+                                                        const int64_t *__restrict__ kstart,
+                                                        const int64_t *__restrict__ tbase, int64_t nM, int64_t nbM,
                                                         int log2D, int bb, uint8_t *__restrict__ M) {
     __shared__ uint32_t flags[MT / 32];
     __shared__ uint32_t wtot[32];
@@ -207,15 +242,9 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     const int64_t k0 = kstart[t], k1 = kstart[t + 1];
     const int64_t j0 = q0 - k0;
     for (int i = threadIdx.x; i < MT / 32; i += MT_THREADS) flags[i] = 0;
-    if (threadIdx.x < SIGMA) base6[threadIdx.x] = 0;
+    if (threadIdx.x < SIGMA) base6[threadIdx.x] = tbase[t * SIGMA + threadIdx.x];
     for (int i = threadIdx.x; i < (MT / 64) * SIGMA; i += MT_THREADS) (&bcnt[0][0])[i] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t r1[SIGMA], r2[SIGMA];
-        rank_all_any(B1, j0, r1);
-        rank_all_any(B2, k0, r2);
-        for (int a = 0; a < SIGMA; ++a) base6[a] = r1[a] + r2[a];
-    }
     for (int64_t k = k0 + threadIdx.x; k < k1; k += MT_THREADS) {
         int d = (int)(pos[k] - q0);
         atomicOr(&flags[d >> 5], 1u << (d & 31));
@@ -228,18 +257,37 @@ __global__ void __launch_bounds__(MT_THREADS) k_scatter(OccView B1, OccView B2, 
     uint32_t before = block_excl<uint32_t>(nf, 0, wtot);
     int64_t kb = k0 + before;              // next B2 row
     int64_t jb = j0 + (o8 - (int64_t)before);  // next B1 row
+    // symbols of this thread: the flagged ones are the next B2 rows, the others the next B1 rows
+    const int64_t qt = q0 + o8;
+    const int valid = qt >= nM ? 0 : (nM - qt < 8 ? (int)(nM - qt) : 8);
+    const int n2t = (int)nf, n1t = valid - (int)nf;
+    uint32_t s1[3], s2[3];
+    plane_bits(B1, jb, n1t, s1);
+    plane_bits(B2, kb, n2t, s2);
     uint32_t pl[3] = {0, 0, 0};  // plane bytes of these 8 output symbols
-    uint32_t c[SIGMA] = {0, 0, 0, 0, 0, 0};
+    int i1 = 0, i2 = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        int64_t q = q0 + o8 + j;
-        if (q < nM) {
-            int s = ((fw >> j) & 1u) ? nib_get(B2, kb++) : nib_get(B1, jb++);
-            pl[0] |= ((uint32_t)s & 1u) << j;
-            pl[1] |= (((uint32_t)s >> 1) & 1u) << j;
-            pl[2] |= (((uint32_t)s >> 2) & 1u) << j;
-            c[s]++;
+        if (j < valid) {
+            const bool from2 = (fw >> j) & 1u;
+            const int sh = from2 ? i2 : i1;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) pl[b] |= (((from2 ? s2[b] : s1[b]) >> sh) & 1u) << j;
+            i2 += from2;
+            i1 += !from2;
         }
+    }
+    uint32_t c[SIGMA];
+    {
+        const uint32_t mv = (1u << valid) - 1u;
+        const uint32_t b0 = pl[0], n0 = ~pl[0] & mv, t00 = ~pl[1] & ~pl[2] & mv, t10 = pl[1] & ~pl[2],
+                       t01 = ~pl[1] & pl[2];
+        c[0] = __popc(n0 & t00);
+        c[1] = __popc(b0 & t00);
+        c[2] = __popc(n0 & t10);
+        c[3] = __popc(b0 & t10);
+        c[4] = __popc(n0 & t01);
+        c[5] = __popc(b0 & t01);
     }
     // counts per 64-symbol group (8 threads)
     const int grp = o8 >> 6;
@@ -318,9 +366,10 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
     int log2D = ilog2(D), bb = HEADER_BYTES + D / 2;
     int64_t nbM = nM / D + 1;
     int64_t ntiles = (nbM * D + MT - 1) / MT;
-    DevBuf posb, kst, Mb;
+    DevBuf posb, kst, Mb, tbase;
     RB3_TRY(posb.alloc(sizeof(int64_t) * n2, st));
     RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
+    RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
     RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
     int64_t *pos = posb.as<int64_t>();
     OccView V1 = occ_view(dst), V2 = occ_view(src);
@@ -433,9 +482,11 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             // every input block read once, every output block written once, 8 B pos per new symbol
             double bytes = (double)dst->nblocks * dst->block_bytes + (double)src->nblocks * src->block_bytes +
                            (double)nbM * bb + 8.0 * n2;
+            RB3_LAUNCH(k_tile_bases, nb_for(ntiles, 128), 128, 0, st, V1, V2, kst.as<int64_t>(), ntiles,
+                       tbase.as<int64_t>());
             Phase pk("k.scatter", st, bytes);
-            RB3_LAUNCH(k_scatter, (unsigned)ntiles, MT_THREADS, 0, st, V1, V2, pos, kst.as<int64_t>(), nM, nbM, log2D,
-                       bb, Mb.as<uint8_t>());
+            RB3_LAUNCH(k_scatter, (unsigned)ntiles, MT_THREADS, 0, st, V1, V2, pos, kst.as<int64_t>(),
+                       tbase.as<int64_t>(), nM, nbM, log2D, bb, Mb.as<uint8_t>());
         }
     }
     // install

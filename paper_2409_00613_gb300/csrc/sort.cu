@@ -175,11 +175,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
     unsigned lt = (1u << lane) - 1u;
     unsigned long long kk[RS_ITERS];
     uint32_t vv[RS_ITERS], lr[RS_ITERS];
+    // the whole tile's keys and values are loaded before any is ranked
+#pragma unroll
+    for (int it = 0; it < RS_ITERS; ++it) {
+        int64_t g = base + it * 32 + lane;
+        kk[it] = g < n ? (unsigned long long)kin[g] : 0ull;
+        vv[it] = g < n ? vin[g] : 0u;
+    }
 #pragma unroll
     for (int it = 0; it < RS_ITERS; ++it) {
         int64_t g = base + it * 32 + lane;
         bool valid = g < n;
-        unsigned long long k = valid ? (unsigned long long)kin[g] : 0ull;
+        unsigned long long k = kk[it];
         uint32_t d = valid ? ((uint32_t)(k >> shift) & mask) : (RS_BINS + lane);
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = 31 - __clz(peers);
@@ -187,8 +194,6 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
         __syncwarp();
         if (valid && lane == leader) S.wh[w][d] = c0 + __popc(peers);
         __syncwarp();
-        kk[it] = k;
-        vv[it] = valid ? vin[g] : 0u;
         lr[it] = c0 + __popc(peers & lt);
     }
     __syncthreads();
