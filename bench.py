@@ -5,7 +5,8 @@ Workload (default): the pangenome merge -- a 5 Mb uniform-random founder, 50
 haplotypes with 0.1% SNPs and 0.01% indels, both strands (~500 M symbols),
 built incrementally in batches of 10 haplotypes.  Batch 0 is built before the
 timed region; each timed step builds the next batch's BWT on the device and
-merges it into the running index (step k uses batch 1 + (k mod 4)).  value =
+merges it into the running index (step k uses batch 1 + (k mod 4)); the steps
+run through rb3_append_batches, which builds batch k+1 while batch k merges.  value =
 new symbols per second (Msym/s) over the K timed steps, inputs resident in HBM.
 After the timed steps the index holds all 50 haplotypes (for K = 4) and is
 searched for SMEMs (>= 31 bp) of 1 M queries (lognormal lengths, median 150 bp;
@@ -171,14 +172,27 @@ def run_rb3(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    # ---- warm-up: build batch 0, then W steps merging into it ----
+    # the K timed steps' batches, back to back (device, and pinned host for e2e)
+    step_seq = np.concatenate([S.seq[off[batches[b][0]]:off[batches[b][1]]] for b in step_batch])
+    step_lens = np.concatenate([S.lens[batches[b][0]:batches[b][1]] for b in step_batch]).astype(np.int64)
+    step_ends = np.cumsum([batches[b][1] - batches[b][0] for b in step_batch]).astype(np.int64)
+    step_dev = torch.from_numpy(step_seq).to(dev)
+    step_host = torch.empty(len(step_seq), dtype=torch.uint8, pin_memory=True)
+    step_host.numpy()[:] = step_seq
+    new_syms = int(sum(ds[b] for b in step_batch))
+
+    # ---- warm-up: W batches appended to a batch-0 index ----
     idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
-    for w in range(args.warmup):
-        src = rb.rb3_build_batch(*dev_batches[1 + w % (len(batches) - 1)], opts=opts, stream=st)
-        rb.rb3_merge_opts(idx, src, opts, stream=st)
-        src.free()
+    wb = [1 + w % (len(batches) - 1) for w in range(args.warmup)]
+    if wb:
+        wseq = torch.from_numpy(np.concatenate([S.seq[off[batches[b][0]]:off[batches[b][1]]] for b in wb])).to(dev)
+        wlens = np.concatenate([S.lens[batches[b][0]:batches[b][1]] for b in wb]).astype(np.int64)
+        wends = np.cumsum([batches[b][1] - batches[b][0] for b in wb]).astype(np.int64)
+        rb.rb3_append_batches(idx, wseq, wlens, wends, opts, stream=st)
+        del wseq
     idx.free()
-    # ---- timed: fresh batch-0 index (untimed), then K steps ----
+    # ---- timed: fresh batch-0 index (untimed), then the K steps' batches, each
+    # built and merged, builds overlapping merges ----
     idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
     barrier()
     rb.rb3_profile_reset()
@@ -190,13 +204,7 @@ def run_rb3(args, rank, world, local_rank):
     t1 = torch.cuda.Event(enable_timing=True)
     barrier()
     t0.record(st)
-    new_syms = 0
-    for k in range(args.steps):
-        b = step_batch[k]
-        src = rb.rb3_build_batch(dev_batches[b][0], dev_batches[b][1], opts=opts, stream=st)
-        rb.rb3_merge_opts(idx, src, opts, stream=st)
-        src.free()
-        new_syms += ds[b]
+    rb.rb3_append_batches(idx, step_dev, step_lens, step_ends, opts, stream=st)
     t1.record(st)
     barrier()
     ms = t0.elapsed_time(t1)
@@ -217,22 +225,34 @@ def run_rb3(args, rank, world, local_rank):
         total_syms = float(new_syms)
     value = total_syms / (ms * 1e3)
 
-    # ---- e2e: same steps through the public API from pinned host buffers ----
-    e2e_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    # ---- the same steps one at a time (build, then merge): no overlap ----
+    seq_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
     barrier()
-    h2d = 0
-    e0 = time.perf_counter()
+    a_ev = torch.cuda.Event(enable_timing=True)
+    b_ev = torch.cuda.Event(enable_timing=True)
+    a_ev.record(st)
     for k in range(args.steps):
         b = step_batch[k]
-        src = rb.rb3_build_batch(host_batches[b][0], host_batches[b][1], opts=opts, stream=st)
-        rb.rb3_merge_opts(e2e_idx, src, opts, stream=st)  # reads the merged counts back (2 x 48 B)
+        src = rb.rb3_build_batch(dev_batches[b][0], dev_batches[b][1], opts=opts, stream=st)
+        rb.rb3_merge_opts(seq_idx, src, opts, stream=st)
         src.free()
-        h2d += host_batches[b][0].numel() + 8 * len(host_batches[b][1])
+    b_ev.record(st)
+    barrier()
+    seq_ms = a_ev.elapsed_time(b_ev)
+    same = bool(np.array_equal(rb.rb3_export(seq_idx), rb.rb3_export(idx)))
+    seq_idx.free()
+
+    # ---- e2e: the public call on pinned host buffers (h2d inside the call) ----
+    e2e_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    barrier()
+    e0 = time.perf_counter()
+    rb.rb3_append_batches(e2e_idx, step_host, step_lens, step_ends, opts, stream=st)  # reads merged counts back
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - e0) * 1e3
     e2e_idx.free()
     e2e = {"value": round(new_syms / (e_ms * 1e3), 3), "unit": "Msym/s",
-           "h2d_bytes_per_step": int(h2d // max(1, args.steps)), "d2h_bytes_per_step": 96}
+           "h2d_bytes_per_step": int((len(step_seq) + 8 * len(step_lens)) // max(1, args.steps)),
+           "d2h_bytes_per_step": 96}
 
     # ---- roofline of the dominant kernel (live CUDA events of the timed region) ----
     hbm, peak_kind = peaks()
@@ -256,7 +276,12 @@ def run_rb3(args, rank, world, local_rank):
                       "occ_interval": info["occ_interval"], "seg_len": args.seg_len or "auto",
                       "l2": "inputs larger than L2 (batch ~100 Msym text + 100-500 MB index per step)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-           "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases}
+           "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases,
+           "one_by_one": {"ms_per_step": round(seq_ms / args.steps, 3),
+                          "value": round(new_syms / (seq_ms * 1e3), 3), "unit": "Msym/s",
+                          "equal_output": same,
+                          "note": "each step's build then its merge, no overlap (the timed value overlaps "
+                                  "the next batch's build with the current merge)"}}
 
     # ---- comparison with the plain one-walk-per-string form on one merge ----
     if not args.no_plain and rank == 0:

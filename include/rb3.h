@@ -115,6 +115,19 @@ int rb3_index_empty(const rb3_opts *o, rb3_index **out);
 int rb3_merge(rb3_index *dst, const rb3_index *src, void *stream);
 int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_opts *o, void *stream);
 
+/* The build loop of Section "Methods": for each batch of strings, build its
+ * BWT (as rb3_build_batch) and merge it into dst (as rb3_merge), in order.
+ * The build of batch b+1 runs on the device while batch b is merged, as the
+ * paper runs partial BWT construction and BWT merge together (Table 2, note
+ * 7); this uses two internal streams (ordered after the work already on
+ * `stream`) and one host thread, and keeps at most two built batches beyond
+ * the one being merged.  seq / len: all strings back to back (host or device);
+ * batch_end[b] = number of strings in batches 0..b (non-decreasing, the last
+ * equal to n_seq).  The result is the same as building and merging the
+ * batches one by one.  Synchronizes `stream`. */
+int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *len, int64_t n_seq,
+                       const int64_t *batch_end, int64_t n_batches, const rb3_opts *o, void *stream);
+
 /* Backward search (Section "Suffix array interval and backward search"):
  * for query i = q[qoff[i] .. qoff[i+1]) writes lo_hi[2i] = lo(P) (the number of
  * suffixes smaller than P) and lo_hi[2i+1] = hi(P) = lo(P) + occ(P).

@@ -22,6 +22,8 @@ void set_error(const char *fmt, ...) {
     g_err = buf;
 }
 
+std::string rb3_last_error_str() { return g_err; }
+
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
     cudaGetLastError();  // clear a sticky-free error so later calls start clean
     set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
@@ -29,17 +31,18 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 }
 
 static void ensure_pool() {
-    static bool done = false;
-    if (done) return;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        // keep up to 64 GiB of freed scratch in the pool between calls
-        uint64_t thr = 64ull << 30;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    done = true;
+    static const bool done = [] {  // thread-safe one-time initialisation
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return false;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            // keep up to 64 GiB of freed scratch in the pool between calls
+            uint64_t thr = 64ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        return true;
+    }();
+    (void)done;
 }
 
 int dev_alloc(void **p, size_t bytes, cudaStream_t st) {

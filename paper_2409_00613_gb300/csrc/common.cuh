@@ -43,6 +43,7 @@ constexpr int HEADER_BYTES = 32;
 
 // ---- errors ---------------------------------------------------------------
 void set_error(const char *fmt, ...);
+std::string rb3_last_error_str();  // this thread's message
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
 #define RB3_CUDA_TRY(expr)                                                       \
@@ -432,6 +433,8 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
 int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n_seq, const rb3_opts &o,
                      cudaStream_t st, rb3_index *out);
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
+int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int64_t n_seq, const int64_t *batch_end,
+                   int64_t n_batches, const rb3_opts &o, cudaStream_t caller);
 int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
                          int64_t *lohi, cudaStream_t st);
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
@@ -463,13 +466,12 @@ inline int ilog2(int64_t x) {
 }
 
 inline int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {  // thread-safe one-time initialisation
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
     return sms;
 }
 

@@ -1,0 +1,189 @@
+// Incremental construction driver: build the BWT of each batch and merge it
+// into the index, one batch after another (the driver loop of Section
+// "Methods"), with the build of batch b+1 on the device while batch b is being
+// merged -- the paper runs BWT merge and partial BWT construction together
+// (Table 2, note 7) to keep its threads busy when few, long strings leave the
+// merge with little parallelism.  On one GPU the two run on separate streams
+// from two host threads.  At most one built batch waits for its merge while
+// the next is being built, which bounds the extra memory to two batches'
+// indexes and build data.
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+
+#include "common.cuh"
+
+namespace rb3 {
+
+namespace {
+
+struct Built {
+    rb3_index *idx = nullptr;
+    int code = RB3_OK;
+    std::string err;
+};
+
+struct Channel {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Built> q;
+    bool stop = false;  // consumer gave up
+};
+
+void free_built(rb3_index *x) {
+    if (!x) return;
+    dev_free(x->blocks, 0);
+    dev_free(x->text, 0);
+    dev_free(x->isa, 0);
+    cudaStreamSynchronize(0);
+    delete x;
+}
+
+}  // namespace
+
+int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int64_t n_seq, const int64_t *batch_end,
+                   int64_t n_batches, const rb3_opts &o, cudaStream_t caller) {
+    int dev = 0;
+    RB3_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<int64_t> off(n_seq + 1, 0);
+    for (int64_t i = 0; i < n_seq; ++i) off[i + 1] = off[i] + lens[i];
+    const bool seq_dev = off[n_seq] == 0 || is_device_ptr(seq);
+    cudaStream_t sb = nullptr, sm = nullptr;
+    cudaEvent_t start = nullptr;
+    RB3_CUDA_TRY(cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking));
+    RB3_CUDA_TRY(cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking));
+    RB3_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    // both internal streams start after the work already on the caller's stream
+    RB3_CUDA_TRY(cudaEventRecord(start, caller));
+    RB3_CUDA_TRY(cudaStreamWaitEvent(sb, start, 0));
+    RB3_CUDA_TRY(cudaStreamWaitEvent(sm, start, 0));
+
+    Channel ch;
+    std::thread builder([&] {
+        cudaSetDevice(dev);
+        for (int64_t b = 0; b < n_batches; ++b) {
+            const int64_t s0 = b == 0 ? 0 : batch_end[b - 1], s1 = batch_end[b];
+            Built out;
+            rb3_index *x = new rb3_index();
+            x->device = dev;
+            int r = RB3_OK;
+            DevBuf staged;
+            const uint8_t *src = seq + off[s0];
+            const size_t bytes = (size_t)(off[s1] - off[s0]);
+            if (!seq_dev && bytes) {
+                r = staged.alloc(bytes, sb);
+                if (r == RB3_OK && cudaMemcpyAsync(staged.p, src, bytes, cudaMemcpyHostToDevice, sb) != cudaSuccess)
+                    r = cuda_fail(cudaGetLastError(), "append: copy batch", __FILE__, __LINE__);
+                src = staged.as<uint8_t>();
+            }
+            if (r == RB3_OK) r = build_batch_impl(src, lens + s0, s1 - s0, o, sb, x);
+            if (r == RB3_OK && cudaStreamSynchronize(sb) != cudaSuccess)
+                r = cuda_fail(cudaGetLastError(), "append: build", __FILE__, __LINE__);
+            staged.release();
+            if (r != RB3_OK) {
+                out.code = r;
+                out.err = rb3_last_error_str();
+                free_built(x);
+            } else {
+                out.idx = x;
+            }
+            std::unique_lock<std::mutex> lk(ch.mu);
+            // hand over; wait while one built batch is already waiting for its merge
+            ch.cv.wait(lk, [&] { return ch.stop || ch.q.size() < 1; });
+            if (ch.stop) {
+                free_built(out.idx);
+                return;
+            }
+            ch.q.push_back(std::move(out));
+            ch.cv.notify_all();
+            if (r != RB3_OK) return;
+        }
+    });
+
+    int result = RB3_OK;
+    std::string err;
+    for (int64_t b = 0; b < n_batches; ++b) {
+        Built got;
+        {
+            std::unique_lock<std::mutex> lk(ch.mu);
+            ch.cv.wait(lk, [&] { return !ch.q.empty(); });
+            got = std::move(ch.q.front());
+            ch.q.pop_front();
+            ch.cv.notify_all();
+        }
+        if (got.code != RB3_OK) {
+            result = got.code;
+            err = got.err;
+            break;
+        }
+        {
+            Phase ph("append.merge", sm);
+            result = merge_impl(dst, got.idx, o, sm);
+        }
+        if (result == RB3_OK && cudaStreamSynchronize(sm) != cudaSuccess)
+            result = cuda_fail(cudaGetLastError(), "append: merge", __FILE__, __LINE__);
+        free_built(got.idx);
+        if (result != RB3_OK) {
+            err = rb3_last_error_str();
+            break;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(ch.mu);
+        ch.stop = true;
+        for (auto &g : ch.q) free_built(g.idx);
+        ch.q.clear();
+        ch.cv.notify_all();
+    }
+    builder.join();
+    cudaStreamSynchronize(sb);
+    cudaStreamSynchronize(sm);
+    cudaStreamDestroy(sb);
+    cudaStreamDestroy(sm);
+    cudaEventDestroy(start);
+    if (result != RB3_OK) set_error("%s", err.c_str());
+    return result;
+}
+
+}  // namespace rb3
+
+using namespace rb3;
+
+RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *len, int64_t n_seq,
+                                  const int64_t *batch_end, int64_t n_batches, const rb3_opts *o, void *stream) {
+    set_error("%s", "");
+    RB3_CHECK_ARG(dst != nullptr, "NULL index");
+    RB3_CHECK_ARG(n_seq >= 0 && n_batches >= 0, "negative size");
+    if (n_batches == 0) return RB3_OK;
+    RB3_CHECK_ARG(batch_end != nullptr && (n_seq == 0 || len != nullptr), "NULL argument");
+    rb3_opts opts;
+    rb3_opts_default(&opts);
+    if (o) opts = *o;
+    RB3_CHECK_ARG(dst->n == 0 || dst->single_strand == opts.single_strand,
+                  "strand mode of the batches differs from the index's");
+    std::vector<int64_t> lens(n_seq), ends(n_batches);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_seq) {
+        if (is_device_ptr(len)) RB3_CUDA_TRY(cudaMemcpy(lens.data(), len, sizeof(int64_t) * n_seq, cudaMemcpyDeviceToHost));
+        else memcpy(lens.data(), len, sizeof(int64_t) * n_seq);
+    }
+    if (is_device_ptr(batch_end))
+        RB3_CUDA_TRY(cudaMemcpy(ends.data(), batch_end, sizeof(int64_t) * n_batches, cudaMemcpyDeviceToHost));
+    else
+        memcpy(ends.data(), batch_end, sizeof(int64_t) * n_batches);
+    int64_t prev = 0, total = 0;
+    for (int64_t b = 0; b < n_batches; ++b) {
+        RB3_CHECK_ARG(ends[b] >= prev && ends[b] <= n_seq, "batch_end must be non-decreasing and <= n_seq");
+        prev = ends[b];
+    }
+    RB3_CHECK_ARG(ends[n_batches - 1] == n_seq, "batch_end[n_batches-1] must be n_seq");
+    for (int64_t i = 0; i < n_seq; ++i) {
+        RB3_CHECK_ARG(lens[i] >= 0, "negative string length");
+        total += lens[i];
+    }
+    RB3_CHECK_ARG(total == 0 || seq != nullptr, "seq is NULL");
+    RB3_TRY(append_batches(dst, seq, lens.data(), n_seq, ends.data(), n_batches, opts, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}

@@ -238,12 +238,9 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
         set_error("radix sort: too many elements (%lld)", (long long)n);
         return RB3_E_INVAL;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        RB3_CUDA_TRY(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(RsSmem)));
-        attr_set = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)sizeof(RsSmem));  // once, thread-safe
+    RB3_CUDA_TRY(attr);
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     DevBuf counts;
     RB3_TRY(counts.alloc(sizeof(uint32_t) * RS_BINS * ntiles, st));

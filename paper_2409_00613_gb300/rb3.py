@@ -52,6 +52,7 @@ def lib():
             "rb3_index_empty": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
             "rb3_merge": (ctypes.c_int, [_vp, _vp, _vp]),
             "rb3_merge_opts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rb3_append_batches": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
             "rb3_backward_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
             "rb3_mem_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
                                               ctypes.POINTER(_i64), _vp]),
@@ -177,6 +178,15 @@ def rb3_merge(dst: Index, src: Index, stream=None):
 def rb3_merge_opts(dst: Index, src: Index, opts=None, stream=None):
     o = _opts(opts)
     _check(lib().rb3_merge_opts(dst.handle, src.handle, ctypes.byref(o) if o else None, _stream(stream)))
+
+
+def rb3_append_batches(dst: Index, seq, lens, batch_end, opts=None, stream=None):
+    """Build each batch and merge it into dst, builds overlapping merges."""
+    o = _opts(opts)
+    lens_a = np.ascontiguousarray(lens, dtype=np.int64) if not hasattr(lens, "data_ptr") else lens
+    ends = np.ascontiguousarray(batch_end, dtype=np.int64)
+    _check(lib().rb3_append_batches(dst.handle, _ptr(seq), _ptr(lens_a), _len(lens_a), _ptr(ends), len(ends),
+                                    ctypes.byref(o) if o else None, _stream(stream)))
 
 
 def rb3_backward_search(idx: Index, q, qoff, nq=None, lo_hi=None, stream=None):

@@ -209,3 +209,34 @@ def test_save_load_resume(tmp_path):
     rb.rb3_merge(idx, build(S, 4, 6))
     check_index(back, ref_bwt(S))
     check_index(idx, ref_bwt(S))
+
+
+def test_append_batches_pipeline():
+    """Build-and-merge of several batches with builds overlapping merges equals
+    building and merging them one by one (and the oracle)."""
+    S = synth.pangenome(seed=71, founder_len=40_000, n_hap=15, batch=3)
+    want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=4)
+    ends = np.array([b for (_, b) in S.batches[1:]], dtype=np.int64) - S.batches[0][1]
+    off = S.offsets
+    rest = S.seq[off[S.batches[0][1]]:]
+    lens = S.lens[S.batches[0][1]:].copy()
+    for host in (False, True):
+        idx = build(S, 0, S.batches[0][1])
+        seq = rest.copy() if host else torch.from_numpy(rest.copy()).to(DEV)
+        rb.rb3_append_batches(idx, seq, lens, ends)
+        check_index(idx, want)
+    # an empty index as the start, batches of different sizes, empty batches
+    idx = rb.rb3_index_empty()
+    rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens.copy(),
+                          np.array([0, 2, 2, 7, 15], dtype=np.int64))
+    check_index(idx, want)
+
+
+def test_append_batches_error_propagates():
+    S = synth.pangenome(seed=72, founder_len=5_000, n_hap=6, batch=2)
+    seq = S.seq.copy()
+    seq[S.offsets[4] + 10] = 9  # invalid symbol in the third batch
+    idx = rb.rb3_index_empty()
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_append_batches(idx, seq, S.lens.copy(), np.array([2, 4, 6], dtype=np.int64))
+    assert e.value.code == rb.RB3_E_INVAL
