@@ -208,7 +208,9 @@ int64_t rb3_launch_count(void);
  * larger than L2), with threads_per_sm threads on every SM.  dependent = 0:
  * each thread keeps 4 independent reads in flight; dependent = 1: each thread
  * follows a chain whose next address depends on the data read (the pattern of
- * an LF walk).  Writes the delivered GB/s and millions of reads per second. */
+ * an LF walk); 2 and 3: the same with bytes_per_access/32 lanes reading the
+ * sectors of one access in a single instruction (one request per access).
+ * Writes the delivered GB/s and millions of reads per second. */
 int rb3_probe_random_gather(int32_t bytes_per_access, int32_t dependent, int32_t threads_per_sm, int64_t buffer_bytes,
                             double *gbs, double *maccess_per_s, void *stream);
 

@@ -65,6 +65,30 @@ __global__ void k_probe_chain(const uint8_t *__restrict__ buf, uint64_t nunits, 
     if (acc == 0x9e3779b9u) sink[0] = acc;
 }
 
+// Cooperative forms: the NSEC lanes of a group read the NSEC sectors of one
+// unit in the same instruction (one request per unit instead of one per
+// sector).  Dependent: the group's next address comes from the data of all
+// its lanes (shuffled together).
+template <int NSEC>
+__global__ void k_probe_coop(const uint8_t *__restrict__ buf, uint64_t nunits, int iters, int dependent, uint64_t seed,
+                             uint32_t *__restrict__ sink) {
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t grp = t / NSEC;
+    const int sub = (int)(t % NSEC);
+    uint32_t acc = 0;
+    uint64_t u = mix64(seed ^ grp) % nunits;
+    for (int i = 0; i < iters; ++i) {
+        if (!dependent) u = mix64(seed ^ (grp * (uint64_t)iters + i)) % nunits;
+        Sec s = ld_sec(buf + u * (32 * NSEC) + 32 * sub);
+        uint32_t v = s.w[0] + s.w[7];
+#pragma unroll
+        for (int d = 1; d < NSEC; d <<= 1) v ^= __shfl_xor_sync(0xffffffffu, v, d, NSEC);
+        acc += v;
+        if (dependent) u = mix64(u ^ v ^ (uint64_t)i) % nunits;
+    }
+    if (acc == 0x9e3779b9u) sink[0] = acc;
+}
+
 int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t buffer_bytes, double *gbs,
                         double *maccess, cudaStream_t st) {
     RB3_CHECK_ARG(bytes == 32 || bytes == 64 || bytes == 128, "bytes must be 32, 64 or 128");
@@ -90,7 +114,12 @@ int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t bu
         const uint8_t *p = buf.as<uint8_t>();
         uint32_t *s = sink.as<uint32_t>();
         uint64_t seed = 1000 + rep;
-        if (dependent) {
+        if (dependent >= 2) {  // cooperative: 2 = independent, 3 = dependent
+            const int dep = dependent == 3;
+            if (bytes == 32) RB3_LAUNCH(k_probe_coop<1>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
+            else if (bytes == 64) RB3_LAUNCH(k_probe_coop<2>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
+            else RB3_LAUNCH(k_probe_coop<4>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
+        } else if (dependent) {
             if (bytes == 32) RB3_LAUNCH(k_probe_chain<1>, grid, block, 0, st, p, nunits, iters, seed, s);
             else if (bytes == 64) RB3_LAUNCH(k_probe_chain<2>, grid, block, 0, st, p, nunits, iters, seed, s);
             else RB3_LAUNCH(k_probe_chain<4>, grid, block, 0, st, p, nunits, iters, seed, s);
@@ -108,6 +137,7 @@ int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t bu
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     double accesses = (double)threads * iters;
+    if (dependent >= 2) accesses /= (bytes / 32);  // one access per lane group
     if (gbs) *gbs = accesses * bytes / (best * 1e-3) / 1e9;
     if (maccess) *maccess = accesses / (best * 1e-3) / 1e6;
     return RB3_OK;
