@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--seg-len", type=int, default=0)
     p.add_argument("--occ", type=int, default=64)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-full", action="store_true",
+                   help="also build the served index (20 haplotypes of a 150 Mb founder, ~6 Gsym) and serve on it")
     return p.parse_args()
 
 
@@ -290,7 +293,11 @@ def run_rb3(args, rank, world, local_rank):
     # ---- MEM search on the finished index ----
     if not args.no_search and rank == 0:
         out["mem_search"] = mem_search(rb, torch, S, idx, args, st, dev)
+        if not args.no_serve:
+            out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
     idx.free()
+    if args.serve_full and rank == 0:
+        out["served_full"] = served_full(rb, torch, st, dev, opts)
     if rank == 0 and not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_sample(S)
     if world > 1:
@@ -356,6 +363,75 @@ def mem_search(rb, torch, S, idx, args, st, dev):
         res["smems"] = int(n)
     res["speedup_vs_plain"] = round(res["value"] / res["plain_value"], 2)
     return res
+
+
+def _serve_trace(rb, srv, arr, Q):
+    """Open-loop replay: submit each request at its arrival time, collect
+    completions; latency = completion time - scheduled arrival time."""
+    n = Q.nq
+    qs = [Q.q[Q.qoff[i]:Q.qoff[i + 1]] for i in range(n)]
+    t0 = time.monotonic_ns() + 20_000_000
+    sched = t0 + (arr * 1e9).astype(np.int64)
+    done = []
+    i = 0
+    while i < n or len(done) < n:
+        now = time.monotonic_ns()
+        while i < n and sched[i] <= now:
+            rb.rb3_server_submit(srv, qs[i], i)
+            i += 1
+        if i < n:
+            wait_us = int(max(0, min(2000, (sched[i] - time.monotonic_ns()) // 1000)))
+        else:
+            wait_us = 20000
+        c = rb.rb3_server_poll(srv, 8192, wait_us)
+        for r in c:
+            done.append((int(r["tag"]), int(r["t_done_ns"]), int(r["batch_requests"])))
+            rb.rb3_server_take(srv, r["req_id"], int(r["n_smem"]))
+    lat = np.array([(td - sched[tag]) / 1e6 for tag, td, _ in done])
+    last = max(td for _, td, _ in done)
+    bp = int(Q.qoff[-1])
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "Mbp_per_s": round(bp / ((last - t0) / 1e9) / 1e6, 1),
+            "mean_batch": round(float(np.mean([b for _, _, b in done])), 2)}
+
+
+def served(rb, S, idx, index_desc, rates=(2000, 10000, 50000), n_cap=10000):
+    """Poisson arrivals, query lengths log-uniform in [100, 100000] bp with 0.1-5%
+    substitutions (the served workload's request law); continuous batching (4
+    slots) against the plain server (one request at a time, one slot)."""
+    res = {"index": index_desc, "requests": "Poisson arrivals; lengths log-uniform 100 bp-100 kb; "
+                                            "0.1-5% substitutions; SMEMs >= 31 bp", "rates": {}}
+    for rate in rates:
+        n = min(n_cap, int(rate))
+        arr, Q = synth.served_requests(S, rate=float(rate), n_req=n)
+        row = {"n_requests": n, "offered_Mbp_per_s": round(float(Q.qoff[-1]) / arr[-1] / 1e6, 1)}
+        for name, kw in (("batched", dict(slots=4)), ("plain", dict(slots=1, max_batch_requests=1))):
+            srv = rb.rb3_server_create(idx, **kw)
+            row[name] = _serve_trace(rb, srv, arr, Q)
+            srv.close()
+        res["rates"][str(rate)] = row
+    return res
+
+
+def served_full(rb, torch, st, dev, opts):
+    """The served workload on its own index: 20 haplotypes of a 150 Mb founder,
+    built through rb3_append_batches in batches of 4 haplotypes."""
+    S = synth.served_index_strings()
+    off = S.offsets
+    seq = torch.from_numpy(S.seq).to(dev)
+    idx = rb.rb3_index_empty(opts)
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    t = time.perf_counter()
+    rb.rb3_append_batches(idx, seq, S.lens.copy(), ends, opts, stream=st)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t
+    del seq
+    info = rb.rb3_index_info(idx)
+    out = {"index_symbols": info["n"], "build_s": round(build_s, 2),
+           "build_Msym_per_s": round(info["n"] / build_s / 1e6, 1),
+           "served": served(rb, S, idx, "served index: 20 haplotypes of a 150 Mb founder (~6 Gsym)")}
+    idx.free()
+    return out
 
 
 # ---------------------------------------------------------------------------

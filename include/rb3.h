@@ -165,6 +165,46 @@ int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *q
 int rb3_mem_search_noalloc(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
                            int64_t min_occ, rb3_smem *out, int64_t cap, int64_t *n_out, void *stream);
 
+/* ---- Served SMEM search (continuous batching) ----------------------------
+ * A server keeps an index resident and answers SMEM requests (one query each)
+ * as they arrive.  `slots` worker threads, each with its own stream and fixed
+ * buffers, take every waiting request that fits a budget of query bases (a
+ * longer request alone) as soon as they are free, and run them as one chunked
+ * micro-batch (as rb3_mem_search); requests arriving while others run are
+ * admitted by the next free slot, so micro-batches overlap on the device.
+ * Each request gets exactly the SMEMs rb3_mem_search gives for its query
+ * alone (qid field 0).  The index must outlive the server and must not be
+ * merged into while it serves. */
+typedef struct rb3_server rb3_server;
+
+typedef struct {
+    int32_t min_len;            /* SMEM length threshold (default 31) */
+    int32_t slots;              /* micro-batches in flight (default 4) */
+    int64_t min_occ;            /* occurrence threshold (default 1) */
+    int64_t max_batch_bases;    /* query bases per micro-batch (default 8 Mi) */
+    int64_t max_batch_requests; /* requests per micro-batch (default 4096; 1 = no batching) */
+    int64_t reserved[4];
+} rb3_server_opts;
+
+typedef struct {
+    int64_t req_id, tag, n_smem;
+    int32_t status;         /* RB3_OK or the error of its micro-batch */
+    int32_t batch_requests; /* size of the micro-batch it ran in */
+    int64_t t_submit_ns;    /* CLOCK_MONOTONIC at rb3_server_submit */
+    int64_t t_done_ns;      /* CLOCK_MONOTONIC when its results reached the host */
+} rb3_completion;
+
+void rb3_server_opts_default(rb3_server_opts *o);
+int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o, rb3_server **out);
+/* Queues one query (host memory, copied; codes 1..5); returns at once. */
+int rb3_server_submit(rb3_server *s, const uint8_t *q, int64_t len, int64_t tag, int64_t *req_id);
+/* Up to cap completions, oldest first; waits up to wait_us for the first. */
+int rb3_server_poll(rb3_server *s, rb3_completion *out, int64_t cap, int64_t *n, int32_t wait_us);
+/* Copies a completed request's SMEMs (start-ordered) and releases them. */
+int rb3_server_take(rb3_server *s, int64_t req_id, rb3_smem *out, int64_t cap, int64_t *n);
+int64_t rb3_server_batches(rb3_server *s);
+void rb3_server_destroy(rb3_server *s);
+
 /* Unpacks B into codes (n bytes, one symbol per byte) and, when occ != NULL,
  * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */
 int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);

@@ -30,6 +30,15 @@ class rb3_opts(ctypes.Structure):
                 ("chunk_len", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
 
 
+class rb3_server_opts(ctypes.Structure):
+    _fields_ = [("min_len", ctypes.c_int32), ("slots", ctypes.c_int32), ("min_occ", ctypes.c_int64),
+                ("max_batch_bases", ctypes.c_int64), ("max_batch_requests", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+COMPLETION_DTYPE = np.dtype([("req_id", "<i8"), ("tag", "<i8"), ("n_smem", "<i8"), ("status", "<i4"),
+                             ("batch_requests", "<i4"), ("t_submit_ns", "<i8"), ("t_done_ns", "<i8")])
+
 SMEM_DTYPE = np.dtype([("qid", "<i8"), ("start", "<i4"), ("end", "<i4"), ("k", "<i8"), ("kp", "<i8"),
                        ("s", "<i8")])
 assert SMEM_DTYPE.itemsize == 40
@@ -75,6 +84,13 @@ def lib():
                                                 ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _i32,
                                                 ctypes.POINTER(_i32)]),
             "rb3_launch_count": (_i64, []),
+            "rb3_server_opts_default": (None, [_vp]),
+            "rb3_server_create": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+            "rb3_server_submit": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_i64)]),
+            "rb3_server_poll": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64), _i32]),
+            "rb3_server_take": (ctypes.c_int, [_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)]),
+            "rb3_server_batches": (_i64, [_vp]),
+            "rb3_server_destroy": (None, [_vp]),
             "rb3_probe_random_gather": (ctypes.c_int, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double),
                                                        ctypes.POINTER(ctypes.c_double), _vp]),
         }
@@ -316,3 +332,61 @@ def rb3_probe_random_gather(bytes_per_access: int, dependent: bool, threads_per_
     _check(lib().rb3_probe_random_gather(int(bytes_per_access), int(dependent), int(threads_per_sm),
                                          int(buffer_bytes), ctypes.byref(g), ctypes.byref(m), _stream(stream)))
     return g.value, m.value
+
+
+class Server:
+    """Owns one rb3_server (served SMEM search with continuous batching)."""
+
+    def __init__(self, handle: int, index: "Index"):
+        self.handle = handle
+        self.index = index  # keeps the index alive while serving
+
+    def close(self):
+        if self.handle:
+            lib().rb3_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rb3_server_create(idx: Index, **opts) -> Server:
+    o = rb3_server_opts()
+    lib().rb3_server_opts_default(ctypes.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, int(v))
+    out = _vp()
+    _check(lib().rb3_server_create(idx.handle, ctypes.byref(o), ctypes.byref(out)))
+    return Server(out.value, idx)
+
+
+def rb3_server_submit(srv: Server, q, tag: int = 0) -> int:
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    rid = _i64()
+    _check(lib().rb3_server_submit(srv.handle, q.ctypes.data if q.size else None, q.size, int(tag), ctypes.byref(rid)))
+    return rid.value
+
+
+def rb3_server_poll(srv: Server, cap: int = 4096, wait_us: int = 0) -> np.ndarray:
+    out = np.empty(cap, dtype=COMPLETION_DTYPE)
+    n = _i64()
+    _check(lib().rb3_server_poll(srv.handle, out.ctypes.data, cap, ctypes.byref(n), int(wait_us)))
+    return out[:n.value]
+
+
+def rb3_server_take(srv: Server, req_id: int, n_smem: int) -> np.ndarray:
+    out = np.empty(max(1, n_smem), dtype=SMEM_DTYPE)
+    n = _i64()
+    _check(lib().rb3_server_take(srv.handle, int(req_id), out.ctypes.data, len(out), ctypes.byref(n)))
+    return out[:n.value]
+
+
+def rb3_server_batches(srv: Server) -> int:
+    return int(lib().rb3_server_batches(srv.handle))
+
+
+def rb3_server_destroy(srv: Server):
+    srv.close()
