@@ -184,8 +184,17 @@ def run_rb3(args, rank, world, local_rank):
     step_host.numpy()[:] = step_seq
     new_syms = int(sum(ds[b] for b in step_batch))
 
-    # ---- warm-up: W batches appended to a batch-0 index ----
+    # ---- autotune the merge's segment length on batch 1 into batch 0 (untimed) ----
     idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    tune = {}
+    if not args.seg_len:
+        src = rb.rb3_build_batch(*dev_batches[1], opts=opts, stream=st)
+        best, tms = rb.rb3_tune_merge(idx, src, opts, stream=st)
+        src.free()
+        opts["seg_len"] = int(best.seg_len)
+        tune = {"seg_len": int(best.seg_len), "walk_ms": round(tms, 3),
+                "candidates": "default L0 = n2/(SMs*512) and L0/2, 2*L0, 4*L0"}
+    # ---- warm-up: W batches appended to a batch-0 index ----
     wb = [1 + w % (len(batches) - 1) for w in range(args.warmup)]
     if wb:
         wseq = torch.from_numpy(np.concatenate([S.seq[off[batches[b][0]]:off[batches[b][1]]] for b in wb])).to(dev)
@@ -276,10 +285,11 @@ def run_rb3(args, rank, world, local_rank):
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "founder_bp": founder, "haplotypes": 50, "batch_haplotypes": 10,
                       "new_symbols_per_gpu": new_syms, "final_index_symbols": info["n"],
-                      "occ_interval": info["occ_interval"], "seg_len": args.seg_len or "auto",
+                      "occ_interval": info["occ_interval"], "seg_len": opts["seg_len"],
                       "l2": "inputs larger than L2 (batch ~100 Msym text + 100-500 MB index per step)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases,
+           "autotune": tune,
            "one_by_one": {"ms_per_step": round(seq_ms / args.steps, 3),
                           "value": round(new_syms / (seq_ms * 1e3), 3), "unit": "Msym/s",
                           "equal_output": same,
@@ -345,8 +355,12 @@ def mem_search(rb, torch, S, idx, args, st, dev):
            "query_bp": bp, "unit": "Mbp/s"}
     cap = max(1 << 20, bp // 16)
     out = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
+    # autotune the chunk length on the first 100k queries (untimed)
+    ns = min(Q.nq, 100_000)
+    best, tms = rb.rb3_tune_search(idx, q[:int(Q.qoff[ns])], qoff[:ns + 1], 31, 1, stream=st)
+    res["autotune_chunk_len"] = int(best.chunk_len)
     for form, key in ((0, "value"), (1, "plain_value")):
-        o = {"search_form": form}
+        o = {"search_form": form, "chunk_len": int(best.chunk_len)}
         reps = 2 if form == 0 else 1
         _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up
         torch.cuda.synchronize()

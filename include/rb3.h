@@ -205,6 +205,20 @@ int rb3_server_take(rb3_server *s, int64_t req_id, rb3_smem *out, int64_t cap, i
 int64_t rb3_server_batches(rb3_server *s);
 void rb3_server_destroy(rb3_server *s);
 
+/* ---- Autotuner (no counterpart in the paper; tunes this build's knobs) ----
+ * rb3_tune_merge times the merge's walk phase (into scratch: dst and src are
+ * not modified) for several segment lengths around the default and writes the
+ * fastest into best->seg_len; rb3_tune_search times the chunked SMEM search
+ * (q, qoff: device) for several chunk lengths and writes best->chunk_len.  The
+ * choice is remembered per input shape (device, D, strand mode, log2 size
+ * classes) and used by rb3_merge / rb3_mem_search when their knob is 0; with
+ * RB3_TUNE_FILE set it is also persisted there.  best_ms (optional) receives
+ * the winner's time.  Both synchronize the stream. */
+int rb3_tune_merge(const rb3_index *dst, const rb3_index *src, const rb3_opts *base, rb3_opts *best, double *best_ms,
+                   void *stream);
+int rb3_tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
+                    int64_t min_occ, const rb3_opts *base, rb3_opts *best, double *best_ms, void *stream);
+
 /* Unpacks B into codes (n bytes, one symbol per byte) and, when occ != NULL,
  * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */
 int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);

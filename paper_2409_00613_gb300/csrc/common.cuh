@@ -433,6 +433,10 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
 int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n_seq, const rb3_opts &o,
                      cudaStream_t st, rb3_index *out);
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
+int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos);
+// Autotuner memory (tune.cu): 0 when nothing was tuned for this input shape.
+int64_t tuned_seg_len(const rb3_index *dst, const rb3_index *src);
+int64_t tuned_chunk_len(const rb3_index *idx, int64_t nq, int64_t total_q);
 int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int64_t n_seq, const int64_t *batch_end,
                    int64_t n_batches, const rb3_opts &o, cudaStream_t caller);
 int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,

@@ -351,27 +351,11 @@ __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
     if (k < n) pos[k] = k;
 }
 
-int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
-    RB3_CHECK_ARG(dst != src, "dst and src must differ");
-    RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
-                  "cannot merge a single-strand index with a double-strand one");
-    if (src->n == 0) return RB3_OK;
-    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
-    if (nM >= (int64_t(1) << 40)) {
-        set_error("merged index would exceed 2^40 symbols");
-        return RB3_E_INVAL;
-    }
-    // output layout: D of dst (or of src when dst is empty)
-    int D = n1 ? dst->D : src->D;
-    int log2D = ilog2(D), bb = HEADER_BYTES + D / 2;
-    int64_t nbM = nM / D + 1;
-    int64_t ntiles = (nbM * D + MT - 1) / MT;
-    DevBuf posb, kst, Mb, tbase;
-    RB3_TRY(posb.alloc(sizeof(int64_t) * n2, st));
-    RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
-    RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
-    RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
-    int64_t *pos = posb.as<int64_t>();
+// pos[k] = merged row of every B2 row k (the walk of Algorithm 1), into a
+// caller-provided array of src->n entries; dst and src are not modified.
+int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos) {
+    const int64_t n1 = dst->n, n2 = src->n;
+    if (n2 == 0) return RB3_OK;
     OccView V1 = occ_view(dst), V2 = occ_view(src);
     const int64_t m1 = dst->m, m2 = src->m;
     {
@@ -399,6 +383,7 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
         } else {
             // segment plan (host): strings of src from its sentinel positions
             int64_t L = o.seg_len;
+            if (L <= 0) L = tuned_seg_len(dst, src);  // the autotuner's choice for this shape, if any
             if (L <= 0) {
                 // about 512 segments per SM, length clamped to [512, 16384]
                 int64_t target = (int64_t)num_sms() * 512;
@@ -475,6 +460,33 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
             }
         }
     }
+    return RB3_OK;
+}
+
+int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
+    RB3_CHECK_ARG(dst != src, "dst and src must differ");
+    RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
+                  "cannot merge a single-strand index with a double-strand one");
+    if (src->n == 0) return RB3_OK;
+    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
+    if (nM >= (int64_t(1) << 40)) {
+        set_error("merged index would exceed 2^40 symbols");
+        return RB3_E_INVAL;
+    }
+    // output layout: D of dst (or of src when dst is empty)
+    int D = n1 ? dst->D : src->D;
+    int log2D = ilog2(D), bb = HEADER_BYTES + D / 2;
+    int64_t nbM = nM / D + 1;
+    int64_t ntiles = (nbM * D + MT - 1) / MT;
+    DevBuf posb, kst, Mb, tbase;
+    RB3_TRY(posb.alloc(sizeof(int64_t) * n2, st));
+    RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
+    RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
+    RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
+    int64_t *pos = posb.as<int64_t>();
+    OccView V1 = occ_view(dst), V2 = occ_view(src);
+    const int64_t m1 = dst->m, m2 = src->m;
+    RB3_TRY(merge_positions(dst, src, o, st, pos));
     {
         Phase ph("merge.scatter", st);
         RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst.as<int64_t>());

@@ -148,7 +148,8 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
     *n_out = 0;
     if (nq == 0) return RB3_OK;
     OccView V = occ_view(idx);
-    int64_t chunk = o.chunk_len > 0 ? o.chunk_len : 256;
+    int64_t chunk = o.chunk_len > 0 ? o.chunk_len : tuned_chunk_len(idx, nq, total_q);
+    if (chunk <= 0) chunk = 256;
     const bool plain = o.search_form == 1;
     std::vector<int64_t> item_off;
     int64_t nitems = nq;

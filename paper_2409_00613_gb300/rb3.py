@@ -84,6 +84,9 @@ def lib():
                                                 ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _i32,
                                                 ctypes.POINTER(_i32)]),
             "rb3_launch_count": (_i64, []),
+            "rb3_tune_merge": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+            "rb3_tune_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp,
+                                               ctypes.POINTER(ctypes.c_double), _vp]),
             "rb3_server_opts_default": (None, [_vp]),
             "rb3_server_create": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
             "rb3_server_submit": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_i64)]),
@@ -252,6 +255,26 @@ def rb3_mem_search_noalloc(idx: Index, q, qoff, min_len: int, min_occ: int, out,
     _check(lib().rb3_mem_search_noalloc(idx.handle, _ptr(q), _ptr(qoff), nq, int(min_len), int(min_occ), _ptr(out),
                                         int(cap), ctypes.byref(n_out), _stream(stream)))
     return int(n_out.value)
+
+
+def rb3_tune_merge(dst: Index, src: Index, opts=None, stream=None):
+    """(best rb3_opts, ms of the best walk phase) for merging src into dst."""
+    o = _opts(opts) or rb3_opts_default()
+    best = rb3_opts()
+    ms = ctypes.c_double()
+    _check(lib().rb3_tune_merge(dst.handle, src.handle, ctypes.byref(o), ctypes.byref(best), ctypes.byref(ms),
+                                _stream(stream)))
+    return best, ms.value
+
+
+def rb3_tune_search(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opts=None, stream=None):
+    """(best rb3_opts, ms) of the chunked SMEM search on these (device) queries."""
+    o = _opts(opts) or rb3_opts_default()
+    best = rb3_opts()
+    ms = ctypes.c_double()
+    _check(lib().rb3_tune_search(idx.handle, _ptr(q), _ptr(qoff), _len(qoff) - 1, int(min_len), int(min_occ),
+                                 ctypes.byref(o), ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
+    return best, ms.value
 
 
 def rb3_index_info(idx: Index) -> dict:

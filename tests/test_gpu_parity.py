@@ -240,3 +240,21 @@ def test_append_batches_error_propagates():
     with pytest.raises(rb.RB3Error) as e:
         rb.rb3_append_batches(idx, seq, S.lens.copy(), np.array([2, 4, 6], dtype=np.int64))
     assert e.value.code == rb.RB3_E_INVAL
+
+
+def test_autotuner_choices_keep_results():
+    S = synth.pangenome(seed=91, founder_len=50_000, n_hap=8, batch=4)
+    want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=4)
+    idx = build(S, 0, 4)
+    src = build(S, 4, 8)
+    best, ms = rb.rb3_tune_merge(idx, src)
+    assert best.seg_len >= 256 and ms > 0
+    check_index(idx, oracle.bwt(oracle.concat(S.subset(0, 4).seq, S.subset(0, 4).lens, True)))  # untouched
+    rb.rb3_merge(idx, src)  # uses the remembered segment length
+    check_index(idx, want)
+    Q = synth.mem_queries(S, seed=92, nq=2000, median=150, lo=31, hi=3000)
+    q, qoff = torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV)
+    best, ms = rb.rb3_tune_search(idx, q, qoff, 31, 1)
+    assert best.chunk_len in (64, 128, 256, 512, 1024, 4096)
+    recs, n = rb.rb3_mem_search(idx, q, qoff, 31, 1)
+    assert np.array_equal(smem_rows(recs, n), oracle.smem(want, Q.q, Q.qoff, 31, 1))
