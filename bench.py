@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--seg-len", type=int, default=0)
-    p.add_argument("--occ", type=int, default=64)
+    p.add_argument("--walk-ctas", type=int, default=0, help="merge walk CTAs per SM (0 = library default)")
+    p.add_argument("--occ", type=int, default=32)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-full", action="store_true",
                    help="also build the served index (20 haplotypes of a 150 Mb founder, ~6 Gsym) and serve on it")
@@ -166,7 +167,7 @@ def run_rb3(args, rank, world, local_rank):
         pinned.numpy()[:] = seq
         host_batches.append((pinned, lens))
     ds = [int(2 * (lens.sum() + len(lens))) for (_, lens) in dev_batches]
-    opts = {"occ_interval": args.occ, "seg_len": args.seg_len}
+    opts = {"occ_interval": args.occ, "seg_len": args.seg_len, "walk_ctas_per_sm": args.walk_ctas}
     step_batch = [1 + (k % (len(batches) - 1)) for k in range(args.steps)]
 
     def barrier():

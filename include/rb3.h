@@ -61,21 +61,28 @@ extern "C" {
  * bytes at 24..29) followed by D/2 payload bytes: every 64 symbols form one
  * 32-byte sector holding their 4-bit codes bit-sliced, as four 64-bit planes
  * (plane j, bytes 8j..8j+7, has bit o set iff bit j of the code of symbol o is
- * set; plane 3 is zero since codes are 0..5).  An index returned by rb3_build_batch also keeps
+ * set; plane 3 is zero since codes are 0..5).  D = 32 packs a whole block into
+ * one 32-byte sector, so that a rank is a single memory request: uint32 words
+ * 0..4 hold rank_B(a, b*32) for a = A..N minus rank_B(a, s*2^32) for the span
+ * s = (b*32) >> 32 the block lies in (the index keeps those span bases, one row
+ * per 2^32 symbols), and words 5..7 are the three 32-bit planes of its 32 codes;
+ * rank_B($, l) = l minus the other five.  An index returned by rb3_build_batch also keeps
  * the batch's text and inverse suffix array, which rb3_merge uses to walk the
  * new strings in segments; rb3_drop_build_data frees them. */
 typedef struct rb3_index rb3_index;
 
 /* Tuning knobs.  Zero in any field means "default / autotuned". */
 typedef struct {
-    int32_t occ_interval;  /* D, symbols per Occ block: 64, 128 or 256 (default 64) */
+    int32_t occ_interval;  /* D, symbols per Occ block: 32, 64, 128 or 256 (default 32) */
     int32_t single_strand; /* 0: index both strands (the paper's default, Section "Methods"); 1: forward only */
     int64_t seg_len;       /* merge: walk segment length L (default: autotuned) */
     int64_t seed_cap;      /* merge: most ForwardExt steps spent on one segment seed (default 4*L) */
     int32_t merge_form;    /* 0: segmented batched walk; 1: plain Algorithm 1, one walk per string */
     int32_t search_form;   /* 0: chunked work-stealing SMEM search; 1: plain, one query per thread */
     int64_t chunk_len;     /* SMEM: query chunk length (default 256) */
-    int32_t reserved[8];
+    int32_t walk_ctas_per_sm; /* merge: 256-thread CTAs per SM in the persistent walk's grid, 1..8
+                                 (default 8, of which 4 are resident at once) */
+    int32_t reserved[7];
 } rb3_opts;
 
 /* One SMEM: query qid, query interval [start, end), and the SA bi-interval
@@ -232,7 +239,7 @@ int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int
 int rb3_drop_build_data(rb3_index *idx);
 
 /* Static on-disk image (header + the packed blocks, which already hold the
- * Occ checkpoints), in the spirit of the paper's static, memory-mappable BWT
+ * Occ checkpoints, + the span bases of a D = 32 index past 2^32), in the spirit of the paper's static, memory-mappable BWT
  * (Section "BWT construction").  Appending after a load continues the build. */
 int rb3_index_save(const rb3_index *idx, const char *path);
 int rb3_index_load(const char *path, void *stream, rb3_index **out);

@@ -152,7 +152,8 @@ __global__ void k_unpack(OccView V, uint8_t *__restrict__ codes) {
     if (q0 >= V.n) return;
     const uint8_t *blk = V.blocks + (q0 >> V.log2D) * (int64_t)V.bb;
     int o = (int)(q0 & ((1 << V.log2D) - 1));
-    uint32_t p0 = blk[plane_byte(o, 0)], p1 = blk[plane_byte(o, 1)], p2 = blk[plane_byte(o, 2)];
+    uint32_t p0 = blk[plane_byte(o, 0, V.log2D)], p1 = blk[plane_byte(o, 1, V.log2D)],
+             p2 = blk[plane_byte(o, 2, V.log2D)];
     for (int j = 0; j < 8 && q0 + j < V.n; ++j)
         codes[q0 + j] = (uint8_t)(((p0 >> j) & 1u) | (((p1 >> j) & 1u) << 1) | (((p2 >> j) & 1u) << 2));
 }
@@ -161,6 +162,12 @@ __global__ void k_occ_export(OccView V, int64_t nblocks, int64_t *__restrict__ o
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nblocks) return;
     const uint8_t *h = V.blocks + b * (int64_t)V.bb;
+    if (V.log2D == 5) {  // D = 32: the rank at the block start (offset 0)
+        int64_t r[SIGMA];
+        rank_all<0>(V, b * 32, r);
+        for (int a = 0; a < SIGMA; ++a) occ[b * SIGMA + a] = r[a];
+        return;
+    }
     for (int a = 0; a < SIGMA; ++a)
         occ[b * SIGMA + a] = (int64_t)(*reinterpret_cast<const uint32_t *>(h + 4 * a)) | ((int64_t)h[24 + a] << 32);
 }
@@ -176,12 +183,12 @@ int export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t s
 }
 
 static int make_empty(const rb3_opts *o, cudaStream_t st, rb3_index **out) {
-    int D = (o && o->occ_interval) ? o->occ_interval : 64;
-    RB3_CHECK_ARG(D == 64 || D == 128 || D == 256, "occ_interval must be 64, 128 or 256");
+    int D = (o && o->occ_interval) ? o->occ_interval : kDefaultOccInterval;
+    RB3_CHECK_ARG(valid_occ_interval(D), "occ_interval must be 32, 64, 128 or 256");
     rb3_index *x = new rb3_index();
     x->D = D;
     x->log2D = ilog2(D);
-    x->block_bytes = HEADER_BYTES + D / 2;
+    x->block_bytes = block_bytes_for(D);
     x->single_strand = (o && o->single_strand) ? 1 : 0;
     x->nblocks = 1;
     cudaGetDevice(&x->device);
@@ -205,6 +212,7 @@ static void free_index(rb3_index *x) {
     if (!x) return;
     cudaStream_t st = 0;
     dev_free(x->blocks, st);
+    dev_free(x->gbase, st);
     dev_free(x->text, st);
     dev_free(x->isa, st);
     cudaStreamSynchronize(st);
@@ -459,6 +467,14 @@ RB3_EXPORT int rb3_index_save(const rb3_index *idx, const char *path) {
                        idx->C[6], idx->nblocks, ((int64_t)idx->D << 8) | (idx->single_strand ? 1 : 0)};
     bool ok = fwrite(k_magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               fwrite(host.data(), 1, bytes, f) == bytes;
+    if (ok && idx->gbase) {  // D = 32 past 2^32 symbols: the span bases follow the blocks
+        std::vector<int64_t> gb(5 * gbase_rows(idx->n));
+        if (cudaMemcpy(gb.data(), idx->gbase, sizeof(int64_t) * gb.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            return cuda_fail(cudaGetLastError(), "rb3_index_save", __FILE__, __LINE__);
+        }
+        ok = fwrite(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
+    }
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
         set_error("write to %s failed", path);
@@ -485,7 +501,7 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     }
     int D = (int)(hdr[11] >> 8);
     int64_t n = hdr[1], nblocks = hdr[10];
-    if (!(D == 64 || D == 128 || D == 256) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
+    if (!valid_occ_interval(D) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
         fclose(f);
         set_error("%s: inconsistent header", path);
         return RB3_E_IO;
@@ -496,13 +512,18 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     for (int a = 0; a < 7; ++a) x->C[a] = hdr[3 + a];
     x->D = D;
     x->log2D = ilog2(D);
-    x->block_bytes = HEADER_BYTES + D / 2;
+    x->block_bytes = block_bytes_for(D);
     x->single_strand = (int)(hdr[11] & 1);
     x->nblocks = nblocks;
     cudaGetDevice(&x->device);
     size_t bytes = (size_t)nblocks * x->block_bytes;
     std::vector<uint8_t> host(bytes);
     bool ok = fread(host.data(), 1, bytes, f) == bytes;
+    std::vector<int64_t> gb;
+    if (ok && D == 32 && (n >> GSPAN_LOG2)) {
+        gb.resize(5 * gbase_rows(n));
+        ok = fread(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
+    }
     fclose(f);
     if (!ok) {
         delete x;
@@ -515,6 +536,14 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
         cudaError_t e = cudaMemcpyAsync(x->blocks, host.data(), bytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+    }
+    if (r == RB3_OK && !gb.empty()) {
+        r = dev_alloc((void **)&x->gbase, sizeof(int64_t) * gb.size(), st);
+        if (r == RB3_OK) {
+            cudaError_t e = cudaMemcpyAsync(x->gbase, gb.data(), sizeof(int64_t) * gb.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+        }
     }
     if (r == RB3_OK) {
         int64_t C0[7];

@@ -117,7 +117,7 @@ __global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_
 // copies of one locus, so neighbouring groups are neighbouring loci and the
 // rank[p + h] reads and rank writes of a round touch nearby addresses.
 __global__ void k_head_pairs(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ fs,
-                             const uint32_t *__restrict__ ps, int64_t n, uint64_t *__restrict__ hkey,
+                             const uint32_t *__restrict__ ps, int64_t n, uint32_t *__restrict__ hkey,
                              uint32_t *__restrict__ hval) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || !fs[i]) return;
@@ -380,8 +380,9 @@ __global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict_
     }
     int o = (int)(q0 & ((1 << log2D) - 1));
     uint8_t *blk = blocks + b * bb;
-    store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], __activemask(), true);
-    // segmented reduce over the D/8 lanes of this block (D/8 in {8,16,32})
+    if (log2D == 5) store_planes32(blk, pl[0], pl[1], pl[2], __activemask(), true);
+    else store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], __activemask(), true);
+    // segmented reduce over the D/8 lanes of this block (D/8 in {4,8,16,32})
     int seg = 1 << (log2D - 3);
     unsigned full = __activemask();
 #pragma unroll
@@ -395,12 +396,18 @@ __global__ void k_pack(const uint8_t *__restrict__ T, const int32_t *__restrict_
 }
 
 // Header of block b: rank(a, b*D) = (exclusive prefix of row a at b).  The
-// scan ran over the whole [6][nblocks] array, so subtract the row's start.
+// scan ran over the whole [6][nblocks] array, so subtract the row's start.  A
+// batch has fewer than 2^31 symbols, so D = 32 counts need no span base.
 __global__ void k_headers(const uint32_t *__restrict__ ex, int64_t nblocks, int bb, uint8_t *__restrict__ blocks) {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nblocks) return;
     uint8_t *h = blocks + b * bb;
     uint32_t *h32 = reinterpret_cast<uint32_t *>(h);
+    if (bb == 32) {  // D = 32: words 0..4 = A..N; words 5..7 hold the planes
+#pragma unroll
+        for (int a = 1; a < SIGMA; ++a) h32[a - 1] = ex[(int64_t)a * nblocks + b] - ex[(int64_t)a * nblocks];
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < SIGMA; ++a) h32[a] = ex[(int64_t)a * nblocks + b] - ex[(int64_t)a * nblocks];
     *reinterpret_cast<uint32_t *>(h + 24) = 0;  // high bytes 0..3
@@ -413,8 +420,8 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
                      cudaStream_t st, rb3_index *out) {
     const int both = o.single_strand ? 0 : 1;
     const int mult = both ? 2 : 1;
-    int D = o.occ_interval ? o.occ_interval : 64;
-    RB3_CHECK_ARG(D == 64 || D == 128 || D == 256, "occ_interval must be 64, 128 or 256");
+    int D = o.occ_interval ? o.occ_interval : kDefaultOccInterval;
+    RB3_CHECK_ARG(valid_occ_interval(D), "occ_interval must be 32, 64, 128 or 256");
     std::vector<int64_t> in_off(n_seq + 1, 0), out_off(n_seq + 1, 0);
     for (int64_t s = 0; s < n_seq; ++s) {
         RB3_CHECK_ARG(lens[s] >= 0, "negative string length");
@@ -428,7 +435,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
     }
     out->D = D;
     out->log2D = ilog2(D);
-    out->block_bytes = HEADER_BYTES + D / 2;
+    out->block_bytes = block_bytes_for(D);
     out->single_strand = !both;
     out->n = n;
     out->m = n_seq * mult;
@@ -526,17 +533,17 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             NL = hc[1];
             // small groups in order of their first member's text position
             DevBuf hk0, hk1, hv0, hv1, gsz, goff;
-            RB3_TRY(hk0.alloc(sizeof(uint64_t) * (G + 1), st));
-            RB3_TRY(hk1.alloc(sizeof(uint64_t) * (G + 1), st));
+            RB3_TRY(hk0.alloc(sizeof(uint32_t) * (G + 1), st));
+            RB3_TRY(hk1.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(hv0.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(hv1.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(gsz.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(goff.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_LAUNCH(k_head_pairs, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), fs.as<uint32_t>(),
-                       ps.as<uint32_t>(), n, hk0.as<uint64_t>(), hv0.as<uint32_t>());
+                       ps.as<uint32_t>(), n, hk0.as<uint32_t>(), hv0.as<uint32_t>());
             bool halt = false;
-            RB3_TRY(radix_sort_pairs(hk0.as<uint64_t>(), hv0.as<uint32_t>(), hk1.as<uint64_t>(), hv1.as<uint32_t>(), G,
-                                     0, ilog2(n) + 1, st, &halt));
+            RB3_TRY(radix_sort_pairs32(hk0.as<uint32_t>(), hv0.as<uint32_t>(), hk1.as<uint32_t>(), hv1.as<uint32_t>(),
+                                       G, 0, ilog2(n) + 1, st, &halt));
             const uint32_t *hval = halt ? hv1.as<uint32_t>() : hv0.as<uint32_t>();
             if (G > 0)
                 RB3_LAUNCH(k_group_sizes, nb_for(G, 256), 256, 0, st, hval, G, hv.as<uint32_t>(), n, gsz.as<uint32_t>());

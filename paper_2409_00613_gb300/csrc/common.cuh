@@ -16,11 +16,17 @@
 #define RB3_EXPORT extern "C" __attribute__((visibility("default")))
 
 // ---------------------------------------------------------------------------
-// The index.  Blocks of D symbols: 32-byte header (rank of each symbol at the
-// block start: uint32 low words at bytes 0..23, uint8 high bytes at 24..29)
-// then D/2 payload bytes: one 32-byte sector per 64 symbols holding their 4-bit
-// codes as four 64-bit bit-planes.  nblocks = n/D + 1 so that rank(a, n) reads
-// a header that exists.
+// The index.  Blocks of D symbols, nblocks = n/D + 1 so that rank(a, n) reads a
+// block that exists.
+//  D = 64, 128, 256: 32-byte header (rank of each symbol at the block start:
+//    uint32 low words at bytes 0..23, uint8 high bytes at 24..29), then D/2
+//    payload bytes: one 32-byte sector per 64 symbols holding their codes as
+//    four 64-bit bit-planes.
+//  D = 32: one 32-byte sector per block, so that a rank is one memory request:
+//    uint32 words 0..4 = rank of A, C, G, T, N at the block start minus that
+//    symbol's rank at the start of the block's 2^32-symbol span (gbase; zero
+//    below 2^32), words 5..7 = the three 32-bit bit-planes of the block's
+//    symbols.  rank($, l) = l minus the other five ranks.
 // ---------------------------------------------------------------------------
 struct rb3_index {
     int64_t n = 0, m = 0;
@@ -29,6 +35,9 @@ struct rb3_index {
     int32_t single_strand = 0;
     int64_t nblocks = 0;
     uint8_t *blocks = nullptr;  // device
+    // D = 32 and n >= 2^32 only: gbase[5 g + a - 1] = rank(a, g * 2^32), a = 1..5,
+    // g = 0 .. n >> 32 (device; null otherwise)
+    int64_t *gbase = nullptr;
     // build data of a batch (optional): its text and inverse suffix array
     uint8_t *text = nullptr;   // device, n codes (0 = sentinel)
     int32_t *isa = nullptr;    // device, n entries
@@ -40,6 +49,12 @@ namespace rb3 {
 
 constexpr int SIGMA = 6;
 constexpr int HEADER_BYTES = 32;
+constexpr int GSPAN_LOG2 = 32;  // D = 32 counts are relative to spans of 2^32 symbols
+
+constexpr int kDefaultOccInterval = 32;  // one sector per rank
+inline bool valid_occ_interval(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
+inline int block_bytes_for(int D) { return D == 32 ? 32 : HEADER_BYTES + D / 2; }
+inline int64_t gbase_rows(int64_t n) { return (n >> GSPAN_LOG2) + 1; }
 
 // ---- errors ---------------------------------------------------------------
 void set_error(const char *fmt, ...);
@@ -140,6 +155,7 @@ __host__ __device__ __forceinline__ int comp_sym(int a) {
 // Read-only view of an index for kernels (passed by value).
 struct OccView {
     const uint8_t *__restrict__ blocks;
+    const int64_t *__restrict__ gbase;  // D = 32 above 2^32 symbols, else null
     int64_t n;
     int64_t C[7];
     int32_t log2D;
@@ -149,6 +165,7 @@ struct OccView {
 inline OccView occ_view(const rb3_index *x) {
     OccView v;
     v.blocks = x->blocks;
+    v.gbase = x->gbase;
     v.n = x->n;
     for (int i = 0; i < 7; ++i) v.C[i] = x->C[i];
     v.log2D = x->log2D;
@@ -161,7 +178,7 @@ __device__ __forceinline__ uint64_t ldg_u64(const uint8_t *p) {
 }
 
 // One 32-byte sector in a single 256-bit load (read-only path).  Occ blocks are
-// 32-byte aligned: block sizes are 64, 96 or 160 bytes from a 256-aligned base.
+// 32-byte aligned: block sizes are 32, 64, 96 or 160 bytes from a 256-aligned base.
 struct Sec {
     uint32_t w[8];
 };
@@ -230,35 +247,89 @@ __device__ __forceinline__ void hdr_all(const Sec &h, int64_t r[6]) {
 
 // Loads of one rank: the header sector and the payload sectors that hold the
 // nibbles before offset o, all issued before any is used.  NS = D/64 payload
-// sectors per block (1, 2 or 4); sectors past o are not loaded.
+// sectors per block (1, 2 or 4); sectors past o are not loaded.  NS = 0 is the
+// D = 32 layout: the block is one sector, and the rank also needs the position
+// (for $) and the span base.
 template <int NS> struct BlockLd {
     Sec h, p[NS];
     int o;
 };
+template <> struct BlockLd<0> {
+    Sec h;
+    int o;
+    int64_t l;
+    const int64_t *gb;
+};
+
 template <int NS> __device__ __forceinline__ BlockLd<NS> block_load(const OccView &v, int64_t l) {
     BlockLd<NS> b;
-    const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
-    b.o = (int)(l & (64 * NS - 1));
-    b.h = ld_sec(blk);
+    if constexpr (NS == 0) {
+        b.h = ld_sec(v.blocks + (l >> 5) * 32);
+        b.o = (int)(l & 31);
+        b.l = l;
+        b.gb = v.gbase ? v.gbase + 5 * (l >> GSPAN_LOG2) : nullptr;
+    } else {
+        const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
+        b.o = (int)(l & (64 * NS - 1));
+        b.h = ld_sec(blk);
 #pragma unroll
-    for (int j = 0; j < NS; ++j)
-        if (NS == 1 || b.o > 64 * j) b.p[j] = ld_sec(blk + HEADER_BYTES + 32 * j);
+        for (int j = 0; j < NS; ++j)
+            if (NS == 1 || b.o > 64 * j) b.p[j] = ld_sec(blk + HEADER_BYTES + 32 * j);
+    }
     return b;
 }
 
-template <int NS> __device__ __forceinline__ int64_t block_rank(const BlockLd<NS> &b, int c) {
-    int64_t r = hdr_get(b.h, c);
-#pragma unroll
-    for (int j = 0; j < NS; ++j)
-        if (NS == 1 || b.o > 64 * j) r += sec_count(b.p[j], c, b.o - 64 * j);
-    return r;
+// D = 32: symbols equal to c among the block's symbols, as a bit mask.
+__device__ __forceinline__ uint32_t s32_match(const Sec &s, int c) {
+    const uint32_t p0 = s.w[5], p1 = s.w[6], p2 = s.w[7];
+    return ((c & 1) ? p0 : ~p0) & ((c & 2) ? p1 : ~p1) & ((c & 4) ? p2 : ~p2);
 }
 
 template <int NS> __device__ __forceinline__ void block_rank_all(const BlockLd<NS> &b, int64_t r[6]) {
-    hdr_all(b.h, r);
+    if constexpr (NS == 0) {
+        const uint32_t mk = (1u << b.o) - 1u;  // o <= 31
+        const uint32_t p0 = b.h.w[5], p1 = b.h.w[6], p2 = b.h.w[7];
+        const uint32_t b0 = p0 & mk, n0 = ~p0 & mk;
+        const uint32_t t00 = ~p1 & ~p2, t10 = p1 & ~p2, t01 = ~p1 & p2;
+        r[1] = (int64_t)b.h.w[0] + __popc(b0 & t00);
+        r[2] = (int64_t)b.h.w[1] + __popc(n0 & t10);
+        r[3] = (int64_t)b.h.w[2] + __popc(b0 & t10);
+        r[4] = (int64_t)b.h.w[3] + __popc(n0 & t01);
+        r[5] = (int64_t)b.h.w[4] + __popc(b0 & t01);
+        if (b.gb) {
 #pragma unroll
-    for (int j = 0; j < NS; ++j)
-        if (NS == 1 || b.o > 64 * j) sec_count_all(b.p[j], b.o - 64 * j, r);
+            for (int a = 1; a < SIGMA; ++a) r[a] += b.gb[a - 1];
+        }
+        r[0] = b.l - (r[1] + r[2] + r[3] + r[4] + r[5]);
+    } else {
+        hdr_all(b.h, r);
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            if (NS == 1 || b.o > 64 * j) sec_count_all(b.p[j], b.o - 64 * j, r);
+    }
+}
+
+template <int NS> __device__ __forceinline__ int64_t block_rank(const BlockLd<NS> &b, int c) {
+    if constexpr (NS == 0) {
+        if (c == 0) {  // $: position minus the other five ranks
+            int64_t r[SIGMA];
+            block_rank_all<0>(b, r);
+            return r[0];
+        }
+        uint32_t w = b.h.w[0];
+#pragma unroll
+        for (int a = 2; a < SIGMA; ++a)
+            if (c == a) w = b.h.w[a - 1];
+        int64_t r = (int64_t)w + __popc(s32_match(b.h, c) & ((1u << b.o) - 1u));
+        if (b.gb) r += b.gb[c - 1];
+        return r;
+    } else {
+        int64_t r = hdr_get(b.h, c);
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            if (NS == 1 || b.o > 64 * j) r += sec_count(b.p[j], c, b.o - 64 * j);
+        return r;
+    }
 }
 
 // rank_B(c, l) = |{i < l : B[i] = c}|  (Table 1).
@@ -275,14 +346,24 @@ template <int NS> __device__ __forceinline__ void rank_all(const OccView &v, int
 
 // Any D (tile-level lookups outside the hot loops).
 __device__ __forceinline__ void rank_all_any(const OccView &v, int64_t l, int64_t r[SIGMA]) {
+    if (v.log2D == 5) {
+        rank_all<0>(v, l, r);
+        return;
+    }
     const int ns = (1 << v.log2D) >> 6;
     if (ns == 1) rank_all<1>(v, l, r);
     else if (ns == 2) rank_all<2>(v, l, r);
     else rank_all<4>(v, l, r);
 }
 
-// Symbol B[i]: bit o&63 of the three planes of its sector.
+// Symbol B[i]: bit o of the three planes that hold it.
 __device__ __forceinline__ int sym_at(const OccView &v, int64_t i) {
+    if (v.log2D == 5) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(v.blocks + (i >> 5) * 32);
+        const int bit = (int)(i & 31);
+        const uint32_t p0 = __ldg(w + 5), p1 = __ldg(w + 6), p2 = __ldg(w + 7);
+        return (int)(((p0 >> bit) & 1u) | (((p1 >> bit) & 1u) << 1) | (((p2 >> bit) & 1u) << 2));
+    }
     const uint8_t *blk = v.blocks + (i >> v.log2D) * (int64_t)v.bb;
     int o = (int)(i & ((1 << v.log2D) - 1));
     const uint8_t *sec = blk + HEADER_BYTES + 32 * (o >> 6);
@@ -308,8 +389,25 @@ __device__ __forceinline__ void store_planes(uint8_t *sec, uint32_t b0, uint32_t
     if (do_store && j < 4) *reinterpret_cast<uint64_t *>(sec + 8 * j) = j == 0 ? v0 : (j == 1 ? v1 : (j == 2 ? v2 : 0ull));
 }
 
-// Writer side: byte of plane b that holds symbols [8j, 8j+8) of a sector.
-__device__ __forceinline__ int plane_byte(int o_in_block, int b) {
+// The same for a D = 32 block: the 4 lanes 4g..4g+3 hold the plane bytes of its
+// four 8-symbol groups; lanes 0..2 of the group store the 32-bit planes at
+// words 5..7.  mask: the active lanes (whole 4-lane groups).
+__device__ __forceinline__ void store_planes32(uint8_t *blk, uint32_t b0, uint32_t b1, uint32_t b2, unsigned mask,
+                                               bool do_store) {
+    const int j = threadIdx.x & 3;
+    uint32_t v0 = b0 << (8 * j), v1 = b1 << (8 * j), v2 = b2 << (8 * j);
+#pragma unroll
+    for (int d = 1; d < 4; d <<= 1) {
+        v0 |= __shfl_xor_sync(mask, v0, d);
+        v1 |= __shfl_xor_sync(mask, v1, d);
+        v2 |= __shfl_xor_sync(mask, v2, d);
+    }
+    if (do_store && j < 3) reinterpret_cast<uint32_t *>(blk)[5 + j] = j == 0 ? v0 : (j == 1 ? v1 : v2);
+}
+
+// Writer side: byte of plane b that holds symbols [8j, 8j+8) of a block.
+__device__ __forceinline__ int plane_byte(int o_in_block, int b, int log2D) {
+    if (log2D == 5) return 20 + 4 * b + (o_in_block >> 3);
     return HEADER_BYTES + 32 * (o_in_block >> 6) + 8 * b + ((o_in_block & 63) >> 3);
 }
 
@@ -327,19 +425,25 @@ template <int NS> __device__ __forceinline__ BiInt backward_ext(const OccView &v
         // both ends' blocks are requested before either is counted; when both
         // ends fall in one block it is read once
         const int64_t e = x.k + x.s;
-        const bool same = (e >> v.log2D) == (x.k >> v.log2D);
+        const int lg = NS == 0 ? 5 : v.log2D;
+        const bool same = (e >> lg) == (x.k >> lg);
         BlockLd<NS> b0 = block_load<NS>(v, x.k);
         BlockLd<NS> b1;
         if (!same) {
             b1 = block_load<NS>(v, e);
         } else {
             b1 = b0;
-            b1.o = (int)(e & (64 * NS - 1));
-            if (NS > 1)  // payload sectors the first offset did not need (block_load skips them)
+            if constexpr (NS == 0) {
+                b1.o = (int)(e & 31);
+                b1.l = e;
+            } else {
+                b1.o = (int)(e & (64 * NS - 1));
+                if (NS > 1)  // payload sectors the first offset did not need (block_load skips them)
 #pragma unroll
-                for (int j = 0; j < NS; ++j)
-                    if (b1.o > 64 * j && !(b0.o > 64 * j))
-                        b1.p[j] = ld_sec(v.blocks + (e >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * j);
+                    for (int j = 0; j < NS; ++j)
+                        if (b1.o > 64 * j && !(b0.o > 64 * j))
+                            b1.p[j] = ld_sec(v.blocks + (e >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * j);
+            }
         }
         block_rank_all<NS>(b0, r0);
         block_rank_all<NS>(b1, r1);
@@ -428,6 +532,8 @@ int scan_u32_ws(const uint32_t *in, uint32_t *out, int64_t n, bool inclusive, ui
 // The result ends in (k0, v0) if *in_alt comes back false, else in (k1, v1).
 int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, int begin_bit,
                      int end_bit, cudaStream_t st, bool *in_alt);
+int radix_sort_pairs32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
+                       cudaStream_t st, bool *in_alt);
 
 // ---- phases (build.cu / merge.cu / search.cu) -------------------------------
 int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n_seq, const rb3_opts &o,
@@ -448,10 +554,13 @@ int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cuda
 // Fills idx->C from its blocks (rank of every symbol at n).
 int finalize_counts(rb3_index *idx, cudaStream_t st);
 
-// Calls body with a compile-time NS = D/64 for D in {64, 128, 256}.
+// Calls body with a compile-time NS = D/64 for D in {64, 128, 256}, NS = 0 for D = 32.
 #define RB3_WITH_NS(D, ...)                      \
     do {                                         \
-        if ((D) == 64) {                         \
+        if ((D) == 32) {                         \
+            constexpr int NS = 0;                \
+            __VA_ARGS__;                         \
+        } else if ((D) == 64) {                  \
             constexpr int NS = 1;                \
             __VA_ARGS__;                         \
         } else if ((D) == 128) {                 \

@@ -199,6 +199,18 @@ __global__ void k_tile_starts(const int64_t *__restrict__ pos, int64_t n2, int64
 __device__ __forceinline__ void plane_bits(const OccView &v, int64_t start, int cnt, uint32_t out[3]) {
     out[0] = out[1] = out[2] = 0u;
     if (cnt <= 0) return;
+    if (v.log2D == 5) {  // D = 32: 32-bit planes at words 5..7 of each block
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(v.blocks + (start >> 5) * 32);
+        const int bit = (int)(start & 31);
+        const uint32_t m = (1u << cnt) - 1u;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) out[b] = (__ldg(w + 5 + b) >> bit) & m;
+        if (bit + cnt > 32) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) out[b] |= (__ldg(w + 8 + 5 + b) << (32 - bit)) & m;
+        }
+        return;
+    }
     const int D = 1 << v.log2D;
     const int o = (int)(start & (D - 1));
     const uint8_t *sec = v.blocks + (start >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * (o >> 6);
@@ -236,14 +248,14 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
     __shared__ uint32_t flags[MT / 32];
     __shared__ uint32_t wtot[32];
     __shared__ int64_t base6[SIGMA];
-    __shared__ uint32_t bcnt[MT / 64][SIGMA];  // per 64-symbol group counts
+    __shared__ uint32_t bcnt[MT / 32][SIGMA];  // per 32-symbol group counts
     const int64_t t = blockIdx.x;
     const int64_t q0 = t * MT;
     const int64_t k0 = kstart[t], k1 = kstart[t + 1];
     const int64_t j0 = q0 - k0;
     for (int i = threadIdx.x; i < MT / 32; i += MT_THREADS) flags[i] = 0;
     if (threadIdx.x < SIGMA) base6[threadIdx.x] = tbase[t * SIGMA + threadIdx.x];
-    for (int i = threadIdx.x; i < (MT / 64) * SIGMA; i += MT_THREADS) (&bcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < (MT / 32) * SIGMA; i += MT_THREADS) (&bcnt[0][0])[i] = 0;
     __syncthreads();
     for (int64_t k = k0 + threadIdx.x; k < k1; k += MT_THREADS) {
         int d = (int)(pos[k] - q0);
@@ -289,8 +301,8 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
         c[4] = __popc(n0 & t01);
         c[5] = __popc(b0 & t01);
     }
-    // counts per 64-symbol group (8 threads)
-    const int grp = o8 >> 6;
+    // counts per 32-symbol group (4 threads)
+    const int grp = o8 >> 5;
 #pragma unroll
     for (int a = 0; a < SIGMA; ++a)
         if (c[a]) atomicAdd(&bcnt[grp][a], c[a]);
@@ -301,11 +313,25 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
     const bool live = (q >> log2D) < nbM;  // past the last output block nothing is stored
     uint8_t *blk = M + (q >> log2D) * (int64_t)bb;
     const int o = (int)(q & (D - 1));
-    store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], 0xffffffffu, live);
+    if (log2D == 5) store_planes32(blk, pl[0], pl[1], pl[2], 0xffffffffu, live);
+    else store_planes(blk + HEADER_BYTES + 32 * (o >> 6), pl[0], pl[1], pl[2], 0xffffffffu, live);
     if (!live) return;  // no barrier follows
-    if (o == 0) {
+    if (o == 0 && log2D == 5) {
+        // D = 32: rank at q relative to the start of q's 2^32-symbol span, whose
+        // absolute ranks are those of the tile that starts there
+        const int ng = o8 >> 5;
+        const int64_t gi = q >> GSPAN_LOG2;
+        uint32_t *h32 = reinterpret_cast<uint32_t *>(blk);
+#pragma unroll
+        for (int a = 1; a < SIGMA; ++a) {
+            int64_t r = base6[a];
+            for (int g = 0; g < ng; ++g) r += bcnt[g][a];
+            if (gi) r -= tbase[((gi << GSPAN_LOG2) / MT) * SIGMA + a];
+            h32[a - 1] = (uint32_t)r;
+        }
+    } else if (o == 0) {
         // rank at q = base + counts of the groups of this tile before q
-        int ng = o8 >> 6;
+        int ng = o8 >> 5;
         uint32_t *h32 = reinterpret_cast<uint32_t *>(blk);
         uint8_t hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int a = 0; a < SIGMA; ++a) {
@@ -322,11 +348,27 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Bytes one rank needs: the symbol's count word(s) and, on average, the payload
+// before the offset (D = 32: the count word and the three 4-byte planes).
+static inline double rank_bytes(int D) { return D == 32 ? 16.0 : 5.0 + D / 4.0; }
+
+// gbase[5 g + a - 1] = rank(a, g * 2^32) = the tile base of the tile starting there.
+__global__ void k_span_bases(const int64_t *__restrict__ tbase, int64_t rows, int64_t *__restrict__ gb) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows * 5) return;
+    const int64_t g = i / 5;
+    const int a = (int)(i % 5) + 1;
+    gb[i] = tbase[((g << GSPAN_LOG2) / MT) * SIGMA + a];
+}
+
 template <int NS1>
 static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
                                unsigned int *err, cudaStream_t st) {
     unsigned grid = nb_for(m2, 32);
-    if (D2 == 64) {
+    if (D2 == 32) {
+        auto kern = k_walk_plain<NS1, 0>;
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+    } else if (D2 == 64) {
         auto kern = k_walk_plain<NS1, 1>;
         RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
     } else if (D2 == 128) {
@@ -341,6 +383,7 @@ static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64
 
 static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
                              unsigned int *err, cudaStream_t st) {
+    if (D1 == 32) return launch_walk_plain_1<0>(D2, V1, V2, m1, m2, pos, err, st);
     if (D1 == 64) return launch_walk_plain_1<1>(D2, V1, V2, m1, m2, pos, err, st);
     if (D1 == 128) return launch_walk_plain_1<2>(D2, V1, V2, m1, m2, pos, err, st);
     return launch_walk_plain_1<4>(D2, V1, V2, m1, m2, pos, err, st);
@@ -369,8 +412,8 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
             RB3_TRY(err.alloc(sizeof(unsigned int), st));
             RB3_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(unsigned int), st));
             {
-                // per new symbol: two ranks (B2 row, B1 l) of 5 + D/4 B each and an 8 B pos
-                Phase pk("k.walk_plain", st, (double)n2 * (2.0 * (5.0 + dst->D / 4.0) + 8.0));
+                // per new symbol: two ranks (B2 row, B1 l) and an 8 B pos
+                Phase pk("k.walk_plain", st, (double)n2 * (rank_bytes(src->D) + rank_bytes(dst->D) + 8.0));
                 RB3_TRY(launch_walk_plain(dst->D, src->D, V1, V2, m1, m2, pos, err.as<unsigned int>(), st));
             }
             unsigned int herr = 0;
@@ -443,10 +486,12 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
             RB3_CUDA_TRY(cudaMemsetAsync(d_state, 0, sizeof(int32_t) * nw, st));
             RB3_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st));
             {
-                // per new symbol: 1 B text, 4 B ISA, 4+1 B Occ count, D/4 B payload on average,
-                // 8 B pos (seed steps not counted)
-                Phase pw("k.merge_walk", st, (double)n2 * (18.0 + dst->D / 4.0));
-                int64_t resident = (int64_t)num_sms() * 2048;
+                // per new symbol: 1 B text, 4 B ISA, one rank, 8 B pos (seed steps not counted)
+                Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
+                // the walk is persistent: a grid of cps 256-thread CTAs per SM (default 8,
+                // of which registers let 4 be resident at once)
+                const int cps = o.walk_ctas_per_sm > 0 ? (o.walk_ctas_per_sm < 8 ? o.walk_ctas_per_sm : 8) : 8;
+                int64_t resident = (int64_t)num_sms() * 256 * cps;
                 int64_t threads = nw < resident ? nw : resident;
                 unsigned grid = nb_for(threads, 256);
                 if (dst->single_strand)
@@ -475,7 +520,7 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
     }
     // output layout: D of dst (or of src when dst is empty)
     int D = n1 ? dst->D : src->D;
-    int log2D = ilog2(D), bb = HEADER_BYTES + D / 2;
+    int log2D = ilog2(D), bb = block_bytes_for(D);
     int64_t nbM = nM / D + 1;
     int64_t ntiles = (nbM * D + MT - 1) / MT;
     DevBuf posb, kst, Mb, tbase;
@@ -501,7 +546,16 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                        tbase.as<int64_t>(), nM, nbM, log2D, bb, Mb.as<uint8_t>());
         }
     }
+    // D = 32 past 2^32 symbols: the span bases are the ranks at the tiles where spans start
+    int64_t *gb = nullptr;
+    if (D == 32 && nM >> GSPAN_LOG2) {
+        const int64_t rows = gbase_rows(nM);
+        RB3_TRY(dev_alloc((void **)&gb, sizeof(int64_t) * 5 * rows, st));
+        RB3_LAUNCH(k_span_bases, nb_for(rows * 5, 128), 128, 0, st, tbase.as<int64_t>(), rows, gb);
+    }
     // install
+    if (dst->gbase) dev_free(dst->gbase, st);
+    dst->gbase = gb;
     if (dst->blocks) dev_free(dst->blocks, st);
     if (dst->text) dev_free(dst->text, st);
     if (dst->isa) dev_free(dst->isa, st);

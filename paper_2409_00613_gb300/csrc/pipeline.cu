@@ -34,6 +34,7 @@ struct Channel {
 void free_built(rb3_index *x) {
     if (!x) return;
     dev_free(x->blocks, 0);
+    dev_free(x->gbase, 0);
     dev_free(x->text, 0);
     dev_free(x->isa, 0);
     cudaStreamSynchronize(0);

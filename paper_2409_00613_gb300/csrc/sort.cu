@@ -1,6 +1,6 @@
 // Device-wide primitives used by the batch builder and the search output:
-// reduce-then-scan prefix sums and a stable LSD radix sort of (uint64 key,
-// uint32 value) pairs.  Both are written for this library; no CUB.
+// reduce-then-scan prefix sums and a stable LSD radix sort of (uint64 or
+// uint32 key, uint32 value) pairs.  Both are written for this library; no CUB.
 #include "common.cuh"
 
 namespace rb3 {
@@ -119,12 +119,16 @@ int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, bool inclusive, cudaS
 }
 
 // ---------------------------------------------------------------------------
-// Radix sort: 8-bit digits, tiles of 4096 pairs (8 warps x 16 iterations x 32
-// lanes, item order = (warp, iteration, lane) = input order).  Per pass:
+// Radix sort: 8-bit digits, tiles of 4096 pairs (warp w takes items
+// [512w, 512w + 512) of the tile, lane-interleaved over 16 iterations, so item
+// order = (warp, iteration, lane) = input order).  Per pass:
 //   hist    -- per-tile digit counts, digit-major [256][ntiles]
 //   scan    -- exclusive prefix over that array = global digit offsets
 //   scatter -- stable in-tile ranks by warp multi-split (__match_any_sync),
-//              keys reordered in shared memory, then written out in runs.
+//              pairs reordered in shared memory, then written out in runs.
+// The scatter holds only the keys and their ranks in registers; a pair's value
+// is loaded after the tile's ranks are known and goes straight to its place in
+// shared memory.  That keeps the kernel at three CTAs per SM.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -132,7 +136,8 @@ constexpr int RS_ITERS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITERS;
 constexpr int RS_BINS = 256;
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K *__restrict__ keys, int64_t n, int shift,
                                                         uint32_t mask, uint32_t *__restrict__ counts,
                                                         int64_t ntiles) {
     __shared__ uint32_t h[RS_WARPS][RS_BINS];
@@ -151,8 +156,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
     counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = t;
 }
 
-struct RsSmem {
-    unsigned long long k[RS_TILE];
+template <class K> struct RsSmem {
+    K k[RS_TILE];
     uint32_t v[RS_TILE];
     uint32_t wh[RS_WARPS][RS_BINS];
     uint32_t dstart[RS_BINS];
@@ -160,33 +165,33 @@ struct RsSmem {
     uint32_t wtot[32];
 };
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
-                                                           const uint32_t *__restrict__ vin,
-                                                           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                           int64_t n, int shift, uint32_t mask,
-                                                           const uint32_t *__restrict__ offs, int64_t ntiles) {
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K *__restrict__ kin,
+                                                              const uint32_t *__restrict__ vin,
+                                                              K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                              int64_t n, int shift, uint32_t mask,
+                                                              const uint32_t *__restrict__ offs, int64_t ntiles) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    RsSmem &S = *reinterpret_cast<RsSmem *>(smraw);
+    RsSmem<K> &S = *reinterpret_cast<RsSmem<K> *>(smraw);
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.wh[0][0])[i] = 0;
     S.goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE + w * (RS_ITERS * 32);
     unsigned lt = (1u << lane) - 1u;
-    unsigned long long kk[RS_ITERS];
-    uint32_t vv[RS_ITERS], lr[RS_ITERS];
-    // the whole tile's keys and values are loaded before any is ranked
+    K kk[RS_ITERS];
+    uint32_t lr[RS_ITERS];
+    // the whole tile's keys are loaded before any is ranked
 #pragma unroll
     for (int it = 0; it < RS_ITERS; ++it) {
         int64_t g = base + it * 32 + lane;
-        kk[it] = g < n ? (unsigned long long)kin[g] : 0ull;
-        vv[it] = g < n ? vin[g] : 0u;
+        kk[it] = g < n ? kin[g] : K(0);
     }
 #pragma unroll
     for (int it = 0; it < RS_ITERS; ++it) {
         int64_t g = base + it * 32 + lane;
         bool valid = g < n;
-        unsigned long long k = kk[it];
+        K k = kk[it];
         uint32_t d = valid ? ((uint32_t)(k >> shift) & mask) : (RS_BINS + lane);
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = 31 - __clz(peers);
@@ -213,16 +218,21 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
         int64_t g = base + it * 32 + lane;
         if (g < n) {
             uint32_t d = (uint32_t)(kk[it] >> shift) & mask;
-            uint32_t lp = S.dstart[d] + S.wh[w][d] + lr[it];
-            S.k[lp] = kk[it];
-            S.v[lp] = vv[it];
+            lr[it] += S.dstart[d] + S.wh[w][d];
+            S.k[lr[it]] = kk[it];
         }
+    }
+    // values: loaded now, stored at their pair's place
+#pragma unroll
+    for (int it = 0; it < RS_ITERS; ++it) {
+        int64_t g = base + it * 32 + lane;
+        if (g < n) S.v[lr[it]] = vin[g];
     }
     __syncthreads();
     int64_t tb = (int64_t)blockIdx.x * RS_TILE;
     int cnt = (int)((n - tb) < RS_TILE ? (n - tb) : RS_TILE);
     for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
-        unsigned long long k = S.k[i];
+        K k = S.k[i];
         uint32_t d = (uint32_t)(k >> shift) & mask;
         int64_t gp = (int64_t)S.goff[d] + (i - (int64_t)S.dstart[d]);
         kout[gp] = k;
@@ -230,43 +240,57 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
     }
 }
 
-int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
-                     cudaStream_t st, bool *in_alt) {
+template <class K>
+static int radix_sort_impl(K *k0, uint32_t *v0, K *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
+                           cudaStream_t st, bool *in_alt) {
     *in_alt = false;
     if (n <= 1 || end_bit <= begin_bit) return RB3_OK;
     if (n > 0xFFFFFFFFll) {
         set_error("radix sort: too many elements (%lld)", (long long)n);
         return RB3_E_INVAL;
     }
-    static const cudaError_t attr = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)sizeof(RsSmem));  // once, thread-safe
+    static const cudaError_t attr = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)sizeof(RsSmem<K>));  // once, thread-safe
     RB3_CUDA_TRY(attr);
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     DevBuf counts;
     RB3_TRY(counts.alloc(sizeof(uint32_t) * RS_BINS * ntiles, st));
-    uint64_t *ka = k0, *kb = k1;
+    K *ka = k0, *kb = k1;
     uint32_t *va = v0, *vb = v1;
     bool alt = false;
+    const double kv = (double)sizeof(K) + 4.0;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         int nb = end_bit - shift < 8 ? end_bit - shift : 8;
         uint32_t mask = (1u << nb) - 1u;
         {
-            Phase ph("k.rs_hist", st, 8.0 * n);  // reads the keys
-            RB3_LAUNCH(k_rs_hist, (unsigned)ntiles, RS_THREADS, 0, st, ka, n, shift, mask, counts.as<uint32_t>(),
+            Phase ph("k.rs_hist", st, (double)sizeof(K) * n);  // reads the keys
+            RB3_LAUNCH(k_rs_hist<K>, (unsigned)ntiles, RS_THREADS, 0, st, ka, n, shift, mask, counts.as<uint32_t>(),
                        ntiles);
         }
         RB3_TRY(scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), RS_BINS * ntiles, false, 0, st));
         {
-            Phase ph("k.rs_scatter", st, 24.0 * n);  // reads and writes (8-byte key, 4-byte value)
-            RB3_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem), st, ka, va, kb, vb, n, shift,
+            Phase ph("k.rs_scatter", st, 2.0 * kv * n);  // reads and writes (key, 4-byte value)
+            RB3_LAUNCH(k_rs_scatter<K>, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem<K>), st, ka, va, kb, vb, n, shift,
                        mask, counts.as<uint32_t>(), ntiles);
         }
-        uint64_t *tk = ka; ka = kb; kb = tk;
+        K *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
         alt = !alt;
     }
     *in_alt = alt;
     return RB3_OK;
+}
+
+int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
+                     cudaStream_t st, bool *in_alt) {
+    return radix_sort_impl<unsigned long long>(reinterpret_cast<unsigned long long *>(k0), v0,
+                                               reinterpret_cast<unsigned long long *>(k1), v1, n, begin_bit, end_bit,
+                                               st, in_alt);
+}
+
+int radix_sort_pairs32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
+                       cudaStream_t st, bool *in_alt) {
+    return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, begin_bit, end_bit, st, in_alt);
 }
 
 }  // namespace rb3

@@ -27,7 +27,8 @@ class rb3_opts(ctypes.Structure):
     _fields_ = [("occ_interval", ctypes.c_int32), ("single_strand", ctypes.c_int32),
                 ("seg_len", ctypes.c_int64), ("seed_cap", ctypes.c_int64),
                 ("merge_form", ctypes.c_int32), ("search_form", ctypes.c_int32),
-                ("chunk_len", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+                ("chunk_len", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class rb3_server_opts(ctypes.Structure):

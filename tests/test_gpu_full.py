@@ -49,8 +49,8 @@ def test_pangenome_full_bwt_equals_oracle(pangenome_full):
     assert np.array_equal(codes, want)
     T = oracle.concat(S.seq, S.lens, True)
     assert oracle.certify(codes, T, nthreads=NTH) == 0
-    assert np.array_equal(occ, oracle.occ_table(want, 64))
     info = rb.rb3_index_info(idx)
+    assert np.array_equal(occ, oracle.occ_table(want, info["occ_interval"]))
     assert info["m"] == 100 and info["C"] == list(oracle.counts(want))
 
 
@@ -83,3 +83,45 @@ def test_uneven_genomes_reduced():
     want = oracle.build_incremental(S.seq, S.lens, True, 1, nthreads=NTH)
     assert np.array_equal(codes, want)
     assert oracle.certify(codes, oracle.concat(S.seq, S.lens, True), nthreads=NTH) == 0
+
+
+def test_occ32_index_past_2_to_32():
+    """D = 32 keeps 32-bit counts relative to 2^32-symbol spans.  The served
+    index (150 Mb founder, 20 haplotypes, batches of 4: ~6 Gsym) crosses 2^32
+    after four batches, so the last merge walks over span 1 and writes span
+    bases.  Pins that hold at any size: every backward-search interval of the
+    merged index is the sum of the batches' intervals (a pattern without $
+    compares with each suffix by its first |P| symbols only, so lo and hi add up
+    over the batches), checked on patterns sampled from every batch."""
+    S = synth.served_index_strings()
+    off = S.offsets
+    opts = {"occ_interval": 32}
+    parts = []
+    idx = rb.rb3_index_empty(opts)
+    for a, b in S.batches:
+        dev_seq = torch.from_numpy(S.seq[off[a]:off[b]].copy()).to(DEV)
+        part = rb.rb3_build_batch(dev_seq, S.lens[a:b].copy(), opts=opts)
+        del dev_seq
+        rb.rb3_merge_opts(idx, part, opts)
+        rb.rb3_drop_build_data(part)
+        parts.append(part)
+    info = rb.rb3_index_info(idx)
+    assert info["n"] == S.ds_symbols() > 2**32 and info["occ_interval"] == 32
+    g = synth.rng(4242)
+    pats = [np.array([c], np.uint8) for c in range(1, 6)]
+    for _ in range(4000):
+        L = int(g.integers(2, 60))
+        s = int(g.integers(0, len(S.seq) - L))
+        p = S.seq[s:s + L].copy()
+        if g.random() < 0.2:
+            p[int(g.integers(0, L))] = int(g.integers(1, 5))
+        pats.append(p)
+    q = np.concatenate(pats)
+    qoff = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.int64)
+    got = rb.rb3_backward_search(idx, q, qoff)
+    want = sum(rb.rb3_backward_search(p, q, qoff) for p in parts)
+    assert np.array_equal(got, want)
+    assert (got[:, 1] > 2**32).sum() > 100  # intervals in the second span were exercised
+    for p in parts:
+        p.free()
+    idx.free()

@@ -35,11 +35,13 @@ def smem_rows(recs, n):
     return np.stack([recs[f].astype(np.int64) for f in FIELDS], axis=1)
 
 
-def check_index(idx, B, D=64):
+def check_index(idx, B, D=None):
+    info = rb.rb3_index_info(idx)
+    if D is not None:
+        assert info["occ_interval"] == D
     codes, occ = rb.rb3_export(idx, want_occ=True)
     assert np.array_equal(codes, B)
-    assert np.array_equal(occ, oracle.occ_table(B, D))
-    info = rb.rb3_index_info(idx)
+    assert np.array_equal(occ, oracle.occ_table(B, info["occ_interval"]))
     assert info["n"] == len(B)
     assert info["C"] == list(oracle.counts(B))
 
@@ -68,7 +70,7 @@ def test_config0_tiny_build_merge_search():
     assert np.all(want[:, 1] > want[:, 0])  # every query was sampled from the text
 
 
-@pytest.mark.parametrize("D", [64, 128, 256])
+@pytest.mark.parametrize("D", [32, 64, 128, 256])
 @pytest.mark.parametrize("both", [True, False])
 def test_random_lists_batches(D, both):
     g = synth.rng(1000 + D + both)
@@ -122,11 +124,25 @@ def test_large_groups_low_complexity():
     check_index(A, ref_bwt(S))
 
 
-def test_backward_search_edges():
+def test_mixed_occ_intervals():
+    """Merges between indexes of different Occ intervals (the result takes the
+    destination's), segmented and plain walks."""
+    g = synth.rng(606)
+    S = synth.random_strings(g, 24, 900, n_frac=0.03)
+    for D1, D2 in [(32, 64), (64, 32), (32, 256), (128, 32)]:
+        for form in (0, 1):
+            idx = build(S, 0, 10, occ_interval=D1)
+            rb.rb3_merge_opts(idx, build(S, 10, 24, occ_interval=D2), {"merge_form": form, "seg_len": 50})
+            assert rb.rb3_index_info(idx)["occ_interval"] == D1
+            check_index(idx, ref_bwt(S), D1)
+
+
+@pytest.mark.parametrize("D", [32, 64])
+def test_backward_search_edges(D):
     g = synth.rng(9)
     S = synth.random_strings(g, 12, 200, n_frac=0.05)
     B = ref_bwt(S)
-    idx = build(S)
+    idx = build(S, occ_interval=D)
     pats = [np.zeros(0, np.uint8), np.array([5], np.uint8), np.array([5, 5, 5], np.uint8)]
     for _ in range(200):
         L = int(g.integers(1, 15))
@@ -137,13 +153,14 @@ def test_backward_search_edges():
     assert np.array_equal(rb.rb3_backward_search(idx, q, qoff), oracle.backward_search(B, q, qoff))
 
 
+@pytest.mark.parametrize("D", [32, 64])
 @pytest.mark.parametrize("chunk", [0, 5, 17, 64])
 @pytest.mark.parametrize("ell,smin", [(1, 1), (4, 1), (12, 2), (19, 1)])
-def test_smem_vs_oracle(chunk, ell, smin):
+def test_smem_vs_oracle(chunk, ell, smin, D):
     S = synth.pangenome(seed=31, founder_len=3000, n_hap=6, batch=3)
     B = ref_bwt(S)
-    idx = build(S, 0, 3)
-    rb.rb3_merge(idx, build(S, 3, 6))
+    idx = build(S, 0, 3, occ_interval=D)
+    rb.rb3_merge(idx, build(S, 3, 6, occ_interval=D))
     Q = synth.mem_queries(S, seed=32, nq=300, median=80, lo=1, hi=600, sub=0.02)
     want = oracle.smem(B, Q.q, Q.qoff, ell, smin)
     for form in (0, 1):
@@ -197,18 +214,19 @@ def test_pangenome_medium_incremental():
     check_index(idx2, want)
 
 
-def test_save_load_resume(tmp_path):
+@pytest.mark.parametrize("D", [32, 64])
+def test_save_load_resume(tmp_path, D):
     S = synth.pangenome(seed=51, founder_len=5000, n_hap=6, batch=2)
-    idx = build(S, 0, 2)
-    rb.rb3_merge(idx, build(S, 2, 4))
+    idx = build(S, 0, 2, occ_interval=D)
+    rb.rb3_merge(idx, build(S, 2, 4, occ_interval=D))
     p = str(tmp_path / "x.rb3")
     rb.rb3_index_save(idx, p)
     back = rb.rb3_index_load(p)
     assert rb.rb3_index_info(back)["has_build_data"] is False
-    rb.rb3_merge(back, build(S, 4, 6))  # resume: load + further merge
-    rb.rb3_merge(idx, build(S, 4, 6))
-    check_index(back, ref_bwt(S))
-    check_index(idx, ref_bwt(S))
+    rb.rb3_merge(back, build(S, 4, 6, occ_interval=D))  # resume: load + further merge
+    rb.rb3_merge(idx, build(S, 4, 6, occ_interval=D))
+    check_index(back, ref_bwt(S), D)
+    check_index(idx, ref_bwt(S), D)
 
 
 def test_append_batches_pipeline():
