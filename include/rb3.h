@@ -261,6 +261,12 @@ int rb3_encode_ascii(const char *ascii, int64_t n, uint8_t *codes);
 int rb3_profile_enable(int on);
 int rb3_profile_reset(void);
 int rb3_profile_read(const char **names, double *ms, int64_t *calls, double *bytes, int32_t cap, int32_t *n);
+/* Every phase recorded since rb3_profile_reset, in the order they were drained
+ * (per stream, the order they ran), with its start relative to the reset (an
+ * event recorded on the legacy stream then) and its duration, in ms: shows
+ * which phases of different streams ran at the same time.  names[i] are static
+ * strings.  *n receives the number of phases (up to cap are written). */
+int rb3_profile_timeline(const char **names, double *start_ms, double *dur_ms, int64_t cap, int64_t *n);
 int64_t rb3_launch_count(void);
 
 /* Random-access roofline probe (measurement only; touches no index).  Times

@@ -39,6 +39,10 @@ static void ensure_pool() {
             // keep up to 64 GiB of freed scratch in the pool between calls
             uint64_t thr = 64ull << 30;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            // never make a stream wait for another stream's frees to reuse memory:
+            // builds and merges run on separate streams and must not be serialised
+            int no = 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
         }
         return true;
     }();
@@ -96,6 +100,14 @@ struct Acc {
 static std::vector<Pending> g_pending;
 static std::map<std::string, Acc> g_acc;
 static std::vector<std::string> g_names;  // stable storage for names handed out
+// Timeline: every drained phase with its start relative to the origin event
+// recorded by rb3_profile_reset (events of any stream of the device compare).
+struct Span {
+    const char *name;
+    float start, dur;
+};
+static std::vector<Span> g_spans;
+static cudaEvent_t g_origin = nullptr;
 
 bool profile_on() { return g_prof.load(std::memory_order_relaxed); }
 
@@ -107,12 +119,13 @@ void profile_push(const char *name, cudaEvent_t a, cudaEvent_t b, double bytes) 
 static void profile_drain() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto &p : g_pending) {
-        float ms = 0.f;
+        float ms = 0.f, t0 = 0.f;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             Acc &e = g_acc[p.name];
             e.ms += ms;
             e.bytes += p.bytes;
             e.calls += 1;
+            if (g_origin && cudaEventElapsedTime(&t0, g_origin, p.a) == cudaSuccess) g_spans.push_back({p.name, t0, ms});
         }
         cudaGetLastError();
         cudaEventDestroy(p.a);
@@ -588,6 +601,22 @@ RB3_EXPORT int rb3_profile_reset(void) {
     profile_drain();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_acc.clear();
+    g_spans.clear();
+    if (!g_origin) RB3_CUDA_TRY(cudaEventCreate(&g_origin));
+    RB3_CUDA_TRY(cudaEventRecord(g_origin, 0));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_profile_timeline(const char **names, double *start_ms, double *dur_ms, int64_t cap, int64_t *n) {
+    profile_drain();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const int64_t m = (int64_t)g_spans.size();
+    for (int64_t i = 0; i < m && i < cap; ++i) {
+        if (names) names[i] = g_spans[i].name;
+        if (start_ms) start_ms[i] = g_spans[i].start;
+        if (dur_ms) dur_ms[i] = g_spans[i].dur;
+    }
+    if (n) *n = m;
     return RB3_OK;
 }
 

@@ -117,8 +117,13 @@ __device__ __forceinline__ int64_t seed_backward(const OccView &B1, int64_t m1, 
     return exact ? lo : -1;
 }
 
+// One warp per CTA: a CTA's registers go back to the SM as soon as its 32
+// walks are done, so work on other streams (the next batch's build) can use
+// the SMs while the last long walks finish.
+constexpr int WALK_THREADS = 32;
+
 template <int NS, bool DS>
-__global__ void __launch_bounds__(256) k_merge_walk(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
+__global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int64_t m1, const uint8_t *__restrict__ T2,
                                                     const int32_t *__restrict__ isa2,
                                                     const int64_t *__restrict__ w_hi,
                                                     const int64_t *__restrict__ w_send,
@@ -389,6 +394,32 @@ static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1,
     return launch_walk_plain_1<4>(D2, V1, V2, m1, m2, pos, err, st);
 }
 
+// Segment w of the plan: string s with segoff[s] <= w < segoff[s+1], r = w -
+// segoff[s] segments below the string's sentinel: top hi = end - r*L, the next
+// segment down (or -1 at the string start), and (r, w) as the sort key/value of
+// the processing order.
+__global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int32_t *__restrict__ segoff, int64_t ns,
+                           int64_t L, int64_t nw, int64_t *__restrict__ w_hi, int64_t *__restrict__ w_send,
+                           int64_t *__restrict__ w_sstart, int32_t *__restrict__ w_next, uint32_t *__restrict__ key,
+                           uint32_t *__restrict__ val) {
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    int64_t lo = 0, hi = ns;  // largest s with segoff[s] <= w
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (segoff[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    const int64_t s = lo, r = w - segoff[s], R = segoff[s + 1] - segoff[s];
+    const int64_t end = str_end[s], start = s == 0 ? 0 : str_end[s - 1] + 1;
+    w_hi[w] = end - r * L;
+    w_send[w] = end;
+    w_sstart[w] = start;
+    w_next[w] = r == R - 1 ? -1 : (int32_t)(w + 1);
+    key[w] = (uint32_t)r;
+    val[w] = (uint32_t)w;
+}
+
 __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < n) pos[k] = k;
@@ -437,69 +468,68 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
             // double strand: seeds are self-limiting (claimed from above), so no cap
             // unless asked; single strand: the backward seed looks cap symbols ahead
             int64_t cap = o.seed_cap > 0 ? o.seed_cap : (dst->single_strand ? 4 * L : (int64_t)1 << 62);
+            // segments per string (host, one number per string); the segments
+            // themselves and their order are laid out on the device
             const int64_t ns = (int64_t)src->str_end.size();
-            std::vector<int64_t> w_hi, w_send, w_sstart;
-            std::vector<int32_t> w_next, w_rank;
-            int64_t maxr = 0;
+            std::vector<int32_t> segoff(ns + 1, 0);
+            int64_t nw = 0, maxr = 0;
             for (int64_t s = 0; s < ns; ++s) {
                 const int64_t start = s == 0 ? 0 : src->str_end[s - 1] + 1;
-                const int64_t end = src->str_end[s];
-                // segment r starts at end - r*L (r = 0 at the sentinel) while > start
-                int64_t r = 0;
-                for (int64_t x = end;; x -= L, ++r) {
-                    w_hi.push_back(x);
-                    w_send.push_back(end);
-                    w_sstart.push_back(start);
-                    w_rank.push_back((int32_t)r);
-                    const bool last = x - L <= start;
-                    w_next.push_back(last ? -1 : (int32_t)w_hi.size());
-                    if (last) break;
+                const int64_t len = src->str_end[s] - start;
+                const int64_t R = len > L ? (len + L - 1) / L : 1;
+                if (R - 1 > maxr) maxr = R - 1;
+                nw += R;
+                if (nw >= (int64_t(1) << 31)) {
+                    set_error("merge: too many segments");
+                    return RB3_E_INVAL;
                 }
-                if (r > maxr) maxr = r;
+                segoff[s + 1] = (int32_t)nw;
             }
-            const int64_t nw = (int64_t)w_hi.size();
-            if (nw >= (int64_t(1) << 31)) {
-                set_error("merge: too many segments");
-                return RB3_E_INVAL;
-            }
-            // processing order: by rank from the string end, then string, so the
-            // homologous segments of a batch's strings run side by side
-            std::vector<int32_t> order(nw);
-            {
-                std::vector<int64_t> cnt(maxr + 2, 0);
-                for (int64_t w = 0; w < nw; ++w) cnt[w_rank[w] + 1]++;
-                for (int64_t r = 0; r <= maxr; ++r) cnt[r + 1] += cnt[r];
-                for (int64_t w = 0; w < nw; ++w) order[cnt[w_rank[w]]++] = (int32_t)w;
-            }
-            DevBuf plan;
+            DevBuf plan, sk0, sk1, sv1, ends;
             size_t bytes = sizeof(int64_t) * (3 * nw) + sizeof(int32_t) * (3 * nw) + sizeof(unsigned long long) + 64;
             RB3_TRY(plan.alloc(bytes, st));
+            RB3_TRY(sk0.alloc(sizeof(uint32_t) * nw, st));
+            RB3_TRY(sk1.alloc(sizeof(uint32_t) * nw, st));
+            RB3_TRY(sv1.alloc(sizeof(uint32_t) * nw, st));
+            RB3_TRY(ends.alloc(sizeof(int64_t) * ns + sizeof(int32_t) * (ns + 1), st));
             int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_sstart = d_send + nw;
             int32_t *d_next = reinterpret_cast<int32_t *>(d_sstart + nw), *d_state = d_next + nw, *d_order = d_state + nw;
             unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(
                 (reinterpret_cast<uintptr_t>(d_order + nw) + 15) & ~uintptr_t(15));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_hi, w_hi.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_send, w_send.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_sstart, w_sstart.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_next, w_next.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
+            int64_t *d_end = ends.as<int64_t>();
+            int32_t *d_segoff = reinterpret_cast<int32_t *>(d_end + ns);
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_end, src->str_end.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_segoff, segoff.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, st));
+            // order: by rank from the string end, then string (a stable sort by rank of
+            // the segments in string order), so homologous segments of the batch's
+            // strings run side by side
+            uint32_t *ord_v0 = reinterpret_cast<uint32_t *>(d_order);
+            RB3_LAUNCH(k_seg_fill, nb_for(nw, 256), 256, 0, st, d_end, d_segoff, ns, L, nw, d_hi, d_send, d_sstart,
+                       d_next, sk0.as<uint32_t>(), ord_v0);
+            if (maxr > 0) {
+                bool alt = false;
+                RB3_TRY(radix_sort_pairs32(sk0.as<uint32_t>(), ord_v0, sk1.as<uint32_t>(), sv1.as<uint32_t>(), nw, 0,
+                                           ilog2(maxr) + 1, st, &alt));
+                if (alt)
+                    RB3_CUDA_TRY(cudaMemcpyAsync(ord_v0, sv1.p, sizeof(uint32_t) * nw, cudaMemcpyDeviceToDevice, st));
+            }
             RB3_CUDA_TRY(cudaMemsetAsync(d_state, 0, sizeof(int32_t) * nw, st));
             RB3_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st));
             {
                 // per new symbol: 1 B text, 4 B ISA, one rank, 8 B pos (seed steps not counted)
                 Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
-                // the walk is persistent: a grid of cps 256-thread CTAs per SM (default 8,
-                // of which registers let 4 be resident at once)
+                // the walk is persistent: cps x 256 threads per SM (default 8, of which
+                // registers let half be resident at once)
                 const int cps = o.walk_ctas_per_sm > 0 ? (o.walk_ctas_per_sm < 8 ? o.walk_ctas_per_sm : 8) : 8;
                 int64_t resident = (int64_t)num_sms() * 256 * cps;
                 int64_t threads = nw < resident ? nw : resident;
-                unsigned grid = nb_for(threads, 256);
+                unsigned grid = nb_for(threads, WALK_THREADS);
                 if (dst->single_strand)
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, 256, 0, st, V1, m1, src->text,
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
                                                    src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
                                                    cap, d_ctr, pos));
                 else
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, 256, 0, st, V1, m1, src->text,
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
                                                    src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
                                                    cap, d_ctr, pos));
             }

@@ -84,6 +84,8 @@ def lib():
             "rb3_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _i32,
                                                 ctypes.POINTER(_i32)]),
+            "rb3_profile_timeline": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                                    ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(_i64)]),
             "rb3_launch_count": (_i64, []),
             "rb3_tune_merge": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
             "rb3_tune_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp,
@@ -343,6 +345,19 @@ def rb3_profile_read() -> dict:
     n = _i32()
     _check(lib().rb3_profile_read(names, ms, calls, byts, cap, ctypes.byref(n)))
     return {names[i].decode(): (ms[i], calls[i], byts[i]) for i in range(min(n.value, cap))}
+
+
+def rb3_profile_timeline() -> list:
+    """[(name, start_ms, duration_ms)] of every phase since the last reset, start
+    relative to the reset."""
+    n = _i64()
+    _check(lib().rb3_profile_timeline(None, None, None, 0, ctypes.byref(n)))
+    cap = n.value
+    names = (ctypes.c_char_p * max(cap, 1))()
+    st = (ctypes.c_double * max(cap, 1))()
+    du = (ctypes.c_double * max(cap, 1))()
+    _check(lib().rb3_profile_timeline(names, st, du, cap, ctypes.byref(n)))
+    return [(names[i].decode(), st[i], du[i]) for i in range(min(n.value, cap))]
 
 
 def rb3_launch_count() -> int:
