@@ -360,7 +360,7 @@ def mem_search(rb, torch, S, idx, args, st, dev):
     ns = min(Q.nq, 100_000)
     best, tms = rb.rb3_tune_search(idx, q[:int(Q.qoff[ns])], qoff[:ns + 1], 31, 1, stream=st)
     res["autotune_chunk_len"] = int(best.chunk_len)
-    for form, key in ((0, "value"), (1, "plain_value")):
+    for form, key in ((0, "value"), (2, "loops_value"), (1, "plain_value")):
         o = {"search_form": form, "chunk_len": int(best.chunk_len)}
         reps = 2 if form == 0 else 1
         _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up

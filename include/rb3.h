@@ -78,7 +78,8 @@ typedef struct {
     int64_t seg_len;       /* merge: walk segment length L (default: autotuned) */
     int64_t seed_cap;      /* merge: most ForwardExt steps spent on one segment seed (default 4*L) */
     int32_t merge_form;    /* 0: segmented batched walk; 1: plain Algorithm 1, one walk per string */
-    int32_t search_form;   /* 0: chunked work-stealing SMEM search; 1: plain, one query per thread */
+    int32_t search_form;   /* 0: chunked work-stealing SMEM search, one extension per lane per step;
+                              1: plain, one query per thread; 2: chunked, each lane looping on its own */
     int64_t chunk_len;     /* SMEM: query chunk length (default 256) */
     int32_t walk_ctas_per_sm; /* merge: 256-thread CTAs per SM in the persistent walk's grid, 1..8
                                  (default 8, of which 4 are resident at once) */

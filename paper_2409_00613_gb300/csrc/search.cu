@@ -98,6 +98,163 @@ __global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *
     }
 }
 
+// Step-machine form of the chunked search.  The loops of FindSMEM1 (the
+// backward check of a start's first min_len symbols, the forward extension,
+// the chunk-start check and the backward scan for the next start) have
+// data-dependent lengths, so lanes that run them as loops spend most of their
+// time waiting for one another.  Here every lane keeps its place in those
+// loops as a small state, and each turn of the kernel's loop performs exactly
+// one extension for every lane -- a ForwardExt is a BackwardExt of the
+// swapped bi-interval by the complement symbol (Algorithm 3), so all lanes run
+// the same code -- then moves each lane's state on.  Same starts, same
+// extensions, same records as smem_range.
+enum : int { SM_ITEM = 0, SM_B1, SM_F, SM_CHK, SM_B2, SM_DONE };
+
+template <int NS> __device__ __forceinline__ BiInt ext_dir(const OccView &V, BiInt x, int a, bool fwd) {
+    const BiInt xi = fwd ? BiInt{x.kp, x.k, x.s} : x;
+    const BiInt y = backward_ext<NS>(V, xi, fwd ? comp_sym(a) : a);
+    return fwd ? BiInt{y.kp, y.k, y.s} : y;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_smem_steps(OccView V, const uint8_t *__restrict__ q,
+                                                    const int64_t *__restrict__ qoff, int64_t nq,
+                                                    const int64_t *__restrict__ item_off, int64_t nitems,
+                                                    int64_t chunk, int ell, int64_t smin,
+                                                    unsigned long long *__restrict__ next,
+                                                    rb3_smem *__restrict__ out, int64_t cap,
+                                                    unsigned long long *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    EmitAppend em{out, cap, count};
+    int phase = SM_ITEM;
+    const uint8_t *P = q;
+    int64_t qi = 0, len = 0, x0 = 0, x1 = 0, i = 0, j = 0, e = 0, nxt = 0;
+    bool first = false;
+    BiInt x = {0, 0, V.n};
+    for (;;) {
+        // lanes without a chunk take the next ones (one atomic per warp)
+        const unsigned need = __ballot_sync(0xffffffffu, phase == SM_ITEM);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (phase == SM_ITEM) {
+                const int64_t it = (int64_t)base + __popc(need & lt);
+                if (it >= nitems) {
+                    phase = SM_DONE;
+                } else {
+                    int64_t lo = 0, hi = nq;  // query of item it: largest i with item_off[i] <= it
+                    while (hi - lo > 1) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (item_off[mid] <= it) lo = mid;
+                        else hi = mid;
+                    }
+                    qi = lo;
+                    P = q + qoff[qi];
+                    len = qoff[qi + 1] - qoff[qi];
+                    x0 = (it - item_off[qi]) * chunk;
+                    x1 = x0 + chunk < len ? x0 + chunk : len;
+                    i = x0;
+                    first = x0 > 0;
+                    if (i >= x1 || i + ell > len) {
+                        phase = SM_ITEM;  // nothing starts in this chunk
+                    } else {
+                        x = BiInt{0, 0, V.n};
+                        j = i + ell - 1;
+                        phase = SM_B1;
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(0xffffffffu, phase != SM_DONE) == 0) break;
+        if (phase == SM_ITEM || phase == SM_DONE) continue;
+        // one extension per lane
+        const int64_t at = phase == SM_CHK ? x0 - 1 : j;
+        const BiInt y = ext_dir<NS>(V, x, P[at], phase == SM_F);
+        bool to_start = false, after_f = false;
+        if (phase == SM_B1) {
+            if (y.s < smin) {
+                i = j + 1;
+                first = false;
+                to_start = true;
+            } else {
+                x = y;
+                if (j == i) {
+                    j = i + ell;
+                    if (j >= len) {
+                        e = len;
+                        after_f = true;
+                    } else {
+                        phase = SM_F;
+                    }
+                } else {
+                    --j;
+                }
+            }
+        } else if (phase == SM_F) {
+            if (y.s < smin) {
+                e = j;
+                after_f = true;
+            } else {
+                x = y;
+                if (++j == len) {
+                    e = len;
+                    after_f = true;
+                }
+            }
+        } else if (phase == SM_CHK) {
+            // chunk start x0 > 0: spurious if P[x0-1, e) still occurs >= smin times
+            first = false;
+            if (y.s < smin) em(qi, i, e, x);
+            if (e == len) {
+                phase = SM_ITEM;
+            } else {
+                x = BiInt{0, 0, V.n};
+                j = e;
+                nxt = i + 1;
+                phase = SM_B2;
+            }
+        } else {  // SM_B2: the next start
+            if (y.s < smin) {
+                i = j + 1;
+                to_start = true;
+            } else {
+                x = y;
+                if (--j < i + 1) {
+                    i = nxt;
+                    to_start = true;
+                }
+            }
+        }
+        if (after_f) {
+            if (first) {
+                phase = SM_CHK;
+            } else {
+                em(qi, i, e, x);
+                if (e == len) {
+                    phase = SM_ITEM;
+                } else {
+                    x = BiInt{0, 0, V.n};
+                    j = e;
+                    nxt = i + 1;
+                    phase = SM_B2;
+                }
+            }
+        }
+        if (to_start) {
+            if (i >= x1 || i + ell > len) {
+                phase = SM_ITEM;
+            } else {
+                x = BiInt{0, 0, V.n};
+                j = i + ell - 1;
+                phase = SM_B1;
+            }
+        }
+    }
+}
+
 __global__ void k_smem_keys(const rb3_smem *__restrict__ r, int64_t n, uint64_t *__restrict__ key,
                             uint32_t *__restrict__ val) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -151,6 +308,7 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
     int64_t chunk = o.chunk_len > 0 ? o.chunk_len : tuned_chunk_len(idx, nq, total_q);
     if (chunk <= 0) chunk = 256;
     const bool plain = o.search_form == 1;
+    const bool loops = o.search_form == 2;  // chunked, each lane running FindSMEM1's loops
     std::vector<int64_t> item_off;
     int64_t nitems = nq;
     if (!plain) {
@@ -181,16 +339,22 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
         RB3_CUDA_TRY(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), st));
         unsigned long long *d_next = ctr.as<unsigned long long>(), *d_count = d_next + 1;
         {
-            Phase ph(plain ? "k.smem_plain" : "k.smem_chunked", st, (double)total_q);  // bytes = query bases
+            Phase ph(plain ? "k.smem_plain" : (loops ? "k.smem_chunked" : "k.smem_steps"), st,
+                     (double)total_q);  // bytes = query bases
             if (plain) {
                 RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_plain<NS>, nb_for(nq, 128), 128, 0, st, V, q, qoff, nq,
                                                (int)min_len, min_occ, raw.as<rb3_smem>(), scap, d_count));
             } else {
                 int64_t resident = (int64_t)num_sms() * 2048;
                 int64_t threads = nitems < resident ? nitems : resident;
-                RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_chunked<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff, nq,
-                                               items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ, d_next,
-                                               raw.as<rb3_smem>(), scap, d_count));
+                if (loops)
+                    RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_chunked<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff,
+                                                   nq, items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ,
+                                                   d_next, raw.as<rb3_smem>(), scap, d_count));
+                else
+                    RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_steps<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff,
+                                                   nq, items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ,
+                                                   d_next, raw.as<rb3_smem>(), scap, d_count));
             }
         }
         RB3_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));

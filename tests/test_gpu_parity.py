@@ -163,7 +163,7 @@ def test_smem_vs_oracle(chunk, ell, smin, D):
     rb.rb3_merge(idx, build(S, 3, 6, occ_interval=D))
     Q = synth.mem_queries(S, seed=32, nq=300, median=80, lo=1, hi=600, sub=0.02)
     want = oracle.smem(B, Q.q, Q.qoff, ell, smin)
-    for form in (0, 1):
+    for form in (0, 1, 2):
         recs, n = rb.rb3_mem_search_opts(idx, torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV),
                                          ell, smin, {"chunk_len": chunk, "search_form": form})
         assert np.array_equal(smem_rows(recs, n), want), (form, chunk, ell, smin)
