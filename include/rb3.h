@@ -277,7 +277,8 @@ int64_t rb3_launch_count(void);
  * each thread keeps 4 independent reads in flight; dependent = 1: each thread
  * follows a chain whose next address depends on the data read (the pattern of
  * an LF walk); 2 and 3: the same with bytes_per_access/32 lanes reading the
- * sectors of one access in a single instruction (one request per access).
+ * sectors of one access in a single instruction (one request per access);
+ * 4 and 5: 0 and 1 with a 64-byte L2 fetch-size hint on every read.
  * Writes the delivered GB/s and millions of reads per second. */
 int rb3_probe_random_gather(int32_t bytes_per_access, int32_t dependent, int32_t threads_per_sm, int64_t buffer_bytes,
                             double *gbs, double *maccess_per_s, void *stream);

@@ -191,6 +191,19 @@ __device__ __forceinline__ Sec ld_sec(const uint8_t *p) {
     return s;
 }
 
+// The same load with a 64-byte L2 fetch-size hint: on a miss L2 asks DRAM for
+// the 64-byte half-line holding the sector instead of the whole 128-byte line
+// (measured: half the DRAM bytes per random sector read, same request rate).
+// Every rank's block reads use it: they are random.
+__device__ __forceinline__ Sec ld_sec64(const uint8_t *p) {
+    Sec s;
+    asm("ld.global.nc.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(s.w[0]), "=r"(s.w[1]), "=r"(s.w[2]), "=r"(s.w[3]), "=r"(s.w[4]), "=r"(s.w[5]), "=r"(s.w[6]),
+          "=r"(s.w[7])
+        : "l"(p));
+    return s;
+}
+
 // Payload layout: every 64 symbols of a block form one 32-byte sector holding
 // their 4-bit codes as four 64-bit bit-planes: plane b (bytes 8b..8b+7) has bit
 // o set iff bit b of the code of symbol o is set.  Codes are 0..5, so plane 3
@@ -264,17 +277,17 @@ template <> struct BlockLd<0> {
 template <int NS> __device__ __forceinline__ BlockLd<NS> block_load(const OccView &v, int64_t l) {
     BlockLd<NS> b;
     if constexpr (NS == 0) {
-        b.h = ld_sec(v.blocks + (l >> 5) * 32);
+        b.h = ld_sec64(v.blocks + (l >> 5) * 32);
         b.o = (int)(l & 31);
         b.l = l;
         b.gb = v.gbase ? v.gbase + 5 * (l >> GSPAN_LOG2) : nullptr;
     } else {
         const uint8_t *blk = v.blocks + (l >> v.log2D) * (int64_t)v.bb;
         b.o = (int)(l & (64 * NS - 1));
-        b.h = ld_sec(blk);
+        b.h = ld_sec64(blk);
 #pragma unroll
         for (int j = 0; j < NS; ++j)
-            if (NS == 1 || b.o > 64 * j) b.p[j] = ld_sec(blk + HEADER_BYTES + 32 * j);
+            if (NS == 1 || b.o > 64 * j) b.p[j] = ld_sec64(blk + HEADER_BYTES + 32 * j);
     }
     return b;
 }
@@ -442,7 +455,7 @@ template <int NS> __device__ __forceinline__ BiInt backward_ext(const OccView &v
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
                         if (b1.o > 64 * j && !(b0.o > 64 * j))
-                            b1.p[j] = ld_sec(v.blocks + (e >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * j);
+                            b1.p[j] = ld_sec64(v.blocks + (e >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * j);
             }
         }
         block_rank_all<NS>(b0, r0);

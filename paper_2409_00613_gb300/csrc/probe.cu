@@ -24,17 +24,17 @@ __global__ void k_probe_fill(uint32_t *__restrict__ buf, int64_t nwords, uint64_
         buf[i] = (uint32_t)mix64(seed ^ (uint64_t)i);
 }
 
-template <int NSEC> __device__ __forceinline__ uint32_t read_unit(const uint8_t *p) {
+template <int NSEC, bool H64> __device__ __forceinline__ uint32_t read_unit(const uint8_t *p) {
     uint32_t acc = 0;
     Sec s[NSEC];
 #pragma unroll
-    for (int j = 0; j < NSEC; ++j) s[j] = ld_sec(p + 32 * j);
+    for (int j = 0; j < NSEC; ++j) s[j] = H64 ? ld_sec64(p + 32 * j) : ld_sec(p + 32 * j);
 #pragma unroll
     for (int j = 0; j < NSEC; ++j) acc ^= s[j].w[0] + s[j].w[7];
     return acc;
 }
 
-template <int NSEC>
+template <int NSEC, bool H64>
 __global__ void k_probe_indep(const uint8_t *__restrict__ buf, uint64_t nunits, int iters, uint64_t seed,
                               uint32_t *__restrict__ sink) {
     uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -45,26 +45,28 @@ __global__ void k_probe_indep(const uint8_t *__restrict__ buf, uint64_t nunits, 
         for (int j = 0; j < 4; ++j) u[j] = mix64(seed ^ (t * (uint64_t)iters + i + j)) % nunits;
         uint32_t v[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = read_unit<NSEC>(buf + u[j] * (32 * NSEC));
+        for (int j = 0; j < 4; ++j) v[j] = read_unit<NSEC, H64>(buf + u[j] * (32 * NSEC));
         acc += v[0] ^ v[1] ^ v[2] ^ v[3];
     }
     if (acc == 0x9e3779b9u) sink[0] = acc;
 }
 
-template <int NSEC>
+template <int NSEC, bool H64>
 __global__ void k_probe_chain(const uint8_t *__restrict__ buf, uint64_t nunits, int steps, uint64_t seed,
                               uint32_t *__restrict__ sink) {
     uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     uint64_t u = mix64(seed ^ t) % nunits;
     uint32_t acc = 0;
     for (int s = 0; s < steps; ++s) {
-        uint32_t v = read_unit<NSEC>(buf + u * (32 * NSEC));
+        uint32_t v = read_unit<NSEC, H64>(buf + u * (32 * NSEC));
         acc += v;
         u = mix64(u ^ v ^ (uint64_t)s) % nunits;
     }
     if (acc == 0x9e3779b9u) sink[0] = acc;
 }
 
+// Modes 4 / 5: modes 0 / 1 with a 64-byte L2 fetch-size hint on every read.
+//
 // Cooperative forms: the NSEC lanes of a group read the NSEC sectors of one
 // unit in the same instruction (one request per unit instead of one per
 // sector).  Dependent: the group's next address comes from the data of all
@@ -92,6 +94,7 @@ __global__ void k_probe_coop(const uint8_t *__restrict__ buf, uint64_t nunits, i
 int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t buffer_bytes, double *gbs,
                         double *maccess, cudaStream_t st) {
     RB3_CHECK_ARG(bytes == 32 || bytes == 64 || bytes == 128, "bytes must be 32, 64 or 128");
+    RB3_CHECK_ARG(dependent >= 0 && dependent <= 5, "mode must be 0..5");
     RB3_CHECK_ARG(threads_per_sm >= 32 && threads_per_sm <= 2048 && threads_per_sm % 32 == 0,
                   "threads_per_sm must be a multiple of 32 in [32, 2048]");
     RB3_CHECK_ARG(buffer_bytes >= (int64_t)(1 << 26), "buffer must be at least 64 MiB");
@@ -104,7 +107,7 @@ int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t bu
     const int block = threads_per_sm < 256 ? threads_per_sm : 256;
     const unsigned grid = (unsigned)((int64_t)num_sms() * threads_per_sm / block);
     const int64_t threads = (int64_t)grid * block;
-    const int iters = dependent ? 256 : 512;
+    const int iters = (dependent == 1 || dependent == 3 || dependent == 5) ? 256 : 512;
     cudaEvent_t a, b;
     RB3_CUDA_TRY(cudaEventCreate(&a));
     RB3_CUDA_TRY(cudaEventCreate(&b));
@@ -114,19 +117,31 @@ int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t bu
         const uint8_t *p = buf.as<uint8_t>();
         uint32_t *s = sink.as<uint32_t>();
         uint64_t seed = 1000 + rep;
-        if (dependent >= 2) {  // cooperative: 2 = independent, 3 = dependent
+        if (dependent == 2 || dependent == 3) {  // cooperative: 2 = independent, 3 = dependent
             const int dep = dependent == 3;
             if (bytes == 32) RB3_LAUNCH(k_probe_coop<1>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
             else if (bytes == 64) RB3_LAUNCH(k_probe_coop<2>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
             else RB3_LAUNCH(k_probe_coop<4>, grid, block, 0, st, p, nunits, iters, dep, seed, s);
-        } else if (dependent) {
-            if (bytes == 32) RB3_LAUNCH(k_probe_chain<1>, grid, block, 0, st, p, nunits, iters, seed, s);
-            else if (bytes == 64) RB3_LAUNCH(k_probe_chain<2>, grid, block, 0, st, p, nunits, iters, seed, s);
-            else RB3_LAUNCH(k_probe_chain<4>, grid, block, 0, st, p, nunits, iters, seed, s);
+        } else if (dependent == 1 || dependent == 5) {
+            if (dependent == 5) {
+                if (bytes == 32) RB3_LAUNCH((k_probe_chain<1, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else if (bytes == 64) RB3_LAUNCH((k_probe_chain<2, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else RB3_LAUNCH((k_probe_chain<4, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+            } else {
+                if (bytes == 32) RB3_LAUNCH((k_probe_chain<1, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else if (bytes == 64) RB3_LAUNCH((k_probe_chain<2, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else RB3_LAUNCH((k_probe_chain<4, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+            }
         } else {
-            if (bytes == 32) RB3_LAUNCH(k_probe_indep<1>, grid, block, 0, st, p, nunits, iters, seed, s);
-            else if (bytes == 64) RB3_LAUNCH(k_probe_indep<2>, grid, block, 0, st, p, nunits, iters, seed, s);
-            else RB3_LAUNCH(k_probe_indep<4>, grid, block, 0, st, p, nunits, iters, seed, s);
+            if (dependent == 4) {
+                if (bytes == 32) RB3_LAUNCH((k_probe_indep<1, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else if (bytes == 64) RB3_LAUNCH((k_probe_indep<2, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else RB3_LAUNCH((k_probe_indep<4, true>), grid, block, 0, st, p, nunits, iters, seed, s);
+            } else {
+                if (bytes == 32) RB3_LAUNCH((k_probe_indep<1, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else if (bytes == 64) RB3_LAUNCH((k_probe_indep<2, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+                else RB3_LAUNCH((k_probe_indep<4, false>), grid, block, 0, st, p, nunits, iters, seed, s);
+            }
         }
         RB3_CUDA_TRY(cudaEventRecord(b, st));
         RB3_CUDA_TRY(cudaEventSynchronize(b));
@@ -137,7 +152,7 @@ int probe_random_gather(int bytes, int dependent, int threads_per_sm, int64_t bu
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     double accesses = (double)threads * iters;
-    if (dependent >= 2) accesses /= (bytes / 32);  // one access per lane group
+    if (dependent == 2 || dependent == 3) accesses /= (bytes / 32);  // one access per lane group
     if (gbs) *gbs = accesses * bytes / (best * 1e-3) / 1e9;
     if (maccess) *maccess = accesses / (best * 1e-3) / 1e6;
     return RB3_OK;
