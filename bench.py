@@ -43,6 +43,17 @@ WORKLOAD = ("pangenome merge: 5 Mb uniform founder, 50 haplotypes (0.1% SNPs, 0.
 METRIC = "BWT-merge Msymbols/s"
 
 
+# DRAM traffic per launch of the kernel the roofline reports, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the four
+# timed merges of the default workload, averaged:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+#       -k regex:k_merge_walk -s 3 -c 4 python bench.py --no-cpu --no-serve --no-search --no-plain
+#       --warmup 3 --steps 4 --seg-len 642
+# Keyed by (kernel, Occ interval, founder bp); reported only for that workload.
+# Must be taken again (or removed) whenever the kernel changes.
+NCU_TRAFFIC = {("k.merge_walk", 32, 5_000_000): 16.12e9}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -276,7 +287,8 @@ def run_rb3(args, rank, world, local_rank):
         kms, kcalls, kbytes = kern[top]
         achieved = kbytes / (kms * 1e-3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": NCU_TRAFFIC.get((top, info["occ_interval"], founder)),
                 "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),
                 "launches": kcalls, "share_of_step": round(kms / ms, 4)}
     phases = {k: round(v[0], 3) for k, v in sorted(prof.items())}
