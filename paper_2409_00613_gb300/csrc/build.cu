@@ -99,16 +99,19 @@ __global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__r
 // (fs) and of larger groups (fl).  A group starting at g has more than SMALL_MAX
 // members iff the entry SMALL_MAX places after g still has group start g.
 __global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart, int64_t n,
-                                  int32_t *__restrict__ rank, uint32_t *__restrict__ fs, uint32_t *__restrict__ fl) {
+                                  int32_t *__restrict__ rank, uint32_t *__restrict__ fs, uint32_t *__restrict__ fl,
+                                  uint32_t *__restrict__ gsize) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t g = gstart[i];
-    bool single = g == (uint32_t)i && (i + 1 == n || gstart[i + 1] == (uint32_t)(i + 1));
+    const bool last = i + 1 == n || gstart[i + 1] != g;
+    bool single = g == (uint32_t)i && last;
     bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
     // members of small groups get their rank from k_expand_groups, in locus order
     if (single || large) rank[SA[i]] = (int32_t)g;
     fs[i] = (g == (uint32_t)i && !single && !large) ? 1u : 0u;  // head of a group of 2..SMALL_MAX
     fl[i] = large ? 1u : 0u;
+    if (last && !single && !large) gsize[g] = (uint32_t)(i - g + 1);  // a small group's size, at its head
 }
 
 // The groups of 2..SMALL_MAX members are listed in the order of their first
@@ -125,14 +128,12 @@ __global__ void k_head_pairs(const uint32_t *__restrict__ SA, const uint32_t *__
     hval[ps[i]] = (uint32_t)i;
 }
 
-__global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, const uint32_t *__restrict__ gstart,
-                              int64_t n, uint32_t *__restrict__ gsz) {
+// Small group j in locus order: its size, kept at its head by k_init_rank_flags.
+__global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, const uint32_t *__restrict__ gsize,
+                              uint32_t *__restrict__ gsz) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= G) return;
-    uint32_t h = hval[j];
-    int64_t t = 1;
-    while (h + t < n && gstart[h + t] == h) ++t;
-    gsz[j] = (uint32_t)t;
+    gsz[j] = gsize[hval[j]];
 }
 
 __global__ void k_expand_groups(const uint32_t *__restrict__ hval, const uint32_t *__restrict__ gsz,
@@ -521,7 +522,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(ps.alloc(sizeof(uint32_t) * n, st));
             RB3_TRY(pl.alloc(sizeof(uint32_t) * n, st));
             RB3_LAUNCH(k_init_rank_flags, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA),
-                       hv.as<uint32_t>(), n, rank, fs.as<uint32_t>(), fl.as<uint32_t>());
+                       hv.as<uint32_t>(), n, rank, fs.as<uint32_t>(), fl.as<uint32_t>(), gsize);
             RB3_TRY(scan_u32(fs.as<uint32_t>(), ps.as<uint32_t>(), n, false, 0, st));
             RB3_TRY(scan_u32(fl.as<uint32_t>(), pl.as<uint32_t>(), n, false, 0, st));
             RB3_LAUNCH(k_tally, 1, 1, 0, st, ps.as<uint32_t>(), fs.as<uint32_t>(), n, d_cnt, 0);
@@ -546,7 +547,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
                                        G, 0, ilog2(n) + 1, st, &halt));
             const uint32_t *hval = halt ? hv1.as<uint32_t>() : hv0.as<uint32_t>();
             if (G > 0)
-                RB3_LAUNCH(k_group_sizes, nb_for(G, 256), 256, 0, st, hval, G, hv.as<uint32_t>(), n, gsz.as<uint32_t>());
+                RB3_LAUNCH(k_group_sizes, nb_for(G, 256), 256, 0, st, hval, G, gsize, gsz.as<uint32_t>());
             RB3_TRY(scan_u32(gsz.as<uint32_t>(), goff.as<uint32_t>(), G, false, 0, st));
             RB3_LAUNCH(k_tally, 1, 1, 0, st, goff.as<uint32_t>(), gsz.as<uint32_t>(), G, d_cnt, 0);
             RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
