@@ -121,39 +121,65 @@ int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, bool inclusive, cudaS
 // ---------------------------------------------------------------------------
 // Radix sort: 8-bit digits, tiles of 4096 pairs (warp w takes items
 // [512w, 512w + 512) of the tile, lane-interleaved over 16 iterations, so item
-// order = (warp, iteration, lane) = input order).  Per pass:
-//   hist    -- per-tile digit counts, digit-major [256][ntiles]
-//   scan    -- exclusive prefix over that array = global digit offsets
-//   scatter -- stable in-tile ranks by warp multi-split (__match_any_sync),
-//              pairs reordered in shared memory, then written out in runs.
-// The scatter holds only the keys and their ranks in registers; a pair's value
-// is loaded after the tile's ranks are known and goes straight to its place in
-// shared memory.  That keeps the kernel at three CTAs per SM.
+// order = (warp, iteration, lane) = input order).  One pass over the keys
+// counts the digits of every pass (a digit's global count does not depend on
+// the order); then each pass is one kernel: a tile takes the next tile number
+// from a counter, ranks its pairs by warp multi-split (__match_any_sync),
+// publishes its digit counts, adds up the counts of the tiles before it
+// (decoupled look-back: a tile's flag is either its own count or the count of
+// everything up to it), and writes its pairs out in runs through shared
+// memory.  A tile only waits for tiles that took their numbers before it, so
+// they are running or done; every wait has an iteration limit, after which
+// the tile records an error (read by the host after the sort).
+// The keys stay in registers with their ranks; a pair's value is loaded after
+// the tile's ranks are known and goes straight to its place in shared memory
+// (80 registers: three CTAs per SM).
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITERS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITERS;
 constexpr int RS_BINS = 256;
+constexpr int RS_MAXPASS = 8;
+constexpr uint64_t RS_AGG = 1ull << 62, RS_INC = 2ull << 62, RS_VAL = (1ull << 62) - 1;
+constexpr int RS_SPIN_LIMIT = 1 << 22;
 
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K *__restrict__ keys, int64_t n, int shift,
-                                                        uint32_t mask, uint32_t *__restrict__ counts,
-                                                        int64_t ntiles) {
-    __shared__ uint32_t h[RS_WARPS][RS_BINS];
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&h[0][0])[i] = 0;
+__global__ void __launch_bounds__(RS_THREADS) k_rs_allhist(const K *__restrict__ keys, int64_t n, int begin_bit,
+                                                           int end_bit, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[RS_MAXPASS][RS_BINS];
+    const int npass = (end_bit - begin_bit + 7) / 8;
+    for (int i = threadIdx.x; i < RS_MAXPASS * RS_BINS; i += RS_THREADS) (&h[0][0])[i] = 0;
     __syncthreads();
-    int w = threadIdx.x >> 5;
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-        int64_t g = base + i;
-        if (g < n) atomicAdd(&h[w][(uint32_t)(keys[g] >> shift) & mask], 1u);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const K k = keys[g];
+        for (int p = 0; p < npass; ++p) {
+            const int sh = begin_bit + 8 * p;
+            const int nb = end_bit - sh < 8 ? end_bit - sh : 8;
+            atomicAdd(&h[p][(uint32_t)(k >> sh) & ((1u << nb) - 1u)], 1u);
+        }
     }
     __syncthreads();
-    uint32_t t = 0;
-#pragma unroll
-    for (int j = 0; j < RS_WARPS; ++j) t += h[j][threadIdx.x];
-    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = t;
+    for (int i = threadIdx.x; i < npass * RS_BINS; i += RS_THREADS) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&counts[i], c);
+    }
+}
+
+// base[p][d] = number of keys whose digit p is below d (one block per pass).
+__global__ void k_rs_bases(const uint32_t *__restrict__ counts, uint32_t *__restrict__ base) {
+    __shared__ uint32_t wtot[32];
+    const int p = blockIdx.x;
+    base[p * RS_BINS + threadIdx.x] = block_excl<uint32_t>(counts[p * RS_BINS + threadIdx.x], 0, wtot);
+}
+
+__device__ __forceinline__ void rs_flag_store(uint64_t *p, uint64_t v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t rs_flag_load(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 template <class K> struct RsSmem {
@@ -163,21 +189,27 @@ template <class K> struct RsSmem {
     uint32_t dstart[RS_BINS];
     uint32_t goff[RS_BINS];
     uint32_t wtot[32];
+    uint32_t tile;
 };
 
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K *__restrict__ kin,
-                                                              const uint32_t *__restrict__ vin,
-                                                              K *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                              int64_t n, int shift, uint32_t mask,
-                                                              const uint32_t *__restrict__ offs, int64_t ntiles) {
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const K *__restrict__ kin,
+                                                               const uint32_t *__restrict__ vin,
+                                                               K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                               int64_t n, int shift, uint32_t mask,
+                                                               const uint32_t *__restrict__ dbase,
+                                                               unsigned int *__restrict__ tile_ctr,
+                                                               uint64_t *__restrict__ flags,
+                                                               unsigned int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smraw[];
     RsSmem<K> &S = *reinterpret_cast<RsSmem<K> *>(smraw);
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.wh[0][0])[i] = 0;
-    S.goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    if (threadIdx.x == 0) S.tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE + w * (RS_ITERS * 32);
+    const int64_t t = S.tile;
+    const int64_t tb = t * RS_TILE;
+    int64_t base = tb + w * (RS_ITERS * 32);
     unsigned lt = (1u << lane) - 1u;
     K kk[RS_ITERS];
     uint32_t lr[RS_ITERS];
@@ -203,22 +235,49 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K *__restric
     }
     __syncthreads();
     // per digit (thread = digit): warp-exclusive offsets and tile total
+    const int d = threadIdx.x;
     uint32_t tot = 0;
 #pragma unroll
     for (int j = 0; j < RS_WARPS; ++j) {
-        uint32_t c = S.wh[j][threadIdx.x];
-        S.wh[j][threadIdx.x] = tot;
+        uint32_t c = S.wh[j][d];
+        S.wh[j][d] = tot;
         tot += c;
     }
+    // publish, look back over the tiles before this one, publish the inclusive count
+    uint64_t *F = flags + t * RS_BINS + d;
+    uint64_t excl = 0;
+    if (t == 0) {
+        rs_flag_store(F, RS_INC | tot);
+    } else {
+        rs_flag_store(F, RS_AGG | tot);
+        for (int64_t tt = t - 1; tt >= 0; --tt) {
+            const uint64_t *G = flags + tt * RS_BINS + d;
+            uint64_t v = rs_flag_load(G);
+            int spins = 0;
+            while ((v >> 62) == 0) {
+                if (++spins > RS_SPIN_LIMIT) {  // recorded; the result is then invalid
+                    atomicOr(err, 1u);
+                    v = RS_INC;
+                    break;
+                }
+                __nanosleep(32);
+                v = rs_flag_load(G);
+            }
+            excl += v & RS_VAL;
+            if ((v >> 62) == 2) break;
+        }
+        rs_flag_store(F, RS_INC | (excl + tot));
+    }
+    S.goff[d] = dbase[d] + (uint32_t)excl;
     uint32_t ds = block_excl<uint32_t>(tot, 0, S.wtot);
-    S.dstart[threadIdx.x] = ds;
+    S.dstart[d] = ds;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < RS_ITERS; ++it) {
         int64_t g = base + it * 32 + lane;
         if (g < n) {
-            uint32_t d = (uint32_t)(kk[it] >> shift) & mask;
-            lr[it] += S.dstart[d] + S.wh[w][d];
+            uint32_t dd = (uint32_t)(kk[it] >> shift) & mask;
+            lr[it] += S.dstart[dd] + S.wh[w][dd];
             S.k[lr[it]] = kk[it];
         }
     }
@@ -229,12 +288,11 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K *__restric
         if (g < n) S.v[lr[it]] = vin[g];
     }
     __syncthreads();
-    int64_t tb = (int64_t)blockIdx.x * RS_TILE;
     int cnt = (int)((n - tb) < RS_TILE ? (n - tb) : RS_TILE);
     for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
         K k = S.k[i];
-        uint32_t d = (uint32_t)(k >> shift) & mask;
-        int64_t gp = (int64_t)S.goff[d] + (i - (int64_t)S.dstart[d]);
+        uint32_t dd = (uint32_t)(k >> shift) & mask;
+        int64_t gp = (int64_t)S.goff[dd] + (i - (int64_t)S.dstart[dd]);
         kout[gp] = k;
         vout[gp] = S.v[i];
     }
@@ -249,33 +307,55 @@ static int radix_sort_impl(K *k0, uint32_t *v0, K *k1, uint32_t *v1, int64_t n, 
         set_error("radix sort: too many elements (%lld)", (long long)n);
         return RB3_E_INVAL;
     }
-    static const cudaError_t attr = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int npass = (end_bit - begin_bit + 7) / 8;
+    if (npass > RS_MAXPASS) {
+        set_error("radix sort: %d key bits", end_bit - begin_bit);
+        return RB3_E_INVAL;
+    }
+    static const cudaError_t attr = cudaFuncSetAttribute(k_rs_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)sizeof(RsSmem<K>));  // once, thread-safe
     RB3_CUDA_TRY(attr);
-    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    DevBuf counts;
-    RB3_TRY(counts.alloc(sizeof(uint32_t) * RS_BINS * ntiles, st));
+    const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    // one buffer: digit counts and bases of every pass, tile counters, error flag, look-back flags
+    const size_t head = sizeof(uint32_t) * (2 * RS_MAXPASS * RS_BINS + RS_MAXPASS + 2);
+    const size_t head_al = (head + 255) & ~size_t(255);
+    DevBuf work;
+    RB3_TRY(work.alloc(head_al + sizeof(uint64_t) * RS_BINS * ntiles, st));
+    uint32_t *counts = work.as<uint32_t>(), *bases = counts + RS_MAXPASS * RS_BINS;
+    unsigned int *ctr = bases + RS_MAXPASS * RS_BINS, *err = ctr + RS_MAXPASS;
+    uint64_t *flags = reinterpret_cast<uint64_t *>(work.as<uint8_t>() + head_al);
+    RB3_CUDA_TRY(cudaMemsetAsync(work.p, 0, head, st));
+    {
+        Phase ph("k.rs_hist", st, (double)sizeof(K) * n);  // reads the keys once for every pass
+        unsigned grid = (unsigned)((n + RS_THREADS * 16 - 1) / (RS_THREADS * 16));
+        if (grid > (unsigned)num_sms() * 8) grid = (unsigned)num_sms() * 8;
+        RB3_LAUNCH(k_rs_allhist<K>, grid, RS_THREADS, 0, st, k0, n, begin_bit, end_bit, counts);
+        RB3_LAUNCH(k_rs_bases, (unsigned)npass, RS_BINS, 0, st, counts, bases);
+    }
     K *ka = k0, *kb = k1;
     uint32_t *va = v0, *vb = v1;
     bool alt = false;
     const double kv = (double)sizeof(K) + 4.0;
-    for (int shift = begin_bit; shift < end_bit; shift += 8) {
-        int nb = end_bit - shift < 8 ? end_bit - shift : 8;
-        uint32_t mask = (1u << nb) - 1u;
-        {
-            Phase ph("k.rs_hist", st, (double)sizeof(K) * n);  // reads the keys
-            RB3_LAUNCH(k_rs_hist<K>, (unsigned)ntiles, RS_THREADS, 0, st, ka, n, shift, mask, counts.as<uint32_t>(),
-                       ntiles);
-        }
-        RB3_TRY(scan_u32(counts.as<uint32_t>(), counts.as<uint32_t>(), RS_BINS * ntiles, false, 0, st));
+    for (int p = 0; p < npass; ++p) {
+        const int shift = begin_bit + 8 * p;
+        const int nb = end_bit - shift < 8 ? end_bit - shift : 8;
+        const uint32_t mask = (1u << nb) - 1u;
+        RB3_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(uint64_t) * RS_BINS * ntiles, st));
         {
             Phase ph("k.rs_scatter", st, 2.0 * kv * n);  // reads and writes (key, 4-byte value)
-            RB3_LAUNCH(k_rs_scatter<K>, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem<K>), st, ka, va, kb, vb, n, shift,
-                       mask, counts.as<uint32_t>(), ntiles);
+            RB3_LAUNCH(k_rs_onesweep<K>, (unsigned)ntiles, RS_THREADS, sizeof(RsSmem<K>), st, ka, va, kb, vb, n,
+                       shift, mask, bases + p * RS_BINS, ctr + p, flags, err);
         }
         K *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
         alt = !alt;
+    }
+    unsigned int herr = 0;
+    RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("radix sort: a tile gave up waiting for the counts of the tiles before it");
+        return RB3_E_TIMEOUT;
     }
     *in_alt = alt;
     return RB3_OK;
