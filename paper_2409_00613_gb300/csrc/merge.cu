@@ -312,6 +312,17 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
     for (int a = 0; a < SIGMA; ++a)
         if (c[a]) atomicAdd(&bcnt[grp][a], c[a]);
     __syncthreads();
+    // exclusive prefix over the groups, one thread per symbol: bcnt[g][a] = count
+    // of a in the tile's symbols before group g
+    if (threadIdx.x < SIGMA) {
+        uint32_t run = 0;
+        for (int g = 0; g < MT / 32; ++g) {
+            const uint32_t v = bcnt[g][threadIdx.x];
+            bcnt[g][threadIdx.x] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
     // write payload word; headers at block starts
     const int D = 1 << log2D;
     const int64_t q = q0 + o8;
@@ -329,8 +340,7 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
         uint32_t *h32 = reinterpret_cast<uint32_t *>(blk);
 #pragma unroll
         for (int a = 1; a < SIGMA; ++a) {
-            int64_t r = base6[a];
-            for (int g = 0; g < ng; ++g) r += bcnt[g][a];
+            int64_t r = base6[a] + bcnt[ng][a];
             if (gi) r -= tbase[((gi << GSPAN_LOG2) / MT) * SIGMA + a];
             h32[a - 1] = (uint32_t)r;
         }
@@ -340,8 +350,7 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
         uint32_t *h32 = reinterpret_cast<uint32_t *>(blk);
         uint8_t hb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int a = 0; a < SIGMA; ++a) {
-            int64_t r = base6[a];
-            for (int g = 0; g < ng; ++g) r += bcnt[g][a];
+            int64_t r = base6[a] + bcnt[ng][a];
             h32[a] = (uint32_t)r;
             hb[a] = (uint8_t)(r >> 32);
         }
