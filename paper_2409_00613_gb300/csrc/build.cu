@@ -136,17 +136,36 @@ __global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, cons
     gsz[j] = gsize[hval[j]];
 }
 
+// A warp lays out 32 consecutive groups, whose places in the list are one
+// contiguous range: lanes stride over that range (coalesced list writes and
+// SA reads), each finding its group among the warp's 32 by a shuffle search.
 __global__ void k_expand_groups(const uint32_t *__restrict__ hval, const uint32_t *__restrict__ gsz,
                                 const uint32_t *__restrict__ goff, int64_t G, const uint32_t *__restrict__ SA,
                                 uint32_t *__restrict__ sp, uint32_t *__restrict__ sg, int32_t *__restrict__ rank) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= G) return;
-    uint32_t h = hval[j], o = goff[j], z = gsz[j];
-    for (uint32_t t = 0; t < z; ++t) {
-        uint32_t p = SA[h + t];
-        sp[o + t] = p;
-        sg[o + t] = h;
-        rank[p] = (int32_t)h;
+    const int lane = threadIdx.x & 31;
+    const int64_t j0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32;
+    if (j0 >= G) return;  // the whole warp
+    const int nvalid = G - j0 < 32 ? (int)(G - j0) : 32;
+    const bool ok = lane < nvalid;
+    const uint32_t h = ok ? hval[j0 + lane] : 0u, o = ok ? goff[j0 + lane] : 0u, z = ok ? gsz[j0 + lane] : 0u;
+    const uint32_t first = __shfl_sync(0xffffffffu, o, 0);
+    const uint32_t end = __shfl_sync(0xffffffffu, o + z, nvalid - 1);
+    for (uint32_t base = first; base < end; base += 32) {
+        const uint32_t x = base + lane;
+        int g = 0;  // the last of the warp's groups that starts at or before x
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int mid = g + step;
+            const uint32_t om = __shfl_sync(0xffffffffu, o, mid < 32 ? mid : 31);
+            if (mid < nvalid && om <= x) g = mid;
+        }
+        const uint32_t hg = __shfl_sync(0xffffffffu, h, g), og = __shfl_sync(0xffffffffu, o, g);
+        if (x < end) {
+            const uint32_t p = SA[hg + (x - og)];
+            sp[x] = p;
+            sg[x] = hg;
+            rank[p] = (int32_t)hg;
+        }
     }
 }
 
