@@ -83,7 +83,10 @@ typedef struct {
     int64_t chunk_len;     /* SMEM: query chunk length (default 256) */
     int32_t walk_ctas_per_sm; /* merge: 256-thread CTAs per SM in the persistent walk's grid, 1..8
                                  (default 8, of which 4 are resident at once) */
-    int32_t reserved[7];
+    int32_t sa_sample;     /* build: keep a sampled suffix array for rb3_locate: every suffix starting at
+                              an offset of its string that is a multiple of sa_sample (a power of two,
+                              2..1024; 0 = none).  A merge keeps it when both inputs have the same rate. */
+    int32_t reserved[6];
 } rb3_opts;
 
 /* One SMEM: query qid, query interval [start, end), and the SA bi-interval
@@ -142,6 +145,18 @@ int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *len, i
  * qoff: nq+1 non-decreasing offsets; lo_hi: 2*nq int64, caller-owned. */
 int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                         int64_t *lo_hi, void *stream);
+
+/* Locate (Section "Locating with FM-index", Algorithm 2): for each row i of
+ * the BWT (0 <= rows[j] < n), out[2j] = the index of the string its suffix
+ * starts in (strings numbered as concatenated: P0, rc(P0), P1, ... for a
+ * double-strand index, in the order they were built and merged) and
+ * out[2j+1] = the offset of the suffix on that string.  Needs an index built
+ * with opts.sa_sample = s (merges keep the sample when both inputs have the
+ * same rate); the sample holds every suffix starting at an offset that is a
+ * multiple of s, so a row takes at most s - 1 LF steps.  rows and out may be
+ * host or device memory.  RB3_E_INVAL on a row outside [0, n) or an index
+ * without a sample. */
+int rb3_locate(const rb3_index *idx, const int64_t *rows, int64_t n_rows, int64_t *out, void *stream);
 
 /* SMEMs of length >= min_len occurring >= min_occ times (Section "Finding
  * supermaximal exact matches", Algorithm 4 with Algorithm 3), for every query.
@@ -232,7 +247,8 @@ int rb3_tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
 int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);
 
 /* n, m, C[0..6] (C[a] = C_B(a), C[6] = n), D and flags (bit0: single strand,
- * bit1: holds build data).  Any output pointer may be NULL. */
+ * bit1: holds build data, bits 8..: the sampled suffix array's rate, 0 if none).
+ * Any output pointer may be NULL. */
 int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int32_t *occ_interval,
                    int32_t *flags);
 
@@ -240,7 +256,8 @@ int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int
 int rb3_drop_build_data(rb3_index *idx);
 
 /* Static on-disk image (header + the packed blocks, which already hold the
- * Occ checkpoints, + the span bases of a D = 32 index past 2^32), in the spirit of the paper's static, memory-mappable BWT
+ * Occ checkpoints, + the span bases of a D = 32 index past 2^32, + the sampled
+ * suffix array when there is one), in the spirit of the paper's static, memory-mappable BWT
  * (Section "BWT construction").  Appending after a load continues the build. */
 int rb3_index_save(const rb3_index *idx, const char *path);
 int rb3_index_load(const char *path, void *stream, rb3_index **out);

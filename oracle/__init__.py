@@ -194,6 +194,19 @@ def backward_search(B, q, qoff) -> np.ndarray:
     return out
 
 
+def locate(T, SA, rows) -> np.ndarray:
+    """Section "Locating with FM-index": the suffix of BWT row i starts at text
+    position S(i); reported as (index of the string it lies in, offset on that
+    string), strings numbered in the order of their sentinels in T.  Written
+    out from that definition (numpy), not from Algorithm 2's sampling."""
+    T = np.asarray(T)
+    ends = np.flatnonzero(T == 0)  # the sentinel ending each string, in order
+    p = np.asarray(SA, dtype=np.int64)[np.asarray(rows, dtype=np.int64)]
+    t = np.searchsorted(ends, p)  # first sentinel at or after p
+    start = np.where(t == 0, 0, ends[np.maximum(t - 1, 0)] + 1)
+    return np.stack([t.astype(np.int64), p - start], axis=1)
+
+
 def ext(B, kks, a: int, forward: bool):
     B, pb = _u8(B)
     x = np.array(kks, dtype=np.int64)

@@ -228,6 +228,7 @@ static void free_index(rb3_index *x) {
     dev_free(x->gbase, st);
     dev_free(x->text, st);
     dev_free(x->isa, st);
+    free_samples(x);
     cudaStreamSynchronize(st);
     delete x;
 }
@@ -447,7 +448,8 @@ RB3_EXPORT int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int6
     if (C)
         for (int a = 0; a <= SIGMA; ++a) C[a] = idx->C[a];
     if (occ_interval) *occ_interval = idx->D;
-    if (flags) *flags = (idx->single_strand ? 1 : 0) | ((idx->text && idx->isa) ? 2 : 0);
+    if (flags)
+        *flags = (idx->single_strand ? 1 : 0) | ((idx->text && idx->isa) ? 2 : 0) | (idx->sa_s << 8);
     return RB3_OK;
 }
 
@@ -477,7 +479,8 @@ RB3_EXPORT int rb3_index_save(const rb3_index *idx, const char *path) {
         return RB3_E_IO;
     }
     int64_t hdr[12] = {1, idx->n, idx->m, idx->C[0], idx->C[1], idx->C[2], idx->C[3], idx->C[4], idx->C[5],
-                       idx->C[6], idx->nblocks, ((int64_t)idx->D << 8) | (idx->single_strand ? 1 : 0)};
+                       idx->C[6], idx->nblocks,
+                       ((int64_t)idx->sa_s << 32) | ((int64_t)idx->D << 8) | (idx->single_strand ? 1 : 0)};
     bool ok = fwrite(k_magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               fwrite(host.data(), 1, bytes, f) == bytes;
     if (ok && idx->gbase) {  // D = 32 past 2^32 symbols: the span bases follow the blocks
@@ -487,6 +490,18 @@ RB3_EXPORT int rb3_index_save(const rb3_index *idx, const char *path) {
             return cuda_fail(cudaGetLastError(), "rb3_index_save", __FILE__, __LINE__);
         }
         ok = fwrite(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
+    }
+    if (ok && idx->sa_s) {  // sampled suffix array: its count, the row directory, the values
+        std::vector<uint64_t> sd(2 * (idx->n / 64 + 1)), sv(idx->n_samples);
+        if (cudaMemcpy(sd.data(), idx->sdir, sizeof(uint64_t) * sd.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (idx->n_samples && cudaMemcpy(sv.data(), idx->svals, sizeof(uint64_t) * sv.size(),
+                                          cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            fclose(f);
+            return cuda_fail(cudaGetLastError(), "rb3_index_save", __FILE__, __LINE__);
+        }
+        const int64_t ns = idx->n_samples;
+        ok = fwrite(&ns, sizeof(ns), 1, f) == 1 && fwrite(sd.data(), sizeof(uint64_t), sd.size(), f) == sd.size() &&
+             fwrite(sv.data(), sizeof(uint64_t), sv.size(), f) == sv.size();
     }
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
@@ -512,7 +527,8 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
         set_error("%s: not an rb3 index image", path);
         return RB3_E_IO;
     }
-    int D = (int)(hdr[11] >> 8);
+    int D = (int)((hdr[11] >> 8) & 0xFFFFFF);
+    const int sa_s = (int)(hdr[11] >> 32);
     int64_t n = hdr[1], nblocks = hdr[10];
     if (!valid_occ_interval(D) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
         fclose(f);
@@ -537,6 +553,17 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
         gb.resize(5 * gbase_rows(n));
         ok = fread(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
     }
+    std::vector<uint64_t> sd, sv;
+    if (ok && sa_s) {
+        int64_t ns = 0;
+        ok = fread(&ns, sizeof(ns), 1, f) == 1 && ns >= 0 && ns <= n + 1;
+        if (ok) {
+            sd.resize(2 * (n / 64 + 1));
+            sv.resize(ns);
+            ok = fread(sd.data(), sizeof(uint64_t), sd.size(), f) == sd.size() &&
+                 fread(sv.data(), sizeof(uint64_t), sv.size(), f) == sv.size();
+        }
+    }
     fclose(f);
     if (!ok) {
         delete x;
@@ -549,6 +576,19 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
         cudaError_t e = cudaMemcpyAsync(x->blocks, host.data(), bytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+    }
+    if (r == RB3_OK && sa_s) {
+        x->sa_s = sa_s;
+        x->n_samples = (int64_t)sv.size();
+        r = dev_alloc((void **)&x->sdir, sizeof(uint64_t) * sd.size(), st);
+        if (r == RB3_OK) r = dev_alloc((void **)&x->svals, sizeof(uint64_t) * (sv.empty() ? 1 : sv.size()), st);
+        if (r == RB3_OK) {
+            cudaError_t e = cudaMemcpyAsync(x->sdir, sd.data(), sizeof(uint64_t) * sd.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && !sv.empty())
+                e = cudaMemcpyAsync(x->svals, sv.data(), sizeof(uint64_t) * sv.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+        }
     }
     if (r == RB3_OK && !gb.empty()) {
         r = dev_alloc((void **)&x->gbase, sizeof(int64_t) * gb.size(), st);

@@ -442,6 +442,8 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
     const int mult = both ? 2 : 1;
     int D = o.occ_interval ? o.occ_interval : kDefaultOccInterval;
     RB3_CHECK_ARG(valid_occ_interval(D), "occ_interval must be 32, 64, 128 or 256");
+    RB3_CHECK_ARG(o.sa_sample == 0 || (o.sa_sample >= 2 && o.sa_sample <= 1024 && (o.sa_sample & (o.sa_sample - 1)) == 0),
+                  "sa_sample must be 0 or a power of two in [2, 1024]");
     std::vector<int64_t> in_off(n_seq + 1, 0), out_off(n_seq + 1, 0);
     for (int64_t s = 0; s < n_seq; ++s) {
         RB3_CHECK_ARG(lens[s] >= 0, "negative string length");
@@ -704,6 +706,12 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(scan_u32(cnt.as<uint32_t>(), cnt.as<uint32_t>(), SIGMA * nb, false, 0, st));
             RB3_LAUNCH(k_headers, nb_for(nb, 256), 256, 0, st, cnt.as<uint32_t>(), nb, out->block_bytes,
                        blocks_buf.as<uint8_t>());
+        }
+        // ---- sampled suffix array (optional) ----
+        if (o.sa_sample) {
+            Phase ps_("build.sample", st);
+            out->sa_s = o.sa_sample;
+            RB3_TRY(sample_batch(out, SA, st));
         }
     }
     out->blocks = static_cast<uint8_t *>(blocks_buf.detach());

@@ -38,6 +38,14 @@ struct rb3_index {
     // D = 32 and n >= 2^32 only: gbase[5 g + a - 1] = rank(a, g * 2^32), a = 1..5,
     // g = 0 .. n >> 32 (device; null otherwise)
     int64_t *gbase = nullptr;
+    // sampled suffix array (optional): a row is sampled when its suffix starts at
+    // an offset of its string that is a multiple of sa_s.  sdir holds, per 64
+    // rows, {bit set of sampled rows, number of sampled rows before them}; svals
+    // the sampled rows' (string << 40 | offset), in row order.
+    int32_t sa_s = 0;
+    int64_t n_samples = 0;
+    uint64_t *sdir = nullptr;   // device, 2 * (n / 64 + 1) words
+    uint64_t *svals = nullptr;  // device, n_samples
     // build data of a batch (optional): its text and inverse suffix array
     uint8_t *text = nullptr;   // device, n codes (0 = sentinel)
     int32_t *isa = nullptr;    // device, n entries
@@ -424,6 +432,15 @@ __device__ __forceinline__ int plane_byte(int o_in_block, int b, int log2D) {
     return HEADER_BYTES + 32 * (o_in_block >> 6) + 8 * b + ((o_in_block & 63) >> 3);
 }
 
+// Sampled suffix array: is row j sampled, and where is its value.
+constexpr int SVAL_OFF_BITS = 40;
+__device__ __forceinline__ bool sample_at(const uint64_t *__restrict__ sdir, int64_t j, int64_t *vidx) {
+    const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(sdir) + (j >> 6));
+    const uint64_t bit = 1ull << (j & 63);
+    *vidx = (int64_t)w.y + __popcll(w.x & (bit - 1));
+    return (w.x & bit) != 0;
+}
+
 // SA bi-interval (k, k', s) of Section "Double-strand BWT".
 struct BiInt {
     int64_t k, kp, s;
@@ -564,6 +581,11 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
+// Sampled suffix array of a batch from its SA (builder) and of a merge (from pos).
+int sample_batch(rb3_index *x, const int32_t *SA, cudaStream_t st);
+int sample_merge(const rb3_index *dst, const rb3_index *src, const int64_t *pos, const int64_t *kstart,
+                 int64_t ntiles, int64_t nM, int tile_rows, rb3_index *out, cudaStream_t st);
+void free_samples(rb3_index *x);
 // Fills idx->C from its blocks (rank of every symbol at n).
 int finalize_counts(rb3_index *idx, cudaStream_t st);
 

@@ -362,6 +362,144 @@ __global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// ---- sampled suffix array through a merge ---------------------------------------
+// The merged rows come from B1 and B2 in the interleaving pos gives, so the
+// merged sample set is the two inputs' sets interleaved the same way; a B2
+// value's string index moves past B1's m1 strings.  Tiles as in k_scatter:
+// thread owns merged rows [q0 + 8 tid, +8), the flagged ones being the next B2
+// rows, the others the next B1 rows.
+struct MergeRows {
+    uint32_t fw;  // bit i: row i of the thread's 8 comes from B2
+    int64_t kb, jb, q;
+    int valid;
+};
+
+__device__ __forceinline__ MergeRows merge_rows(const int64_t *__restrict__ pos, const int64_t *__restrict__ kstart,
+                                                int64_t nM, uint32_t *flags, uint32_t *wtot) {
+    const int64_t t = blockIdx.x;
+    const int64_t q0 = t * MT;
+    const int64_t k0 = kstart[t], k1 = kstart[t + 1];
+    for (int i = threadIdx.x; i < MT / 32; i += MT_THREADS) flags[i] = 0;
+    __syncthreads();
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += MT_THREADS) {
+        const int d = (int)(pos[k] - q0);
+        atomicOr(&flags[d >> 5], 1u << (d & 31));
+    }
+    __syncthreads();
+    MergeRows r;
+    const int o8 = threadIdx.x * 8;
+    r.fw = (flags[o8 >> 5] >> (o8 & 31)) & 0xFFu;
+    const uint32_t before = block_excl<uint32_t>(__popc(r.fw), 0, wtot);
+    r.kb = k0 + before;
+    r.jb = (q0 - k0) + (o8 - (int64_t)before);
+    r.q = q0 + o8;
+    r.valid = r.q >= nM ? 0 : (nM - r.q < 8 ? (int)(nM - r.q) : 8);
+    return r;
+}
+
+__device__ __forceinline__ bool sample_bit(const uint64_t *__restrict__ sdir, int64_t j) {
+    return (sdir[2 * (j >> 6)] >> (j & 63)) & 1u;
+}
+
+// Merged bit words (64 rows = 8 threads) and their sample counts.
+__global__ void __launch_bounds__(MT_THREADS) k_smerge_bits(const uint64_t *__restrict__ sd1,
+                                                            const uint64_t *__restrict__ sd2,
+                                                            const int64_t *__restrict__ pos,
+                                                            const int64_t *__restrict__ kstart, int64_t nM,
+                                                            int64_t nwords, uint64_t *__restrict__ sdo,
+                                                            uint64_t *__restrict__ cnt) {
+    __shared__ uint32_t flags[MT / 32];
+    __shared__ uint32_t wtot[32];
+    const MergeRows r = merge_rows(pos, kstart, nM, flags, wtot);
+    uint32_t byte = 0;
+    int64_t j = r.jb, k = r.kb;
+    for (int i = 0; i < r.valid; ++i) {
+        const bool from2 = (r.fw >> i) & 1u;
+        const bool b = from2 ? sample_bit(sd2, k++) : sample_bit(sd1, j++);
+        byte |= (uint32_t)b << i;
+    }
+    const int jj = threadIdx.x & 7;
+    uint64_t v = (uint64_t)byte << (8 * jj);
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, d);
+    const int64_t word = r.q >> 6;
+    if (jj == 0 && word < nwords) {
+        sdo[2 * word] = v;
+        cnt[word] = __popcll(v);
+    }
+}
+
+__global__ void k_sdir_ranks(const uint64_t *__restrict__ excl, int64_t nwords, uint64_t *__restrict__ sdo) {
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w < nwords) sdo[2 * w + 1] = excl[w];
+}
+
+// Merged values: a sampled merged row takes its source row's value.
+__global__ void __launch_bounds__(MT_THREADS) k_smerge_vals(const uint64_t *__restrict__ sd1,
+                                                            const uint64_t *__restrict__ sv1,
+                                                            const uint64_t *__restrict__ sd2,
+                                                            const uint64_t *__restrict__ sv2, int64_t m1,
+                                                            const int64_t *__restrict__ pos,
+                                                            const int64_t *__restrict__ kstart, int64_t nM,
+                                                            const uint64_t *__restrict__ sdo,
+                                                            uint64_t *__restrict__ svo) {
+    __shared__ uint32_t flags[MT / 32];
+    __shared__ uint32_t wtot[32];
+    const MergeRows r = merge_rows(pos, kstart, nM, flags, wtot);
+    int64_t j = r.jb, k = r.kb;
+    for (int i = 0; i < r.valid; ++i) {
+        const bool from2 = (r.fw >> i) & 1u;
+        int64_t si;
+        const bool smp = from2 ? sample_at(sd2, k, &si) : sample_at(sd1, j, &si);
+        if (smp) {
+            int64_t oi;
+            sample_at(sdo, r.q + i, &oi);
+            svo[oi] = from2 ? sv2[si] + ((uint64_t)m1 << SVAL_OFF_BITS) : sv1[si];
+        }
+        if (from2) ++k;
+        else ++j;
+    }
+}
+
+int sample_merge(const rb3_index *dst, const rb3_index *src, const int64_t *pos, const int64_t *kstart,
+                 int64_t ntiles, int64_t nM, int tile_rows, rb3_index *out, cudaStream_t st) {
+    (void)tile_rows;
+    const int64_t nwords = nM / 64 + 1;
+    uint64_t *sdo = nullptr, *svo = nullptr;
+    RB3_TRY(dev_alloc((void **)&sdo, sizeof(uint64_t) * 2 * nwords, st));
+    DevBuf cnt, excl;
+    RB3_TRY(cnt.alloc(sizeof(uint64_t) * nwords, st));
+    RB3_TRY(excl.alloc(sizeof(uint64_t) * nwords, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(sdo, 0, sizeof(uint64_t) * 2 * nwords, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(uint64_t) * nwords, st));
+    RB3_LAUNCH(k_smerge_bits, (unsigned)ntiles, MT_THREADS, 0, st, dst->sdir, src->sdir, pos, kstart, nM, nwords,
+               sdo, cnt.as<uint64_t>());
+    RB3_TRY(scan_u64(cnt.as<uint64_t>(), excl.as<uint64_t>(), nwords, false, st));
+    RB3_LAUNCH(k_sdir_ranks, nb_for(nwords, 256), 256, 0, st, excl.as<uint64_t>(), nwords, sdo);
+    int64_t tail[2];
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[0], excl.as<uint64_t>() + nwords - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[1], cnt.as<uint64_t>() + nwords - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t ns = tail[0] + tail[1];
+    if (ns != dst->n_samples + src->n_samples) {
+        dev_free(sdo, st);
+        set_error("merge: sampled rows %lld, inputs %lld + %lld", (long long)ns, (long long)dst->n_samples,
+                  (long long)src->n_samples);
+        return RB3_E_CUDA;
+    }
+    int r = dev_alloc((void **)&svo, sizeof(uint64_t) * (ns > 0 ? ns : 1), st);
+    if (r != RB3_OK) {
+        dev_free(sdo, st);
+        return r;
+    }
+    RB3_LAUNCH(k_smerge_vals, (unsigned)ntiles, MT_THREADS, 0, st, dst->sdir, dst->svals, src->sdir, src->svals,
+               dst->m, pos, kstart, nM, sdo, svo);
+    out->sdir = sdo;
+    out->svals = svo;
+    out->n_samples = ns;
+    return RB3_OK;
+}
+
 // Bytes one rank needs: the symbol's count word(s) and, on average, the payload
 // before the offset (D = 32: the count word and the three 4-byte planes).
 static inline double rank_bytes(int D) { return D == 32 ? 16.0 : 5.0 + D / 4.0; }
@@ -585,6 +723,24 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
                        tbase.as<int64_t>(), nM, nbM, log2D, bb, Mb.as<uint8_t>());
         }
     }
+    // sampled suffix array: kept when both inputs have one at the same rate
+    rb3_index smp;
+    const bool keep_samples = src->sa_s > 0 && src->sdir && (n1 == 0 || (dst->sa_s == src->sa_s && dst->sdir));
+    if (keep_samples) {
+        Phase ph("merge.sample", st);
+        if (n1 == 0) {  // the result is src: a copy of its sample
+            const int64_t nw = n2 / 64 + 1;
+            RB3_TRY(dev_alloc((void **)&smp.sdir, sizeof(uint64_t) * 2 * nw, st));
+            RB3_TRY(dev_alloc((void **)&smp.svals, sizeof(uint64_t) * (src->n_samples > 0 ? src->n_samples : 1), st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(smp.sdir, src->sdir, sizeof(uint64_t) * 2 * nw, cudaMemcpyDeviceToDevice, st));
+            if (src->n_samples > 0)
+                RB3_CUDA_TRY(cudaMemcpyAsync(smp.svals, src->svals, sizeof(uint64_t) * src->n_samples,
+                                             cudaMemcpyDeviceToDevice, st));
+            smp.n_samples = src->n_samples;
+        } else {
+            RB3_TRY(sample_merge(dst, src, pos, kst.as<int64_t>(), ntiles, nM, MT, &smp, st));
+        }
+    }
     // D = 32 past 2^32 symbols: the span bases are the ranks at the tiles where spans start
     int64_t *gb = nullptr;
     if (D == 32 && nM >> GSPAN_LOG2) {
@@ -593,6 +749,13 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
         RB3_LAUNCH(k_span_bases, nb_for(rows * 5, 128), 128, 0, st, tbase.as<int64_t>(), rows, gb);
     }
     // install
+    free_samples(dst);
+    dst->sa_s = keep_samples ? src->sa_s : 0;
+    dst->sdir = smp.sdir;
+    dst->svals = smp.svals;
+    dst->n_samples = smp.n_samples;
+    smp.sdir = nullptr;
+    smp.svals = nullptr;
     if (dst->gbase) dev_free(dst->gbase, st);
     dst->gbase = gb;
     if (dst->blocks) dev_free(dst->blocks, st);

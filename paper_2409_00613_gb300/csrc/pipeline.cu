@@ -35,6 +35,7 @@ void free_built(rb3_index *x) {
     if (!x) return;
     dev_free(x->blocks, 0);
     dev_free(x->gbase, 0);
+    free_samples(x);
     dev_free(x->text, 0);
     dev_free(x->isa, 0);
     cudaStreamSynchronize(0);

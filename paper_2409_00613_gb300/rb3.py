@@ -28,7 +28,7 @@ class rb3_opts(ctypes.Structure):
                 ("seg_len", ctypes.c_int64), ("seed_cap", ctypes.c_int64),
                 ("merge_form", ctypes.c_int32), ("search_form", ctypes.c_int32),
                 ("chunk_len", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("sa_sample", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class rb3_server_opts(ctypes.Structure):
@@ -71,6 +71,7 @@ def lib():
             "rb3_mem_search_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
                                                       ctypes.POINTER(_i64), _vp]),
             "rb3_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rb3_locate": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
             "rb3_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                               ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
             "rb3_drop_build_data": (ctypes.c_int, [_vp]),
@@ -285,7 +286,18 @@ def rb3_index_info(idx: Index) -> dict:
     C = (_i64 * 7)()
     _check(lib().rb3_index_info(idx.handle, ctypes.byref(n), ctypes.byref(m), C, ctypes.byref(D), ctypes.byref(fl)))
     return {"n": n.value, "m": m.value, "C": list(C), "occ_interval": D.value,
-            "single_strand": bool(fl.value & 1), "has_build_data": bool(fl.value & 2)}
+            "single_strand": bool(fl.value & 1), "has_build_data": bool(fl.value & 2),
+            "sa_sample": fl.value >> 8}
+
+
+def rb3_locate(idx: Index, rows, out=None, stream=None):
+    """(string index, offset) of each BWT row; rows: int64 (host array or device tensor)."""
+    r = rows if hasattr(rows, "data_ptr") else np.ascontiguousarray(rows, dtype=np.int64)
+    n = _len(r)
+    if out is None:
+        out = np.empty((n, 2), dtype=np.int64)
+    _check(lib().rb3_locate(idx.handle, _ptr(r), n, _ptr(out), _stream(stream)))
+    return out
 
 
 def rb3_export(idx: Index, codes=None, occ=None, stream=None, want_occ: bool = False):

@@ -276,3 +276,78 @@ def test_autotuner_choices_keep_results():
     assert best.chunk_len in (64, 128, 256, 512, 1024, 4096)
     recs, n = rb.rb3_mem_search(idx, q, qoff, 31, 1)
     assert np.array_equal(smem_rows(recs, n), oracle.smem(want, Q.q, Q.qoff, 31, 1))
+
+
+# ---- locate (sampled suffix array) ------------------------------------------
+
+@pytest.mark.parametrize("D", [32, 64])
+@pytest.mark.parametrize("both", [True, False])
+def test_locate_every_row_vs_oracle(D, both):
+    """Every row of indexes built from several batches (merged into an empty
+    index, segmented and plain merges) located against the oracle's S(i)."""
+    g = synth.rng(800 + D + both)
+    for trial, s in enumerate((2, 8, 32)):
+        n_str = int(g.integers(3, 30))
+        S = synth.random_strings(g, n_str, int(g.integers(5, 500)), n_frac=0.03, allow_empty=True)
+        cuts = sorted(set([0, n_str] + [int(c) for c in g.integers(0, n_str, size=2)]))
+        opts = {"occ_interval": D, "single_strand": int(not both), "sa_sample": s}
+        idx = rb.rb3_index_empty(opts)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            part = build(S, a, b, host=bool(trial & 1), **opts)
+            assert rb.rb3_index_info(part)["sa_sample"] == s
+            rb.rb3_merge_opts(idx, part, dict(opts, merge_form=trial % 2, seg_len=int(g.integers(3, 64))))
+        assert rb.rb3_index_info(idx)["sa_sample"] == s
+        T = oracle.concat(S.seq, S.lens, both)
+        rows = np.arange(len(T), dtype=np.int64)
+        want = oracle.locate(T, oracle.suffix_array(T), rows)
+        assert np.array_equal(rb.rb3_locate(idx, rows), want)
+        assert np.array_equal(rb.rb3_locate(idx, torch.from_numpy(rows).to(DEV)), want)  # device rows
+
+
+def test_locate_smem_hits_spell_the_queries():
+    """SMEM intervals of a pangenome index located: each hit's string, from its
+    offset, spells the query's SMEM; and it equals the oracle's S(i)."""
+    S = synth.pangenome(seed=61, founder_len=30_000, n_hap=9, batch=3)
+    opts = {"sa_sample": 16}
+    idx = rb.rb3_index_empty(opts)
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens.copy(), ends, opts)
+    Q = synth.mem_queries(S, seed=62, nq=400, median=120, lo=31, hi=800, sub=0.01)
+    recs, n = rb.rb3_mem_search(idx, torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV), 31, 1)
+    assert n > 100
+    rows = recs["k"].astype(np.int64)
+    loc = rb.rb3_locate(idx, rows)
+    T = oracle.concat(S.seq, S.lens, True)
+    assert np.array_equal(loc, oracle.locate(T, oracle.suffix_array(T), rows))
+    comp = np.array([0, 4, 3, 2, 1, 5], dtype=np.uint8)
+    ds = []
+    for o, l in zip(S.offsets[:-1], S.lens):
+        s_ = S.seq[o:o + l]
+        ds += [s_, comp[s_[::-1]]]
+    for r, (t, off) in zip(recs, loc):
+        q = Q.q[Q.qoff[r["qid"]] + r["start"]:Q.qoff[r["qid"]] + r["end"]]
+        assert np.array_equal(ds[t][off:off + len(q)], q)
+
+
+def test_locate_errors_and_save_load(tmp_path):
+    S = synth.pangenome(seed=63, founder_len=4_000, n_hap=4, batch=2)
+    plain = build(S)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_locate(plain, np.array([0], np.int64))
+    assert e.value.code == rb.RB3_E_INVAL
+    idx = build(S, 0, 2, sa_sample=8)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_locate(idx, np.array([rb.rb3_index_info(idx)["n"]], np.int64))
+    assert e.value.code == rb.RB3_E_INVAL
+    other = build(S, 0, 2, sa_sample=8)
+    rb.rb3_merge(other, build(S, 2, 4, sa_sample=4))  # different rates: the merge keeps no sample
+    assert rb.rb3_index_info(other)["sa_sample"] == 0
+    rb.rb3_merge(idx, build(S, 2, 4, sa_sample=8))
+    p = str(tmp_path / "s.rb3")
+    rb.rb3_index_save(idx, p)
+    back = rb.rb3_index_load(p)
+    rows = np.arange(rb.rb3_index_info(idx)["n"], dtype=np.int64)
+    assert rb.rb3_index_info(back)["sa_sample"] == 8
+    assert np.array_equal(rb.rb3_locate(back, rows), rb.rb3_locate(idx, rows))
+    T = oracle.concat(S.seq, S.lens, True)
+    assert np.array_equal(rb.rb3_locate(back, rows), oracle.locate(T, oracle.suffix_array(T), rows))

@@ -356,3 +356,41 @@ def test_smem_alg4_equals_definition(ell, smin):
         assert np.array_equal(a, b), (ell, smin, trial)
         a_mt = oracle.smem(B, q, qoff, ell, smin, nthreads=3)
         assert np.array_equal(a, a_mt)
+
+
+# ---- locate -------------------------------------------------------------------
+
+@pytest.mark.parametrize("both", [True, False])
+def test_locate_pins(both):
+    """Section "Locating with FM-index": the oracle's (string, offset) of every
+    row against the input strings written out here: the suffix of row i, read
+    from the brute-force suffix array, is the named string from the named
+    offset followed by its sentinel; every (string, offset) occurs once; and
+    LF moves a row to the row of the same string one offset earlier."""
+    g = synth.rng(4711 + both)
+    S, strs = rand_list(g, 9, 40, n_frac=0.05)
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A", "N": "N"}
+    ds = []
+    for s_ in strs:
+        ds.append(s_)
+        if both:
+            ds.append("".join(comp[c] for c in reversed(s_)))
+    T = oracle.concat(S.seq, S.lens, both)
+    SA = np.array(py_sa(T), dtype=np.int64)
+    loc = oracle.locate(T, SA, np.arange(len(T)))
+    text = dec(T)
+    seen = set()
+    for i, (t, off) in enumerate(loc):
+        want = ds[t][off:] + "$"
+        assert text[SA[i]:SA[i] + len(want)] == want
+        seen.add((int(t), int(off)))
+    assert seen == {(t, o) for t in range(len(ds)) for o in range(len(ds[t]) + 1)}
+    B = oracle.bwt_from_sa(T, SA.astype(np.int64))
+    C = oracle.counts(B)  # C_B(a) for a = $..N, then n
+    row_of = {(int(t), int(o)): i for i, (t, o) in enumerate(loc)}
+    for i, (t, off) in enumerate(loc):
+        if off == 0:
+            continue
+        a = int(B[i])
+        lf = C[a] + int(np.count_nonzero(B[:i] == a))
+        assert lf == row_of[(int(t), int(off) - 1)]
