@@ -319,6 +319,8 @@ def run_rb3(args, rank, world, local_rank):
         if not args.no_serve:
             out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
     idx.free()
+    if not args.no_search and rank == 0:
+        out["locate"] = locate_bench(rb, torch, S, args, st, dev, opts, batches, off)
     if args.serve_full and rank == 0:
         out["served_full"] = served_full(rb, torch, st, dev, opts)
     if rank == 0 and not args.no_cpu and world == 1:
@@ -355,6 +357,49 @@ def plain_vs_segmented(rb, torch, dev_batches, opts, st, ds):
     res["speedup"] = round(res["plain_ms"] / res["segmented_ms"], 2)
     res["batch"] = "batch 1 (10 haplotypes, both strands) into batch 0"
     res["new_symbols"] = ds[1]
+    return res
+
+
+def locate_bench(rb, torch, S, args, st, dev, opts, batches, off, s=32):
+    """Locate (Algorithm 2) on the same workload built with a sampled suffix
+    array: the extra build time of the sample, and the SMEM hits of the
+    benchmark queries located (the first row of every SMEM interval)."""
+    ends = np.array([b for (_, b) in batches], dtype=np.int64)
+    seq = torch.from_numpy(S.seq.copy()).to(dev)
+    res = {"sa_sample": s}
+    times = {}
+    for rate in (0, s):
+        o = dict(opts, sa_sample=rate)
+        idx = rb.rb3_index_empty(o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb.rb3_append_batches(idx, seq, S.lens.copy(), ends, o, stream=st)
+        torch.cuda.synchronize()
+        times[rate] = (time.perf_counter() - t0) * 1e3
+        if rate:
+            Q = synth.mem_queries(S, nq=args.queries)
+            q = torch.from_numpy(Q.q).to(dev)
+            qoff = torch.from_numpy(Q.qoff).to(dev)
+            cap = max(1 << 20, int(Q.qoff[-1]) // 16)
+            recs = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
+            _, n = rb.rb3_mem_search(idx, q, qoff, 31, 1, out=recs, cap=cap, stream=st)
+            rows = recs[:n * 40].view(n, 40)[:, 16:24].contiguous().view(torch.int64).flatten()
+            out = torch.empty((n, 2), dtype=torch.int64, device=dev)
+            rb.rb3_locate(idx, rows, out=out, stream=st)  # warm-up
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            rb.rb3_locate(idx, rows, out=out, stream=st)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            res.update({"rows": int(n), "ms": round(ms, 3), "value": round(n / (ms * 1e3), 2), "unit": "M rows/s",
+                        "what": "the first row of every SMEM of the MEM-search queries"})
+        idx.free()
+    res["append"] = "all five batches appended to an empty index, ms"
+    res["append_ms_without_sample"] = round(times[0], 1)
+    res["append_ms_with_sample"] = round(times[s], 1)
     return res
 
 
