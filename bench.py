@@ -318,6 +318,8 @@ def run_rb3(args, rank, world, local_rank):
         out["mem_search"] = mem_search(rb, torch, S, idx, args, st, dev)
         if not args.no_serve:
             out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
+        out["run_length"] = run_length_bench(rb, torch, S, idx, args, st, dev,
+                                             out["mem_search"]["autotune_chunk_len"])
     idx.free()
     if not args.no_search and rank == 0:
         out["locate"] = locate_bench(rb, torch, S, args, st, dev, opts, batches, off)
@@ -400,6 +402,50 @@ def locate_bench(rb, torch, S, args, st, dev, opts, batches, off, s=32):
     res["append"] = "all five batches appended to an empty index, ms"
     res["append_ms_without_sample"] = round(times[0], 1)
     res["append_ms_with_sample"] = round(times[s], 1)
+    return res
+
+
+def run_length_bench(rb, torch, S, idx, args, st, dev, chunk_len):
+    """The finished index compressed to the run-length layout at a few span
+    lengths: its device bytes against the plain index's, the compression time,
+    and the MEM search of the benchmark queries on it (same outputs as on the
+    plain index, checked on the device)."""
+    Q = synth.mem_queries(S, nq=args.queries)
+    q = torch.from_numpy(Q.q).to(dev)
+    qoff = torch.from_numpy(Q.qoff).to(dev)
+    bp = int(Q.qoff[-1])
+    cap = max(1 << 20, bp // 16)
+    o = {"search_form": 0, "chunk_len": int(chunk_len)}
+    ref = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
+    _, n_ref = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=ref, cap=cap, stream=st)
+    info = rb.rb3_index_info(idx)
+    plain = rb.rb3_index_bytes(idx)["device_bytes"]
+    res = {"plain_bytes": plain, "plain_occ_interval": info["occ_interval"], "spans": []}
+    out = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
+    for span in (1024, 4096, 16384):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R = rb.rb3_index_compress(idx, span, stream=st)
+        torch.cuda.synchronize()
+        cms = (time.perf_counter() - t0) * 1e3
+        nb = rb.rb3_index_bytes(R)
+        _, n = rb.rb3_mem_search_opts(R, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        _, n = rb.rb3_mem_search_opts(R, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        same = n == n_ref and bool(torch.equal(out[:n * 40], ref[:n_ref * 40]))
+        res["spans"].append({"span": span, "runs": nb["runs"], "avg_run": round(info["n"] / max(1, nb["runs"]), 1),
+                             "bytes": nb["device_bytes"], "bytes_per_symbol": round(nb["device_bytes"] / info["n"], 4),
+                             "vs_plain": round(nb["device_bytes"] / plain, 4), "compress_ms": round(cms, 1),
+                             "mem_search_value": round(bp / (ms * 1e3), 2), "mem_search_ms": round(ms, 3),
+                             "equal_output": same})
+        R.free()
+    res["unit"] = "Mbp/s (mem_search_value)"
     return res
 
 

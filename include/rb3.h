@@ -246,19 +246,45 @@ int rb3_tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
  * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */
 int rb3_export(const rb3_index *idx, uint8_t *codes, int64_t *occ, void *stream);
 
-/* n, m, C[0..6] (C[a] = C_B(a), C[6] = n), D and flags (bit0: single strand,
- * bit1: holds build data, bits 8..: the sampled suffix array's rate, 0 if none).
+/* n, m, C[0..6] (C[a] = C_B(a), C[6] = n), D (the span S of a run-length
+ * index) and flags (bit0: single strand, bit1: holds build data, bit2:
+ * run-length layout, bits 8..: the sampled suffix array's rate, 0 if none).
  * Any output pointer may be NULL. */
 int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int32_t *occ_interval,
                    int32_t *flags);
+
+/* Run-length copy of a finished index for queries (Section "BWT construction",
+ * Fig. 2b: the static, run-length encoded BWT with marginal counts per block).
+ * The BWT is cut into spans of `span` symbols (a power of two, 512..65536;
+ * 0 = 1024).  Device layout: one 32-byte header per span (uint32 rank of A..N
+ * at the span start, relative to its 2^32-symbol range, as for D = 32; the
+ * uint64 byte offset of the span's runs; their number), then the runs, cut at
+ * span boundaries, one byte each (symbol << 5 | f: f < 30 gives length f + 1,
+ * f = 30 length 31 + the next byte, f = 31 length 287 + the next two bytes,
+ * little-endian).  A rank reads the span's header and decodes its runs up to
+ * the position.  The copy keeps src's sampled suffix array; src is unchanged.
+ * rb3_backward_search, rb3_mem_search (all forms), rb3_mem_search_noalloc,
+ * the server, rb3_locate, rb3_export (occ rows = the span headers),
+ * rb3_index_save / rb3_index_load take it; rb3_merge and rb3_append_batches
+ * reject it (RB3_E_INVAL): merge plain indexes, then compress.
+ * RB3_E_INVAL for a bad span or a src that is already run-length encoded. */
+int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_index **out);
+
+/* Device bytes the index holds (blocks or span headers, runs, span bases,
+ * sampled suffix array; build data not counted) and its number of runs (-1
+ * for a plain index).  Either pointer may be NULL. */
+int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs);
 
 /* Frees the batch text and inverse suffix array kept by rb3_build_batch. */
 int rb3_drop_build_data(rb3_index *idx);
 
 /* Static on-disk image (header + the packed blocks, which already hold the
- * Occ checkpoints, + the span bases of a D = 32 index past 2^32, + the sampled
- * suffix array when there is one), in the spirit of the paper's static, memory-mappable BWT
- * (Section "BWT construction").  Appending after a load continues the build. */
+ * Occ checkpoints, + the span bases of a D = 32 or run-length index past 2^32,
+ * + a run-length index's runs, + the sampled suffix array when there is one),
+ * in the spirit of the paper's static, memory-mappable BWT (Section "BWT
+ * construction").  Appending after a load continues the build.  A run-length
+ * image is checked on load (offsets, run lengths and counts span by span);
+ * an inconsistent one gives RB3_E_IO. */
 int rb3_index_save(const rb3_index *idx, const char *path);
 int rb3_index_load(const char *path, void *stream, rb3_index **out);
 

@@ -207,6 +207,24 @@ def locate(T, SA, rows) -> np.ndarray:
     return np.stack([t.astype(np.int64), p - start], axis=1)
 
 
+def runs(B, span: int = 0):
+    """Section "BWT construction" (Fig. 2): the run-length form of the BWT, its
+    maximal runs of one symbol, as (symbols, lengths); with span > 0 every run
+    is also cut at the positions that are multiples of span (the blocks of the
+    static encoding).  Written out from that definition (numpy)."""
+    B = np.asarray(B, dtype=np.uint8)
+    n = len(B)
+    if n == 0:
+        return np.zeros(0, np.uint8), np.zeros(0, np.int64)
+    starts = np.ones(n, dtype=bool)  # position i starts a run
+    starts[1:] = B[1:] != B[:-1]
+    if span > 0:
+        starts[::span] = True
+    first = np.flatnonzero(starts)
+    lengths = np.diff(np.append(first, n)).astype(np.int64)
+    return B[first].copy(), lengths
+
+
 def ext(B, kks, a: int, forward: bool):
     B, pb = _u8(B)
     x = np.array(kks, dtype=np.int64)

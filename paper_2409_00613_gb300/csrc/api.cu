@@ -186,6 +186,7 @@ __global__ void k_occ_export(OccView V, int64_t nblocks, int64_t *__restrict__ o
 }
 
 int export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st) {
+    if (x->rle) return rle_export_impl(x, codes, occ, st);
     OccView V = occ_view(x);
     if (codes && x->n > 0) {
         int64_t th = (x->n + 7) / 8;
@@ -226,6 +227,7 @@ static void free_index(rb3_index *x) {
     cudaStream_t st = 0;
     dev_free(x->blocks, st);
     dev_free(x->gbase, st);
+    dev_free(x->payload, st);
     dev_free(x->text, st);
     dev_free(x->isa, st);
     free_samples(x);
@@ -449,7 +451,8 @@ RB3_EXPORT int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int6
         for (int a = 0; a <= SIGMA; ++a) C[a] = idx->C[a];
     if (occ_interval) *occ_interval = idx->D;
     if (flags)
-        *flags = (idx->single_strand ? 1 : 0) | ((idx->text && idx->isa) ? 2 : 0) | (idx->sa_s << 8);
+        *flags = (idx->single_strand ? 1 : 0) | ((idx->text && idx->isa) ? 2 : 0) | (idx->rle ? 4 : 0) |
+                 (idx->sa_s << 8);
     return RB3_OK;
 }
 
@@ -480,16 +483,27 @@ RB3_EXPORT int rb3_index_save(const rb3_index *idx, const char *path) {
     }
     int64_t hdr[12] = {1, idx->n, idx->m, idx->C[0], idx->C[1], idx->C[2], idx->C[3], idx->C[4], idx->C[5],
                        idx->C[6], idx->nblocks,
-                       ((int64_t)idx->sa_s << 32) | ((int64_t)idx->D << 8) | (idx->single_strand ? 1 : 0)};
+                       ((int64_t)idx->sa_s << 32) | ((int64_t)idx->D << 8) | (idx->rle ? 2 : 0) |
+                           (idx->single_strand ? 1 : 0)};
     bool ok = fwrite(k_magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               fwrite(host.data(), 1, bytes, f) == bytes;
-    if (ok && idx->gbase) {  // D = 32 past 2^32 symbols: the span bases follow the blocks
+    if (ok && idx->gbase) {  // D = 32 or run-length past 2^32 symbols: the span bases follow the blocks
         std::vector<int64_t> gb(5 * gbase_rows(idx->n));
         if (cudaMemcpy(gb.data(), idx->gbase, sizeof(int64_t) * gb.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
             fclose(f);
             return cuda_fail(cudaGetLastError(), "rb3_index_save", __FILE__, __LINE__);
         }
         ok = fwrite(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
+    }
+    if (ok && idx->rle) {  // run-length layout: payload size, run count, the runs
+        std::vector<uint8_t> pl((size_t)idx->payload_bytes);
+        if (!pl.empty() &&
+            cudaMemcpy(pl.data(), idx->payload, pl.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            return cuda_fail(cudaGetLastError(), "rb3_index_save", __FILE__, __LINE__);
+        }
+        const int64_t pr[2] = {idx->payload_bytes, idx->runs};
+        ok = fwrite(pr, sizeof(pr), 1, f) == 1 && fwrite(pl.data(), 1, pl.size(), f) == pl.size();
     }
     if (ok && idx->sa_s) {  // sampled suffix array: its count, the row directory, the values
         std::vector<uint64_t> sd(2 * (idx->n / 64 + 1)), sv(idx->n_samples);
@@ -529,8 +543,9 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     }
     int D = (int)((hdr[11] >> 8) & 0xFFFFFF);
     const int sa_s = (int)(hdr[11] >> 32);
+    const bool rle = (hdr[11] & 2) != 0;
     int64_t n = hdr[1], nblocks = hdr[10];
-    if (!valid_occ_interval(D) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
+    if (!(rle ? valid_rle_span(D) : valid_occ_interval(D)) || n < 0 || nblocks != n / D + 1 || hdr[9] != n) {
         fclose(f);
         set_error("%s: inconsistent header", path);
         return RB3_E_IO;
@@ -541,7 +556,8 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     for (int a = 0; a < 7; ++a) x->C[a] = hdr[3 + a];
     x->D = D;
     x->log2D = ilog2(D);
-    x->block_bytes = block_bytes_for(D);
+    x->rle = rle ? 1 : 0;
+    x->block_bytes = rle ? 32 : block_bytes_for(D);
     x->single_strand = (int)(hdr[11] & 1);
     x->nblocks = nblocks;
     cudaGetDevice(&x->device);
@@ -549,9 +565,21 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     std::vector<uint8_t> host(bytes);
     bool ok = fread(host.data(), 1, bytes, f) == bytes;
     std::vector<int64_t> gb;
-    if (ok && D == 32 && (n >> GSPAN_LOG2)) {
+    if (ok && (D == 32 || rle) && (n >> GSPAN_LOG2)) {
         gb.resize(5 * gbase_rows(n));
         ok = fread(gb.data(), sizeof(int64_t), gb.size(), f) == gb.size();
+    }
+    std::vector<uint8_t> pl;
+    if (ok && rle) {
+        int64_t pr[2];
+        // a run takes at least one byte and at most three per symbol it covers
+        ok = fread(pr, sizeof(pr), 1, f) == 1 && pr[0] >= 0 && pr[0] <= 3 * n && pr[1] >= 0 && pr[1] <= n;
+        if (ok) {
+            x->payload_bytes = pr[0];
+            x->runs = pr[1];
+            pl.resize((size_t)pr[0]);
+            ok = fread(pl.data(), 1, pl.size(), f) == pl.size();
+        }
     }
     std::vector<uint64_t> sd, sv;
     if (ok && sa_s) {
@@ -597,6 +625,18 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
         }
+    }
+    if (r == RB3_OK && rle) {  // the runs, checked before any rank decodes them
+        r = dev_alloc((void **)&x->payload, pl.size() + 16, st);
+        if (r == RB3_OK) {
+            cudaError_t e = cudaMemsetAsync(x->payload + pl.size(), 0, 16, st);
+            if (e == cudaSuccess && !pl.empty())
+                e = cudaMemcpyAsync(x->payload, pl.data(), pl.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) r = cuda_fail(e, "rb3_index_load", __FILE__, __LINE__);
+        }
+        if (r == RB3_OK) r = rle_check_impl(x, st);
+        if (r != RB3_OK && r != RB3_E_CUDA) set_error("%s: run-length data inconsistent", path);
     }
     if (r == RB3_OK) {
         int64_t C0[7];

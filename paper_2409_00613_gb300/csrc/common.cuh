@@ -27,6 +27,12 @@
 //    symbol's rank at the start of the block's 2^32-symbol span (gbase; zero
 //    below 2^32), words 5..7 = the three 32-bit bit-planes of the block's
 //    symbols.  rank($, l) = l minus the other five ranks.
+//  Run-length layout (rle = 1, made from a finished index by
+//    rb3_index_compress, read-only): D = S symbols per span, `blocks` holds one
+//    32-byte header per span (uint32 words 0..4 = rank of A..N at the span
+//    start minus the gbase of its 2^32-symbol range, words 5..6 = byte offset
+//    of the span's runs in `payload`, word 7 = their number) and `payload` the
+//    runs, cut at span boundaries (format at rle_run below).
 // ---------------------------------------------------------------------------
 struct rb3_index {
     int64_t n = 0, m = 0;
@@ -46,6 +52,11 @@ struct rb3_index {
     int64_t n_samples = 0;
     uint64_t *sdir = nullptr;   // device, 2 * (n / 64 + 1) words
     uint64_t *svals = nullptr;  // device, n_samples
+    // run-length layout: the runs of every span (device, payload_bytes + 16 bytes
+    // of padding, so that the decoder's 8-byte reads stay inside)
+    int32_t rle = 0;
+    uint8_t *payload = nullptr;
+    int64_t payload_bytes = 0, runs = 0;
     // build data of a batch (optional): its text and inverse suffix array
     uint8_t *text = nullptr;   // device, n codes (0 = sentinel)
     int32_t *isa = nullptr;    // device, n entries
@@ -61,6 +72,10 @@ constexpr int GSPAN_LOG2 = 32;  // D = 32 counts are relative to spans of 2^32 s
 
 constexpr int kDefaultOccInterval = 32;  // one sector per rank
 inline bool valid_occ_interval(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
+// Run-length spans: a power of two from 512 (above every plain D, so that D alone
+// tells the layouts apart) to 65536 (a run's length always fits the run format).
+inline bool valid_rle_span(int S) { return S >= 512 && S <= 65536 && (S & (S - 1)) == 0; }
+constexpr int kDefaultRleSpan = 1024;
 inline int block_bytes_for(int D) { return D == 32 ? 32 : HEADER_BYTES + D / 2; }
 inline int64_t gbase_rows(int64_t n) { return (n >> GSPAN_LOG2) + 1; }
 
@@ -163,7 +178,8 @@ __host__ __device__ __forceinline__ int comp_sym(int a) {
 // Read-only view of an index for kernels (passed by value).
 struct OccView {
     const uint8_t *__restrict__ blocks;
-    const int64_t *__restrict__ gbase;  // D = 32 above 2^32 symbols, else null
+    const int64_t *__restrict__ gbase;  // D = 32 / run-length above 2^32 symbols, else null
+    const uint8_t *__restrict__ payload;  // run-length layout only, else null
     int64_t n;
     int64_t C[7];
     int32_t log2D;
@@ -174,6 +190,7 @@ inline OccView occ_view(const rb3_index *x) {
     OccView v;
     v.blocks = x->blocks;
     v.gbase = x->gbase;
+    v.payload = x->rle ? x->payload : nullptr;
     v.n = x->n;
     for (int i = 0; i < 7; ++i) v.C[i] = x->C[i];
     v.log2D = x->log2D;
@@ -266,6 +283,132 @@ __device__ __forceinline__ void hdr_all(const Sec &h, int64_t r[6]) {
     }
 }
 
+// ---- run-length layout -------------------------------------------------------
+// A run is one byte (symbol << 5 | f) and, for long runs, one or two length
+// bytes: f < 30: length f + 1; f = 30: length 31 + the next byte; f = 31:
+// length 287 + the next two bytes (little-endian).  Spans are at most 65536
+// symbols, so every run fits.
+constexpr int NS_RLE = -1;  // compile-time layout tag next to NS = D / 64
+constexpr int RLE_F1 = 30, RLE_F2 = 31;
+constexpr int RLE_BASE1 = 31, RLE_BASE2 = 287;
+
+__host__ __device__ __forceinline__ int rle_run_bytes(int64_t len) {
+    return len < RLE_BASE1 ? 1 : (len < RLE_BASE2 ? 2 : 3);
+}
+
+// Sequential reader of a span's runs: aligned 8-byte loads, consumed a byte at
+// a time (the payload is padded so that the last word read is inside it).
+struct RunRd {
+    const unsigned long long *w;
+    uint64_t cur;
+    int avail;
+    __device__ __forceinline__ void init(const uint8_t *p) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        w = reinterpret_cast<const unsigned long long *>(a & ~(uintptr_t)7);
+        const int sk = (int)(a & 7);
+        cur = __ldg(w) >> (8 * sk);
+        avail = 8 - sk;
+    }
+    __device__ __forceinline__ uint32_t byte() {
+        if (avail == 0) {
+            cur = __ldg(++w);
+            avail = 8;
+        }
+        const uint32_t b = (uint32_t)(cur & 0xFFu);
+        cur >>= 8;
+        --avail;
+        return b;
+    }
+    __device__ __forceinline__ void run(int *sym, int64_t *len) {
+        const uint32_t b = byte(), f = b & 31u;
+        *sym = (int)(b >> 5);
+        if (f < (uint32_t)RLE_F1) {
+            *len = (int64_t)f + 1;
+        } else if (f == (uint32_t)RLE_F1) {
+            *len = RLE_BASE1 + (int64_t)byte();
+        } else {
+            const uint32_t lo = byte();
+            *len = RLE_BASE2 + (int64_t)(lo | (byte() << 8));
+        }
+    }
+};
+
+// Header of span sp: rank of A..N at its start (gbase added) and its runs.
+__device__ __forceinline__ const uint8_t *rle_header(const OccView &v, int64_t sp, int64_t base[SIGMA]) {
+    const Sec h = ld_sec64(v.blocks + sp * 32);
+    base[0] = 0;
+#pragma unroll
+    for (int a = 1; a < SIGMA; ++a) base[a] = (int64_t)h.w[a - 1];
+    if (v.gbase) {
+        const int64_t *g = v.gbase + 5 * ((sp << v.log2D) >> GSPAN_LOG2);
+#pragma unroll
+        for (int a = 1; a < SIGMA; ++a) base[a] += g[a - 1];
+    }
+    return v.payload + ((uint64_t)h.w[5] | ((uint64_t)h.w[6] << 32));
+}
+
+__device__ __forceinline__ void rle_add(int64_t r[SIGMA], int a, int64_t t) {
+#pragma unroll
+    for (int b = 1; b < SIGMA; ++b)
+        if (a == b) r[b] += t;
+}
+
+// rank(a, l) for every a, and (WANT_SYM, l < n) the symbol B[l]: the span of l
+// is decoded from its start to the run holding l.
+template <bool WANT_SYM>
+__device__ __forceinline__ void rle_rank(const OccView &v, int64_t l, int64_t r[SIGMA], int *sym) {
+    const int64_t sp = l >> v.log2D, s0 = sp << v.log2D, o = l - s0;
+    const uint8_t *p = rle_header(v, sp, r);
+    int64_t slen = v.n - s0;
+    if (slen > ((int64_t)1 << v.log2D)) slen = (int64_t)1 << v.log2D;
+    int64_t stop = WANT_SYM ? o + 1 : o;  // decode runs while they start before stop
+    if (stop > slen) stop = slen;
+    int sy = 0;
+    if (stop > 0) {
+        RunRd rd;
+        rd.init(p);
+        int64_t pos = 0;
+        while (pos < stop) {
+            int a;
+            int64_t len;
+            rd.run(&a, &len);
+            const int64_t t = o - pos < len ? o - pos : len;  // o > pos here unless WANT_SYM's last run
+            rle_add(r, a, t > 0 ? t : 0);
+            sy = a;
+            pos += len;
+        }
+    }
+    r[0] = l - (r[1] + r[2] + r[3] + r[4] + r[5]);
+    if (WANT_SYM) *sym = sy;
+}
+
+// rank_all at l0 <= l1 of one span, decoded once.
+__device__ __forceinline__ void rle_rank2(const OccView &v, int64_t l0, int64_t l1, int64_t r0[SIGMA],
+                                          int64_t r1[SIGMA]) {
+    const int64_t sp = l1 >> v.log2D, s0 = sp << v.log2D, o0 = l0 - s0, o1 = l1 - s0;
+    const uint8_t *p = rle_header(v, sp, r1);
+#pragma unroll
+    for (int a = 0; a < SIGMA; ++a) r0[a] = r1[a];
+    if (o1 > 0) {
+        RunRd rd;
+        rd.init(p);
+        int64_t pos = 0;
+        while (pos < o1) {
+            int a;
+            int64_t len;
+            rd.run(&a, &len);
+            const int64_t t1 = o1 - pos < len ? o1 - pos : len;
+            int64_t t0 = o0 - pos < len ? o0 - pos : len;
+            t0 = t0 > 0 ? t0 : 0;
+            rle_add(r1, a, t1);
+            rle_add(r0, a, t0);
+            pos += len;
+        }
+    }
+    r0[0] = l0 - (r0[1] + r0[2] + r0[3] + r0[4] + r0[5]);
+    r1[0] = l1 - (r1[1] + r1[2] + r1[3] + r1[4] + r1[5]);
+}
+
 // Loads of one rank: the header sector and the payload sectors that hold the
 // nibbles before offset o, all issued before any is used.  NS = D/64 payload
 // sectors per block (1, 2 or 4); sectors past o are not loaded.  NS = 0 is the
@@ -281,10 +424,18 @@ template <> struct BlockLd<0> {
     int64_t l;
     const int64_t *gb;
 };
+// Run-length layout: the span is decoded at load time; the load keeps every
+// rank at l and the symbol B[l].
+template <> struct BlockLd<NS_RLE> {
+    int64_t r[SIGMA];
+    int sym;
+};
 
 template <int NS> __device__ __forceinline__ BlockLd<NS> block_load(const OccView &v, int64_t l) {
     BlockLd<NS> b;
-    if constexpr (NS == 0) {
+    if constexpr (NS == NS_RLE) {
+        rle_rank<true>(v, l, b.r, &b.sym);
+    } else if constexpr (NS == 0) {
         b.h = ld_sec64(v.blocks + (l >> 5) * 32);
         b.o = (int)(l & 31);
         b.l = l;
@@ -307,7 +458,10 @@ __device__ __forceinline__ uint32_t s32_match(const Sec &s, int c) {
 }
 
 template <int NS> __device__ __forceinline__ void block_rank_all(const BlockLd<NS> &b, int64_t r[6]) {
-    if constexpr (NS == 0) {
+    if constexpr (NS == NS_RLE) {
+#pragma unroll
+        for (int a = 0; a < SIGMA; ++a) r[a] = b.r[a];
+    } else if constexpr (NS == 0) {
         const uint32_t mk = (1u << b.o) - 1u;  // o <= 31
         const uint32_t p0 = b.h.w[5], p1 = b.h.w[6], p2 = b.h.w[7];
         const uint32_t b0 = p0 & mk, n0 = ~p0 & mk;
@@ -331,7 +485,13 @@ template <int NS> __device__ __forceinline__ void block_rank_all(const BlockLd<N
 }
 
 template <int NS> __device__ __forceinline__ int64_t block_rank(const BlockLd<NS> &b, int c) {
-    if constexpr (NS == 0) {
+    if constexpr (NS == NS_RLE) {
+        int64_t r = b.r[0];
+#pragma unroll
+        for (int a = 1; a < SIGMA; ++a)
+            if (c == a) r = b.r[a];
+        return r;
+    } else if constexpr (NS == 0) {
         if (c == 0) {  // $: position minus the other five ranks
             int64_t r[SIGMA];
             block_rank_all<0>(b, r);
@@ -361,12 +521,20 @@ template <int NS> __device__ __forceinline__ int64_t rank1(const OccView &v, int
 
 // rank_B(a, l) for every symbol a.
 template <int NS> __device__ __forceinline__ void rank_all(const OccView &v, int64_t l, int64_t r[SIGMA]) {
-    BlockLd<NS> b = block_load<NS>(v, l);
-    block_rank_all<NS>(b, r);
+    if constexpr (NS == NS_RLE) {
+        rle_rank<false>(v, l, r, nullptr);
+    } else {
+        BlockLd<NS> b = block_load<NS>(v, l);
+        block_rank_all<NS>(b, r);
+    }
 }
 
 // Any D (tile-level lookups outside the hot loops).
 __device__ __forceinline__ void rank_all_any(const OccView &v, int64_t l, int64_t r[SIGMA]) {
+    if (v.payload) {
+        rank_all<NS_RLE>(v, l, r);
+        return;
+    }
     if (v.log2D == 5) {
         rank_all<0>(v, l, r);
         return;
@@ -379,6 +547,12 @@ __device__ __forceinline__ void rank_all_any(const OccView &v, int64_t l, int64_
 
 // Symbol B[i]: bit o of the three planes that hold it.
 __device__ __forceinline__ int sym_at(const OccView &v, int64_t i) {
+    if (v.payload) {
+        int64_t r[SIGMA];
+        int a;
+        rle_rank<true>(v, i, r, &a);
+        return a;
+    }
     if (v.log2D == 5) {
         const uint32_t *w = reinterpret_cast<const uint32_t *>(v.blocks + (i >> 5) * 32);
         const int bit = (int)(i & 31);
@@ -451,7 +625,15 @@ struct BiInt {
 // Both blocks are loaded before either is counted.
 template <int NS> __device__ __forceinline__ BiInt backward_ext(const OccView &v, BiInt x, int a) {
     int64_t r0[SIGMA], r1[SIGMA];
-    {
+    if constexpr (NS == NS_RLE) {  // one decode when both ends share a span
+        const int64_t e = x.k + x.s;
+        if ((e >> v.log2D) == (x.k >> v.log2D)) {
+            rle_rank2(v, x.k, e, r0, r1);
+        } else {
+            rle_rank<false>(v, x.k, r0, nullptr);
+            rle_rank<false>(v, e, r1, nullptr);
+        }
+    } else {
         // both ends' blocks are requested before either is counted; when both
         // ends fall in one block it is read once
         const int64_t e = x.k + x.s;
@@ -581,6 +763,8 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
+int rle_export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st);
+int rle_check_impl(const rb3_index *x, cudaStream_t st);
 // Sampled suffix array of a batch from its SA (builder) and of a merge (from pos).
 int sample_batch(rb3_index *x, const int32_t *SA, cudaStream_t st);
 int sample_merge(const rb3_index *dst, const rb3_index *src, const int64_t *pos, const int64_t *kstart,
@@ -589,8 +773,31 @@ void free_samples(rb3_index *x);
 // Fills idx->C from its blocks (rank of every symbol at n).
 int finalize_counts(rb3_index *idx, cudaStream_t st);
 
-// Calls body with a compile-time NS = D/64 for D in {64, 128, 256}, NS = 0 for D = 32.
+// Calls body with a compile-time NS = D/64 for D in {64, 128, 256}, NS = 0 for
+// D = 32 and NS = NS_RLE for a run-length index (D = its span, 512 or more).
 #define RB3_WITH_NS(D, ...)                      \
+    do {                                         \
+        if ((D) > 256) {                         \
+            constexpr int NS = NS_RLE;           \
+            __VA_ARGS__;                         \
+        } else if ((D) == 32) {                  \
+            constexpr int NS = 0;                \
+            __VA_ARGS__;                         \
+        } else if ((D) == 64) {                  \
+            constexpr int NS = 1;                \
+            __VA_ARGS__;                         \
+        } else if ((D) == 128) {                 \
+            constexpr int NS = 2;                \
+            __VA_ARGS__;                         \
+        } else {                                 \
+            constexpr int NS = 4;                \
+            __VA_ARGS__;                         \
+        }                                        \
+    } while (0)
+
+// The same over the plain layouts only (kernels that never see a run-length
+// index: the merge, whose callers reject one first).
+#define RB3_WITH_NS_PLAIN(D, ...)                \
     do {                                         \
         if ((D) == 32) {                         \
             constexpr int NS = 0;                \

@@ -129,6 +129,10 @@ __global__ void k_locate(OccView V, const uint64_t *__restrict__ sdir, const uin
             const BlockLd<0> b = block_load<0>(V, j);
             a = (int)(((b.h.w[5] >> b.o) & 1u) | (((b.h.w[6] >> b.o) & 1u) << 1) | (((b.h.w[7] >> b.o) & 1u) << 2));
             r = block_rank<0>(b, a);
+        } else if constexpr (NS == NS_RLE) {  // symbol and rank from one decode of the span
+            const BlockLd<NS_RLE> b = block_load<NS_RLE>(V, j);
+            a = b.sym;
+            r = block_rank<NS_RLE>(b, a);
         } else {
             a = sym_at(V, j);
             r = rank1<NS>(V, a, j);

@@ -672,11 +672,11 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 int64_t threads = nw < resident ? nw : resident;
                 unsigned grid = nb_for(threads, WALK_THREADS);
                 if (dst->single_strand)
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
+                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
                                                    src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
                                                    cap, d_ctr, pos));
                 else
-                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
+                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
                                                    src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
                                                    cap, d_ctr, pos));
             }
@@ -687,6 +687,7 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
 
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
     RB3_CHECK_ARG(dst != src, "dst and src must differ");
+    RB3_CHECK_ARG(!dst->rle && !src->rle, "a run-length index is read-only (merge plain indexes, then compress)");
     RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
                   "cannot merge a single-strand index with a double-strand one");
     if (src->n == 0) return RB3_OK;

@@ -159,6 +159,7 @@ RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int6
                                   const int64_t *batch_end, int64_t n_batches, const rb3_opts *o, void *stream) {
     set_error("%s", "");
     RB3_CHECK_ARG(dst != nullptr, "NULL index");
+    RB3_CHECK_ARG(!dst->rle, "a run-length index is read-only (append to a plain index, then compress)");
     RB3_CHECK_ARG(n_seq >= 0 && n_batches >= 0, "negative size");
     if (n_batches == 0) return RB3_OK;
     RB3_CHECK_ARG(batch_end != nullptr && (n_seq == 0 || len != nullptr), "NULL argument");

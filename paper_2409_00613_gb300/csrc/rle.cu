@@ -1,0 +1,318 @@
+// Run-length index (Section "BWT construction", Fig. 2b: the static form of the
+// BWT, run-length encoded and interleaved with marginal counts per block, with
+// an index into it for fast access).
+//
+// Here the BWT is cut into spans of S symbols.  Each span has a 32-byte header
+// (the marginal counts at its start and where its runs begin) in a directory
+// indexed by l >> log2 S, so a rank is a header read plus a decode of the
+// span's runs up to l.  Runs are bytes (a 3-bit symbol and a 5-bit length,
+// with one or two extra length bytes for long runs; format in common.cuh),
+// not the paper's Elias-delta bit code: a byte code decodes with plain shifts
+// and needs no bit-level cursor on the GPU.  The index is built from a finished
+// plain index and is read-only: every query (backward search, SMEM search,
+// locate, export) runs on it through the same kernels, with the rank primitives
+// of the run-length layout.
+#include "common.cuh"
+
+namespace rb3 {
+
+static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// One thread per span: runs of codes[s0, s1) and the bytes they take.
+__global__ void k_rle_size(const uint8_t *__restrict__ codes, int64_t n, int log2S, int64_t nspans,
+                           uint64_t *__restrict__ bytes, uint64_t *__restrict__ runs) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    const int64_t s0 = sp << log2S, s1 = s0 + ((int64_t)1 << log2S) < n ? s0 + ((int64_t)1 << log2S) : n;
+    uint64_t nb = 0, nr = 0;
+    int64_t i = s0;
+    while (i < s1) {
+        const uint8_t a = codes[i];
+        int64_t j = i + 1;
+        while (j < s1 && codes[j] == a) ++j;
+        nb += rle_run_bytes(j - i);
+        ++nr;
+        i = j;
+    }
+    bytes[sp] = nb;
+    runs[sp] = nr;
+}
+
+// One thread per span: header (ranks at the span start from the plain index,
+// minus the gbase of their 2^32 range) and runs.
+__global__ void k_rle_write(const uint8_t *__restrict__ codes, OccView src, int log2S, int64_t nspans,
+                            const uint64_t *__restrict__ off, const uint64_t *__restrict__ runs,
+                            const int64_t *__restrict__ gbase, uint8_t *__restrict__ hdr,
+                            uint8_t *__restrict__ payload) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    const int64_t n = src.n, s0 = sp << log2S;
+    const int64_t s1 = s0 + ((int64_t)1 << log2S) < n ? s0 + ((int64_t)1 << log2S) : n;
+    int64_t r[SIGMA];
+    rank_all_any(src, s0, r);
+    uint32_t w[8];
+    const int64_t *g = gbase ? gbase + 5 * (s0 >> GSPAN_LOG2) : nullptr;
+    for (int a = 1; a < SIGMA; ++a) w[a - 1] = (uint32_t)(r[a] - (g ? g[a - 1] : 0));
+    w[5] = (uint32_t)off[sp];
+    w[6] = (uint32_t)(off[sp] >> 32);
+    w[7] = (uint32_t)runs[sp];
+    uint4 *h = reinterpret_cast<uint4 *>(hdr + sp * 32);
+    h[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    h[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    uint8_t *p = payload + off[sp];
+    int64_t i = s0;
+    while (i < s1) {
+        const uint8_t a = codes[i];
+        int64_t j = i + 1;
+        while (j < s1 && codes[j] == a) ++j;
+        const int64_t len = j - i;
+        if (len < RLE_BASE1) {
+            *p++ = (uint8_t)((a << 5) | (len - 1));
+        } else if (len < RLE_BASE2) {
+            *p++ = (uint8_t)((a << 5) | RLE_F1);
+            *p++ = (uint8_t)(len - RLE_BASE1);
+        } else {
+            const int64_t x = len - RLE_BASE2;
+            *p++ = (uint8_t)((a << 5) | RLE_F2);
+            *p++ = (uint8_t)(x & 0xFF);
+            *p++ = (uint8_t)(x >> 8);
+        }
+        i = j;
+    }
+}
+
+// gbase[5 g + a - 1] = rank(a, g * 2^32) of the plain index.
+__global__ void k_rle_gbase(OccView src, int64_t rows, int64_t *__restrict__ gbase) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= rows) return;
+    int64_t r[SIGMA];
+    rank_all_any(src, g << GSPAN_LOG2, r);
+    for (int a = 1; a < SIGMA; ++a) gbase[5 * g + a - 1] = r[a];
+}
+
+// One thread per span: its runs written out as codes.
+__global__ void k_rle_unpack(OccView V, int64_t nspans, uint8_t *__restrict__ codes) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    const int64_t s0 = sp << V.log2D;
+    int64_t slen = V.n - s0;
+    if (slen > ((int64_t)1 << V.log2D)) slen = (int64_t)1 << V.log2D;
+    if (slen <= 0) return;
+    int64_t base[SIGMA];
+    RunRd rd;
+    rd.init(rle_header(V, sp, base));
+    int64_t pos = 0;
+    while (pos < slen) {
+        int a;
+        int64_t len;
+        rd.run(&a, &len);
+        for (int64_t t = 0; t < len && pos + t < slen; ++t) codes[s0 + pos + t] = (uint8_t)a;
+        pos += len;
+    }
+}
+
+// occ[sp * 6 + a] = rank(a, sp * S): the span headers.
+__global__ void k_rle_occ(OccView V, int64_t nspans, int64_t *__restrict__ occ) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    int64_t r[SIGMA];
+    rle_header(V, sp, r);
+    r[0] = (sp << V.log2D) - (r[1] + r[2] + r[3] + r[4] + r[5]);
+    for (int a = 0; a < SIGMA; ++a) occ[sp * SIGMA + a] = r[a];
+}
+
+// Consistency of a run-length image read from a file, every read bounds-checked:
+// each span's runs start at its header's offset, end where the next span's
+// begin, cover exactly its symbols, match the header's run count, and advance
+// the counts to the next header's.  bad != 0 on the first failure.
+__global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned int *__restrict__ bad) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    const uint8_t *hdr = V.blocks, *payload = V.payload;
+    const int64_t n = V.n, *gbase = V.gbase;
+    const int log2S = V.log2D;
+    const uint32_t *h = reinterpret_cast<const uint32_t *>(hdr + sp * 32);
+    const int64_t s0 = sp << log2S;
+    int64_t slen = n - s0;
+    if (slen > ((int64_t)1 << log2S)) slen = (int64_t)1 << log2S;
+    if (slen < 0) slen = 0;
+    const uint64_t b0 = (uint64_t)h[5] | ((uint64_t)h[6] << 32);
+    uint64_t b1 = (uint64_t)pbytes;
+    if (sp + 1 < nspans) {
+        const uint32_t *hn = reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * 32);
+        b1 = (uint64_t)hn[5] | ((uint64_t)hn[6] << 32);
+    }
+    if (b0 > b1 || b1 > (uint64_t)pbytes) {
+        atomicOr(bad, 1u);
+        return;
+    }
+    int64_t cnt[SIGMA] = {0, 0, 0, 0, 0, 0};
+    int64_t pos = 0, nr = 0;
+    uint64_t q = b0;
+    while (pos < slen) {
+        if (q >= b1) {
+            atomicOr(bad, 2u);
+            return;
+        }
+        const uint32_t b = payload[q++], f = b & 31u;
+        const int a = (int)(b >> 5);
+        int64_t len;
+        if (f < (uint32_t)RLE_F1) {
+            len = (int64_t)f + 1;
+        } else if (f == (uint32_t)RLE_F1) {
+            if (q >= b1) {
+                atomicOr(bad, 2u);
+                return;
+            }
+            len = RLE_BASE1 + (int64_t)payload[q++];
+        } else {
+            if (q + 1 >= b1) {
+                atomicOr(bad, 2u);
+                return;
+            }
+            len = RLE_BASE2 + (int64_t)(payload[q] | (payload[q + 1] << 8));
+            q += 2;
+        }
+        if (a >= SIGMA || pos + len > slen) {
+            atomicOr(bad, 4u);
+            return;
+        }
+        cnt[a] += len;
+        pos += len;
+        ++nr;
+    }
+    if (q != b1 || nr != (int64_t)h[7]) {
+        atomicOr(bad, 8u);
+        return;
+    }
+    // the counts start at 0, advance by the span's runs to the next header's
+    // (both relative to their 2^32 range) and end at the symbol totals
+    const int64_t *g0 = gbase ? gbase + 5 * (s0 >> GSPAN_LOG2) : nullptr;
+    const uint32_t *hn = sp + 1 < nspans ? reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * 32) : nullptr;
+    const int64_t *g1 = gbase ? gbase + 5 * ((s0 + ((int64_t)1 << log2S)) >> GSPAN_LOG2) : nullptr;
+    for (int a = 1; a < SIGMA; ++a) {
+        const int64_t c0 = (int64_t)h[a - 1] + (g0 ? g0[a - 1] : 0);
+        const int64_t c1 = hn ? (int64_t)hn[a - 1] + (g1 ? g1[a - 1] : 0) : V.C[a + 1] - V.C[a];
+        if ((sp == 0 && c0 != 0) || c0 + cnt[a] != c1) {
+            atomicOr(bad, 16u);
+            return;
+        }
+    }
+}
+
+int rle_export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st) {
+    OccView V = occ_view(x);
+    if (codes && x->n > 0) RB3_LAUNCH(k_rle_unpack, nb_for(x->nblocks, 128), 128, 0, st, V, x->nblocks, codes);
+    if (occ) RB3_LAUNCH(k_rle_occ, nb_for(x->nblocks, 256), 256, 0, st, V, x->nblocks, occ);
+    return RB3_OK;
+}
+
+int rle_check_impl(const rb3_index *x, cudaStream_t st) {
+    DevBuf bad;
+    RB3_TRY(bad.alloc(sizeof(unsigned int), st));
+    RB3_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(unsigned int), st));
+    RB3_LAUNCH(k_rle_check, nb_for(x->nblocks, 128), 128, 0, st, occ_view(x), x->payload_bytes, x->nblocks,
+               bad.as<unsigned int>());
+    unsigned int h = 0;
+    RB3_CUDA_TRY(cudaMemcpyAsync(&h, bad.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("run-length image is inconsistent (check bits %u)", h);
+        return RB3_E_IO;
+    }
+    return RB3_OK;
+}
+
+static int compress_impl(const rb3_index *src, int S, cudaStream_t st, rb3_index *x) {
+    const int64_t n = src->n;
+    x->n = n;
+    x->m = src->m;
+    for (int a = 0; a < 7; ++a) x->C[a] = src->C[a];
+    x->rle = 1;
+    x->D = S;
+    x->log2D = ilog2(S);
+    x->block_bytes = 32;
+    x->single_strand = src->single_strand;
+    x->nblocks = n / S + 1;
+    x->str_end = src->str_end;
+    x->device = src->device;
+    const int64_t ns = x->nblocks;
+    OccView V = occ_view(src);
+    if (n >> GSPAN_LOG2) {
+        const int64_t rows = gbase_rows(n);
+        RB3_TRY(dev_alloc((void **)&x->gbase, sizeof(int64_t) * 5 * rows, st));
+        RB3_LAUNCH(k_rle_gbase, nb_for(rows, 64), 64, 0, st, V, rows, x->gbase);
+    }
+    DevBuf codes, bytes, runs, off;
+    RB3_TRY(codes.alloc((size_t)(n > 0 ? n : 1), st));
+    RB3_TRY(bytes.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(runs.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(off.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(export_impl(src, codes.as<uint8_t>(), nullptr, st));
+    RB3_LAUNCH(k_rle_size, nb_for(ns, 128), 128, 0, st, codes.as<uint8_t>(), n, x->log2D, ns, bytes.as<uint64_t>(),
+               runs.as<uint64_t>());
+    RB3_TRY(scan_u64(bytes.as<uint64_t>(), off.as<uint64_t>(), ns, false, st));
+    uint64_t tail[4];
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[0], off.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[1], bytes.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    // total runs: the same exclusive scan over the run counts, reusing `bytes` as its output
+    RB3_TRY(scan_u64(runs.as<uint64_t>(), bytes.as<uint64_t>(), ns, false, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[2], bytes.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[3], runs.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    x->payload_bytes = (int64_t)(tail[0] + tail[1]);
+    x->runs = (int64_t)(tail[2] + tail[3]);
+    RB3_TRY(dev_alloc((void **)&x->blocks, (size_t)ns * 32, st));
+    RB3_TRY(dev_alloc((void **)&x->payload, (size_t)x->payload_bytes + 16, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(x->payload + x->payload_bytes, 0, 16, st));
+    RB3_LAUNCH(k_rle_write, nb_for(ns, 128), 128, 0, st, codes.as<uint8_t>(), V, x->log2D, ns, off.as<uint64_t>(),
+               runs.as<uint64_t>(), x->gbase, x->blocks, x->payload);
+    if (src->sa_s && src->sdir) {  // the sampled suffix array is per row: rows do not change
+        const int64_t nw = n / 64 + 1;
+        x->sa_s = src->sa_s;
+        x->n_samples = src->n_samples;
+        RB3_TRY(dev_alloc((void **)&x->sdir, sizeof(uint64_t) * 2 * nw, st));
+        RB3_TRY(dev_alloc((void **)&x->svals, sizeof(uint64_t) * (x->n_samples > 0 ? x->n_samples : 1), st));
+        RB3_CUDA_TRY(cudaMemcpyAsync(x->sdir, src->sdir, sizeof(uint64_t) * 2 * nw, cudaMemcpyDeviceToDevice, st));
+        if (x->n_samples)
+            RB3_CUDA_TRY(cudaMemcpyAsync(x->svals, src->svals, sizeof(uint64_t) * x->n_samples,
+                                         cudaMemcpyDeviceToDevice, st));
+    }
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+}  // namespace rb3
+
+using namespace rb3;
+
+RB3_EXPORT int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_index **out) {
+    set_error("%s", "");
+    RB3_CHECK_ARG(src && out, "NULL argument");
+    *out = nullptr;
+    const int S = span ? span : kDefaultRleSpan;
+    RB3_CHECK_ARG(valid_rle_span(S), "span must be a power of two from 512 to 65536");
+    RB3_CHECK_ARG(!src->rle, "the index is already run-length encoded");
+    cudaStream_t st = (cudaStream_t)stream;
+    rb3_index *x = new rb3_index();
+    const int r = compress_impl(src, S, st, x);
+    if (r != RB3_OK) {
+        cudaStreamSynchronize(st);
+        rb3_index_free(x);
+        return r;
+    }
+    *out = x;
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs) {
+    set_error("%s", "");
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    int64_t b = idx->nblocks * (int64_t)idx->block_bytes;
+    if (idx->rle) b += idx->payload_bytes + 16;
+    if (idx->gbase) b += (int64_t)sizeof(int64_t) * 5 * gbase_rows(idx->n);
+    if (idx->sa_s && idx->sdir) b += (int64_t)sizeof(uint64_t) * (2 * (idx->n / 64 + 1) + idx->n_samples);
+    if (device_bytes) *device_bytes = b;
+    if (runs) *runs = idx->rle ? idx->runs : -1;
+    return RB3_OK;
+}

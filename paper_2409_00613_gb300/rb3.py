@@ -75,6 +75,8 @@ def lib():
             "rb3_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                               ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
             "rb3_drop_build_data": (ctypes.c_int, [_vp]),
+            "rb3_index_compress": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
+            "rb3_index_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_free": (None, [_vp]),
@@ -287,7 +289,20 @@ def rb3_index_info(idx: Index) -> dict:
     _check(lib().rb3_index_info(idx.handle, ctypes.byref(n), ctypes.byref(m), C, ctypes.byref(D), ctypes.byref(fl)))
     return {"n": n.value, "m": m.value, "C": list(C), "occ_interval": D.value,
             "single_strand": bool(fl.value & 1), "has_build_data": bool(fl.value & 2),
-            "sa_sample": fl.value >> 8}
+            "run_length": bool(fl.value & 4), "sa_sample": fl.value >> 8}
+
+
+def rb3_index_compress(idx: Index, span: int = 0, stream=None) -> Index:
+    """Run-length copy of idx (read-only; queries run on it unchanged)."""
+    out = _vp()
+    _check(lib().rb3_index_compress(idx.handle, span, _stream(stream), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def rb3_index_bytes(idx: Index) -> dict:
+    b, r = _i64(), _i64()
+    _check(lib().rb3_index_bytes(idx.handle, ctypes.byref(b), ctypes.byref(r)))
+    return {"device_bytes": b.value, "runs": r.value}
 
 
 def rb3_locate(idx: Index, rows, out=None, stream=None):

@@ -394,3 +394,46 @@ def test_locate_pins(both):
         a = int(B[i])
         lf = C[a] + int(np.count_nonzero(B[:i] == a))
         assert lf == row_of[(int(t), int(off) - 1)]
+
+
+def py_runs(B, span):
+    """Runs by a plain scan: a run ends where the symbol changes or a span ends."""
+    out = []
+    for i, a in enumerate(B):
+        if out and out[-1][0] == a and not (span and i % span == 0):
+            out[-1][1] += 1
+        else:
+            out.append([a, 1])
+    return out
+
+
+def test_runs_pins():
+    """The run-length form: a hand-worked case, then a plain scan, the
+    expansion back to B, maximality inside a span, and each span's lengths
+    summing to its size, on random BWTs with long runs (near-identical
+    strings) and short ones."""
+    sym, ln = oracle.runs(np.array([1, 1, 2, 2, 2, 0, 1], np.uint8))
+    assert sym.tolist() == [1, 2, 0, 1] and ln.tolist() == [2, 3, 1, 1]
+    sym, ln = oracle.runs(np.array([1, 1, 2, 2, 2, 0, 1], np.uint8), 4)
+    assert sym.tolist() == [1, 2, 2, 0, 1] and ln.tolist() == [2, 2, 1, 1, 1]
+    assert [len(x) for x in oracle.runs(np.zeros(0, np.uint8), 8)] == [0, 0]
+    g = synth.rng(2718)
+    for trial in range(12):
+        if trial % 2:
+            S = synth.pangenome(seed=100 + trial, founder_len=int(g.integers(50, 400)), n_hap=4, batch=4)
+            B = oracle.bwt(oracle.concat(S.seq, S.lens, True))
+        else:
+            S, _ = rand_list(g, int(g.integers(1, 12)), int(g.integers(1, 60)), n_frac=0.1)
+            B = oracle.bwt(oracle.concat(S.seq, S.lens, bool(trial & 2)))
+        for span in (0, 1, 2, 8, 64):
+            sym, ln = oracle.runs(B, span)
+            assert [[int(a), int(b)] for a, b in zip(sym, ln)] == py_runs(B.tolist(), span)
+            assert np.array_equal(np.repeat(sym, ln), B)
+            ends = np.cumsum(ln)
+            starts = ends - ln
+            same = sym[1:] == sym[:-1]
+            if span:
+                assert np.all((starts[1:][same] % span) == 0)  # equal neighbours only across a cut
+                assert np.all(starts // span == (ends - 1) // span)  # no run crosses a cut
+            else:
+                assert not np.any(same)
