@@ -422,7 +422,7 @@ def run_length_bench(rb, torch, S, idx, args, st, dev, chunk_len):
     plain = rb.rb3_index_bytes(idx)["device_bytes"]
     res = {"plain_bytes": plain, "plain_occ_interval": info["occ_interval"], "spans": []}
     out = torch.empty(cap * 40, dtype=torch.uint8, device=dev)
-    for span in (1024, 4096, 16384):
+    for span in (512, 1024, 2048, 4096, 16384):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         R = rb.rb3_index_compress(idx, span, stream=st)

@@ -255,14 +255,16 @@ int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int
 
 /* Run-length copy of a finished index for queries (Section "BWT construction",
  * Fig. 2b: the static, run-length encoded BWT with marginal counts per block).
- * The BWT is cut into spans of `span` symbols (a power of two, 512..65536;
- * 0 = 1024).  Device layout: one 32-byte header per span (uint32 rank of A..N
+ * The BWT is cut into spans of `span` symbols (a power of two, 512..16384;
+ * 0 = 2048).  Device layout: one 64-byte header per span (uint32 rank of A..N
  * at the span start, relative to its 2^32-symbol range, as for D = 32; the
- * uint64 byte offset of the span's runs; their number), then the runs, cut at
- * span boundaries, one byte each (symbol << 5 | f: f < 30 gives length f + 1,
- * f = 30 length 31 + the next byte, f = 31 length 287 + the next two bytes,
- * little-endian).  A rank reads the span's header and decodes its runs up to
- * the position.  The copy keeps src's sampled suffix array; src is unchanged.
+ * uint64 byte offset of the span's runs; their number; two decode marks: the
+ * span offset, in-span ranks of A..N and byte offset of the runs holding
+ * offsets len/3 and 2 len/3), then the runs, cut at span boundaries, one byte
+ * each (symbol << 5 | f: f < 30 gives length f + 1, f = 30 length 31 + the
+ * next byte, f = 31 length 287 + the next two bytes, little-endian).  A rank
+ * reads the span's header and decodes its runs from the last mark before the
+ * position.  The copy keeps src's sampled suffix array; src is unchanged.
  * rb3_backward_search, rb3_mem_search (all forms), rb3_mem_search_noalloc,
  * the server, rb3_locate, rb3_export (occ rows = the span headers),
  * rb3_index_save / rb3_index_load take it; rb3_merge and rb3_append_batches

@@ -557,7 +557,7 @@ RB3_EXPORT int rb3_index_load(const char *path, void *stream, rb3_index **out) {
     x->D = D;
     x->log2D = ilog2(D);
     x->rle = rle ? 1 : 0;
-    x->block_bytes = rle ? 32 : block_bytes_for(D);
+    x->block_bytes = rle ? RLE_HDR_BYTES : block_bytes_for(D);
     x->single_strand = (int)(hdr[11] & 1);
     x->nblocks = nblocks;
     cudaGetDevice(&x->device);

@@ -29,10 +29,9 @@
 //    symbols.  rank($, l) = l minus the other five ranks.
 //  Run-length layout (rle = 1, made from a finished index by
 //    rb3_index_compress, read-only): D = S symbols per span, `blocks` holds one
-//    32-byte header per span (uint32 words 0..4 = rank of A..N at the span
-//    start minus the gbase of its 2^32-symbol range, words 5..6 = byte offset
-//    of the span's runs in `payload`, word 7 = their number) and `payload` the
-//    runs, cut at span boundaries (format at rle_run below).
+//    64-byte header per span (ranks at the span start, where its runs begin,
+//    two decode marks) and `payload` the runs, cut at span boundaries (format
+//    at NS_RLE below).
 // ---------------------------------------------------------------------------
 struct rb3_index {
     int64_t n = 0, m = 0;
@@ -73,9 +72,9 @@ constexpr int GSPAN_LOG2 = 32;  // D = 32 counts are relative to spans of 2^32 s
 constexpr int kDefaultOccInterval = 32;  // one sector per rank
 inline bool valid_occ_interval(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
 // Run-length spans: a power of two from 512 (above every plain D, so that D alone
-// tells the layouts apart) to 65536 (a run's length always fits the run format).
-inline bool valid_rle_span(int S) { return S >= 512 && S <= 65536 && (S & (S - 1)) == 0; }
-constexpr int kDefaultRleSpan = 1024;
+// tells the layouts apart) to 16384 (in-span offsets and ranks fit 16 bits).
+inline bool valid_rle_span(int S) { return S >= 512 && S <= 16384 && (S & (S - 1)) == 0; }
+constexpr int kDefaultRleSpan = 2048;
 inline int block_bytes_for(int D) { return D == 32 ? 32 : HEADER_BYTES + D / 2; }
 inline int64_t gbase_rows(int64_t n) { return (n >> GSPAN_LOG2) + 1; }
 
@@ -286,11 +285,26 @@ __device__ __forceinline__ void hdr_all(const Sec &h, int64_t r[6]) {
 // ---- run-length layout -------------------------------------------------------
 // A run is one byte (symbol << 5 | f) and, for long runs, one or two length
 // bytes: f < 30: length f + 1; f = 30: length 31 + the next byte; f = 31:
-// length 287 + the next two bytes (little-endian).  Spans are at most 65536
-// symbols, so every run fits.
+// length 287 + the next two bytes (little-endian).  Spans are at most 16384
+// symbols, so every run fits and a span's runs take under 64 KiB.
+//
+// Span header, 64 bytes (two sectors, read as one 64-byte request):
+//   uint32 w[0..4]  rank of A..N at the span start, minus the gbase of its
+//                   2^32-symbol range (as for D = 32)
+//   uint32 w[5..6]  byte offset of the span's runs in the payload (low, high)
+//   uint32 w[7]     number of runs in the span
+//   bytes 32..63    two decode marks, 16 bytes each: uint16 pos (offset in
+//                   the span of the first symbol of a run), uint16 ranks of
+//                   A..N from the span start to pos, uint32 byte offset of
+//                   that run from the span's first run byte.  Mark j is the
+//                   run holding offset (j + 1) * len / 3 of a span of len
+//                   symbols (pos 0 for an empty span), so a rank decodes at
+//                   most about a third of the span.
 constexpr int NS_RLE = -1;  // compile-time layout tag next to NS = D / 64
 constexpr int RLE_F1 = 30, RLE_F2 = 31;
 constexpr int RLE_BASE1 = 31, RLE_BASE2 = 287;
+constexpr int RLE_HDR_BYTES = 64;
+constexpr int RLE_MARKS = 2;
 
 __host__ __device__ __forceinline__ int rle_run_bytes(int64_t len) {
     return len < RLE_BASE1 ? 1 : (len < RLE_BASE2 ? 2 : 3);
@@ -333,9 +347,36 @@ struct RunRd {
     }
 };
 
-// Header of span sp: rank of A..N at its start (gbase added) and its runs.
-__device__ __forceinline__ const uint8_t *rle_header(const OccView &v, int64_t sp, int64_t base[SIGMA]) {
-    const Sec h = ld_sec64(v.blocks + sp * 32);
+// Ranks inside a span (each below 2^16) packed three to a word, 21 bits each:
+// acc[0] holds A, C, G; acc[1] T, N.  $ is never counted (rank($) = l minus
+// the others).
+__device__ __forceinline__ void rle_acc_add(uint64_t acc[2], int a, int64_t t) {
+    const bool hi = a >= 4;
+    const int sh = 21 * (hi ? a - 4 : a - 1);
+    if (a != 0) {
+        if (hi) acc[1] += (uint64_t)t << sh;
+        else acc[0] += (uint64_t)t << sh;
+    }
+}
+
+__device__ __forceinline__ void rle_acc_out(const uint64_t acc[2], const int64_t base[SIGMA], int64_t l,
+                                            int64_t r[SIGMA]) {
+    constexpr uint64_t M = (1ull << 21) - 1;
+    r[1] = base[1] + (int64_t)(acc[0] & M);
+    r[2] = base[2] + (int64_t)((acc[0] >> 21) & M);
+    r[3] = base[3] + (int64_t)((acc[0] >> 42) & M);
+    r[4] = base[4] + (int64_t)(acc[1] & M);
+    r[5] = base[5] + (int64_t)((acc[1] >> 21) & M);
+    r[0] = l - (r[1] + r[2] + r[3] + r[4] + r[5]);
+}
+
+// Span sp: the ranks at its start (gbase added), and the decode start for
+// offset o: the last mark at or before o (or the span start), as its offset,
+// packed ranks and first run byte.
+__device__ __forceinline__ const uint8_t *rle_start(const OccView &v, int64_t sp, int64_t o, int64_t base[SIGMA],
+                                                    int64_t *pos, uint64_t acc[2]) {
+    const uint8_t *hp = v.blocks + sp * RLE_HDR_BYTES;
+    const Sec h = ld_sec64(hp), mk = ld_sec64(hp + 32);
     base[0] = 0;
 #pragma unroll
     for (int a = 1; a < SIGMA; ++a) base[a] = (int64_t)h.w[a - 1];
@@ -344,69 +385,77 @@ __device__ __forceinline__ const uint8_t *rle_header(const OccView &v, int64_t s
 #pragma unroll
         for (int a = 1; a < SIGMA; ++a) base[a] += g[a - 1];
     }
-    return v.payload + ((uint64_t)h.w[5] | ((uint64_t)h.w[6] << 32));
-}
-
-__device__ __forceinline__ void rle_add(int64_t r[SIGMA], int a, int64_t t) {
-#pragma unroll
-    for (int b = 1; b < SIGMA; ++b)
-        if (a == b) r[b] += t;
+    const uint8_t *p = v.payload + ((uint64_t)h.w[5] | ((uint64_t)h.w[6] << 32));
+    // mark j: words 8j..8j+3 of the second sector = pos | A << 16, C | G << 16, T | N << 16, byte offset
+    const uint32_t p0 = mk.w[0] & 0xFFFFu, p1 = mk.w[4] & 0xFFFFu;
+    const int j = (uint32_t)o >= p1 ? 1 : ((uint32_t)o >= p0 ? 0 : -1);
+    acc[0] = acc[1] = 0;
+    *pos = 0;
+    if (j >= 0) {
+        const uint32_t w0 = j ? mk.w[4] : mk.w[0], w1 = j ? mk.w[5] : mk.w[1], w2 = j ? mk.w[6] : mk.w[2],
+                       w3 = j ? mk.w[7] : mk.w[3];
+        *pos = w0 & 0xFFFFu;
+        acc[0] = (uint64_t)(w0 >> 16) | ((uint64_t)(w1 & 0xFFFFu) << 21) | ((uint64_t)(w1 >> 16) << 42);
+        acc[1] = (uint64_t)(w2 & 0xFFFFu) | ((uint64_t)(w2 >> 16) << 21);
+        p += w3;
+    }
+    return p;
 }
 
 // rank(a, l) for every a, and (WANT_SYM, l < n) the symbol B[l]: the span of l
-// is decoded from its start to the run holding l.
+// is decoded from the last mark before l to the run holding l.
 template <bool WANT_SYM>
 __device__ __forceinline__ void rle_rank(const OccView &v, int64_t l, int64_t r[SIGMA], int *sym) {
     const int64_t sp = l >> v.log2D, s0 = sp << v.log2D, o = l - s0;
-    const uint8_t *p = rle_header(v, sp, r);
+    int64_t base[SIGMA], pos;
+    uint64_t acc[2];
+    const uint8_t *p = rle_start(v, sp, o, base, &pos, acc);
     int64_t slen = v.n - s0;
     if (slen > ((int64_t)1 << v.log2D)) slen = (int64_t)1 << v.log2D;
     int64_t stop = WANT_SYM ? o + 1 : o;  // decode runs while they start before stop
     if (stop > slen) stop = slen;
     int sy = 0;
-    if (stop > 0) {
+    if (pos < stop) {
         RunRd rd;
         rd.init(p);
-        int64_t pos = 0;
         while (pos < stop) {
             int a;
             int64_t len;
             rd.run(&a, &len);
-            const int64_t t = o - pos < len ? o - pos : len;  // o > pos here unless WANT_SYM's last run
-            rle_add(r, a, t > 0 ? t : 0);
+            const int64_t t = o - pos < len ? o - pos : len;  // below 0 only for WANT_SYM's last run
+            rle_acc_add(acc, a, t > 0 ? t : 0);
             sy = a;
             pos += len;
         }
     }
-    r[0] = l - (r[1] + r[2] + r[3] + r[4] + r[5]);
+    rle_acc_out(acc, base, l, r);
     if (WANT_SYM) *sym = sy;
 }
 
-// rank_all at l0 <= l1 of one span, decoded once.
+// rank_all at l0 <= l1 of one span, decoded once (from the last mark before l0).
 __device__ __forceinline__ void rle_rank2(const OccView &v, int64_t l0, int64_t l1, int64_t r0[SIGMA],
                                           int64_t r1[SIGMA]) {
     const int64_t sp = l1 >> v.log2D, s0 = sp << v.log2D, o0 = l0 - s0, o1 = l1 - s0;
-    const uint8_t *p = rle_header(v, sp, r1);
-#pragma unroll
-    for (int a = 0; a < SIGMA; ++a) r0[a] = r1[a];
-    if (o1 > 0) {
+    int64_t base[SIGMA], pos;
+    uint64_t acc1[2];
+    const uint8_t *p = rle_start(v, sp, o0, base, &pos, acc1);
+    uint64_t acc0[2] = {acc1[0], acc1[1]};
+    if (pos < o1) {
         RunRd rd;
         rd.init(p);
-        int64_t pos = 0;
         while (pos < o1) {
             int a;
             int64_t len;
             rd.run(&a, &len);
             const int64_t t1 = o1 - pos < len ? o1 - pos : len;
-            int64_t t0 = o0 - pos < len ? o0 - pos : len;
-            t0 = t0 > 0 ? t0 : 0;
-            rle_add(r1, a, t1);
-            rle_add(r0, a, t0);
+            const int64_t t0 = o0 - pos < len ? o0 - pos : len;
+            rle_acc_add(acc1, a, t1);
+            rle_acc_add(acc0, a, t0 > 0 ? t0 : 0);
             pos += len;
         }
     }
-    r0[0] = l0 - (r0[1] + r0[2] + r0[3] + r0[4] + r0[5]);
-    r1[0] = l1 - (r1[1] + r1[2] + r1[3] + r1[4] + r1[5]);
+    rle_acc_out(acc0, base, l0, r0);
+    rle_acc_out(acc1, base, l1, r1);
 }
 
 // Loads of one rank: the header sector and the payload sectors that hold the

@@ -2,10 +2,11 @@
 // BWT, run-length encoded and interleaved with marginal counts per block, with
 // an index into it for fast access).
 //
-// Here the BWT is cut into spans of S symbols.  Each span has a 32-byte header
-// (the marginal counts at its start and where its runs begin) in a directory
-// indexed by l >> log2 S, so a rank is a header read plus a decode of the
-// span's runs up to l.  Runs are bytes (a 3-bit symbol and a 5-bit length,
+// Here the BWT is cut into spans of S symbols.  Each span has a 64-byte header
+// (the marginal counts at its start, where its runs begin, and two decode
+// marks inside it) in a directory indexed by l >> log2 S, so a rank is one
+// header read plus a decode of the span's runs from the last mark before l.
+// Runs are bytes (a 3-bit symbol and a 5-bit length,
 // with one or two extra length bytes for long runs; format in common.cuh),
 // not the paper's Elias-delta bit code: a byte code decodes with plain shifts
 // and needs no bit-level cursor on the GPU.  The index is built from a finished
@@ -38,8 +39,11 @@ __global__ void k_rle_size(const uint8_t *__restrict__ codes, int64_t n, int log
     runs[sp] = nr;
 }
 
+// Mark j of a span of slen symbols: the run holding offset (j + 1) * slen / 3.
+__host__ __device__ __forceinline__ int64_t rle_mark_target(int j, int64_t slen) { return (j + 1) * slen / 3; }
+
 // One thread per span: header (ranks at the span start from the plain index,
-// minus the gbase of their 2^32 range) and runs.
+// minus the gbase of their 2^32 range; where the runs begin; the marks) and runs.
 __global__ void k_rle_write(const uint8_t *__restrict__ codes, OccView src, int log2S, int64_t nspans,
                             const uint64_t *__restrict__ off, const uint64_t *__restrict__ runs,
                             const int64_t *__restrict__ gbase, uint8_t *__restrict__ hdr,
@@ -50,22 +54,31 @@ __global__ void k_rle_write(const uint8_t *__restrict__ codes, OccView src, int 
     const int64_t s1 = s0 + ((int64_t)1 << log2S) < n ? s0 + ((int64_t)1 << log2S) : n;
     int64_t r[SIGMA];
     rank_all_any(src, s0, r);
-    uint32_t w[8];
+    uint32_t w[16];
     const int64_t *g = gbase ? gbase + 5 * (s0 >> GSPAN_LOG2) : nullptr;
     for (int a = 1; a < SIGMA; ++a) w[a - 1] = (uint32_t)(r[a] - (g ? g[a - 1] : 0));
     w[5] = (uint32_t)off[sp];
     w[6] = (uint32_t)(off[sp] >> 32);
     w[7] = (uint32_t)runs[sp];
-    uint4 *h = reinterpret_cast<uint4 *>(hdr + sp * 32);
-    h[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    h[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    uint8_t *p = payload + off[sp];
+    for (int k = 8; k < 16; ++k) w[k] = 0;
+    uint8_t *const p0 = payload + off[sp];
+    uint8_t *p = p0;
+    uint32_t cnt[SIGMA] = {0, 0, 0, 0, 0, 0};
+    const int64_t slen = s1 - s0;
+    int j = 0;  // next mark to place
     int64_t i = s0;
     while (i < s1) {
         const uint8_t a = codes[i];
-        int64_t j = i + 1;
-        while (j < s1 && codes[j] == a) ++j;
-        const int64_t len = j - i;
+        int64_t e = i + 1;
+        while (e < s1 && codes[e] == a) ++e;
+        const int64_t len = e - i;
+        while (j < RLE_MARKS && rle_mark_target(j, slen) < e - s0) {  // this run holds mark j's offset
+            w[8 + 4 * j] = (uint32_t)(i - s0) | (cnt[1] << 16);
+            w[9 + 4 * j] = cnt[2] | (cnt[3] << 16);
+            w[10 + 4 * j] = cnt[4] | (cnt[5] << 16);
+            w[11 + 4 * j] = (uint32_t)(p - p0);
+            ++j;
+        }
         if (len < RLE_BASE1) {
             *p++ = (uint8_t)((a << 5) | (len - 1));
         } else if (len < RLE_BASE2) {
@@ -77,8 +90,11 @@ __global__ void k_rle_write(const uint8_t *__restrict__ codes, OccView src, int 
             *p++ = (uint8_t)(x & 0xFF);
             *p++ = (uint8_t)(x >> 8);
         }
-        i = j;
+        cnt[a] += (uint32_t)len;
+        i = e;
     }
+    uint4 *h = reinterpret_cast<uint4 *>(hdr + sp * RLE_HDR_BYTES);
+    for (int k = 0; k < 4; ++k) h[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
 }
 
 // gbase[5 g + a - 1] = rank(a, g * 2^32) of the plain index.
@@ -98,10 +114,10 @@ __global__ void k_rle_unpack(OccView V, int64_t nspans, uint8_t *__restrict__ co
     int64_t slen = V.n - s0;
     if (slen > ((int64_t)1 << V.log2D)) slen = (int64_t)1 << V.log2D;
     if (slen <= 0) return;
-    int64_t base[SIGMA];
+    int64_t base[SIGMA], pos;
+    uint64_t acc[2];
     RunRd rd;
-    rd.init(rle_header(V, sp, base));
-    int64_t pos = 0;
+    rd.init(rle_start(V, sp, 0, base, &pos, acc));  // offset 0: the span's first run
     while (pos < slen) {
         int a;
         int64_t len;
@@ -115,8 +131,9 @@ __global__ void k_rle_unpack(OccView V, int64_t nspans, uint8_t *__restrict__ co
 __global__ void k_rle_occ(OccView V, int64_t nspans, int64_t *__restrict__ occ) {
     const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (sp >= nspans) return;
-    int64_t r[SIGMA];
-    rle_header(V, sp, r);
+    int64_t r[SIGMA], pos;
+    uint64_t acc[2];
+    rle_start(V, sp, 0, r, &pos, acc);
     r[0] = (sp << V.log2D) - (r[1] + r[2] + r[3] + r[4] + r[5]);
     for (int a = 0; a < SIGMA; ++a) occ[sp * SIGMA + a] = r[a];
 }
@@ -131,7 +148,7 @@ __global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned 
     const uint8_t *hdr = V.blocks, *payload = V.payload;
     const int64_t n = V.n, *gbase = V.gbase;
     const int log2S = V.log2D;
-    const uint32_t *h = reinterpret_cast<const uint32_t *>(hdr + sp * 32);
+    const uint32_t *h = reinterpret_cast<const uint32_t *>(hdr + sp * RLE_HDR_BYTES);
     const int64_t s0 = sp << log2S;
     int64_t slen = n - s0;
     if (slen > ((int64_t)1 << log2S)) slen = (int64_t)1 << log2S;
@@ -139,7 +156,7 @@ __global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned 
     const uint64_t b0 = (uint64_t)h[5] | ((uint64_t)h[6] << 32);
     uint64_t b1 = (uint64_t)pbytes;
     if (sp + 1 < nspans) {
-        const uint32_t *hn = reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * 32);
+        const uint32_t *hn = reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * RLE_HDR_BYTES);
         b1 = (uint64_t)hn[5] | ((uint64_t)hn[6] << 32);
     }
     if (b0 > b1 || b1 > (uint64_t)pbytes) {
@@ -149,6 +166,9 @@ __global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned 
     int64_t cnt[SIGMA] = {0, 0, 0, 0, 0, 0};
     int64_t pos = 0, nr = 0;
     uint64_t q = b0;
+    uint32_t mk[4 * RLE_MARKS];  // the marks as the encoder places them
+    for (int k = 0; k < 4 * RLE_MARKS; ++k) mk[k] = 0;
+    int j = 0;
     while (pos < slen) {
         if (q >= b1) {
             atomicOr(bad, 2u);
@@ -177,6 +197,13 @@ __global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned 
             atomicOr(bad, 4u);
             return;
         }
+        while (j < RLE_MARKS && rle_mark_target(j, slen) < pos + len) {
+            mk[4 * j] = (uint32_t)pos | ((uint32_t)cnt[1] << 16);
+            mk[4 * j + 1] = (uint32_t)cnt[2] | ((uint32_t)cnt[3] << 16);
+            mk[4 * j + 2] = (uint32_t)cnt[4] | ((uint32_t)cnt[5] << 16);
+            mk[4 * j + 3] = (uint32_t)(q - b0 - rle_run_bytes(len));
+            ++j;
+        }
         cnt[a] += len;
         pos += len;
         ++nr;
@@ -185,10 +212,15 @@ __global__ void k_rle_check(OccView V, int64_t pbytes, int64_t nspans, unsigned 
         atomicOr(bad, 8u);
         return;
     }
+    for (int k = 0; k < 4 * RLE_MARKS; ++k)
+        if (h[8 + k] != mk[k]) {
+            atomicOr(bad, 32u);
+            return;
+        }
     // the counts start at 0, advance by the span's runs to the next header's
     // (both relative to their 2^32 range) and end at the symbol totals
     const int64_t *g0 = gbase ? gbase + 5 * (s0 >> GSPAN_LOG2) : nullptr;
-    const uint32_t *hn = sp + 1 < nspans ? reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * 32) : nullptr;
+    const uint32_t *hn = sp + 1 < nspans ? reinterpret_cast<const uint32_t *>(hdr + (sp + 1) * RLE_HDR_BYTES) : nullptr;
     const int64_t *g1 = gbase ? gbase + 5 * ((s0 + ((int64_t)1 << log2S)) >> GSPAN_LOG2) : nullptr;
     for (int a = 1; a < SIGMA; ++a) {
         const int64_t c0 = (int64_t)h[a - 1] + (g0 ? g0[a - 1] : 0);
@@ -231,7 +263,7 @@ static int compress_impl(const rb3_index *src, int S, cudaStream_t st, rb3_index
     x->rle = 1;
     x->D = S;
     x->log2D = ilog2(S);
-    x->block_bytes = 32;
+    x->block_bytes = RLE_HDR_BYTES;
     x->single_strand = src->single_strand;
     x->nblocks = n / S + 1;
     x->str_end = src->str_end;
@@ -262,7 +294,7 @@ static int compress_impl(const rb3_index *src, int S, cudaStream_t st, rb3_index
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     x->payload_bytes = (int64_t)(tail[0] + tail[1]);
     x->runs = (int64_t)(tail[2] + tail[3]);
-    RB3_TRY(dev_alloc((void **)&x->blocks, (size_t)ns * 32, st));
+    RB3_TRY(dev_alloc((void **)&x->blocks, (size_t)ns * RLE_HDR_BYTES, st));
     RB3_TRY(dev_alloc((void **)&x->payload, (size_t)x->payload_bytes + 16, st));
     RB3_CUDA_TRY(cudaMemsetAsync(x->payload + x->payload_bytes, 0, 16, st));
     RB3_LAUNCH(k_rle_write, nb_for(ns, 128), 128, 0, st, codes.as<uint8_t>(), V, x->log2D, ns, off.as<uint64_t>(),
@@ -291,7 +323,7 @@ RB3_EXPORT int rb3_index_compress(const rb3_index *src, int32_t span, void *stre
     RB3_CHECK_ARG(src && out, "NULL argument");
     *out = nullptr;
     const int S = span ? span : kDefaultRleSpan;
-    RB3_CHECK_ARG(valid_rle_span(S), "span must be a power of two from 512 to 65536");
+    RB3_CHECK_ARG(valid_rle_span(S), "span must be a power of two from 512 to 16384");
     RB3_CHECK_ARG(!src->rle, "the index is already run-length encoded");
     cudaStream_t st = (cudaStream_t)stream;
     rb3_index *x = new rb3_index();
