@@ -267,8 +267,11 @@ int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int
  * position.  The copy keeps src's sampled suffix array; src is unchanged.
  * rb3_backward_search, rb3_mem_search (all forms), rb3_mem_search_noalloc,
  * the server, rb3_locate, rb3_export (occ rows = the span headers),
- * rb3_index_save / rb3_index_load take it; rb3_merge and rb3_append_batches
- * reject it (RB3_E_INVAL): merge plain indexes, then compress.
+ * rb3_index_save / rb3_index_load take it.  rb3_merge / rb3_merge_opts take it
+ * on either side and rb3_append_batches as dst: a run-length input is expanded
+ * to a transient plain D = 32 copy (one byte per symbol), merged, and a
+ * run-length dst is re-encoded at its span (dst unchanged on failure);
+ * rb3_tune_merge rejects it (RB3_E_INVAL).
  * RB3_E_INVAL for a bad span or a src that is already run-length encoded. */
 int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_index **out);
 

@@ -330,7 +330,7 @@ RB3_EXPORT int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_op
     rb3_opts_default(&opts);
     if (o) opts = *o;
     cudaStream_t st = (cudaStream_t)stream;
-    RB3_TRY(merge_impl(dst, src, opts, st));
+    RB3_TRY(merge_any(dst, src, opts, st));
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     return RB3_OK;
 }

@@ -813,6 +813,11 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
 int rle_export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st);
+// Merge of any two layouts: a run-length input is merged through a plain copy,
+// and a run-length dst is re-encoded (same span) after the merge.
+int merge_any(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
+int rle_plain_copy(const rb3_index *x, cudaStream_t st, rb3_index **out);
+int rle_recompress_into(rb3_index *dst, const rb3_index *plain, int span, cudaStream_t st);
 int rle_check_impl(const rb3_index *x, cudaStream_t st);
 // Sampled suffix array of a batch from its SA (builder) and of a merge (from pos).
 int sample_batch(rb3_index *x, const int32_t *SA, cudaStream_t st);

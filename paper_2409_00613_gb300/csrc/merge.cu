@@ -575,6 +575,7 @@ __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
 // pos[k] = merged row of every B2 row k (the walk of Algorithm 1), into a
 // caller-provided array of src->n entries; dst and src are not modified.
 int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos) {
+    RB3_CHECK_ARG(!dst->rle && !src->rle, "the merge walk reads plain-layout indexes only");
     const int64_t n1 = dst->n, n2 = src->n;
     if (n2 == 0) return RB3_OK;
     OccView V1 = occ_view(dst), V2 = occ_view(src);

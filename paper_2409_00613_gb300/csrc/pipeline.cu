@@ -159,7 +159,6 @@ RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int6
                                   const int64_t *batch_end, int64_t n_batches, const rb3_opts *o, void *stream) {
     set_error("%s", "");
     RB3_CHECK_ARG(dst != nullptr, "NULL index");
-    RB3_CHECK_ARG(!dst->rle, "a run-length index is read-only (append to a plain index, then compress)");
     RB3_CHECK_ARG(n_seq >= 0 && n_batches >= 0, "negative size");
     if (n_batches == 0) return RB3_OK;
     RB3_CHECK_ARG(batch_end != nullptr && (n_seq == 0 || len != nullptr), "NULL argument");
@@ -189,6 +188,15 @@ RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int6
         total += lens[i];
     }
     RB3_CHECK_ARG(total == 0 || seq != nullptr, "seq is NULL");
+    if (dst->rle) {  // appended to a plain copy, re-encoded once at the end
+        rb3_index *P = nullptr;
+        RB3_TRY(rle_plain_copy(dst, st, &P));
+        int r = append_batches(P, seq, lens.data(), n_seq, ends.data(), n_batches, opts, st);
+        if (r == RB3_OK) r = rle_recompress_into(dst, P, dst->D, st);
+        cudaStreamSynchronize(st);
+        rb3_index_free(P);
+        return r;
+    }
     RB3_TRY(append_batches(dst, seq, lens.data(), n_seq, ends.data(), n_batches, opts, st));
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     return RB3_OK;

@@ -255,6 +255,20 @@ int rle_check_impl(const rb3_index *x, cudaStream_t st) {
     return RB3_OK;
 }
 
+static int copy_samples(const rb3_index *src, rb3_index *x, cudaStream_t st) {
+    if (!(src->sa_s && src->sdir)) return RB3_OK;
+    const int64_t nw = src->n / 64 + 1;
+    x->sa_s = src->sa_s;
+    x->n_samples = src->n_samples;
+    RB3_TRY(dev_alloc((void **)&x->sdir, sizeof(uint64_t) * 2 * nw, st));
+    RB3_TRY(dev_alloc((void **)&x->svals, sizeof(uint64_t) * (x->n_samples > 0 ? x->n_samples : 1), st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(x->sdir, src->sdir, sizeof(uint64_t) * 2 * nw, cudaMemcpyDeviceToDevice, st));
+    if (x->n_samples)
+        RB3_CUDA_TRY(
+            cudaMemcpyAsync(x->svals, src->svals, sizeof(uint64_t) * x->n_samples, cudaMemcpyDeviceToDevice, st));
+    return RB3_OK;
+}
+
 static int compress_impl(const rb3_index *src, int S, cudaStream_t st, rb3_index *x) {
     const int64_t n = src->n;
     x->n = n;
@@ -299,18 +313,139 @@ static int compress_impl(const rb3_index *src, int S, cudaStream_t st, rb3_index
     RB3_CUDA_TRY(cudaMemsetAsync(x->payload + x->payload_bytes, 0, 16, st));
     RB3_LAUNCH(k_rle_write, nb_for(ns, 128), 128, 0, st, codes.as<uint8_t>(), V, x->log2D, ns, off.as<uint64_t>(),
                runs.as<uint64_t>(), x->gbase, x->blocks, x->payload);
-    if (src->sa_s && src->sdir) {  // the sampled suffix array is per row: rows do not change
-        const int64_t nw = n / 64 + 1;
-        x->sa_s = src->sa_s;
-        x->n_samples = src->n_samples;
-        RB3_TRY(dev_alloc((void **)&x->sdir, sizeof(uint64_t) * 2 * nw, st));
-        RB3_TRY(dev_alloc((void **)&x->svals, sizeof(uint64_t) * (x->n_samples > 0 ? x->n_samples : 1), st));
-        RB3_CUDA_TRY(cudaMemcpyAsync(x->sdir, src->sdir, sizeof(uint64_t) * 2 * nw, cudaMemcpyDeviceToDevice, st));
-        if (x->n_samples)
-            RB3_CUDA_TRY(cudaMemcpyAsync(x->svals, src->svals, sizeof(uint64_t) * x->n_samples,
-                                         cudaMemcpyDeviceToDevice, st));
-    }
+    RB3_TRY(copy_samples(src, x, st));  // the sampled suffix array is per row: rows do not change
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+// One thread per D = 32 block of a plain copy: the ranks at its start from the
+// run-length index (minus the same span bases), the planes from the codes.
+__global__ void k_rle_to_plain32(OccView V, const uint8_t *__restrict__ codes, int64_t nb32,
+                                 uint8_t *__restrict__ blocks) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb32) return;
+    const int64_t l0 = b * 32;
+    int64_t r[SIGMA];
+    rle_rank<false>(V, l0, r, nullptr);
+    const int64_t *g = V.gbase ? V.gbase + 5 * (l0 >> GSPAN_LOG2) : nullptr;
+    uint32_t w[8];
+    for (int a = 1; a < SIGMA; ++a) w[a - 1] = (uint32_t)(r[a] - (g ? g[a - 1] : 0));
+    uint32_t p0 = 0, p1 = 0, p2 = 0;
+    for (int j = 0; j < 32 && l0 + j < V.n; ++j) {
+        const uint32_t c = codes[l0 + j];
+        p0 |= (c & 1u) << j;
+        p1 |= ((c >> 1) & 1u) << j;
+        p2 |= ((c >> 2) & 1u) << j;
+    }
+    w[5] = p0;
+    w[6] = p1;
+    w[7] = p2;
+    uint4 *h = reinterpret_cast<uint4 *>(blocks + b * 32);
+    h[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    h[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Plain D = 32 copy of a run-length index (same rows, same sampled suffix array).
+static int decompress_impl(const rb3_index *x, cudaStream_t st, rb3_index *P) {
+    const int64_t n = x->n;
+    P->n = n;
+    P->m = x->m;
+    for (int a = 0; a < 7; ++a) P->C[a] = x->C[a];
+    P->D = 32;
+    P->log2D = 5;
+    P->block_bytes = 32;
+    P->single_strand = x->single_strand;
+    P->nblocks = n / 32 + 1;
+    P->str_end = x->str_end;
+    P->device = x->device;
+    DevBuf codes;
+    RB3_TRY(codes.alloc((size_t)(n > 0 ? n : 1), st));
+    RB3_TRY(rle_export_impl(x, codes.as<uint8_t>(), nullptr, st));
+    RB3_TRY(dev_alloc((void **)&P->blocks, (size_t)P->nblocks * 32, st));
+    RB3_LAUNCH(k_rle_to_plain32, nb_for(P->nblocks, 128), 128, 0, st, occ_view(x), codes.as<uint8_t>(), P->nblocks,
+               P->blocks);
+    if (x->gbase) {  // the same span bases: rank(a, g * 2^32)
+        const size_t gb = sizeof(int64_t) * 5 * gbase_rows(n);
+        RB3_TRY(dev_alloc((void **)&P->gbase, gb, st));
+        RB3_CUDA_TRY(cudaMemcpyAsync(P->gbase, x->gbase, gb, cudaMemcpyDeviceToDevice, st));
+    }
+    RB3_TRY(copy_samples(x, P, st));
+    int64_t Cw[7];
+    for (int a = 0; a < 7; ++a) Cw[a] = P->C[a];
+    RB3_TRY(finalize_counts(P, st));
+    for (int a = 0; a < 7; ++a)
+        if (P->C[a] != Cw[a]) {
+            set_error("run-length decode: counts differ from the index's");
+            return RB3_E_CUDA;
+        }
+    return RB3_OK;
+}
+
+// Owns a temporary index.
+struct TmpIndex {
+    rb3_index *p = nullptr;
+    ~TmpIndex() {
+        if (p) rb3_index_free(p);
+    }
+};
+
+// dst <- x's contents; dst's old arrays are freed with x's shell.
+static void install(rb3_index *dst, rb3_index *x) {
+    std::swap(*dst, *x);
+    rb3_index_free(x);
+}
+
+int merge_any(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
+    if (!dst->rle && !src->rle) return merge_impl(dst, src, o, st);
+    RB3_CHECK_ARG(dst != src, "dst and src must differ");
+    TmpIndex P, Q;
+    rb3_index *d = dst;
+    const rb3_index *s = src;
+    if (src->rle) {  // the walk reads B2's LF (no build data): a plain copy of it
+        Q.p = new rb3_index();
+        RB3_TRY(decompress_impl(src, st, Q.p));
+        s = Q.p;
+    }
+    if (dst->rle) {
+        P.p = new rb3_index();
+        RB3_TRY(decompress_impl(dst, st, P.p));
+        d = P.p;
+    }
+    RB3_TRY(merge_impl(d, s, o, st));
+    if (dst->rle) {
+        rb3_index *R = new rb3_index();
+        const int r = compress_impl(P.p, dst->D, st, R);
+        if (r != RB3_OK) {
+            cudaStreamSynchronize(st);
+            rb3_index_free(R);
+            return r;
+        }
+        install(dst, R);
+    }
+    return RB3_OK;
+}
+
+int rle_plain_copy(const rb3_index *x, cudaStream_t st, rb3_index **out) {
+    rb3_index *P = new rb3_index();
+    const int r = decompress_impl(x, st, P);
+    if (r != RB3_OK) {
+        cudaStreamSynchronize(st);
+        rb3_index_free(P);
+        return r;
+    }
+    *out = P;
+    return RB3_OK;
+}
+
+int rle_recompress_into(rb3_index *dst, const rb3_index *plain, int span, cudaStream_t st) {
+    rb3_index *R = new rb3_index();
+    const int r = compress_impl(plain, span, st, R);
+    if (r != RB3_OK) {
+        cudaStreamSynchronize(st);
+        rb3_index_free(R);
+        return r;
+    }
+    install(dst, R);
     return RB3_OK;
 }
 

@@ -175,6 +175,7 @@ RB3_EXPORT int rb3_tune_merge(const rb3_index *dst, const rb3_index *src, const 
                               double *best_ms, void *stream) {
     set_error("%s", "");
     RB3_CHECK_ARG(dst && src && best, "NULL argument");
+    RB3_CHECK_ARG(!dst->rle && !src->rle, "merge tuning needs plain-layout indexes");
     rb3_opts o;
     rb3_opts_default(&o);
     if (base) o = *base;

@@ -24,6 +24,11 @@ def build(S, s0=0, s1=None, **opts):
     return rb.rb3_build_batch(seq, S.lens[s0:s1].copy(), opts=opts or None)
 
 
+def ref(S, a, b):
+    sub = S.subset(a, b)
+    return oracle.bwt(oracle.concat(sub.seq, sub.lens, True))
+
+
 def smem_rows(recs, n):
     if n == 0:
         return np.zeros((0, 6), dtype=np.int64)
@@ -104,8 +109,8 @@ def test_rle_smem_all_forms_vs_oracle(span, ell, smin):
 
 def test_rle_locate_save_load_and_refusals(tmp_path):
     """Locate every row of a compressed index with a sampled suffix array;
-    save / load keeps every byte; a damaged image is refused on load; merges
-    and appends refuse a run-length index."""
+    save / load keeps every byte; a damaged image is refused on load; bad
+    spans, double compression and merge tuning are refused."""
     S = synth.pangenome(seed=63, founder_len=6_000, n_hap=6, batch=3)
     idx = build(S, 0, 3, sa_sample=8)
     rb.rb3_merge(idx, build(S, 3, 6, sa_sample=8))
@@ -149,17 +154,52 @@ def test_rle_locate_save_load_and_refusals(tmp_path):
     with pytest.raises(rb.RB3Error) as e:
         rb.rb3_index_compress(R)
     assert e.value.code == rb.RB3_E_INVAL
-    for call in (lambda: rb.rb3_merge(R, build(S, 0, 1)), lambda: rb.rb3_merge(idx, R)):
+    for call in (lambda: rb.rb3_tune_merge(R, build(S, 0, 1)), lambda: rb.rb3_tune_merge(idx, R)):
         with pytest.raises(rb.RB3Error) as e:
             call()
         assert e.value.code == rb.RB3_E_INVAL
-    with pytest.raises(rb.RB3Error) as e:
-        rb.rb3_append_batches(R, torch.from_numpy(S.seq[:S.offsets[1]].copy()).to(DEV), S.lens[:1].copy(),
-                              np.array([1], np.int64))
-    assert e.value.code == rb.RB3_E_INVAL
     # the plain index is untouched by all of it
     codes = rb.rb3_export(idx)
     assert np.array_equal(codes, B)
+
+
+@pytest.mark.parametrize("span", [512, 2048])
+def test_rle_merges_and_appends(span):
+    """Merges with a run-length input on either side, and appends to a
+    run-length index (through a plain copy, re-encoded at the same span): the
+    result against the oracle's BWT of the concatenation, the sampled suffix
+    array carried along, the inputs unchanged."""
+    S = synth.pangenome(seed=77, founder_len=5_000, n_hap=8, batch=2)
+    T_all = oracle.concat(S.seq, S.lens, True)
+    B_all = oracle.bwt(T_all)
+    parts = [(0, 2), (2, 4), (4, 6), (6, 8)]
+    opts = {"sa_sample": 4}
+    # run-length dst, plain src (segmented and plain walk forms)
+    R = rb.rb3_index_compress(build(S, 0, 2, **opts), span)
+    for k, (a, b) in enumerate(parts[1:3]):
+        src = build(S, a, b, **opts)
+        rb.rb3_merge_opts(R, src, {"merge_form": k % 2})
+        check_rle(R, ref(S, 0, b), span)
+        assert np.array_equal(rb.rb3_export(src), ref(S, a, b))
+    # plain dst, run-length src
+    P = build(S, 0, 6, **opts)
+    Rs = rb.rb3_index_compress(build(S, 6, 8, **opts), span)
+    rb.rb3_merge(P, Rs)
+    assert not rb.rb3_index_info(P)["run_length"]
+    assert np.array_equal(rb.rb3_export(P), B_all)
+    check_rle(Rs, ref(S, 6, 8), span)
+    # both run-length
+    rb.rb3_merge(R, Rs)
+    check_rle(R, B_all, span)
+    # append the last batches to a run-length index, in two batches
+    A = rb.rb3_index_compress(build(S, 0, 4, **opts), span)
+    off = S.offsets
+    seq = torch.from_numpy(S.seq[off[4]:off[8]].copy()).to(DEV)
+    rb.rb3_append_batches(A, seq, S.lens[4:8].copy(), np.array([2, 4], np.int64), opts)
+    check_rle(A, B_all, span)
+    rows = np.arange(len(T_all), dtype=np.int64)
+    assert rb.rb3_index_info(A)["sa_sample"] == 4
+    assert np.array_equal(rb.rb3_locate(A, rows), oracle.locate(T_all, oracle.suffix_array(T_all), rows))
 
 
 def test_rle_server_round_trip():
