@@ -27,6 +27,10 @@ namespace rb3 {
 
 constexpr int H0 = 18;            // symbols in the round-0 key (base-6 digits; 6^18 < 2^47)
 constexpr int H0_BITS = 47;
+// Batches without N: 17 symbols as 2-bit digits (A..T = 0..3) and a 5-bit
+// length field, 39 bits: five radix passes instead of six.
+constexpr int H4 = 17;
+constexpr int H4_BITS = 2 * H4 + 5;
 constexpr int SMALL_MAX = 1024;   // groups up to this size are sorted in shared memory
 constexpr int RT_TILE = 2048;     // round-kernel tile (entries)
 constexpr int RT_THREADS = 256;
@@ -53,6 +57,9 @@ __global__ void k_encode(const uint8_t *__restrict__ seq, const int64_t *__restr
             atomicOr(bad, 1);
             x = 5;
         }
+        // bit 1: the batch holds N (one atomic per warp that sees one)
+        const unsigned nm = __ballot_sync(__activemask(), x == 5);
+        if (nm && (threadIdx.x & 31) == __ffs(nm) - 1) atomicOr(bad, 2);
         int64_t base = out_off[s];
         T[base + o] = (uint8_t)x;
         if (both) T[base + L + 1 + (L - 1 - o)] = (uint8_t)comp_sym(x);
@@ -85,13 +92,44 @@ __global__ void k_init_keys(const uint8_t *__restrict__ T, int64_t n, uint64_t *
     val[p] = (uint32_t)p;
 }
 
+// Round-0 key of an N-free batch.  The window's symbols up to its first
+// sentinel (at most H4) as 2-bit digits, padded with zeros, then the number of
+// those symbols (H4 if the window holds no sentinel).  Ordering by (digits,
+// count) is the suffix order of the windows: a window U$ sorts before every
+// window starting with U and a letter, and the padding ties U$ only with
+// windows U A..A, which the count puts after it.  Windows with the same digits
+// and count are equal (or both end at a sentinel after the same prefix: then
+// the stable sort keeps them in position order, the order of their sentinels).
+__global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, uint64_t *__restrict__ key,
+                             uint32_t *__restrict__ val) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint64_t k = 0;
+    uint32_t len = H4;
+    bool stop = false;
+#pragma unroll
+    for (int j = 0; j < H4; ++j) {
+        const uint32_t c = stop ? 0u : (uint32_t)T[p + j];  // T ends with a sentinel: reads stop at n-1
+        if (!stop && c == 0) {
+            stop = true;
+            len = (uint32_t)j;
+        }
+        k = (k << 2) | (stop ? 0u : c - 1u);
+    }
+    key[p] = (k << 5) | len;
+    val[p] = (uint32_t)p;
+}
+
 // A group starts at i if its key differs from the previous one, or if its
-// window holds a sentinel (then its order is final: singleton).  A window
-// holds a sentinel iff its last base-6 digit is 0.
+// window holds a sentinel (then its order is final: singleton).  A base-6
+// window holds a sentinel iff its last digit is 0; a 2-bit one iff its count
+// field is below H4.
+template <bool B4>
 __global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__restrict__ hv) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool head = i == 0 || K[i] != K[i - 1] || (K[i] % 6u) == 0;
+    const bool sent = B4 ? (K[i] & 31u) < (uint64_t)H4 : (K[i] % 6u) == 0;
+    bool head = i == 0 || K[i] != K[i - 1] || sent;
     hv[i] = head ? (uint32_t)i : 0u;
 }
 
@@ -478,6 +516,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
     int32_t *rank = isab.as<int32_t>();
 
     if (n > 0) {
+        bool has_n = false;  // N-free batches take the 2-bit round-0 key
         // ---- S0 ----
         {
             Phase ph("build.encode", st);
@@ -497,10 +536,11 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             int hbad = 0;
             RB3_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
-            if (hbad) {
+            if (hbad & 1) {
                 set_error("input symbol outside 1..5 (A,C,G,T,N codes)");
                 return RB3_E_INVAL;
             }
+            has_n = (hbad & 2) != 0;
         }
         // ---- S1 round 0 ----
         DevBuf SAb, gsizeb;
@@ -522,18 +562,26 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(k1.alloc(sizeof(uint64_t) * n, st));
             RB3_TRY(v1.alloc(sizeof(uint32_t) * n, st));
             uint32_t *v0 = reinterpret_cast<uint32_t *>(SA);
+            // The sort starts from (ka, va) and ends in (k0, SA): the six base-6 passes
+            // return to their input, the five 2-bit ones end in the other buffer.
+            uint64_t *ka = has_n ? k0.as<uint64_t>() : k1.as<uint64_t>();
+            uint32_t *va = has_n ? v0 : v1.as<uint32_t>();
+            uint64_t *kb = has_n ? k1.as<uint64_t>() : k0.as<uint64_t>();
+            uint32_t *vb = has_n ? v1.as<uint32_t>() : v0;
             {
                 Phase pk("k.init_keys", st, 13.0 * n);  // 1 text byte in, 8-byte key + 4-byte value out
-                RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, k0.as<uint64_t>(), v0);
+                if (has_n) RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, ka, va);
+                else RB3_LAUNCH(k_init_keys4, nb_for(n, 256), 256, 0, st, T, n, ka, va);
             }
             bool alt = false;
-            RB3_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0, k1.as<uint64_t>(), v1.as<uint32_t>(), n, 0, H0_BITS, st,
-                                     &alt));
-            const uint64_t *K = alt ? k1.as<uint64_t>() : k0.as<uint64_t>();
-            if (alt) RB3_CUDA_TRY(cudaMemcpyAsync(SA, v1.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+            RB3_TRY(radix_sort_pairs(ka, va, kb, vb, n, 0, has_n ? H0_BITS : H4_BITS, st, &alt));
+            const uint64_t *K = alt ? kb : ka;
+            if ((alt ? vb : va) != v0)
+                RB3_CUDA_TRY(cudaMemcpyAsync(SA, alt ? vb : va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
             DevBuf hv, fs, fl, ps, pl;
             RB3_TRY(hv.alloc(sizeof(uint32_t) * n, st));
-            RB3_LAUNCH(k_heads, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
+            if (has_n) RB3_LAUNCH(k_heads<false>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
+            else RB3_LAUNCH(k_heads<true>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
             RB3_TRY(scan_u32(hv.as<uint32_t>(), hv.as<uint32_t>(), n, true, 1, st));  // gstart
             k0.release();
             k1.release();
@@ -612,7 +660,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
         RB3_TRY(tbeg.alloc(sizeof(uint32_t) * max_tiles, st));
         RB3_TRY(toff.alloc(sizeof(uint32_t) * max_tiles, st));
         int gbits = ilog2(n) + 1;
-        uint32_t h = H0;
+        uint32_t h = has_n ? H0 : H4;  // symbols the round-0 order is exact to
         int round = 0;
         static const char *kRoundNames[] = {
             "round.00", "round.01", "round.02", "round.03", "round.04", "round.05", "round.06", "round.07",
