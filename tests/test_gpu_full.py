@@ -124,4 +124,17 @@ def test_occ32_index_past_2_to_32():
     assert (got[:, 1] > 2**32).sum() > 100  # intervals in the second span were exercised
     for p in parts:
         p.free()
+    # the run-length copy keeps the span bases: the same intervals.  Merged with
+    # an empty index (expanded to a plain copy and re-encoded): the same again;
+    # merged with one empty string (two new sentinels, which sort before every
+    # letter): every interval moves up by two
+    R = rb.rb3_index_compress(idx, 2048)
+    assert rb.rb3_index_info(R)["run_length"]
+    assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got)
+    rb.rb3_merge(R, rb.rb3_index_empty(opts))
+    assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got)
+    rb.rb3_merge(R, rb.rb3_build_batch(np.zeros(0, np.uint8), np.zeros(1, np.int64), opts=opts))
+    assert rb.rb3_index_info(R)["n"] == info["n"] + 2
+    assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got + 2)
+    R.free()
     idx.free()

@@ -124,6 +124,37 @@ def test_large_groups_low_complexity():
     check_index(A, ref_bwt(S))
 
 
+@pytest.mark.parametrize("both", [True, False])
+def test_n_free_batches_sentinel_windows(both):
+    """Batches without N take the 2-bit round-0 key: strings that end a few
+    symbols after a shared prefix (U$ against U A..A, the ties the count field
+    breaks), all-A strings of every length up to past the key width, empty
+    strings, long A and C runs (groups larger than shared memory), and random
+    N-free lists; against the oracle, built whole and by merges."""
+    g = synth.rng(4242 + both)
+    seqs = [np.zeros(0, np.uint8)]
+    for k in range(0, 24):
+        seqs.append(np.full(k, 1, np.uint8))                                  # A^k
+        seqs.append(np.concatenate([[2], np.full(k, 1, np.uint8)]).astype(np.uint8))  # C A^k
+        seqs.append(np.concatenate([[3, 2], np.full(k, 1, np.uint8), [4]]).astype(np.uint8))  # G C A^k T
+    seqs += [np.full(2500, 1, np.uint8), np.full(1800, 2, np.uint8), synth.random_bases(g, 400)]
+    for _ in range(30):
+        seqs.append(synth.random_bases(g, int(g.integers(0, 60))))
+    order = g.permutation(len(seqs))
+    seqs = [seqs[i] for i in order]
+    S = synth.Strings(np.concatenate(seqs).astype(np.uint8), np.array([len(x) for x in seqs], np.int64))
+    assert not np.any(S.seq == 5)
+    opts = {"single_strand": int(not both)}
+    check_index(build(S, **opts), ref_bwt(S, both=both))
+    half = len(seqs) // 2
+    A = build(S, 0, half, **opts)
+    rb.rb3_merge_opts(A, build(S, half, len(seqs), **opts), dict(opts, seg_len=50))
+    check_index(A, ref_bwt(S, both=both))
+    for trial in range(4):
+        R = synth.random_strings(g, int(g.integers(3, 40)), int(g.integers(5, 300)), n_frac=0.0, allow_empty=True)
+        check_index(build(R, **opts), ref_bwt(R, both=both))
+
+
 def test_mixed_occ_intervals():
     """Merges between indexes of different Occ intervals (the result takes the
     destination's), segmented and plain walks."""
