@@ -188,6 +188,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
 // Tiles of MT output symbols.  kstart[t] = number of B2 rows with pos < t*MT.
 constexpr int MT = 2048;
 constexpr int MT_THREADS = MT / 8;
+// CTAs per SM asked of the register allocator: a tile is short and latency-bound
+// (its phases wait on pos, then on the input blocks), so residency is what hides it.
+#ifndef RB3_SCATTER_MINB
+#define RB3_SCATTER_MINB 8
+#endif
 
 __global__ void k_tile_starts(const int64_t *__restrict__ pos, int64_t n2, int64_t ntiles,
                               int64_t *__restrict__ kstart) {
@@ -246,7 +251,7 @@ __global__ void k_tile_bases(OccView B1, OccView B2, const int64_t *__restrict__
     for (int a = 0; a < SIGMA; ++a) base6[t * SIGMA + a] = r1[a] + r2[a];
 }
 
-__global__ void __launch_bounds__(MT_THREADS, 4) k_scatter(OccView B1, OccView B2, const int64_t *__restrict__ pos,
+__global__ void __launch_bounds__(MT_THREADS, RB3_SCATTER_MINB) k_scatter(OccView B1, OccView B2, const int64_t *__restrict__ pos,
                                                         const int64_t *__restrict__ kstart,
                                                         const int64_t *__restrict__ tbase, int64_t nM, int64_t nbM,
                                                         int log2D, int bb, uint8_t *__restrict__ M) {
