@@ -273,11 +273,30 @@ __global__ void __launch_bounds__(RT_THREADS) k_round_small(const uint32_t *__re
     __syncthreads();
     uint32_t surv = 0;
     for (int i = threadIdx.x; i < cnt; i += RT_THREADS) {
+        // the lanes of a warp hold consecutive entries (a prefix of the warp on
+        // the last pass): a group's bounds inside the warp come from ballots of
+        // its first and last entries; only groups that cross the warp's edge
+        // are followed in shared memory
+        const int lane = threadIdx.x & 31, w0 = i - lane;
+        const unsigned act = cnt - w0 >= 32 ? 0xFFFFFFFFu : (1u << (cnt - w0)) - 1u;
         uint32_t g = sg[i], k = sk[i];
-        int rs = i;
-        while (rs > 0 && sg[rs - 1] == g) --rs;
-        int rend = i + 1;
-        while (rend < cnt && sg[rend] == g) ++rend;
+        const bool first = i == 0 || sg[i - 1] != g;
+        const bool last = i + 1 == cnt || sg[i + 1] != g;
+        const unsigned fb = __ballot_sync(act, first) & (0xFFFFFFFFu >> (31 - lane));  // lanes 0..lane
+        const unsigned lb = __ballot_sync(act, last) & (0xFFFFFFFFu << lane);          // lanes lane..31
+        int rs, rend;
+        if (fb) {
+            rs = w0 + (31 - __clz(fb));
+        } else {
+            rs = w0;
+            while (rs > 0 && sg[rs - 1] == g) --rs;
+        }
+        if (lb) {
+            rend = w0 + __ffs(lb);
+        } else {
+            rend = w0 + 32;
+            while (rend < cnt && sg[rend] == g) ++rend;
+        }
         int less = 0, eqb = 0, eqt = 0;
         for (int j = rs; j < rend; ++j) {
             uint32_t kj = sk[j];
