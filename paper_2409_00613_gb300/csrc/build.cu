@@ -100,24 +100,66 @@ __global__ void k_init_keys(const uint8_t *__restrict__ T, int64_t n, uint64_t *
 // windows U A..A, which the count puts after it.  Windows with the same digits
 // and count are equal (or both end at a sentinel after the same prefix: then
 // the stable sort keeps them in position order, the order of their sentinels).
+constexpr int K4_PER = 16;  // positions per thread of k_init_keys4
+
+// One thread per K4_PER consecutive positions p0 + r: the window bytes
+// T[p0, p0 + 32) in registers (two 16-byte loads), the digits of position r + 1
+// rolled from those of r, the count from a mask of the window's sentinels.
 __global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, uint64_t *__restrict__ key,
                              uint32_t *__restrict__ val) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint64_t k = 0;
-    uint32_t len = H4;
-    bool stop = false;
+    const int64_t p0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * K4_PER;
+    if (p0 >= n) return;
+    uint32_t w[8];
+    if (p0 + 32 <= n) {  // T is 16-byte aligned and p0 a multiple of 16
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(T + p0));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(T + p0) + 1);
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+    } else {  // past the text: zero bytes, read as sentinels (the text ends with one anyway)
 #pragma unroll
-    for (int j = 0; j < H4; ++j) {
-        const uint32_t c = stop ? 0u : (uint32_t)T[p + j];  // T ends with a sentinel: reads stop at n-1
-        if (!stop && c == 0) {
-            stop = true;
-            len = (uint32_t)j;
-        }
-        k = (k << 2) | (stop ? 0u : c - 1u);
+        for (int k = 0; k < 8; ++k) w[k] = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b)
+            if (p0 + b < n) w[b >> 2] |= (uint32_t)T[p0 + b] << (8 * (b & 3));
     }
-    key[p] = (k << 5) | len;
-    val[p] = (uint32_t)p;
+    uint32_t z = 0;  // bit b: byte b of the window is a sentinel
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t e = __vcmpeq4(w[k], 0u);
+        z |= (((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u)) << (4 * k);
+    }
+    constexpr uint64_t M34 = (1ull << (2 * H4)) - 1ull;
+    uint64_t raw = 0;  // digits of T[p0 + r + j], j < H4, as (symbol - 1) & 3
+#pragma unroll
+    for (int j = 0; j < H4; ++j) raw = (raw << 2) | (((w[j >> 2] >> (8 * (j & 3))) - 1u) & 3u);
+    uint64_t kk[K4_PER];
+#pragma unroll
+    for (int r = 0; r < K4_PER; ++r) {
+        const uint32_t zr = z >> r;
+        const uint32_t len = zr ? min((uint32_t)H4, (uint32_t)(__ffs(zr) - 1)) : (uint32_t)H4;
+        const int drop = 2 * (H4 - (int)len);  // digits at and after the first sentinel are zero
+        kk[r] = (((raw >> drop) << drop) << 5) | len;
+        if (r + 1 < K4_PER) {
+            const int b = r + H4;
+            raw = ((raw << 2) | (((w[b >> 2] >> (8 * (b & 3))) - 1u) & 3u)) & M34;
+        }
+    }
+    if (p0 + K4_PER <= n) {
+        ulonglong2 *ko = reinterpret_cast<ulonglong2 *>(key + p0);
+#pragma unroll
+        for (int r = 0; r < K4_PER; r += 2) ko[r / 2] = make_ulonglong2(kk[r], kk[r + 1]);
+        uint4 *vo = reinterpret_cast<uint4 *>(val + p0);
+#pragma unroll
+        for (int r = 0; r < K4_PER; r += 4)
+            vo[r / 4] = make_uint4((uint32_t)(p0 + r), (uint32_t)(p0 + r + 1), (uint32_t)(p0 + r + 2),
+                                   (uint32_t)(p0 + r + 3));
+    } else {
+#pragma unroll
+        for (int r = 0; r < K4_PER; ++r)
+            if (p0 + r < n) {
+                key[p0 + r] = kk[r];
+                val[p0 + r] = (uint32_t)(p0 + r);
+            }
+    }
 }
 
 // A group starts at i if its key differs from the previous one, or if its
@@ -590,7 +632,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             {
                 Phase pk("k.init_keys", st, 13.0 * n);  // 1 text byte in, 8-byte key + 4-byte value out
                 if (has_n) RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, ka, va);
-                else RB3_LAUNCH(k_init_keys4, nb_for(n, 256), 256, 0, st, T, n, ka, va);
+                else RB3_LAUNCH(k_init_keys4, nb_for((n + K4_PER - 1) / K4_PER, 256), 256, 0, st, T, n, ka, va);
             }
             bool alt = false;
             RB3_TRY(radix_sort_pairs(ka, va, kb, vb, n, 0, has_n ? H0_BITS : H4_BITS, st, &alt));
