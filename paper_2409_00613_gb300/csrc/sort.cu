@@ -71,9 +71,93 @@ __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int6
     }
 }
 
+// Vector forms for 16-byte-aligned uint32 arrays, same tiles: the reduce reads
+// each tile as 16-byte words (order does not matter for + and max); the apply
+// gives thread t elements [8t, 8t + 8) of its tile straight from two 16-byte
+// loads and writes them back the same way, without staging in shared memory.
+__global__ void k_scan_reduce_v(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ part, int op) {
+    __shared__ uint32_t wtot[32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE;
+    uint32_t acc = 0;
+    if (base + SC_TILE <= n) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(in + base);
+#pragma unroll
+        for (int j = 0; j < SC_ITEMS / 4; ++j) {
+            const uint4 x = __ldg(v + threadIdx.x + j * SC_THREADS);
+            acc = op2(op2(acc, x.x, op), op2(op2(x.y, x.z, op), x.w, op), op);
+        }
+    } else {
+        for (int i = threadIdx.x; i < SC_TILE; i += SC_THREADS)
+            if (base + i < n) acc = op2(acc, in[base + i], op);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t inc = warp_incl(acc, op);
+    if (lane == 31) wtot[w] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int j = 0; j < SC_THREADS / 32; ++j) t = op2(t, wtot[j], op);
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_scan_apply_v(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                               const uint32_t *__restrict__ part, int inclusive, int op) {
+    __shared__ uint32_t wtot[32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    const bool full = base + SC_ITEMS <= n;
+    if (full) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(in + base));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(in + base) + 1);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < SC_ITEMS; ++j) v[j] = base + j < n ? in[base + j] : 0u;
+    }
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) run = op2(run, v[j], op);
+    const uint32_t ex = block_excl(run, op, wtot);
+    uint32_t acc = op2(part ? part[blockIdx.x] : 0u, ex, op);
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        const uint32_t x = v[j];
+        if (inclusive) {
+            acc = op2(acc, x, op);
+            v[j] = acc;
+        } else {
+            v[j] = acc;
+            acc = op2(acc, x, op);
+        }
+    }
+    if (full) {
+        uint4 *o = reinterpret_cast<uint4 *>(out + base);
+        o[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        o[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SC_ITEMS; ++j)
+            if (base + j < n) out[base + j] = v[j];
+    }
+}
+
 template <class T> static int scan_impl(const T *in, T *out, int64_t n, bool inclusive, int op, cudaStream_t st) {
     if (n <= 0) return RB3_OK;
     int64_t ntiles = (n + SC_TILE - 1) / SC_TILE;
+    if constexpr (sizeof(T) == 4) {
+        if (ntiles > 1 && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0) {
+            DevBuf part;
+            RB3_TRY(part.alloc(sizeof(T) * ntiles, st));
+            const uint32_t *vin = reinterpret_cast<const uint32_t *>(in);
+            uint32_t *vout = reinterpret_cast<uint32_t *>(out), *vp = part.as<uint32_t>();
+            RB3_LAUNCH(k_scan_reduce_v, (unsigned)ntiles, SC_THREADS, 0, st, vin, n, vp, op);
+            RB3_TRY(scan_impl<T>(part.as<T>(), part.as<T>(), ntiles, false, op, st));
+            RB3_LAUNCH(k_scan_apply_v, (unsigned)ntiles, SC_THREADS, 0, st, vin, vout, n, (const uint32_t *)vp,
+                       (int)inclusive, op);
+            return RB3_OK;
+        }
+    }
     if (ntiles == 1) {
         RB3_LAUNCH(k_scan_apply<T>, 1, SC_THREADS, 0, st, in, out, n, (const T *)nullptr, (int)inclusive, op);
         return RB3_OK;
