@@ -175,40 +175,95 @@ __global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__r
     hv[i] = head ? (uint32_t)i : 0u;
 }
 
-// rank[SA[i]] = start of i's group; flags route entries of groups of 2..SMALL_MAX
-// (fs) and of larger groups (fl).  A group starting at g has more than SMALL_MAX
-// members iff the entry SMALL_MAX places after g still has group start g.
-__global__ void k_init_rank_flags(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart, int64_t n,
-                                  int32_t *__restrict__ rank, uint32_t *__restrict__ fs, uint32_t *__restrict__ fl,
-                                  uint32_t *__restrict__ gsize) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t g = gstart[i];
-    const bool last = i + 1 == n || gstart[i + 1] != g;
-    bool single = g == (uint32_t)i && last;
-    bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
-    // members of small groups get their rank from k_expand_groups, in locus order
-    if (single || large) rank[SA[i]] = (int32_t)g;
-    fs[i] = (g == (uint32_t)i && !single && !large) ? 1u : 0u;  // head of a group of 2..SMALL_MAX
-    fl[i] = large ? 1u : 0u;
-    if (last && !single && !large) gsize[g] = (uint32_t)(i - g + 1);  // a small group's size, at its head
+// Round-0 groups, a tile of IG_TILE entries per block.  Singletons and the
+// members of groups above SMALL_MAX get their rank now (members of smaller
+// groups get theirs from k_expand_groups, in locus order); a small group's size
+// is kept at its head.  The head of each group of 2..SMALL_MAX is listed as
+// (its SA value, its index) and every member of a larger group as (its SA
+// value, its group start), each list filled through one counter per tile:
+// their order does not matter (the head list is sorted by SA value next, the
+// large list by (group, key) in every round).  The groups of 2..SMALL_MAX are
+// then laid out in the order of their first member's text position (the
+// stable sort keeps members in position order, so that is the head's SA
+// value): a pangenome's groups are mostly homologous copies of one locus, so
+// neighbouring groups are neighbouring loci and the rank[p + h] reads and rank
+// writes of a round touch nearby addresses.
+constexpr int IG_ITEMS = 8;
+constexpr int IG_THREADS = 256;
+constexpr int IG_TILE = IG_THREADS * IG_ITEMS;
+constexpr int IG_WARPS = IG_THREADS / 32;
+static_assert(IG_ITEMS * IG_WARPS == 64, "one warp scans two counts per lane");
+
+__global__ void __launch_bounds__(IG_THREADS) k_init_groups(const uint32_t *__restrict__ SA,
+                                                            const uint32_t *__restrict__ gstart, int64_t n,
+                                                            int32_t *__restrict__ rank, uint32_t *__restrict__ gsize,
+                                                            uint32_t *__restrict__ cnt, uint32_t *__restrict__ hkey,
+                                                            uint32_t *__restrict__ hval, uint32_t *__restrict__ lp,
+                                                            uint32_t *__restrict__ lg) {
+    __shared__ uint32_t wc[2][IG_ITEMS * IG_WARPS];  // per (list, pass, warp): counts, then offsets
+    __shared__ uint32_t tb[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * IG_TILE;
+    uint32_t sv[IG_ITEMS], gv[IG_ITEMS];
+    unsigned hm = 0, lm = 0;  // bit j: entry j heads a small group / is a member of a large one
+#pragma unroll
+    for (int j = 0; j < IG_ITEMS; ++j) {
+        const int64_t i = t0 + j * IG_THREADS + threadIdx.x;
+        bool hd = false, lgm = false;
+        sv[j] = gv[j] = 0;
+        if (i < n) {
+            const uint32_t g = gstart[i], s = SA[i];
+            const bool last = i + 1 == n || gstart[i + 1] != g;
+            const bool single = g == (uint32_t)i && last;
+            const bool large = (int64_t)g + SMALL_MAX < n && gstart[g + SMALL_MAX] == g;
+            if (single || large) rank[s] = (int32_t)g;
+            if (last && !single && !large) gsize[g] = (uint32_t)(i - g + 1);
+            hd = g == (uint32_t)i && !single && !large;
+            lgm = large;
+            sv[j] = s;
+            gv[j] = g;
+        }
+        const unsigned hb = __ballot_sync(0xFFFFFFFFu, hd), lb = __ballot_sync(0xFFFFFFFFu, lgm);
+        if (lane == 0) {
+            wc[0][j * IG_WARPS + w] = __popc(hb);
+            wc[1][j * IG_WARPS + w] = __popc(lb);
+        }
+        hm |= (unsigned)hd << j;
+        lm |= (unsigned)lgm << j;
+    }
+    __syncthreads();
+    if (w < 2) {  // warp L: exclusive offsets of list L in (pass, warp) order, and the tile's place in it
+        uint32_t *c = wc[w];
+        const uint32_t c0 = c[2 * lane], c1 = c[2 * lane + 1];
+        const uint32_t inc = warp_incl(c0 + c1, 0);
+        const uint32_t ex = inc - c0 - c1;
+        c[2 * lane] = ex;
+        c[2 * lane + 1] = ex + c0;
+        uint32_t base = 0;
+        if (lane == 31 && inc) base = atomicAdd(&cnt[w], inc);
+        if (lane == 31) tb[w] = base;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < IG_ITEMS; ++j) {
+        const int64_t i = t0 + j * IG_THREADS + threadIdx.x;
+        const bool hd = (hm >> j) & 1u, lgm = (lm >> j) & 1u;
+        const unsigned hb = __ballot_sync(0xFFFFFFFFu, hd), lb = __ballot_sync(0xFFFFFFFFu, lgm);
+        if (hd) {
+            const uint32_t o = tb[0] + wc[0][j * IG_WARPS + w] + __popc(hb & lt);
+            hkey[o] = sv[j];
+            hval[o] = (uint32_t)i;
+        }
+        if (lgm) {
+            const uint32_t o = tb[1] + wc[1][j * IG_WARPS + w] + __popc(lb & lt);
+            lp[o] = sv[j];
+            lg[o] = gv[j];
+        }
+    }
 }
 
-// The groups of 2..SMALL_MAX members are listed in the order of their first
-// member's text position (the stable sort keeps members in position order, so
-// that is the head's SA value).  A pangenome's groups are mostly homologous
-// copies of one locus, so neighbouring groups are neighbouring loci and the
-// rank[p + h] reads and rank writes of a round touch nearby addresses.
-__global__ void k_head_pairs(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ fs,
-                             const uint32_t *__restrict__ ps, int64_t n, uint32_t *__restrict__ hkey,
-                             uint32_t *__restrict__ hval) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n || !fs[i]) return;
-    hkey[ps[i]] = SA[i];
-    hval[ps[i]] = (uint32_t)i;
-}
-
-// Small group j in locus order: its size, kept at its head by k_init_rank_flags.
+// Small group j in locus order: its size, kept at its head by k_init_groups.
 __global__ void k_group_sizes(const uint32_t *__restrict__ hval, int64_t G, const uint32_t *__restrict__ gsize,
                               uint32_t *__restrict__ gsz) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -246,19 +301,6 @@ __global__ void k_expand_groups(const uint32_t *__restrict__ hval, const uint32_
             sg[x] = hg;
             rank[p] = (int32_t)hg;
         }
-    }
-}
-
-__global__ void k_init_lists(const uint32_t *__restrict__ SA, const uint32_t *__restrict__ gstart,
-                             const uint32_t *__restrict__ fs, const uint32_t *__restrict__ fl,
-                             const uint32_t *__restrict__ ps, const uint32_t *__restrict__ pl, int64_t n,
-                             uint32_t *__restrict__ sp, uint32_t *__restrict__ sg, uint32_t *__restrict__ lp,
-                             uint32_t *__restrict__ lg) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (fl[i]) {
-        lp[pl[i]] = SA[i];
-        lg[pl[i]] = gstart[i];
     }
 }
 
@@ -639,7 +681,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             const uint64_t *K = alt ? kb : ka;
             if ((alt ? vb : va) != v0)
                 RB3_CUDA_TRY(cudaMemcpyAsync(SA, alt ? vb : va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-            DevBuf hv, fs, fl, ps, pl;
+            DevBuf hv;
             RB3_TRY(hv.alloc(sizeof(uint32_t) * n, st));
             if (has_n) RB3_LAUNCH(k_heads<false>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
             else RB3_LAUNCH(k_heads<true>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
@@ -647,31 +689,31 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             k0.release();
             k1.release();
             v1.release();
-            RB3_TRY(fs.alloc(sizeof(uint32_t) * n, st));
-            RB3_TRY(fl.alloc(sizeof(uint32_t) * n, st));
-            RB3_TRY(ps.alloc(sizeof(uint32_t) * n, st));
-            RB3_TRY(pl.alloc(sizeof(uint32_t) * n, st));
-            RB3_LAUNCH(k_init_rank_flags, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA),
-                       hv.as<uint32_t>(), n, rank, fs.as<uint32_t>(), fl.as<uint32_t>(), gsize);
-            RB3_TRY(scan_u32(fs.as<uint32_t>(), ps.as<uint32_t>(), n, false, 0, st));
-            RB3_TRY(scan_u32(fl.as<uint32_t>(), pl.as<uint32_t>(), n, false, 0, st));
-            RB3_LAUNCH(k_tally, 1, 1, 0, st, ps.as<uint32_t>(), fs.as<uint32_t>(), n, d_cnt, 0);
-            RB3_LAUNCH(k_tally, 1, 1, 0, st, pl.as<uint32_t>(), fl.as<uint32_t>(), n, d_cnt + 1, 0);
+            // the head list holds at most n / 2 groups; the large list at most n entries
+            const int64_t hcap = n / 2 + 2;
+            DevBuf hk0, hk1, hv0, hv1, gsz, goff;
+            RB3_TRY(hk0.alloc(sizeof(uint32_t) * hcap, st));
+            RB3_TRY(hv0.alloc(sizeof(uint32_t) * hcap, st));
+            RB3_TRY(lp.alloc(sizeof(uint32_t) * (n + 1), st));
+            RB3_TRY(lg.alloc(sizeof(uint32_t) * (n + 1), st));
+            RB3_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(uint32_t) * 2, st));
+            RB3_LAUNCH(k_init_groups, nb_for((n + IG_TILE - 1) / IG_TILE, 1), IG_THREADS, 0, st,
+                       reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(), n, rank, gsize, d_cnt, hk0.as<uint32_t>(),
+                       hv0.as<uint32_t>(), lp.as<uint32_t>(), lg.as<uint32_t>());
             uint32_t hc[2];
             RB3_CUDA_TRY(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
             const int64_t G = hc[0];  // groups of 2..SMALL_MAX
             NL = hc[1];
+            if (G >= hcap || NL > n) {
+                set_error("round 0: group lists overflow (%lld heads, %lld large)", (long long)G, (long long)NL);
+                return RB3_E_CUDA;
+            }
             // small groups in order of their first member's text position
-            DevBuf hk0, hk1, hv0, hv1, gsz, goff;
-            RB3_TRY(hk0.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(hk1.alloc(sizeof(uint32_t) * (G + 1), st));
-            RB3_TRY(hv0.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(hv1.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(gsz.alloc(sizeof(uint32_t) * (G + 1), st));
             RB3_TRY(goff.alloc(sizeof(uint32_t) * (G + 1), st));
-            RB3_LAUNCH(k_head_pairs, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), fs.as<uint32_t>(),
-                       ps.as<uint32_t>(), n, hk0.as<uint32_t>(), hv0.as<uint32_t>());
             bool halt = false;
             RB3_TRY(radix_sort_pairs32(hk0.as<uint32_t>(), hv0.as<uint32_t>(), hk1.as<uint32_t>(), hv1.as<uint32_t>(),
                                        G, 0, ilog2(n) + 1, st, &halt));
@@ -689,14 +731,9 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             RB3_TRY(sg2.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
             RB3_TRY(tp.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
             RB3_TRY(tg.alloc(sizeof(uint32_t) * (NS + NL + 1), st));
-            RB3_TRY(lp.alloc(sizeof(uint32_t) * (NL + 1), st));
-            RB3_TRY(lg.alloc(sizeof(uint32_t) * (NL + 1), st));
             if (G > 0)
                 RB3_LAUNCH(k_expand_groups, nb_for(G, 256), 256, 0, st, hval, gsz.as<uint32_t>(), goff.as<uint32_t>(),
                            G, reinterpret_cast<uint32_t *>(SA), sp.as<uint32_t>(), sg.as<uint32_t>(), rank);
-            RB3_LAUNCH(k_init_lists, nb_for(n, 256), 256, 0, st, reinterpret_cast<uint32_t *>(SA), hv.as<uint32_t>(),
-                       fs.as<uint32_t>(), fl.as<uint32_t>(), ps.as<uint32_t>(), pl.as<uint32_t>(), n,
-                       sp.as<uint32_t>(), sg.as<uint32_t>(), lp.as<uint32_t>(), lg.as<uint32_t>());
         }
         // ---- S1 doubling rounds ----
         const int64_t capS = NS + NL + 1;
