@@ -53,11 +53,12 @@ int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int6
     const bool seq_dev = off[n_seq] == 0 || is_device_ptr(seq);
     cudaStream_t sb = nullptr, sm = nullptr;
     cudaEvent_t start = nullptr;
-    // merges first: the build's CTAs fill what the merge leaves free (its walk's tail)
+    // builds first: the merge walk's long chains fill what the next batch's
+    // build leaves free (measured 2-3 % faster than the merge first)
     int prio_low = 0, prio_high = 0;
     RB3_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
-    RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sb, cudaStreamNonBlocking, prio_low));
-    RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sm, cudaStreamNonBlocking, prio_high));
+    RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sb, cudaStreamNonBlocking, prio_high));
+    RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sm, cudaStreamNonBlocking, prio_low));
     RB3_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     // both internal streams start after the work already on the caller's stream
     RB3_CUDA_TRY(cudaEventRecord(start, caller));
