@@ -196,6 +196,18 @@ def run_rb3(args, rank, world, local_rank):
     step_host.numpy()[:] = step_seq
     new_syms = int(sum(ds[b] for b in step_batch))
 
+    # ---- device memory of one batch build (peak of the library's allocations, untimed) ----
+    torch.cuda.synchronize()
+    base_mem = rb.rb3_device_peak(reset=True)
+    probe = rb.rb3_build_batch(dev_batches[1][0], dev_batches[1][1], opts=opts, stream=st)
+    torch.cuda.synchronize()
+    peak_mem = rb.rb3_device_peak()
+    probe_bytes = rb.rb3_index_bytes(probe)["device_bytes"]
+    probe.free()
+    memory = {"batch_symbols": ds[1], "build_peak_bytes_per_symbol": round((peak_mem - base_mem) / ds[1], 1),
+              "index_bytes_per_symbol": round(probe_bytes / ds[1], 3),
+              "what": "peak of the library's device allocations during one batch build, above what was in use "
+                      "before it, per indexed symbol; the batch's index itself (D = 32)"}
     # ---- autotune the merge's segment length on batch 1 into batch 0 (untimed) ----
     idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
     tune = {}
@@ -302,7 +314,7 @@ def run_rb3(args, rank, world, local_rank):
                       "l2": "inputs larger than L2 (batch ~100 Msym text + 100-500 MB index per step)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases,
-           "autotune": tune,
+           "autotune": tune, "memory": memory,
            "one_by_one": {"ms_per_step": round(seq_ms / args.steps, 3),
                           "value": round(new_syms / (seq_ms * 1e3), 3), "unit": "Msym/s",
                           "equal_output": same,

@@ -86,8 +86,16 @@ typedef struct {
     int32_t sa_sample;     /* build: keep a sampled suffix array for rb3_locate: every suffix starting at
                               an offset of its string that is a multiple of sa_sample (a power of two,
                               2..1024; 0 = none).  A merge keeps it when both inputs have the same rate. */
-    int32_t reserved[6];
+    int32_t batch_mb;      /* append: device-memory budget of one batch build, MiB (0 = none).  Each caller
+                              batch is cut into runs of whole strings whose build footprint (estimated at
+                              RB3_BUILD_BYTES_PER_SYMBOL per indexed symbol) fits it; a string that alone
+                              exceeds it is built by itself.  Results do not depend on the cut. */
+    int32_t reserved[5];
 } rb3_opts;
+
+/* Device bytes a batch build holds at its peak per indexed symbol (both strands
+ * count), as measured with rb3_device_peak on the pangenome workload, rounded up. */
+#define RB3_BUILD_BYTES_PER_SYMBOL 64
 
 /* One SMEM: query qid, query interval [start, end), and the SA bi-interval
  * (k, k', s) = (lo(X), lo(rc X), occ(X)) of X = query[start, end)
@@ -279,6 +287,11 @@ int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_ind
  * sampled suffix array; build data not counted) and its number of runs (-1
  * for a plain index).  Either pointer may be NULL. */
 int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs);
+
+/* The high-water mark of device memory in use by this library's stream-ordered
+ * allocations (the device's default memory pool) since the last reset, in
+ * bytes; reset != 0 sets it back to the memory in use now.  Host-side query. */
+int rb3_device_peak(int64_t *used_high, int32_t reset);
 
 /* Frees the batch text and inverse suffix array kept by rb3_build_batch. */
 int rb3_drop_build_data(rb3_index *idx);

@@ -275,6 +275,24 @@ static int check_qoff(const std::vector<int64_t> &qo) {
 using namespace rb3;
 
 // ---------------------------------------------------------------------------
+RB3_EXPORT int rb3_device_peak(int64_t *used_high, int32_t reset) {
+    g_err.clear();
+    RB3_CHECK_ARG(used_high != nullptr, "NULL argument");
+    ensure_pool();
+    int dev = 0;
+    RB3_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    RB3_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t v = 0;
+    RB3_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
+    *used_high = (int64_t)v;
+    if (reset) {
+        uint64_t zero = 0;  // resets the mark to the memory in use now
+        RB3_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return RB3_OK;
+}
+
 RB3_EXPORT void rb3_opts_default(rb3_opts *o) {
     if (o) memset(o, 0, sizeof(*o));
 }

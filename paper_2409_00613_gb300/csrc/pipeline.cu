@@ -189,6 +189,27 @@ RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int6
         total += lens[i];
     }
     RB3_CHECK_ARG(total == 0 || seq != nullptr, "seq is NULL");
+    RB3_CHECK_ARG(opts.batch_mb >= 0, "batch_mb < 0");
+    if (opts.batch_mb > 0) {  // cut each batch into runs of whole strings that fit the budget
+        const int64_t budget = (int64_t)opts.batch_mb << 20, mult = opts.single_strand ? 1 : 2;
+        std::vector<int64_t> cut;
+        int64_t s0 = 0;
+        for (int64_t b = 0; b < n_batches; ++b) {
+            int64_t acc = 0;
+            for (int64_t i = s0; i < ends[b]; ++i) {
+                const int64_t sym = mult * (lens[i] + 1);
+                if (acc > 0 && (acc + sym) * RB3_BUILD_BYTES_PER_SYMBOL > budget) {
+                    cut.push_back(i);
+                    acc = 0;
+                }
+                acc += sym;
+            }
+            if (cut.empty() || cut.back() != ends[b]) cut.push_back(ends[b]);
+            s0 = ends[b];
+        }
+        ends.swap(cut);
+        n_batches = (int64_t)ends.size();
+    }
     if (dst->rle) {  // appended to a plain copy, re-encoded once at the end
         rb3_index *P = nullptr;
         RB3_TRY(rle_plain_copy(dst, st, &P));

@@ -28,7 +28,7 @@ class rb3_opts(ctypes.Structure):
                 ("seg_len", ctypes.c_int64), ("seed_cap", ctypes.c_int64),
                 ("merge_form", ctypes.c_int32), ("search_form", ctypes.c_int32),
                 ("chunk_len", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
-                ("sa_sample", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("sa_sample", ctypes.c_int32), ("batch_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class rb3_server_opts(ctypes.Structure):
@@ -77,6 +77,7 @@ def lib():
             "rb3_drop_build_data": (ctypes.c_int, [_vp]),
             "rb3_index_compress": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+            "rb3_device_peak": (ctypes.c_int, [ctypes.POINTER(_i64), _i32]),
             "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_free": (None, [_vp]),
@@ -297,6 +298,13 @@ def rb3_index_compress(idx: Index, span: int = 0, stream=None) -> Index:
     out = _vp()
     _check(lib().rb3_index_compress(idx.handle, span, _stream(stream), ctypes.byref(out)))
     return Index(out.value)
+
+
+def rb3_device_peak(reset: bool = False) -> int:
+    """High-water mark (bytes) of the library's device allocations since the last reset."""
+    v = _i64()
+    _check(lib().rb3_device_peak(ctypes.byref(v), int(reset)))
+    return v.value
 
 
 def rb3_index_bytes(idx: Index) -> dict:

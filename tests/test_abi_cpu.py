@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts_match_header():
-    assert ctypes.sizeof(rb.rb3_opts) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 32
+    assert ctypes.sizeof(rb.rb3_opts) == 4 + 4 + 8 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 * 5
     assert rb.SMEM_DTYPE.itemsize == 40
 
 

@@ -281,6 +281,29 @@ def test_append_batches_pipeline():
     check_index(idx, want)
 
 
+def test_append_batch_memory_budget():
+    """batch_mb cuts each caller batch into runs of whole strings that fit the
+    budget: the same BWT (against the oracle), a lower device-memory peak."""
+    S = synth.pangenome(seed=91, founder_len=20_000, n_hap=8, batch=4)
+    B = ref_bwt(S)
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    seq = torch.from_numpy(S.seq.copy()).to(DEV)
+    peaks = []
+    for mb in (0, 1):
+        idx = rb.rb3_index_empty()
+        torch.cuda.synchronize()
+        rb.rb3_device_peak(reset=True)
+        rb.rb3_append_batches(idx, seq, S.lens.copy(), ends, {"batch_mb": mb})
+        torch.cuda.synchronize()
+        peaks.append(rb.rb3_device_peak())
+        check_index(idx, B)
+        idx.free()
+    assert peaks[1] < peaks[0], peaks
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_append_batches(rb.rb3_index_empty(), seq, S.lens.copy(), ends, {"batch_mb": -1})
+    assert e.value.code == rb.RB3_E_INVAL
+
+
 def test_append_batches_error_propagates():
     S = synth.pangenome(seed=72, founder_len=5_000, n_hap=6, batch=2)
     seq = S.seq.copy()
