@@ -288,6 +288,13 @@ int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_ind
  * for a plain index).  Either pointer may be NULL. */
 int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs);
 
+/* Self-test of the bounded device-side waits (the radix sort's look-back wait,
+ * the same device function): one thread waits on a flag that nothing sets,
+ * for `limit` polls (1..2^20, about 0.1 us each), then records the time-out
+ * and returns.  Returns RB3_E_TIMEOUT, the status a real wait that gave up
+ * reports; the context stays usable.  Synchronizes the stream. */
+int rb3_selftest_wait(int32_t limit, void *stream);
+
 /* The high-water mark of device memory in use by this library's stream-ordered
  * allocations (the device's default memory pool) since the last reset, in
  * bytes; reset != 0 sets it back to the memory in use now.  Host-side query. */

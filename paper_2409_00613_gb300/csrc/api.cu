@@ -275,6 +275,12 @@ static int check_qoff(const std::vector<int64_t> &qo) {
 using namespace rb3;
 
 // ---------------------------------------------------------------------------
+RB3_EXPORT int rb3_selftest_wait(int32_t limit, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(limit >= 1 && limit <= (1 << 20), "limit must be in [1, 2^20]");
+    return wait_selftest(limit, (cudaStream_t)stream);
+}
+
 RB3_EXPORT int rb3_device_peak(int64_t *used_high, int32_t reset) {
     g_err.clear();
     RB3_CHECK_ARG(used_high != nullptr, "NULL argument");

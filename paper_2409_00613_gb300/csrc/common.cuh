@@ -800,6 +800,7 @@ int radix_sort_pairs32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, i
 int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n_seq, const rb3_opts &o,
                      cudaStream_t st, rb3_index *out);
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
+int wait_selftest(int limit, cudaStream_t st);
 int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos);
 // Autotuner memory (tune.cu): 0 when nothing was tuned for this input shape.
 int64_t tuned_seg_len(const rb3_index *dst, const rb3_index *src);

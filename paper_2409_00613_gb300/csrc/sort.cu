@@ -282,6 +282,29 @@ __device__ __forceinline__ uint64_t rs_flag_load(const uint64_t *p) {
     return v;
 }
 
+// Bounded wait for a tile's look-back flag: polls until its status bits are
+// set or `limit` polls have passed; a time-out is recorded in err (read by the
+// host after the launch, reported as RB3_E_TIMEOUT) and an empty inclusive
+// flag is returned, so the tile finishes and the context stays usable.
+__device__ __forceinline__ uint64_t rs_wait_flag(const uint64_t *G, int limit, unsigned int *err) {
+    uint64_t v = rs_flag_load(G);
+    int spins = 0;
+    while ((v >> 62) == 0) {
+        if (++spins > limit) {
+            atomicOr(err, 1u);
+            return RS_INC;
+        }
+        __nanosleep(32);
+        v = rs_flag_load(G);
+    }
+    return v;
+}
+
+// Self-test of the bounded wait: one thread waits on a flag that nothing sets.
+__global__ void k_wait_selftest(const uint64_t *flag, int limit, unsigned int *err) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) rs_wait_flag(flag, limit, err);
+}
+
 template <class K, bool ALIAS> struct RsStage {
     K k[RS_TILE];
     uint32_t v[RS_TILE];
@@ -360,18 +383,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_MINB) k_rs_onesweep(const K *__
     } else {
         rs_flag_store(F, RS_AGG | tot);
         for (int64_t tt = t - 1; tt >= 0; --tt) {
-            const uint64_t *G = flags + tt * RS_BINS + d;
-            uint64_t v = rs_flag_load(G);
-            int spins = 0;
-            while ((v >> 62) == 0) {
-                if (++spins > RS_SPIN_LIMIT) {  // recorded; the result is then invalid
-                    atomicOr(err, 1u);
-                    v = RS_INC;
-                    break;
-                }
-                __nanosleep(32);
-                v = rs_flag_load(G);
-            }
+            const uint64_t v = rs_wait_flag(flags + tt * RS_BINS + d, RS_SPIN_LIMIT, err);
             excl += v & RS_VAL;
             if ((v >> 62) == 2) break;
         }
@@ -507,6 +519,22 @@ int radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int
 int radix_sort_pairs32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int begin_bit, int end_bit,
                        cudaStream_t st, bool *in_alt) {
     return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, begin_bit, end_bit, st, in_alt);
+}
+
+int wait_selftest(int limit, cudaStream_t st) {
+    DevBuf buf;
+    RB3_TRY(buf.alloc(16, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(buf.p, 0, 16, st));
+    unsigned int *err = reinterpret_cast<unsigned int *>(buf.as<uint8_t>() + 8);
+    RB3_LAUNCH(k_wait_selftest, 1, 32, 0, st, buf.as<uint64_t>(), limit, err);
+    unsigned int h = 0;
+    RB3_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("bounded wait gave up after %d polls (self-test: nothing sets the flag)", limit);
+        return RB3_E_TIMEOUT;
+    }
+    return RB3_OK;
 }
 
 }  // namespace rb3

@@ -78,6 +78,7 @@ def lib():
             "rb3_index_compress": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "rb3_device_peak": (ctypes.c_int, [ctypes.POINTER(_i64), _i32]),
+            "rb3_selftest_wait": (ctypes.c_int, [_i32, _vp]),
             "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_free": (None, [_vp]),
@@ -298,6 +299,11 @@ def rb3_index_compress(idx: Index, span: int = 0, stream=None) -> Index:
     out = _vp()
     _check(lib().rb3_index_compress(idx.handle, span, _stream(stream), ctypes.byref(out)))
     return Index(out.value)
+
+
+def rb3_selftest_wait(limit: int, stream=None):
+    """Runs the bounded-wait self-test; raises RB3Error (RB3_E_TIMEOUT) as designed."""
+    _check(lib().rb3_selftest_wait(int(limit), _stream(stream)))
 
 
 def rb3_device_peak(reset: bool = False) -> int:

@@ -281,6 +281,24 @@ def test_append_batches_pipeline():
     check_index(idx, want)
 
 
+def test_bounded_wait_times_out_and_context_survives():
+    """The look-back wait of the radix passes, run by the self-test on a flag
+    that nothing sets, gives up after its limit and reports RB3_E_TIMEOUT; the
+    context stays usable (a build afterwards matches the oracle)."""
+    import time
+    t0 = time.time()
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_selftest_wait(1 << 16)
+    assert e.value.code == rb.RB3_E_TIMEOUT
+    assert time.time() - t0 < 30
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_selftest_wait(0)
+    assert e.value.code == rb.RB3_E_INVAL
+    g = synth.rng(55)
+    S = synth.random_strings(g, 20, 400, n_frac=0.0)
+    check_index(build(S), ref_bwt(S))
+
+
 def test_append_batch_memory_budget():
     """batch_mb cuts each caller batch into runs of whole strings that fit the
     budget: the same BWT (against the oracle), a lower device-memory peak."""
