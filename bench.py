@@ -233,6 +233,7 @@ def run_rb3(args, rank, world, local_rank):
     barrier()
     rb.rb3_profile_reset()
     rb.rb3_profile_enable(True)
+    rb.rb3_walk_stats(reset=True)
     clocks = ClockSampler(bus_id(torch, local_rank))
     clocks.start()
     launches0 = rb.rb3_launch_count()
@@ -248,6 +249,7 @@ def run_rb3(args, rank, world, local_rank):
     clk = clocks.stop()
     rb.rb3_profile_enable(False)
     prof = rb.rb3_profile_read()
+    wstats = rb.rb3_walk_stats()
     info = rb.rb3_index_info(idx)
     if world > 1:
         import torch.distributed as dist
@@ -303,6 +305,21 @@ def run_rb3(args, rank, world, local_rank):
                 "traffic": NCU_TRAFFIC.get((top, info["occ_interval"], founder)),
                 "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),
                 "launches": kcalls, "share_of_step": round(kms / ms, 4)}
+        if top == "k.merge_walk" and info["occ_interval"] == 32:
+            # the walk against the random-request roofline: every rank read is one
+            # 32-byte request at D = 32, every walk step also writes pos; the
+            # ceiling is the probe's dependent-chain random reads on this GPU
+            req = wstats["seed_block_reads"] + 2 * wstats["walk_block_reads"]
+            _, probe_m = rb.rb3_probe_random_gather(32, 1, 2048, 8 << 30, stream=st)
+            per_s = req / (kms * 1e-3)
+            roof["random_requests"] = {
+                "per_launch": req / max(1, kcalls), "G_per_s": round(per_s / 1e9, 2),
+                "probe_G_per_s": round(probe_m / 1e3, 2), "frac": round(per_s / (probe_m * 1e6), 3),
+                "seeds": wstats["seeds"], "seed_block_reads": wstats["seed_block_reads"],
+                "walk_block_reads": wstats["walk_block_reads"], "taken_over": wstats["taken_over"],
+                "what": "rank block reads of the seeds and walk steps plus the walk's pos writes, counted by "
+                        "the kernel, over its CUDA-event time; ceiling: rb3_probe_random_gather, 32-byte "
+                        "dependent random reads, 2048 threads per SM, 8 GiB buffer"}
     phases = {k: round(v[0], 3) for k, v in sorted(prof.items())}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": "Msym/s", "n_gpus": world, "steps": args.steps,

@@ -288,6 +288,15 @@ int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_ind
  * for a plain index).  Either pointer may be NULL. */
 int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs);
 
+/* Counts of the segmented merge walks (Algorithm 1 with ForwardExt seeds)
+ * since the last reset, added up by the walks as they finish: out[0] seeds
+ * run, out[1] Occ block reads of the seeds (one per ForwardExt whose two ends
+ * share a block, else two), out[2] block reads of the walk steps (one per new
+ * symbol), out[3] segments taken over from above.  At D = 32 a block read is
+ * one 32-byte memory request.  reset != 0 zeroes them after the read.
+ * Synchronizes the device. */
+int rb3_walk_stats(int64_t *out, int32_t reset);
+
 /* Self-test of the bounded device-side waits (the radix sort's look-back wait,
  * the same device function): one thread waits on a flag that nothing sets,
  * for `limit` polls (1..2^20, about 0.1 us each), then records the time-out

@@ -275,6 +275,12 @@ static int check_qoff(const std::vector<int64_t> &qo) {
 using namespace rb3;
 
 // ---------------------------------------------------------------------------
+RB3_EXPORT int rb3_walk_stats(int64_t *out, int32_t reset) {
+    g_err.clear();
+    RB3_CHECK_ARG(out != nullptr, "NULL argument");
+    return walk_stats(out, reset != 0);
+}
+
 RB3_EXPORT int rb3_selftest_wait(int32_t limit, void *stream) {
     g_err.clear();
     RB3_CHECK_ARG(limit >= 1 && limit <= (1 << 20), "limit must be in [1, 2^20]");

@@ -801,6 +801,7 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n
                      cudaStream_t st, rb3_index *out);
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
 int wait_selftest(int limit, cudaStream_t st);
+int walk_stats(int64_t out[4], bool reset);
 int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos);
 // Autotuner memory (tune.cu): 0 when nothing was tuned for this input shape.
 int64_t tuned_seg_len(const rb3_index *dst, const rb3_index *src);

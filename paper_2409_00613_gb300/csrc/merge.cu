@@ -23,6 +23,7 @@
 //                 homologous segments of the batch's strings run together and
 //                 share B1 blocks in L2.
 #include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
 
 #include "common.cuh"
 
@@ -72,17 +73,27 @@ __device__ __forceinline__ int load_state(const int *p) { return *reinterpret_ca
 // the B1 suffixes below X), or to X's sentinel (l = k + occ(Q$): the B1
 // suffixes equal to Q up to a sentinel are older, hence smaller).  Returns -1
 // if claimed from above or after cap steps.
+// Rank block reads of the walks since the last reset (rb3_walk_stats):
+// [0] seeds run, [1] block reads of seeds, [2] block reads of walk steps,
+// [3] segments taken over from above.
+__device__ unsigned long long g_walk_stats[4];
+
 template <int NS>
 __device__ __forceinline__ int64_t seed_forward(const OccView &B1, const uint8_t *__restrict__ T2, int64_t x,
-                                                int64_t send, int64_t cap, const int *state_w) {
+                                                int64_t send, int64_t cap, const int *state_w, uint32_t *reads) {
     BiInt q = {0, 0, B1.n};
     int a = T2[x];
+    const int lg = NS == 0 ? 5 : B1.log2D;
     for (int64_t t = 0;; ++t) {
         const int64_t p = x + t;
-        if (p == send) return q.k + (rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp));
+        if (p == send) {
+            *reads += 2;
+            return q.k + (rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp));
+        }
         if (t >= cap) return -1;
         if ((t & 15) == 15 && load_state(state_w) == ST_CLAIMED) return -1;
         const int an = T2[p + 1];  // next symbol (the sentinel at most), loaded ahead
+        *reads += ((q.kp + q.s) >> lg) == (q.kp >> lg) ? 1u : 2u;  // ForwardExt reads the swapped interval's ends
         const BiInt y = forward_ext<NS>(B1, q, a);
         if (y.s == 0) return y.k;
         q = y;
@@ -97,13 +108,15 @@ __device__ __forceinline__ int64_t seed_forward(const OccView &B1, const uint8_t
 // l(p) = lo exactly.  Returns -1 if it never becomes exact or is claimed.
 template <int NS>
 __device__ __forceinline__ int64_t seed_backward(const OccView &B1, int64_t m1, const uint8_t *__restrict__ T2,
-                                                 int64_t x, int64_t send, int64_t cap, const int *state_w) {
+                                                 int64_t x, int64_t send, int64_t cap, const int *state_w,
+                                                 uint32_t *reads) {
     const int64_t y = x + cap < send ? x + cap : send;
     bool exact = y == send;
     int64_t lo = exact ? m1 : 0, hi = exact ? m1 : B1.n;
     for (int64_t p = y - 1; p >= x; --p) {
         if (((y - p) & 15) == 0 && load_state(state_w) == ST_CLAIMED) return -1;
         const int a = T2[p];
+        *reads += exact ? 1u : 2u;
         if (exact) {
             lo = C_of(B1, a) + rank1<NS>(B1, a, lo);
             hi = lo;
@@ -132,6 +145,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
                                                     const int32_t *__restrict__ order, int64_t nw, int64_t cap,
                                                     unsigned long long *__restrict__ next,
                                                     int64_t *__restrict__ pos) {
+    uint32_t n_seed = 0, r_seed = 0, r_walk = 0, n_claim = 0;  // this lane's counts (rb3_walk_stats)
     for (;;) {
         // warp-aggregated grab of one segment per active lane
         cg::coalesced_group grp = cg::coalesced_threads();
@@ -139,7 +153,21 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
         if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
         base = grp.shfl(base, 0);
         const int64_t idx = (int64_t)base + grp.thread_rank();
-        if (idx >= nw) break;
+        if (idx >= nw) {
+            // the lanes leaving together add their counts with one atomic per counter
+            cg::coalesced_group out = cg::coalesced_threads();
+            const unsigned long long c0 = cg::reduce(out, (unsigned long long)n_seed, cg::plus<unsigned long long>());
+            const unsigned long long c1 = cg::reduce(out, (unsigned long long)r_seed, cg::plus<unsigned long long>());
+            const unsigned long long c2 = cg::reduce(out, (unsigned long long)r_walk, cg::plus<unsigned long long>());
+            const unsigned long long c3 = cg::reduce(out, (unsigned long long)n_claim, cg::plus<unsigned long long>());
+            if (out.thread_rank() == 0) {
+                atomicAdd(&g_walk_stats[0], c0);
+                atomicAdd(&g_walk_stats[1], c1);
+                atomicAdd(&g_walk_stats[2], c2);
+                atomicAdd(&g_walk_stats[3], c3);
+            }
+            break;
+        }
         const int32_t w = order[idx];
         const int64_t hi = w_hi[w], send = w_send[w];
         int64_t l;
@@ -149,8 +177,9 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
             pos[k] = k + l;
         } else {
             if (load_state(&state[w]) == ST_CLAIMED) continue;
-            l = DS ? seed_forward<NS>(B1, T2, hi, send, cap, &state[w])
-                   : seed_backward<NS>(B1, m1, T2, hi, send, cap, &state[w]);
+            ++n_seed;
+            l = DS ? seed_forward<NS>(B1, T2, hi, send, cap, &state[w], &r_seed)
+                   : seed_backward<NS>(B1, m1, T2, hi, send, cap, &state[w], &r_seed);
             if (l < 0) continue;
             if (atomicCAS(&state[w], ST_PENDING, ST_RESOLVED) == ST_CLAIMED) continue;
         }
@@ -171,9 +200,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
             }
             l = C_of(B1, a) + rank1<NS>(B1, a, l);
             pos[k] = k + l;
+            ++r_walk;
             if (p == bnd && nx >= 0) {
                 // reached the top of segment nx: stop if its seed is in, else take it over
                 if (atomicCAS(&state[nx], ST_PENDING, ST_CLAIMED) == ST_RESOLVED) break;
+                ++n_claim;
                 nx = w_next[nx];
                 bnd = nx >= 0 ? w_hi[nx] : lo;
             }
@@ -366,6 +397,17 @@ __global__ void __launch_bounds__(MT_THREADS, RB3_SCATTER_MINB) k_scatter(OccVie
 }
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int walk_stats(int64_t out[4], bool reset) {
+    unsigned long long h[4];
+    RB3_CUDA_TRY(cudaMemcpyFromSymbol(h, g_walk_stats, sizeof(h)));
+    for (int i = 0; i < 4; ++i) out[i] = (int64_t)h[i];
+    if (reset) {
+        const unsigned long long z[4] = {0, 0, 0, 0};
+        RB3_CUDA_TRY(cudaMemcpyToSymbol(g_walk_stats, z, sizeof(z)));
+    }
+    return RB3_OK;
+}
 
 // ---- sampled suffix array through a merge ---------------------------------------
 // The merged rows come from B1 and B2 in the interleaving pos gives, so the

@@ -79,6 +79,7 @@ def lib():
             "rb3_index_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "rb3_device_peak": (ctypes.c_int, [ctypes.POINTER(_i64), _i32]),
             "rb3_selftest_wait": (ctypes.c_int, [_i32, _vp]),
+            "rb3_walk_stats": (ctypes.c_int, [_vp, _i32]),
             "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_free": (None, [_vp]),
@@ -299,6 +300,13 @@ def rb3_index_compress(idx: Index, span: int = 0, stream=None) -> Index:
     out = _vp()
     _check(lib().rb3_index_compress(idx.handle, span, _stream(stream), ctypes.byref(out)))
     return Index(out.value)
+
+
+def rb3_walk_stats(reset: bool = False) -> dict:
+    """Counts of the merge walks since the last reset (see include/rb3.h)."""
+    v = (_i64 * 4)()
+    _check(lib().rb3_walk_stats(v, int(reset)))
+    return {"seeds": v[0], "seed_block_reads": v[1], "walk_block_reads": v[2], "taken_over": v[3]}
 
 
 def rb3_selftest_wait(limit: int, stream=None):

@@ -299,6 +299,26 @@ def test_bounded_wait_times_out_and_context_survives():
     check_index(build(S), ref_bwt(S))
 
 
+def test_walk_stats_count_every_new_symbol_once():
+    """The walk's counters: one rank read per new symbol except the strings'
+    sentinels (n2 - m2), whatever the segment length; seeds at most one per
+    segment below a sentinel."""
+    S = synth.pangenome(seed=93, founder_len=30_000, n_hap=6, batch=3)
+    for L in (50, 700):
+        idx = build(S, 0, 3)
+        src = build(S, 3, 6)
+        info = rb.rb3_index_info(src)
+        rb.rb3_walk_stats(reset=True)
+        rb.rb3_merge_opts(idx, src, {"seg_len": L})
+        st = rb.rb3_walk_stats(reset=True)
+        assert st["walk_block_reads"] == info["n"] - info["m"], st
+        # both strands of each haplotype are strings of len + 1 symbols, cut every L from their end
+        seeds_max = 2 * sum(-(-(int(l) + 1) // L) - 1 for l in S.lens[3:6])
+        assert 0 < st["seeds"] <= seeds_max, (st, seeds_max)
+        assert st["seed_block_reads"] >= st["seeds"]
+        check_index(idx, ref_bwt(S))
+
+
 def test_append_batch_memory_budget():
     """batch_mb cuts each caller batch into runs of whole strings that fit the
     budget: the same BWT (against the oracle), a lower device-memory peak."""
