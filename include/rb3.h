@@ -77,7 +77,10 @@ typedef struct {
     int32_t single_strand; /* 0: index both strands (the paper's default, Section "Methods"); 1: forward only */
     int64_t seg_len;       /* merge: walk segment length L (default: autotuned) */
     int64_t seed_cap;      /* merge: most ForwardExt steps spent on one segment seed (default 4*L) */
-    int32_t merge_form;    /* 0: segmented batched walk; 1: plain Algorithm 1, one walk per string */
+    int32_t merge_form;    /* 0: segmented batched walk, segment tops moved to content anchors (within
+                              +-L/4 of every L-th position, so the batch's homologous segments start at
+                              the same locus and walk side by side); 1: plain Algorithm 1, one walk per
+                              string; 2: segmented walk with tops every L symbols from the string end */
     int32_t search_form;   /* 0: chunked work-stealing SMEM search, one extension per lane per step;
                               1: plain, one query per thread; 2: chunked, each lane looping on its own */
     int64_t chunk_len;     /* SMEM: query chunk length (default 256) */

@@ -14,7 +14,9 @@
 //                 visited by Algorithm 1's walk for string i are ISA2 of the
 //                 positions of P_i read right to left, and the symbol at each
 //                 step is the text symbol.  Each string is cut into segments of
-//                 L symbols; the exact l at a segment's right end (its seed) is
+//                 about L symbols (by default each cut moved, within +-L/4, to a
+//                 content anchor, so that the haplotypes' homologous segments
+//                 start at the same locus); the exact l at a segment's right end (its seed) is
 //                 found with ForwardExt (Algorithm 3) over B1 along the suffix
 //                 that starts there, in the same persistent kernel that walks
 //                 the segment; a walk that reaches a segment whose seed is not
@@ -592,8 +594,42 @@ static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1,
 // segoff[s] segments below the string's sentinel: top hi = end - r*L, the next
 // segment down (or -1 at the string start), and (r, w) as the sort key/value of
 // the processing order.
+// With anchors (T2 given), the top of segment r >= 1 moves within a window of
+// +-L/4 around end - r*L to the position whose following 16 symbols hash
+// lowest: the homologous segments of the batch's haplotypes (processed side by
+// side) then start at the same locus, so their lanes step through homologous
+// suffixes together and their rank reads and pos writes share blocks.  The
+// windows of consecutive tops are disjoint, so segments stay in [L/2, 3L/2].
+__device__ __forceinline__ uint64_t anchor_hash(uint32_t v) {
+    uint64_t x = (uint64_t)v * 0x9E3779B97F4A7C15ull;
+    x ^= x >> 29;
+    x *= 0xBF58476D1CE4E5B9ull;
+    return x ^ (x >> 32);
+}
+
+__device__ int64_t anchor_top(const uint8_t *__restrict__ T2, int64_t n2, int64_t start, int64_t q, int64_t L) {
+    constexpr int K = 16;
+    const int64_t W = L / 4;
+    const int64_t a = q - W > start + 1 ? q - W : start + 1, b = q + W;
+    if (b + K > n2) return q;  // too close to the text's end to hash: the nominal top
+    uint32_t v = 0;
+    for (int64_t t = a; t < a + K - 1; ++t) v = (v << 2) | (((uint32_t)T2[t] - 1u) & 3u);
+    uint64_t best = ~0ull;
+    int64_t top = q;
+    for (int64_t t = a; t <= b; ++t) {  // v = the 16 symbols from t
+        v = (v << 2) | (((uint32_t)T2[t + K - 1] - 1u) & 3u);
+        const uint64_t h = anchor_hash(v);
+        if (h < best) {
+            best = h;
+            top = t;
+        }
+    }
+    return top;
+}
+
 __global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int32_t *__restrict__ segoff, int64_t ns,
-                           int64_t L, int64_t nw, int64_t *__restrict__ w_hi, int64_t *__restrict__ w_send,
+                           int64_t L, int64_t nw, const uint8_t *__restrict__ T2, int64_t n2,
+                           int64_t *__restrict__ w_hi, int64_t *__restrict__ w_send,
                            int64_t *__restrict__ w_sstart, int32_t *__restrict__ w_next, uint32_t *__restrict__ key,
                            uint32_t *__restrict__ val) {
     const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -606,7 +642,7 @@ __global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int32_t *_
     }
     const int64_t s = lo, r = w - segoff[s], R = segoff[s + 1] - segoff[s];
     const int64_t end = str_end[s], start = s == 0 ? 0 : str_end[s - 1] + 1;
-    w_hi[w] = end - r * L;
+    w_hi[w] = (T2 && r > 0) ? anchor_top(T2, n2, start, end - r * L, L) : end - r * L;
     w_send[w] = end;
     w_sstart[w] = start;
     w_next[w] = r == R - 1 ? -1 : (int32_t)(w + 1);
@@ -629,7 +665,7 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
     const int64_t m1 = dst->m, m2 = src->m;
     {
         Phase ph("merge.walk", st);
-        bool segmented = o.merge_form == 0 && src->text && src->isa;
+        bool segmented = (o.merge_form == 0 || o.merge_form == 2) && src->text && src->isa;
         if (n1 == 0) {
             // empty B1: every l is 0 (there are no older suffixes), pos[k] = k
             RB3_LAUNCH(k_iota, nb_for(n2, 256), 256, 0, st, pos, n2);
@@ -699,7 +735,8 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
             // the segments in string order), so homologous segments of the batch's
             // strings run side by side
             uint32_t *ord_v0 = reinterpret_cast<uint32_t *>(d_order);
-            RB3_LAUNCH(k_seg_fill, nb_for(nw, 256), 256, 0, st, d_end, d_segoff, ns, L, nw, d_hi, d_send, d_sstart,
+            RB3_LAUNCH(k_seg_fill, nb_for(nw, 256), 256, 0, st, d_end, d_segoff, ns, L, nw,
+                       o.merge_form == 0 ? src->text : (const uint8_t *)nullptr, src->n, d_hi, d_send, d_sstart,
                        d_next, sk0.as<uint32_t>(), ord_v0);
             if (maxr > 0) {
                 bool alt = false;

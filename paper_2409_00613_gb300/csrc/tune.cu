@@ -106,7 +106,7 @@ int tune_merge(const rb3_index *dst, const rb3_index *src, const rb3_opts &base,
     for (int64_t L : {L0 / 2, L0, 2 * L0, 4 * L0})
         if (L >= 256 && L <= 65536) cand.push_back(L);
     rb3_opts o = base;
-    o.merge_form = 0;
+    if (o.merge_form != 2) o.merge_form = 0;  // tune the segmented walk (nominal or anchored tops)
     o.seg_len = L0;
     RB3_TRY(merge_positions(dst, src, o, st, pos.as<int64_t>()));  // warm-up
     float bestt = 1e30f;

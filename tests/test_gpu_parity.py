@@ -86,7 +86,8 @@ def test_random_lists_batches(D, both):
             if idx is None:
                 idx = part
             else:
-                mopts = dict(opts, seg_len=int(g.integers(3, 64)), seed_cap=int(g.integers(1, 20)))
+                mopts = dict(opts, seg_len=int(g.integers(3, 64)), seed_cap=int(g.integers(1, 20)),
+                             merge_form=2 * (trial % 2))
                 rb.rb3_merge_opts(idx, part, mopts)
         check_index(idx, ref_bwt(S, 0, n_str, both), D)
 
@@ -161,7 +162,7 @@ def test_mixed_occ_intervals():
     g = synth.rng(606)
     S = synth.random_strings(g, 24, 900, n_frac=0.03)
     for D1, D2 in [(32, 64), (64, 32), (32, 256), (128, 32)]:
-        for form in (0, 1):
+        for form in (0, 1, 2):
             idx = build(S, 0, 10, occ_interval=D1)
             rb.rb3_merge_opts(idx, build(S, 10, 24, occ_interval=D2), {"merge_form": form, "seg_len": 50})
             assert rb.rb3_index_info(idx)["occ_interval"] == D1
@@ -387,7 +388,7 @@ def test_locate_every_row_vs_oracle(D, both):
         for a, b in zip(cuts[:-1], cuts[1:]):
             part = build(S, a, b, host=bool(trial & 1), **opts)
             assert rb.rb3_index_info(part)["sa_sample"] == s
-            rb.rb3_merge_opts(idx, part, dict(opts, merge_form=trial % 2, seg_len=int(g.integers(3, 64))))
+            rb.rb3_merge_opts(idx, part, dict(opts, merge_form=trial % 3, seg_len=int(g.integers(3, 64))))
         assert rb.rb3_index_info(idx)["sa_sample"] == s
         T = oracle.concat(S.seq, S.lens, both)
         rows = np.arange(len(T), dtype=np.int64)
