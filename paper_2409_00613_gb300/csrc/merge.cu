@@ -609,7 +609,10 @@ __device__ __forceinline__ uint64_t anchor_hash(uint32_t v) {
 
 __device__ int64_t anchor_top(const uint8_t *__restrict__ T2, int64_t n2, int64_t start, int64_t q, int64_t L) {
     constexpr int K = 16;
-    const int64_t W = L / 4;
+#ifndef RB3_ANCHOR_W
+#define RB3_ANCHOR_W 25  // window half-width, percent of L (below 50: windows stay disjoint)
+#endif
+    const int64_t W = L * RB3_ANCHOR_W / 100;
     const int64_t a = q - W > start + 1 ? q - W : start + 1, b = q + W;
     if (b + K > n2) return q;  // too close to the text's end to hash: the nominal top
     uint32_t v = 0;
