@@ -49,9 +49,9 @@ METRIC = "BWT-merge Msymbols/s"
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
 #       -k regex:k_merge_walk -s 3 -c 4 python bench.py --no-cpu --no-serve --no-search --no-plain
 #       --warmup 3 --steps 4 --seg-len 642
-# Keyed by (kernel, Occ interval, founder bp); reported only for that workload.
-# Must be taken again (or removed) whenever the kernel changes.
-NCU_TRAFFIC = {("k.merge_walk", 32, 5_000_000): 16.12e9}
+# Keyed by (kernel, Occ interval, founder bp, merge form); reported only for
+# that workload.  Must be taken again (or removed) whenever the kernel changes.
+NCU_TRAFFIC = {("k.merge_walk", 32, 5_000_000, 0): 10.11e9}
 
 
 def parse():
@@ -307,7 +307,7 @@ def run_rb3(args, rank, world, local_rank):
         achieved = kbytes / (kms * 1e-3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": NCU_TRAFFIC.get((top, info["occ_interval"], founder)),
+                "traffic": NCU_TRAFFIC.get((top, info["occ_interval"], founder, args.merge_form)),
                 "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),
                 "launches": kcalls, "share_of_step": round(kms / ms, 4)}
         if top == "k.merge_walk" and info["occ_interval"] == 32:
