@@ -60,33 +60,53 @@ int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int6
     RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sb, cudaStreamNonBlocking, prio_high));
     RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sm, cudaStreamNonBlocking, prio_low));
     RB3_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    // both internal streams start after the work already on the caller's stream
+    // host strings: the next batch's copy runs on its own stream while the
+    // current batch builds (two staging buffers, an event per copy)
+    cudaStream_t sc = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    if (!seq_dev) {
+        RB3_CUDA_TRY(cudaStreamCreateWithPriority(&sc, cudaStreamNonBlocking, prio_high));
+        RB3_CUDA_TRY(cudaEventCreateWithFlags(&copied[0], cudaEventDisableTiming));
+        RB3_CUDA_TRY(cudaEventCreateWithFlags(&copied[1], cudaEventDisableTiming));
+    }
+    // the internal streams start after the work already on the caller's stream
     RB3_CUDA_TRY(cudaEventRecord(start, caller));
     RB3_CUDA_TRY(cudaStreamWaitEvent(sb, start, 0));
     RB3_CUDA_TRY(cudaStreamWaitEvent(sm, start, 0));
+    if (sc) RB3_CUDA_TRY(cudaStreamWaitEvent(sc, start, 0));
 
     Channel ch;
     std::thread builder([&] {
         cudaSetDevice(dev);
+        DevBuf stage[2];
+        // copy of batch b's strings into stage[b & 1] on sc, marked by copied[b & 1]
+        auto issue_copy = [&](int64_t b) -> int {
+            const int64_t s0 = b == 0 ? 0 : batch_end[b - 1], s1 = batch_end[b];
+            const size_t bytes = (size_t)(off[s1] - off[s0]);
+            if (bytes == 0) return RB3_OK;
+            RB3_TRY(stage[b & 1].alloc(bytes, sc));  // its last reader, batch b - 2's build, is done
+            RB3_CUDA_TRY(cudaMemcpyAsync(stage[b & 1].p, seq + off[s0], bytes, cudaMemcpyHostToDevice, sc));
+            RB3_CUDA_TRY(cudaEventRecord(copied[b & 1], sc));
+            return RB3_OK;
+        };
+        int rc = (!seq_dev && n_batches > 0) ? issue_copy(0) : RB3_OK;
         for (int64_t b = 0; b < n_batches; ++b) {
             const int64_t s0 = b == 0 ? 0 : batch_end[b - 1], s1 = batch_end[b];
             Built out;
             rb3_index *x = new rb3_index();
             x->device = dev;
-            int r = RB3_OK;
-            DevBuf staged;
+            int r = rc;
             const uint8_t *src = seq + off[s0];
             const size_t bytes = (size_t)(off[s1] - off[s0]);
-            if (!seq_dev && bytes) {
-                r = staged.alloc(bytes, sb);
-                if (r == RB3_OK && cudaMemcpyAsync(staged.p, src, bytes, cudaMemcpyHostToDevice, sb) != cudaSuccess)
-                    r = cuda_fail(cudaGetLastError(), "append: copy batch", __FILE__, __LINE__);
-                src = staged.as<uint8_t>();
+            if (r == RB3_OK && !seq_dev && bytes) {
+                if (cudaStreamWaitEvent(sb, copied[b & 1], 0) != cudaSuccess)
+                    r = cuda_fail(cudaGetLastError(), "append: wait for copy", __FILE__, __LINE__);
+                src = stage[b & 1].as<uint8_t>();
             }
+            if (r == RB3_OK && !seq_dev && b + 1 < n_batches) r = issue_copy(b + 1);  // overlaps this build
             if (r == RB3_OK) r = build_batch_impl(src, lens + s0, s1 - s0, o, sb, x);
             if (r == RB3_OK && cudaStreamSynchronize(sb) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "append: build", __FILE__, __LINE__);
-            staged.release();
             if (r != RB3_OK) {
                 out.code = r;
                 out.err = rb3_last_error_str();
@@ -147,6 +167,12 @@ int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int6
     cudaStreamSynchronize(sm);
     cudaStreamDestroy(sb);
     cudaStreamDestroy(sm);
+    if (sc) {
+        cudaStreamSynchronize(sc);
+        cudaStreamDestroy(sc);
+        cudaEventDestroy(copied[0]);
+        cudaEventDestroy(copied[1]);
+    }
     cudaEventDestroy(start);
     if (result != RB3_OK) set_error("%s", err.c_str());
     return result;

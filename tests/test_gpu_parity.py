@@ -275,11 +275,13 @@ def test_append_batches_pipeline():
         seq = rest.copy() if host else torch.from_numpy(rest.copy()).to(DEV)
         rb.rb3_append_batches(idx, seq, lens, ends)
         check_index(idx, want)
-    # an empty index as the start, batches of different sizes, empty batches
-    idx = rb.rb3_index_empty()
-    rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens.copy(),
-                          np.array([0, 2, 2, 7, 15], dtype=np.int64))
-    check_index(idx, want)
+    # an empty index as the start, batches of different sizes, empty batches,
+    # strings on the device and on the host (copies staged a batch ahead)
+    for host in (False, True):
+        idx = rb.rb3_index_empty()
+        seq = S.seq.copy() if host else torch.from_numpy(S.seq.copy()).to(DEV)
+        rb.rb3_append_batches(idx, seq, S.lens.copy(), np.array([0, 2, 2, 7, 15], dtype=np.int64))
+        check_index(idx, want)
 
 
 def test_bounded_wait_times_out_and_context_survives():
