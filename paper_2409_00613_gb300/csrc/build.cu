@@ -27,10 +27,24 @@ namespace rb3 {
 
 constexpr int H0 = 18;            // symbols in the round-0 key (base-6 digits; 6^18 < 2^47)
 constexpr int H0_BITS = 47;
-// Batches without N: 17 symbols as 2-bit digits (A..T = 0..3) and a 5-bit
-// length field, 39 bits: five radix passes instead of six.
+// Batches without N: H4 symbols as 2-bit digits (A..T = 0..3) and a field
+// counting them.  By default 14 symbols and a 4-bit count, 32 bits: four radix
+// passes over (uint32 key, uint32 value) pairs, 8 bytes each, instead of six
+// over 12-byte pairs for the base-6 key (RB3_KEY4_32 = 0: 17 symbols and a
+// 5-bit count in a uint64 key, five passes).
+#ifndef RB3_KEY4_32
+#define RB3_KEY4_32 1
+#endif
+#if RB3_KEY4_32
+constexpr int H4 = 14;
+constexpr int K4_CNT_BITS = 4;
+using Key4 = uint32_t;
+#else
 constexpr int H4 = 17;
-constexpr int H4_BITS = 2 * H4 + 5;
+constexpr int K4_CNT_BITS = 5;
+using Key4 = uint64_t;
+#endif
+constexpr int H4_BITS = 2 * H4 + K4_CNT_BITS;
 constexpr int SMALL_MAX = 1024;   // groups up to this size are sorted in shared memory
 constexpr int RT_TILE = 2048;     // round-kernel tile (entries)
 constexpr int RT_THREADS = 256;
@@ -105,7 +119,7 @@ constexpr int K4_PER = 16;  // positions per thread of k_init_keys4
 // One thread per K4_PER consecutive positions p0 + r: the window bytes
 // T[p0, p0 + 32) in registers (two 16-byte loads), the digits of position r + 1
 // rolled from those of r, the count from a mask of the window's sentinels.
-__global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, uint64_t *__restrict__ key,
+__global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, Key4 *__restrict__ key,
                              uint32_t *__restrict__ val) {
     const int64_t p0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * K4_PER;
     if (p0 >= n) return;
@@ -127,26 +141,33 @@ __global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, uint64_t 
         const uint32_t e = __vcmpeq4(w[k], 0u);
         z |= (((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u)) << (4 * k);
     }
-    constexpr uint64_t M34 = (1ull << (2 * H4)) - 1ull;
+    constexpr uint64_t MD = (1ull << (2 * H4)) - 1ull;
     uint64_t raw = 0;  // digits of T[p0 + r + j], j < H4, as (symbol - 1) & 3
 #pragma unroll
     for (int j = 0; j < H4; ++j) raw = (raw << 2) | (((w[j >> 2] >> (8 * (j & 3))) - 1u) & 3u);
-    uint64_t kk[K4_PER];
+    Key4 kk[K4_PER];
 #pragma unroll
     for (int r = 0; r < K4_PER; ++r) {
         const uint32_t zr = z >> r;
         const uint32_t len = zr ? min((uint32_t)H4, (uint32_t)(__ffs(zr) - 1)) : (uint32_t)H4;
         const int drop = 2 * (H4 - (int)len);  // digits at and after the first sentinel are zero
-        kk[r] = (((raw >> drop) << drop) << 5) | len;
+        kk[r] = (Key4)((((raw >> drop) << drop) << K4_CNT_BITS) | len);
         if (r + 1 < K4_PER) {
             const int b = r + H4;
-            raw = ((raw << 2) | (((w[b >> 2] >> (8 * (b & 3))) - 1u) & 3u)) & M34;
+            raw = ((raw << 2) | (((w[b >> 2] >> (8 * (b & 3))) - 1u) & 3u)) & MD;
         }
     }
     if (p0 + K4_PER <= n) {
-        ulonglong2 *ko = reinterpret_cast<ulonglong2 *>(key + p0);
+        if constexpr (sizeof(Key4) == 8) {
+            ulonglong2 *ko = reinterpret_cast<ulonglong2 *>(key + p0);
 #pragma unroll
-        for (int r = 0; r < K4_PER; r += 2) ko[r / 2] = make_ulonglong2(kk[r], kk[r + 1]);
+            for (int r = 0; r < K4_PER; r += 2) ko[r / 2] = make_ulonglong2(kk[r], kk[r + 1]);
+        } else {
+            uint4 *ko = reinterpret_cast<uint4 *>(key + p0);
+#pragma unroll
+            for (int r = 0; r < K4_PER; r += 4)
+                ko[r / 4] = make_uint4((uint32_t)kk[r], (uint32_t)kk[r + 1], (uint32_t)kk[r + 2], (uint32_t)kk[r + 3]);
+        }
         uint4 *vo = reinterpret_cast<uint4 *>(val + p0);
 #pragma unroll
         for (int r = 0; r < K4_PER; r += 4)
@@ -166,11 +187,11 @@ __global__ void k_init_keys4(const uint8_t *__restrict__ T, int64_t n, uint64_t 
 // window holds a sentinel (then its order is final: singleton).  A base-6
 // window holds a sentinel iff its last digit is 0; a 2-bit one iff its count
 // field is below H4.
-template <bool B4>
-__global__ void k_heads(const uint64_t *__restrict__ K, int64_t n, uint32_t *__restrict__ hv) {
+template <bool B4, class KT>
+__global__ void k_heads(const KT *__restrict__ K, int64_t n, uint32_t *__restrict__ hv) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const bool sent = B4 ? (K[i] & 31u) < (uint64_t)H4 : (K[i] % 6u) == 0;
+    const bool sent = B4 ? (K[i] & ((1u << K4_CNT_BITS) - 1u)) < (KT)H4 : (K[i] % 6u) == 0;
     bool head = i == 0 || K[i] != K[i - 1] || sent;
     hv[i] = head ? (uint32_t)i : 0u;
 }
@@ -667,24 +688,40 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens, int64_t n_seq,
             uint32_t *v0 = reinterpret_cast<uint32_t *>(SA);
             // The sort starts from (ka, va) and ends in (k0, SA): the six base-6 passes
             // return to their input, the five 2-bit ones end in the other buffer.
-            uint64_t *ka = has_n ? k0.as<uint64_t>() : k1.as<uint64_t>();
-            uint32_t *va = has_n ? v0 : v1.as<uint32_t>();
-            uint64_t *kb = has_n ? k1.as<uint64_t>() : k0.as<uint64_t>();
-            uint32_t *vb = has_n ? v1.as<uint32_t>() : v0;
-            {
-                Phase pk("k.init_keys", st, 13.0 * n);  // 1 text byte in, 8-byte key + 4-byte value out
-                if (has_n) RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, ka, va);
-                else RB3_LAUNCH(k_init_keys4, nb_for((n + K4_PER - 1) / K4_PER, 256), 256, 0, st, T, n, ka, va);
-            }
+            // the sort starts from the (A) buffers and ends in (k0, SA): an even number
+            // of passes returns to its input, an odd one ends in the other buffer
+            const int passes = ((has_n ? H0_BITS : H4_BITS) + 7) / 8;
+            uint32_t *vA = (passes & 1) ? v1.as<uint32_t>() : v0, *vB = (passes & 1) ? v0 : v1.as<uint32_t>();
             bool alt = false;
-            RB3_TRY(radix_sort_pairs(ka, va, kb, vb, n, 0, has_n ? H0_BITS : H4_BITS, st, &alt));
-            const uint64_t *K = alt ? kb : ka;
-            if ((alt ? vb : va) != v0)
-                RB3_CUDA_TRY(cudaMemcpyAsync(SA, alt ? vb : va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
             DevBuf hv;
             RB3_TRY(hv.alloc(sizeof(uint32_t) * n, st));
-            if (has_n) RB3_LAUNCH(k_heads<false>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
-            else RB3_LAUNCH(k_heads<true>, nb_for(n, 256), 256, 0, st, K, n, hv.as<uint32_t>());
+            if (has_n) {
+                uint64_t *kA = (passes & 1) ? k1.as<uint64_t>() : k0.as<uint64_t>();
+                uint64_t *kB = (passes & 1) ? k0.as<uint64_t>() : k1.as<uint64_t>();
+                {
+                    Phase pk("k.init_keys", st, 13.0 * n);  // 1 text byte in, 8-byte key + 4-byte value out
+                    RB3_LAUNCH(k_init_keys, nb_for(n, 256), 256, 0, st, T, n, kA, vA);
+                }
+                RB3_TRY(radix_sort_pairs(kA, vA, kB, vB, n, 0, H0_BITS, st, &alt));
+                RB3_LAUNCH((k_heads<false, uint64_t>), nb_for(n, 256), 256, 0, st, alt ? kB : kA, n,
+                           hv.as<uint32_t>());
+            } else {
+                Key4 *kA = (passes & 1) ? k1.as<Key4>() : k0.as<Key4>();
+                Key4 *kB = (passes & 1) ? k0.as<Key4>() : k1.as<Key4>();
+                {
+                    Phase pk("k.init_keys", st, (1.0 + sizeof(Key4) + 4.0) * n);  // text in, key + value out
+                    RB3_LAUNCH(k_init_keys4, nb_for((n + K4_PER - 1) / K4_PER, 256), 256, 0, st, T, n, kA, vA);
+                }
+                if constexpr (sizeof(Key4) == 4)
+                    RB3_TRY(radix_sort_pairs32(reinterpret_cast<uint32_t *>(kA), vA, reinterpret_cast<uint32_t *>(kB),
+                                               vB, n, 0, H4_BITS, st, &alt));
+                else
+                    RB3_TRY(radix_sort_pairs(reinterpret_cast<uint64_t *>(kA), vA, reinterpret_cast<uint64_t *>(kB),
+                                             vB, n, 0, H4_BITS, st, &alt));
+                RB3_LAUNCH((k_heads<true, Key4>), nb_for(n, 256), 256, 0, st, alt ? kB : kA, n, hv.as<uint32_t>());
+            }
+            if ((alt ? vB : vA) != v0)
+                RB3_CUDA_TRY(cudaMemcpyAsync(SA, alt ? vB : vA, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
             RB3_TRY(scan_u32(hv.as<uint32_t>(), hv.as<uint32_t>(), n, true, 1, st));  // gstart
             k0.release();
             k1.release();
