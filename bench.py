@@ -300,8 +300,8 @@ def run_rb3(args, rank, world, local_rank):
     kern = {k: v for k, v in prof.items() if k.startswith("k.") and v[2] > 0}
     roof = None
     if kern:
-        # the merge walk: the largest share of the serialised launch list (profiles/); the
-        # event totals of the build's kernels overlap the walk and would double count
+        # the merge walk: the largest event total of the timed region (the build's kernels
+        # run beside it on another stream, so their totals overlap its time)
         top = "k.merge_walk" if "k.merge_walk" in kern else max(kern, key=lambda k: kern[k][0])
         kms, kcalls, kbytes = kern[top]
         achieved = kbytes / (kms * 1e-3) / 1e9
