@@ -219,7 +219,16 @@ __device__ __forceinline__ Sec ld_sec(const uint8_t *p) {
 // the 64-byte half-line holding the sector instead of the whole 128-byte line
 // (measured: half the DRAM bytes per random sector read, same request rate).
 // Every rank's block reads use it: they are random.
+// RB3_RANK_HINT64 = 0 drops the hint (a measurement knob: with anchored merge
+// segments the walk alone is ~5 % faster without it, the overlapped
+// build-and-merge step ~1 % slower).
+#ifndef RB3_RANK_HINT64
+#define RB3_RANK_HINT64 1
+#endif
 __device__ __forceinline__ Sec ld_sec64(const uint8_t *p) {
+#if !RB3_RANK_HINT64
+    return ld_sec(p);
+#endif
     Sec s;
     asm("ld.global.nc.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(s.w[0]), "=r"(s.w[1]), "=r"(s.w[2]), "=r"(s.w[3]), "=r"(s.w[4]), "=r"(s.w[5]), "=r"(s.w[6]),
