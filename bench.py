@@ -157,6 +157,20 @@ def bus_id(torch, dev):
 # ---------------------------------------------------------------------------
 # the rb3 arm
 # ---------------------------------------------------------------------------
+def aggregate_ranks(ms, new_syms, world, device):
+    """Whole-job figures over the ranks: the slowest rank's time (max) and the
+    symbols of all ranks (sum); each rank runs its own replica (weak scaling)."""
+    if world == 1:
+        return ms, float(new_syms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(new_syms)], device=device, dtype=torch.float64)
+    dist.all_reduce(s)
+    return float(t.item()), float(s.item())
+
+
 def run_rb3(args, rank, world, local_rank):
     import torch
     import paper_2409_00613_gb300 as rb
@@ -254,16 +268,7 @@ def run_rb3(args, rank, world, local_rank):
     prof = rb.rb3_profile_read()
     wstats = rb.rb3_walk_stats()
     info = rb.rb3_index_info(idx)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        s = torch.tensor([new_syms], device=dev, dtype=torch.float64)
-        dist.all_reduce(s)
-        total_syms = float(s.item())
-    else:
-        total_syms = float(new_syms)
+    ms, total_syms = aggregate_ranks(ms, new_syms, world, dev)
     value = total_syms / (ms * 1e3)
 
     # ---- the same steps one at a time (build, then merge): no overlap ----
