@@ -11,7 +11,8 @@ $=0 A=1 C=2 G=3 T=4 N=5.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (brute force on tiny inputs, the paper's worked
-SMEM example, closed-form LF/symmetry relations and the LF-decode certificate).
+SMEM and haplotype-diversity examples, closed-form LF/symmetry relations and
+the LF-decode certificate).
 """
 from __future__ import annotations
 
@@ -80,6 +81,10 @@ def lib():
         L.orc_smem_brute.restype = ctypes.c_int64
         L.orc_smem_brute.argtypes = [_u8p, ctypes.c_int64, _u8p, _i64p, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_int64, _i64p, ctypes.c_int64]
+        L.orc_diversity.restype = ctypes.c_int64
+        L.orc_diversity.argtypes = [_u8p, ctypes.c_int64, _u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i64p,
+                                    ctypes.c_int64]
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -248,6 +253,22 @@ def smem(B, q, qoff, min_len: int, min_occ: int = 1, nthreads: int = 1) -> np.nd
         out = np.empty((max(n, 1), 6), dtype=np.int64)
         L.orc_smem_mt(pb, len(B), pq, po, nq, min_len, min_occ, out.ctypes.data_as(_i64p), n, nthreads)
     return out[:n]
+
+
+def haplotype_diversity(B, P, a: int = 1, b: int = 3, q: int = 5, e: int = 2, W: int = 25,
+                        redundancy: bool = True) -> np.ndarray:
+    """Section "Estimating local haplotype diversity": Algorithm 5 (BWA-SW) on
+    the linear query P, end to start, against the text's prefix DAWG, with the
+    top-W band; (N, 4) int64 records (k, k', s, H) of the end-to-end
+    alignments with H > 0, best first, redundant bi-intervals filtered.  The
+    readings the paper leaves open are listed at orc_diversity."""
+    B, pb = _u8(B)
+    P, pp = _u8(P)
+    L = lib()
+    n = L.orc_diversity(pb, len(B), pp, len(P), a, b, q, e, W, int(redundancy), None, 0)
+    out = np.empty((max(n, 1), 4), dtype=np.int64)
+    L.orc_diversity(pb, len(B), pp, len(P), a, b, q, e, W, int(redundancy), out.ctypes.data_as(_i64p), n)
+    return out[:n].copy()
 
 
 def occ_brute(T, P) -> int:

@@ -471,6 +471,142 @@ int64_t orc_smem(const uint8_t *B, int64_t n, const uint8_t *q, const int64_t *q
 
 /* Same as orc_smem, queries spread over threads; each thread appends into its
  * own list and the lists are concatenated in query order. */
+/* ------------------------------------------------------------------------
+ * Section "Estimating local haplotype diversity": Algorithm 5 (BWA-SW) on
+ * the graph of a linear query P, traversed from its end to its start, against
+ * the prefix DAWG of the text: a node is the bi-interval (k, k', s) of a
+ * string occurring in T, its children its BackwardExt by A, C, G and T.
+ * Readings of what the paper leaves open:
+ *   - nodes are told apart by the whole bi-interval: strings with one SA
+ *     interval but different k' (x and xz when every x is followed by z) are
+ *     two nodes, so that the (k, k', s) reported is well defined;
+ *   - scores: match +a, mismatch -b (N in P mismatches every symbol; no node
+ *     has an N child), a gap of length L costs q + L*e, i.e. E and F become
+ *     max(H - q, E or F) - e, as in the recurrences of Section "Finding
+ *     inexact matches with BWA-SW";
+ *   - the cells after P[i..m) are the nodes with H > 0; before any symbol
+ *     the root (the empty string, H = 0) is the only cell;
+ *   - the deletion loop of Algorithm 5 runs to its closure: a cell whose H
+ *     rises by a deletion is extended again;
+ *   - the band keeps the W cells of largest H, ties by smaller k, then k',
+ *     then s (W = 0: no band);
+ *   - the result, the cells after P[0], is ordered by H descending, then k,
+ *     k', s; with redundancy set, a cell is dropped when its [k, k+s) or its
+ *     [k', k'+s) lies inside that of a cell kept before it.
+ * Writes (k, k', s, H) records (at most cap) and returns their number.
+ * Test infrastructure: small inputs, lists searched linearly.
+ * ---------------------------------------------------------------------- */
+typedef struct { int64_t k, kp, s, H, E, F; } dcell_t;
+#define DNEG (INT64_MIN / 4)
+
+typedef struct { dcell_t *c; int64_t n, cap; } dlist_t;
+
+static int64_t dlist_get(dlist_t *L, biint_t v)
+{
+    for (int64_t i = 0; i < L->n; ++i)
+        if (L->c[i].k == v.k && L->c[i].kp == v.kp && L->c[i].s == v.s) return i;
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 64;
+        L->c = (dcell_t *)realloc(L->c, sizeof(dcell_t) * L->cap);
+    }
+    dcell_t z = {v.k, v.kp, v.s, DNEG, DNEG, DNEG};
+    L->c[L->n] = z;
+    return L->n++;
+}
+
+static int dcell_cmp(const void *pa, const void *pb)
+{
+    const dcell_t *x = (const dcell_t *)pa, *y = (const dcell_t *)pb;
+    if (x->H != y->H) return x->H > y->H ? -1 : 1;
+    if (x->k != y->k) return x->k < y->k ? -1 : 1;
+    if (x->kp != y->kp) return x->kp < y->kp ? -1 : 1;
+    if (x->s != y->s) return x->s < y->s ? -1 : 1;
+    return 0;
+}
+
+static int64_t dmax(int64_t x, int64_t y) { return x > y ? x : y; }
+
+int64_t orc_diversity(const uint8_t *B, int64_t n, const uint8_t *P, int64_t m, int64_t a, int64_t b, int64_t q,
+                      int64_t e, int64_t W, int redundancy, int64_t *out, int64_t cap)
+{
+    orc_rank_t *r = rank_new(B, n);
+    dlist_t cur = {0, 0, 0}, nxt = {0, 0, 0};
+    biint_t root = {0, 0, n};
+    int64_t ri = dlist_get(&cur, root);
+    cur.c[ri].H = 0;
+    for (int64_t i = m - 1; i >= 0; --i) {
+        nxt.n = 0;
+        for (int64_t t = 0; t < cur.n; ++t) { /* match or mismatch: a child per symbol */
+            const dcell_t c = cur.c[t];
+            for (int x = 1; x <= 4; ++x) {
+                biint_t v = backward_ext(r, (biint_t){c.k, c.kp, c.s}, x);
+                if (v.s == 0) continue;
+                int64_t j = dlist_get(&nxt, v);
+                nxt.c[j].H = dmax(nxt.c[j].H, c.H + (x == P[i] ? a : -b));
+            }
+        }
+        for (int64_t t = 0; t < cur.n; ++t) { /* insertion: P[i] against a gap, same node */
+            const dcell_t c = cur.c[t];
+            const int64_t ev = dmax(c.H - q, c.E) - e;
+            int64_t j = dlist_get(&nxt, (biint_t){c.k, c.kp, c.s});
+            nxt.c[j].E = dmax(nxt.c[j].E, ev);
+            nxt.c[j].H = dmax(nxt.c[j].H, nxt.c[j].E);
+        }
+        for (int changed = 1; changed;) { /* deletion: a text symbol against a gap, to the closure */
+            changed = 0;
+            for (int64_t t = 0; t < nxt.n; ++t) {
+                if (nxt.c[t].H <= 0) continue;
+                for (int x = 1; x <= 4; ++x) {
+                    const dcell_t c = nxt.c[t];
+                    biint_t v = backward_ext(r, (biint_t){c.k, c.kp, c.s}, x);
+                    if (v.s == 0) continue;
+                    const int64_t fv = dmax(c.H - q, c.F) - e;
+                    int64_t j = dlist_get(&nxt, v);
+                    if (fv > nxt.c[j].F) {
+                        nxt.c[j].F = fv;
+                        nxt.c[j].H = dmax(nxt.c[j].H, fv);
+                        changed = 1;
+                    }
+                }
+            }
+        }
+        cur.n = 0;
+        for (int64_t t = 0; t < nxt.n; ++t) /* the cells: H > 0 */
+            if (nxt.c[t].H > 0) {
+                int64_t j = dlist_get(&cur, (biint_t){nxt.c[t].k, nxt.c[t].kp, nxt.c[t].s});
+                cur.c[j] = nxt.c[t];
+            }
+        if (W > 0 && cur.n > W) { /* the band */
+            qsort(cur.c, (size_t)cur.n, sizeof(dcell_t), dcell_cmp);
+            cur.n = W;
+        }
+        if (cur.n == 0) break;
+    }
+    if (m == 0) cur.n = 0; /* no symbol consumed: only the root, H = 0 */
+    qsort(cur.c, (size_t)cur.n, sizeof(dcell_t), dcell_cmp);
+    int64_t nout = 0;
+    dcell_t *kept = (dcell_t *)malloc(sizeof(dcell_t) * (cur.n ? cur.n : 1));
+    for (int64_t t = 0; t < cur.n; ++t) {
+        const dcell_t c = cur.c[t];
+        int drop = 0;
+        for (int64_t u = 0; redundancy && u < nout && !drop; ++u)
+            drop = (c.k >= kept[u].k && c.k + c.s <= kept[u].k + kept[u].s) ||
+                   (c.kp >= kept[u].kp && c.kp + c.s <= kept[u].kp + kept[u].s);
+        if (drop) continue;
+        kept[nout] = c;
+        if (nout < cap) {
+            int64_t *o = out + 4 * nout;
+            o[0] = c.k; o[1] = c.kp; o[2] = c.s; o[3] = c.H;
+        }
+        ++nout;
+    }
+    free(kept);
+    free(cur.c);
+    free(nxt.c);
+    rank_free(r);
+    return nout;
+}
+
 int64_t orc_smem_mt(const uint8_t *B, int64_t n, const uint8_t *q, const int64_t *qoff, int64_t nq,
                     int64_t ell, int64_t smin, int64_t *out, int64_t cap, int nthreads)
 {

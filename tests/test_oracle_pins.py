@@ -437,3 +437,175 @@ def test_runs_pins():
                 assert np.all(starts // span == (ends - 1) // span)  # no run crosses a cut
             else:
                 assert not np.any(same)
+
+
+# ---- Section "Estimating local haplotype diversity" (Algorithm 5) ---------------
+
+def py_diversity(strings, P, a, b, q, e):
+    """String by string: for every distinct substring x over ACGT of the
+    double-strand text, the semi-global affine-gap score of P against x,
+    filled from the ends of both (P[i..] against x[j..]) with a cell kept only
+    while its score is positive (the empty pair starts at 0).  A positive
+    alignment holds fewer than m*a/e deletions, which bounds |x|."""
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A", "N": "N"}
+    m, NEG = len(P), -(1 << 40)
+    max_len = m + (m * a) // e + 1
+    subs = set()
+    for s in strings:
+        for t in (s, "".join(comp[c] for c in reversed(s))):
+            for i in range(len(t)):
+                for j in range(i + 1, min(len(t), i + max_len) + 1):
+                    if "N" in t[i:j]:
+                        break
+                    subs.add(t[i:j])
+    best = {}
+    for x in subs:
+        L = len(x)
+        H = [[NEG] * (L + 2) for _ in range(m + 2)]
+        E = [[NEG] * (L + 2) for _ in range(m + 2)]
+        F = [[NEG] * (L + 2) for _ in range(m + 2)]
+        live = [[False] * (L + 2) for _ in range(m + 2)]
+        H[m][L], live[m][L] = 0, True
+        for i in range(m, -1, -1):
+            for j in range(L, -1, -1):
+                if i == m and j == L:
+                    continue
+                g = ev = fv = NEG
+                if i < m and j < L and live[i + 1][j + 1]:
+                    g = H[i + 1][j + 1] + (a if P[i] == x[j] else -b)
+                if i < m and live[i + 1][j]:
+                    ev = max(H[i + 1][j] - q, E[i + 1][j]) - e
+                if j < L and live[i][j + 1] and H[i][j + 1] > 0:
+                    fv = max(H[i][j + 1] - q, F[i][j + 1]) - e
+                H[i][j], E[i][j], F[i][j] = max(g, ev, fv), ev, fv
+                live[i][j] = H[i][j] > 0
+        if m and H[0][0] > 0:
+            best[x] = max(best.get(x, NEG), H[0][0])
+    return best
+
+
+def diversity_from_strings(T, best):
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+    cells = {}
+    for x, h in best.items():
+        key = (oracle.lo_brute(T, enc(x)), oracle.lo_brute(T, enc("".join(comp[c] for c in reversed(x)))),
+               oracle.occ_brute(T, enc(x)))
+        cells[key] = max(cells.get(key, -(1 << 40)), h)
+    return cells
+
+
+def test_diversity_paper_worked_example():
+    gd = golden("diversity_worked_example.txt")
+    text, query = gd["text"][0], gd["query"][0]
+    a, b, q, e = (int(v) for v in gd["scores"])
+    T = oracle.concat(enc(text), np.array([len(text)]), True)
+    B = oracle.bwt(T)
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+    def bi(x):
+        rc = "".join(comp[c] for c in reversed(x))
+        return (oracle.lo_brute(T, enc(x)), oracle.lo_brute(T, enc(rc)), oracle.occ_brute(T, enc(x)))
+
+    (xs, hs), (xg, hg) = gd["exact"], gd["gapped"]
+    full = {tuple(r[:3]): r[3] for r in oracle.haplotype_diversity(B, enc(query), a, b, q, e, W=0,
+                                                                   redundancy=False).tolist()}
+    assert full[bi(xs)] == int(hs) and full[bi(xg)] == int(hg)
+    assert max(full.values()) == int(hs)
+    kept = oracle.haplotype_diversity(B, enc(query), a, b, q, e, W=0)
+    keys = [tuple(r[:3]) for r in kept.tolist()]
+    assert keys[0] == bi(xs) and bi(xg) not in keys
+
+
+@pytest.mark.parametrize("scores", [(1, 3, 5, 2), (2, 1, 2, 1), (3, 3, 5, 2), (3, 2, 1, 1), (2, 4, 0, 1)])
+def test_diversity_unbanded_equals_string_brute_force(scores):
+    """No band, no filter: the cells after the whole query equal, bi-interval
+    by bi-interval, the best pruned score over the strings of that interval."""
+    a, b, q, e = scores
+    g = synth.rng(700 + a + 10 * b + 100 * q)
+    n_cells = 0
+    for trial in range(8):
+        S, strs = rand_list(g, int(g.integers(1, 4)), 24, n_frac=0.03, allow_empty=True)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        for _ in range(4):
+            m = int(g.integers(1, 9))
+            if g.random() < 0.6 and len(S.seq) > m:
+                st = int(g.integers(0, len(S.seq) - m))
+                P = S.seq[st:st + m].copy()
+                P[P == 0] = 1
+                if g.random() < 0.5:
+                    P[int(g.integers(0, m))] = int(g.integers(1, 6))
+            else:
+                P = synth.random_bases(g, m)
+            want = diversity_from_strings(T, py_diversity(strs, dec(P), a, b, q, e))
+            got = oracle.haplotype_diversity(B, P, a, b, q, e, W=0, redundancy=False)
+            assert {tuple(r[:3]): r[3] for r in got.tolist()} == want
+            hs = got[:, 3].tolist()
+            assert hs == sorted(hs, reverse=True)
+            n_cells += len(got)
+    assert n_cells >= 10
+
+
+def test_diversity_band_and_redundancy_invariants():
+    """With a band of W cells: at most W results, each a cell of the unbanded
+    run scoring no more there; a wide band changes nothing.  The filter keeps
+    the best cell and drops exactly the cells whose k- or k'-interval lies in
+    that of a cell kept before them."""
+    g = synth.rng(771)
+    S = synth.pangenome(seed=772, founder_len=300, n_hap=5, batch=5)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    for _ in range(8):
+        m = int(g.integers(8, 30))
+        st = int(g.integers(0, len(S.seq) - m))
+        P = S.seq[st:st + m].copy()
+        P[P == 0] = 1
+        P[int(g.integers(0, m))] = int(g.integers(1, 5))
+        full = oracle.haplotype_diversity(B, P, W=0, redundancy=False)
+        fmap = {tuple(r[:3]): r[3] for r in full.tolist()}
+        for W in (1, 3, 25):
+            band = oracle.haplotype_diversity(B, P, W=W, redundancy=False)
+            assert len(band) <= W
+            for r in band.tolist():
+                assert tuple(r[:3]) in fmap and r[3] <= fmap[tuple(r[:3])]
+        assert np.array_equal(oracle.haplotype_diversity(B, P, W=100000, redundancy=False), full)
+        check_filter(full.tolist(), oracle.haplotype_diversity(B, P, W=0).tolist())
+    # cheap gaps on random texts: many overlapping cells, among them chains
+    # where a cell lies inside a dropped one but in no kept one
+    for trial in range(30):
+        S = synth.random_strings(g, int(g.integers(1, 4)), 30, allow_empty=False)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        P = synth.random_bases(g, int(g.integers(3, 10)))
+        full = oracle.haplotype_diversity(B, P, 3, 2, 1, 1, W=0, redundancy=False).tolist()
+        check_filter(full, oracle.haplotype_diversity(B, P, 3, 2, 1, 1, W=0).tolist())
+
+
+def check_filter(full, kept):
+    """Walking the unfiltered list best first: a cell is kept iff neither of
+    its intervals lies inside the same interval of a cell kept before it."""
+    inside = lambda x, y: (x[0] >= y[0] and x[0] + x[2] <= y[0] + y[2]) or \
+        (x[1] >= y[1] and x[1] + x[2] <= y[1] + y[2])
+    kept_set = {tuple(r) for r in kept}
+    seen = []
+    for r in full:
+        if tuple(r) in kept_set:
+            assert not any(inside(r, y) for y in seen)
+            seen.append(r)
+        else:
+            assert any(inside(r, y) for y in seen)
+    assert seen == kept
+
+
+def test_diversity_degenerate_queries():
+    """Empty query: no alignment.  A query of N only: every symbol mismatches,
+    so nothing stays positive.  An exact occurrence scores a*m and comes first."""
+    S = synth.pangenome(seed=773, founder_len=200, n_hap=3, batch=3)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    assert len(oracle.haplotype_diversity(B, np.zeros(0, np.uint8))) == 0
+    assert len(oracle.haplotype_diversity(B, np.full(6, 5, np.uint8), W=0)) == 0
+    P = S.seq[10:40].copy()
+    top = oracle.haplotype_diversity(B, P, a=2)[0]
+    assert top[3] == 2 * len(P)
+    assert (top[0], top[2]) == (oracle.lo_brute(T, P), oracle.occ_brute(T, P))
