@@ -157,6 +157,30 @@ int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *len, i
 int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                         int64_t *lo_hi, void *stream);
 
+/* Local haplotype diversity (Section "Estimating local haplotype diversity"):
+ * Algorithm 5 (the revised BWA-SW of Section "Finding inexact matches with
+ * BWA-SW") on the graph of each linear query q[qoff[i] .. qoff[i+1]), walked
+ * from its end to its start, against the prefix DAWG of the indexed text; a
+ * node is the bi-interval (k, k', s) of a string, its children its
+ * BackwardExt by A, C, G, T.  Scores: match +a, mismatch -b (N in a query
+ * mismatches every symbol), a gap of length L costs gap_open + L * gap_ext.
+ * After each query symbol the W cells of largest H (ties: smaller k, k', s)
+ * are kept; deletions are applied until no cell's score rises.  The result of
+ * query i is the set of nodes aligned end to end with H > 0, best first; with
+ * redundancy = 1 a node is dropped when its [k, k+s) or [k', k'+s) lies
+ * inside that of a node kept before it.
+ * out: nq * W records of 4 int64 (k, k', s, H), query i's from out + 4*W*i;
+ * n_out[i]: the number of query i's records.  Both caller-owned, host or
+ * device memory; q and qoff too.  Needs a double-strand index (any layout).
+ * RB3_E_INVAL: a symbol outside 1..5, W outside 1..32, a < 1, b < 0,
+ * gap_open < 0, gap_ext < 1, a score above 65536, a query longer than
+ * 2^29 / a, or a single-strand index.  RB3_E_CAPACITY when a query symbol
+ * left more than 2048 candidate cells: that query's n_out is -1, every other
+ * query's result is written. */
+int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a,
+                            int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W, int32_t redundancy,
+                            int64_t *out, int64_t *n_out, void *stream);
+
 /* Locate (Section "Locating with FM-index", Algorithm 2): for each row i of
  * the BWT (0 <= rows[j] < n), out[2j] = the index of the string its suffix
  * starts in (strings numbered as concatenated: P0, rc(P0), P1, ... for a

@@ -398,6 +398,56 @@ RB3_EXPORT int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const
     return RB3_OK;
 }
 
+RB3_EXPORT int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
+                                       int32_t a, int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W,
+                                       int32_t redundancy, int64_t *out, int64_t *n_out, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr, "NULL index");
+    RB3_CHECK_ARG(nq >= 0, "nq < 0");
+    RB3_CHECK_ARG(!idx->single_strand, "haplotype diversity needs a double-strand index");
+    RB3_CHECK_ARG(a >= 1 && b >= 0 && gap_open >= 0 && gap_ext >= 1, "scores: a >= 1, b >= 0, q >= 0, e >= 1");
+    RB3_CHECK_ARG(a <= 65536 && b <= 65536 && gap_open <= 65536 && gap_ext <= 65536, "a score above 65536");
+    RB3_CHECK_ARG(W >= 1 && W <= 32, "W must be in 1..32");
+    RB3_CHECK_ARG(redundancy == 0 || redundancy == 1, "redundancy must be 0 or 1");
+    if (nq == 0) return RB3_OK;
+    RB3_CHECK_ARG(qoff && out && n_out, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> qo;
+    RB3_TRY(read_i64(qoff, nq + 1, qo, st));
+    RB3_TRY(check_qoff(qo));
+    RB3_CHECK_ARG(qo[nq] == 0 || q != nullptr, "q is NULL");
+    for (int64_t i = 0; i < nq; ++i) RB3_CHECK_ARG((qo[i + 1] - qo[i]) * (int64_t)a < ((int64_t)1 << 29), "query too long for its match score");
+    InArg dq, doff;
+    RB3_TRY(dq.set(q, (size_t)qo[nq], st));
+    RB3_TRY(doff.set(qoff, sizeof(int64_t) * (nq + 1), st));
+    const size_t out_bytes = sizeof(int64_t) * 4 * (size_t)W * nq, n_bytes = sizeof(int64_t) * nq;
+    const bool dev_out = is_device_ptr(out), dev_n = is_device_ptr(n_out);
+    DevBuf ob, nb;
+    int64_t *o = out, *no = n_out;
+    if (!dev_out) {
+        RB3_TRY(ob.alloc(out_bytes, st));
+        o = ob.as<int64_t>();
+    }
+    if (!dev_n) {
+        RB3_TRY(nb.alloc(n_bytes, st));
+        no = nb.as<int64_t>();
+    }
+    const int32_t prm[6] = {a, b, gap_open, gap_ext, W, redundancy};
+    RB3_TRY(diversity_impl(idx, static_cast<const uint8_t *>(dq.dev), static_cast<const int64_t *>(doff.dev), nq,
+                           qo[nq], prm, o, no, st));
+    if (!dev_out) RB3_CUDA_TRY(cudaMemcpyAsync(out, o, out_bytes, cudaMemcpyDeviceToHost, st));
+    std::vector<int64_t> counts(nq);
+    RB3_CUDA_TRY(cudaMemcpyAsync(counts.data(), no, n_bytes, cudaMemcpyDeviceToHost, st));
+    if (!dev_n) RB3_CUDA_TRY(cudaMemcpyAsync(n_out, no, n_bytes, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < nq; ++i)
+        if (counts[i] < 0) {
+            set_error("query %lld: a step left more than 2048 candidate cells", (long long)i);
+            return RB3_E_CAPACITY;
+        }
+    return RB3_OK;
+}
+
 RB3_EXPORT int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                                    int32_t min_len, int64_t min_occ, const rb3_opts *o, rb3_smem *out, int64_t cap,
                                    int64_t *n_out, void *stream) {

@@ -819,6 +819,12 @@ int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int6
                    int64_t n_batches, const rb3_opts &o, cudaStream_t caller);
 int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
                          int64_t *lohi, cudaStream_t st);
+// RB3_E_INVAL when a query symbol lies outside 1..5.
+int check_codes(const uint8_t *q, int64_t n, cudaStream_t st);
+// Haplotype diversity of every query (prm = a, b, q, e, W, redundancy);
+// device pointers throughout.
+int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
+                   const int32_t prm[6], int64_t *out, int64_t *n_out, cudaStream_t st);
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);

@@ -1,0 +1,319 @@
+// Local haplotype diversity (Section "Estimating local haplotype diversity"):
+// Algorithm 5, the revised BWA-SW, applied to the graph of a linear query P,
+// walked from its end to its start, against the prefix DAWG of the indexed
+// text (a node is the bi-interval of a string, its children its BackwardExt by
+// A, C, G and T, Algorithm 3).  The result is the set of bi-intervals whose
+// end-to-end alignment with P scores H > 0, best first, redundant ones dropped.
+//
+// One warp per query.  The W <= 32 cells kept after a query symbol sit one per
+// lane; a step's candidates go into a table of the warp's own in shared memory
+// (found by a warp-wide compare, written by lane 0).  Only candidates with a
+// positive score enter the table: a cell whose H never rises above 0 extends
+// nothing (a match, an insertion or a deletion from it stays below 0), so the
+// cells with H > 0 and their scores are those of the full recurrence.
+//   match / mismatch  H(child) = H + a or H - b (N in P mismatches everything)
+//   insertion         E = max(H - q, E) - e, same node, next query position
+//   deletion          F(child) = max(H - q, F) - e, same query position, until
+//                     no cell's H or F rises (a worklist of cells to re-extend)
+// The band keeps the W cells of largest H, ties by smaller k, k', s.  The
+// filter walks the band best first and drops a cell whose [k, k+s) or
+// [k', k'+s) lies inside that of a cell kept before it.
+#include "common.cuh"
+
+namespace rb3 {
+namespace {
+
+constexpr int DV_WARPS = 2;     // queries per CTA
+constexpr int DV_CAP = 2048;    // cells one query step may hold
+constexpr int32_t DV_NEG = -(1 << 30);
+constexpr unsigned DV_FULL = 0xffffffffu;
+constexpr size_t DV_WARP_BYTES = (size_t)DV_CAP * (3 * 8 + 3 * 4 + 1);  // 16-byte multiple
+static_assert(DV_WARP_BYTES % 16 == 0, "per-warp table must keep 16-byte alignment");
+
+struct DvParams {
+    int32_t a, b, q, e, W, redundancy;
+};
+
+// One warp's cells, structure of arrays.
+struct DvTab {
+    int64_t *k, *kp, *s;
+    int32_t *H, *E, *F;
+    uint8_t *flag;  // bit 0: to be extended by deletions; bit 1: taken into the band
+};
+
+__device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
+    DvTab t;
+    t.k = reinterpret_cast<int64_t *>(base);
+    t.kp = t.k + DV_CAP;
+    t.s = t.kp + DV_CAP;
+    t.H = reinterpret_cast<int32_t *>(t.s + DV_CAP);
+    t.E = t.H + DV_CAP;
+    t.F = t.E + DV_CAP;
+    t.flag = reinterpret_cast<uint8_t *>(t.F + DV_CAP);
+    return t;
+}
+
+// BackwardExt (Algorithm 3) of (k, k', s) by A, C, G and T at once, from the
+// ranks of every symbol at k and at k + s: child a has s = d(a),
+// k = C(a) + rank(a, k), k' = k' + the d of the complements of the symbols
+// below comp(a).
+template <int NS>
+__device__ __forceinline__ void dv_children(const OccView &V, int64_t k, int64_t kp, int64_t s, int64_t ck[4],
+                                            int64_t ckp[4], int64_t cs[4]) {
+    int64_t r0[SIGMA], r1[SIGMA], d[SIGMA];
+    rank_all<NS>(V, k, r0);
+    rank_all<NS>(V, k + s, r1);
+#pragma unroll
+    for (int i = 0; i < SIGMA; ++i) d[i] = r1[i] - r0[i];
+#pragma unroll
+    for (int a = 1; a <= 4; ++a) {
+        const int ac = comp_sym(a);
+        int64_t add = 0;
+#pragma unroll
+        for (int b = 0; b < SIGMA; ++b)
+            if (b < ac) add += d[comp_sym(b)];
+        ck[a - 1] = V.C[a] + r0[a];
+        ckp[a - 1] = kp + add;
+        cs[a - 1] = d[a];
+    }
+}
+
+// Finds (k, k', s) among the first tn cells: its index or -1 (warp-uniform).
+__device__ __forceinline__ int dv_find(const DvTab &T, int tn, int64_t k, int64_t kp, int64_t s, int lane) {
+    for (int j0 = 0; j0 < tn; j0 += 32) {
+        const int j = j0 + lane;
+        const bool hit = j < tn && T.s[j] == s && T.k[j] == k && T.kp[j] == kp;
+        const unsigned m = __ballot_sync(DV_FULL, hit);
+        if (m) return j0 + __ffs(m) - 1;
+    }
+    return -1;
+}
+
+// Raises the cell (k, k', s) to H = max(H, h), E = max(E, ev), F = max(F, fv),
+// adding it when absent; a cell whose H or F rises is marked for deletion
+// extension.  Warp-uniform; returns the new cell count.
+__device__ __forceinline__ int dv_upsert(const DvTab &T, int tn, int64_t k, int64_t kp, int64_t s, int32_t h,
+                                         int32_t ev, int32_t fv, int lane, bool &overflow) {
+    const int j = dv_find(T, tn, k, kp, s, lane);
+    if (j >= 0) {
+        if (lane == 0) {
+            bool up = false;
+            if (ev > T.E[j]) T.E[j] = ev;
+            if (fv > T.F[j]) {
+                T.F[j] = fv;
+                up = true;
+            }
+            if (h > T.H[j]) {
+                T.H[j] = h;
+                up = true;
+            }
+            if (up) T.flag[j] |= 1;
+        }
+        __syncwarp();
+        return tn;
+    }
+    if (tn >= DV_CAP) {
+        overflow = true;
+        return tn;
+    }
+    if (lane == 0) {
+        T.k[tn] = k;
+        T.kp[tn] = kp;
+        T.s[tn] = s;
+        T.H[tn] = h;
+        T.E[tn] = ev;
+        T.F[tn] = fv;
+        T.flag[tn] = 1;
+    }
+    __syncwarp();
+    return tn + 1;
+}
+
+// Band order: larger H first, then smaller k, k', s.
+__device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, int64_t s1, int32_t h2, int64_t k2,
+                                          int64_t kp2, int64_t s2) {
+    if (h1 != h2) return h1 > h2;
+    if (k1 != k2) return k1 < k2;
+    if (kp1 != kp2) return kp1 < kp2;
+    return s1 < s2;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32 * DV_WARPS)
+    k_diversity(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq, DvParams p,
+                int64_t *__restrict__ out, int64_t *__restrict__ n_out) {
+    extern __shared__ __align__(16) uint8_t dv_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t qi = (int64_t)blockIdx.x * DV_WARPS + w;
+    if (qi >= nq) return;  // the whole warp leaves together
+    const DvTab T = dv_tab(dv_smem + (size_t)w * DV_WARP_BYTES);
+    const int64_t q0 = qoff[qi], m = qoff[qi + 1] - q0;
+
+    // lane r holds the r-th kept cell; before any symbol only the root (H = 0)
+    int64_t ck = 0, ckp = 0, cs = V.n;
+    int32_t cH = 0, cE = DV_NEG;
+    int ncur = m > 0 ? 1 : 0;
+    bool overflow = false;
+
+    for (int64_t i = m - 1; i >= 0 && ncur > 0 && !overflow; --i) {
+        const int c = q[q0 + i];
+        int tn = 0;
+        // match / mismatch: the children of every kept cell
+        {
+            int64_t xk[4] = {0, 0, 0, 0}, xkp[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
+            if (lane < ncur) dv_children<NS>(V, ck, ckp, cs, xk, xkp, xs);
+            for (int t = 0; t < ncur && !overflow; ++t) {
+                const int32_t h = __shfl_sync(DV_FULL, cH, t);
+#pragma unroll
+                for (int a = 1; a <= 4; ++a) {
+                    const int64_t k = __shfl_sync(DV_FULL, xk[a - 1], t);
+                    const int64_t kp = __shfl_sync(DV_FULL, xkp[a - 1], t);
+                    const int64_t s = __shfl_sync(DV_FULL, xs[a - 1], t);
+                    const int32_t g = h + (a == c ? p.a : -p.b);
+                    if (s > 0 && g > 0 && !overflow) tn = dv_upsert(T, tn, k, kp, s, g, DV_NEG, DV_NEG, lane, overflow);
+                }
+            }
+        }
+        // insertion: the query symbol against a gap, the node unchanged
+        {
+            const int32_t ev = max(cH - p.q, cE) - p.e;
+            for (int t = 0; t < ncur && !overflow; ++t) {
+                const int32_t e1 = __shfl_sync(DV_FULL, ev, t);
+                const int64_t k = __shfl_sync(DV_FULL, ck, t);
+                const int64_t kp = __shfl_sync(DV_FULL, ckp, t);
+                const int64_t s = __shfl_sync(DV_FULL, cs, t);
+                if (e1 > 0) tn = dv_upsert(T, tn, k, kp, s, e1, e1, DV_NEG, lane, overflow);
+            }
+        }
+        // deletion: a text symbol against a gap, until no cell is left to extend
+        for (int pass = 0; !overflow; ++pass) {
+            bool any = false;
+            for (int j0 = 0; j0 < tn && !overflow; j0 += 32) {
+                const int j = j0 + lane;
+                const bool act = j < tn && (T.flag[j] & 1);
+                int32_t fv = DV_NEG;
+                int64_t yk[4] = {0, 0, 0, 0}, ykp[4] = {0, 0, 0, 0}, ys[4] = {0, 0, 0, 0};
+                if (act) {
+                    fv = max(T.H[j] - p.q, T.F[j]) - p.e;
+                    if (fv > 0) dv_children<NS>(V, T.k[j], T.kp[j], T.s[j], yk, ykp, ys);
+                    T.flag[j] &= (uint8_t)~1u;
+                }
+                any |= __ballot_sync(DV_FULL, act) != 0;
+                unsigned todo = __ballot_sync(DV_FULL, act && fv > 0);
+                __syncwarp();
+                while (todo && !overflow) {
+                    const int t = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int32_t f = __shfl_sync(DV_FULL, fv, t);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int64_t k = __shfl_sync(DV_FULL, yk[a], t);
+                        const int64_t kp = __shfl_sync(DV_FULL, ykp[a], t);
+                        const int64_t s = __shfl_sync(DV_FULL, ys[a], t);
+                        if (s > 0 && !overflow) tn = dv_upsert(T, tn, k, kp, s, f, DV_NEG, f, lane, overflow);
+                    }
+                }
+            }
+            if (!any) break;
+            if (pass > DV_CAP) overflow = true;  // a chain cannot be longer than the table
+        }
+        if (overflow) break;
+        // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
+        const int keep = min(tn, p.W);
+        int64_t nk = 0, nkp = 0, ns = 0;
+        int32_t nH = 0, nE = DV_NEG;
+        for (int r = 0; r < keep; ++r) {
+            int bj = -1;
+            int32_t bH = 0;
+            int64_t bk = 0, bkp = 0, bs = 0;
+            for (int j = lane; j < tn; j += 32) {
+                if (T.flag[j] & 2) continue;
+                if (bj < 0 || dv_before(T.H[j], T.k[j], T.kp[j], T.s[j], bH, bk, bkp, bs)) {
+                    bj = j;
+                    bH = T.H[j];
+                    bk = T.k[j];
+                    bkp = T.kp[j];
+                    bs = T.s[j];
+                }
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const int oj = __shfl_xor_sync(DV_FULL, bj, off);
+                const int32_t oH = __shfl_xor_sync(DV_FULL, bH, off);
+                const int64_t ok = __shfl_xor_sync(DV_FULL, bk, off);
+                const int64_t okp = __shfl_xor_sync(DV_FULL, bkp, off);
+                const int64_t os = __shfl_xor_sync(DV_FULL, bs, off);
+                if (oj >= 0 && (bj < 0 || dv_before(oH, ok, okp, os, bH, bk, bkp, bs))) {
+                    bj = oj;
+                    bH = oH;
+                    bk = ok;
+                    bkp = okp;
+                    bs = os;
+                }
+            }
+            // keys are distinct, so every lane holds the same best cell
+            if (lane == r) {
+                nk = bk;
+                nkp = bkp;
+                ns = bs;
+                nH = bH;
+                nE = T.E[bj];
+            }
+            __syncwarp();
+            if (lane == 0) T.flag[bj] |= 2;
+            __syncwarp();
+        }
+        ck = nk;
+        ckp = nkp;
+        cs = ns;
+        cH = nH;
+        cE = nE;
+        ncur = keep;
+        __syncwarp();  // every lane is done with the table before the next step refills it
+    }
+
+    if (overflow) {
+        if (lane == 0) n_out[qi] = -1;
+        return;
+    }
+    // redundancy filter over the band, best first
+    unsigned kept_mask = ncur >= 32 ? DV_FULL : ((1u << ncur) - 1);
+    if (p.redundancy) {
+        kept_mask = 0;
+        for (int r = 0; r < ncur; ++r) {
+            const int64_t rk = __shfl_sync(DV_FULL, ck, r);
+            const int64_t rkp = __shfl_sync(DV_FULL, ckp, r);
+            const int64_t rs = __shfl_sync(DV_FULL, cs, r);
+            const bool inside = ((kept_mask >> lane) & 1) &&
+                                ((rk >= ck && rk + rs <= ck + cs) || (rkp >= ckp && rkp + rs <= ckp + cs));
+            if (__ballot_sync(DV_FULL, inside) == 0) kept_mask |= 1u << r;
+        }
+    }
+    int64_t *o = out + qi * (int64_t)p.W * 4;
+    if ((kept_mask >> lane) & 1) {
+        const int pos = __popc(kept_mask & ((1u << lane) - 1));
+        o[4 * pos + 0] = ck;
+        o[4 * pos + 1] = ckp;
+        o[4 * pos + 2] = cs;
+        o[4 * pos + 3] = cH;
+    }
+    if (lane == 0) n_out[qi] = __popc(kept_mask);
+}
+
+}  // namespace
+
+int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
+                   const int32_t prm[6], int64_t *out, int64_t *n_out, cudaStream_t st) {
+    RB3_TRY(check_codes(q, total_q, st));
+    if (nq == 0) return RB3_OK;
+    const DvParams p{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5]};
+    const size_t smem = DV_WARPS * DV_WARP_BYTES;
+    const unsigned grid = (unsigned)((nq + DV_WARPS - 1) / DV_WARPS);
+    Phase ph("search.diversity", st);
+    RB3_WITH_NS(idx->D, RB3_CUDA_TRY(cudaFuncSetAttribute(k_diversity<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)smem));
+                RB3_LAUNCH(k_diversity<NS>, grid, 32 * DV_WARPS, smem, st, occ_view(idx), q, qoff, nq, p, out, n_out));
+    return RB3_OK;
+}
+
+}  // namespace rb3

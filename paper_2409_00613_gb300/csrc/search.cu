@@ -271,7 +271,7 @@ __global__ void k_smem_gather(const rb3_smem *__restrict__ in, const uint32_t *_
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-static int check_codes(const uint8_t *q, int64_t n, cudaStream_t st) {
+int check_codes(const uint8_t *q, int64_t n, cudaStream_t st) {
     if (n <= 0) return RB3_OK;
     DevBuf bad;
     RB3_TRY(bad.alloc(sizeof(int), st));

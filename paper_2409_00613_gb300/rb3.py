@@ -64,6 +64,8 @@ def lib():
             "rb3_merge_opts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rb3_append_batches": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
             "rb3_backward_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+            "rb3_haplotype_diversity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
+                                                       _vp, _vp, _vp]),
             "rb3_mem_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
                                               ctypes.POINTER(_i64), _vp]),
             "rb3_mem_search_opts": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp, _i64,
@@ -223,6 +225,21 @@ def rb3_backward_search(idx: Index, q, qoff, nq=None, lo_hi=None, stream=None):
         lo_hi = np.empty((nq, 2), dtype=np.int64)
     _check(lib().rb3_backward_search(idx.handle, _ptr(q), _ptr(qoff), nq, _ptr(lo_hi), _stream(stream)))
     return lo_hi
+
+
+def rb3_haplotype_diversity(idx: Index, q, qoff, a: int = 1, b: int = 3, gap_open: int = 5, gap_ext: int = 2,
+                            W: int = 25, redundancy: bool = True, nq=None, out=None, n_out=None, stream=None):
+    """Returns (out, n_out): out[i, :n_out[i]] are query i's (k, k', s, H)
+    records, best first.  Raises RB3Error (RB3_E_CAPACITY) when a query step
+    overflows its cell table; n_out of that query is then -1."""
+    nq = _len(qoff) - 1 if nq is None else nq
+    if out is None:
+        out = np.empty((nq, W, 4), dtype=np.int64)
+    if n_out is None:
+        n_out = np.empty(nq, dtype=np.int64)
+    _check(lib().rb3_haplotype_diversity(idx.handle, _ptr(q), _ptr(qoff), nq, a, b, gap_open, gap_ext, W,
+                                         int(redundancy), _ptr(out), _ptr(n_out), _stream(stream)))
+    return out, n_out
 
 
 def rb3_mem_search_opts(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opts=None, out=None, cap=None,
