@@ -131,30 +131,32 @@ def test_diversity_paper_example_and_refusals():
 
 
 def test_diversity_table_overflow_is_reported():
-    """Free gap opens and a large match score on an exact 400-symbol window
-    that starts past offset 2500 of a random 4000-symbol string: after the
-    window's last 300 symbols its own cell scores 3000, and deleting text
-    symbols one by one to its left keeps every left extension of it up to
-    2500 symbols long positive, 2500 distinct nodes in one step, more than
-    the 2048 the table holds.  That query reports -1 and RB3_E_CAPACITY; the
-    short queries beside it are still exact."""
+    """Free gap opens (a = 2, q = 0, e = 1) on an exact 1400-symbol window that
+    starts at offset 4000 of a random 8000-symbol string: after the window's
+    last k symbols its own cell scores 2k, and deleting text symbols one by
+    one to its left keeps every left extension of up to 2k - 1 symbols
+    positive, each a distinct node; past k = 1024 one step holds more than
+    the 2048 cells of the table.  That query reports -1 and RB3_E_CAPACITY;
+    the short queries beside it (at most about 900 cells a step in the
+    oracle) are still exact."""
     import torch
     import paper_2409_00613_gb300 as rb
     dev = torch.device("cuda:0")
     g = synth.rng(813)
-    T = synth.random_bases(g, 4000)
-    idx = rb.rb3_build_batch(torch.from_numpy(T).to(dev), np.array([4000], np.int64))
-    B = oracle.bwt(oracle.concat(T, np.array([4000]), True))
+    T = synth.random_bases(g, 8000)
+    idx = rb.rb3_build_batch(torch.from_numpy(T).to(dev), np.array([8000], np.int64))
+    B = oracle.bwt(oracle.concat(T, np.array([8000]), True))
     short = [T[100:112].copy(), T[2000:2015].copy()]
-    pats = [short[0], T[2600:3000].copy(), short[1]]
+    pats = [short[0], T[4000:5400].copy(), short[1]]
     q = np.concatenate(pats)
-    qoff = np.array([0, 12, 412, 427], np.int64)
+    qoff = np.array([0, 12, 1412, 1427], np.int64)
     out = np.zeros((3, 4, 4), np.int64)
     n = np.zeros(3, np.int64)
     with pytest.raises(rb.RB3Error) as e:
-        rb.rb3_haplotype_diversity(idx, q, qoff, 10, 3, 0, 1, 4, True, out=out, n_out=n)
+        rb.rb3_haplotype_diversity(idx, q, qoff, 2, 3, 0, 1, 4, True, out=out, n_out=n)
     assert e.value.code == rb.RB3_E_CAPACITY
     assert n[1] == -1
     for i in (0, 2):
-        want = oracle.haplotype_diversity(B, short[i // 2], 10, 3, 0, 1, W=4)
+        want = oracle.haplotype_diversity(B, short[i // 2], 2, 3, 0, 1, W=4)
+        assert len(want) > 0
         assert n[i] == len(want) and np.array_equal(out[i, :n[i]], want)
