@@ -361,6 +361,8 @@ def run_rb3(args, rank, world, local_rank):
             out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
         out["run_length"] = run_length_bench(rb, torch, S, idx, args, st, dev,
                                              out["mem_search"]["autotune_chunk_len"])
+        probe = (roof or {}).get("random_requests", {}).get("probe_G_per_s")
+        out["haplotype_diversity"] = diversity_bench(rb, torch, S, idx, st, dev, probe)
     idx.free()
     if not args.no_search and rank == 0:
         out["locate"] = locate_bench(rb, torch, S, args, st, dev, opts, batches, off)
@@ -487,6 +489,59 @@ def run_length_bench(rb, torch, S, idx, args, st, dev, chunk_len):
                              "equal_output": same})
         R.free()
     res["unit"] = "Mbp/s (mem_search_value)"
+    return res
+
+
+def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W=25):
+    """Local haplotype diversity of sliding k-mers of a new sample (a window
+    of one haplotype with 1% substitutions), one k-mer per query, default
+    scores, on the finished index: queries/s, and the kernel's rank-all reads
+    per second against the random-read probe (each read is a dependent random
+    32-byte access at D = 32)."""
+    g = synth.rng(synth.SEED_BASE + 77)
+    off = S.offsets
+    h = int(g.integers(0, len(S.lens)))
+    st0 = int(off[h] + g.integers(0, max(1, S.lens[h] - (n_kmers + k))))
+    win = S.seq[st0:st0 + n_kmers + k - 1].copy()
+    win[win == 0] = 1
+    sub = g.random(len(win)) < 0.01
+    win[sub] = (win[sub] % 4) + 1
+    nq = len(win) - k + 1
+    starts = np.arange(nq, dtype=np.int64)
+    q = win[starts[:, None] + np.arange(k)].reshape(-1).astype(np.uint8)
+    qoff = np.arange(nq + 1, dtype=np.int64) * k
+    dq, doff = torch.from_numpy(q).to(dev), torch.from_numpy(qoff).to(dev)
+    out = torch.empty((nq, W, 4), dtype=torch.int64, device=dev)
+    n_out = torch.empty(nq, dtype=torch.int64, device=dev)
+    res = {"workload": f"{nq} sliding {k}-mers of a haplotype window with 1% substitutions, scores a=1 b=3 q=5 e=2, "
+                       f"W={W}, redundancy filter on, on the finished index", "unit": "queries/s"}
+    try:
+        rb.rb3_haplotype_diversity(idx, dq, doff, 1, 3, 5, 2, W, True, out=out, n_out=n_out, stream=st)  # warm-up
+        torch.cuda.synchronize()
+        rb.rb3_diversity_stats(reset=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = 2
+        a.record(st)
+        for _ in range(reps):
+            rb.rb3_haplotype_diversity(idx, dq, doff, 1, 3, 5, 2, W, True, out=out, n_out=n_out, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        stats = rb.rb3_diversity_stats(reset=True)
+        reads = stats["rank_reads"] / reps
+        n = n_out.cpu().numpy()
+        res.update({"value": round(nq / (ms * 1e-3), 1), "ms": round(ms, 3), "records_per_query": round(float(n.mean()), 2),
+                    "queries_with_records": int((n > 0).sum()), "rank_reads_per_launch": int(reads),
+                    "cells_per_launch": int(stats["cells"] / reps),
+                    "rank_reads_G_per_s": round(reads / (ms * 1e-3) / 1e9, 3)})
+        if probe_g:
+            res["roofline"] = {"bound": "random_requests", "achieved": res["rank_reads_G_per_s"], "peak": probe_g,
+                               "unit": "G req/s", "frac": round(res["rank_reads_G_per_s"] / probe_g, 4),
+                               "what": "rank-all reads counted by the kernel over its CUDA-event time; ceiling: "
+                                       "the random-read probe of the merge walk's roofline"}
+    except rb.RB3Error as e:
+        res["error"] = str(e)
     return res
 
 

@@ -181,6 +181,12 @@ int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_
                             int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W, int32_t redundancy,
                             int64_t *out, int64_t *n_out, void *stream);
 
+/* Counters of rb3_haplotype_diversity since the last reset, summed over
+ * queries: out[0] = rank-all reads (two per extended cell: the ranks of every
+ * symbol at k and at k + s), out[1] = cells entered into the per-step tables.
+ * Synchronises the device; reset != 0 zeroes them after reading. */
+int rb3_diversity_stats(int64_t *out, int32_t reset);
+
 /* Locate (Section "Locating with FM-index", Algorithm 2): for each row i of
  * the BWT (0 <= rows[j] < n), out[2j] = the index of the string its suffix
  * starts in (strings numbered as concatenated: P0, rc(P0), P1, ... for a

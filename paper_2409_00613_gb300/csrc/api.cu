@@ -448,6 +448,13 @@ RB3_EXPORT int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, c
     return RB3_OK;
 }
 
+RB3_EXPORT int rb3_diversity_stats(int64_t *out, int32_t reset) {
+    g_err.clear();
+    RB3_CHECK_ARG(out != nullptr, "out is NULL");
+    RB3_CUDA_TRY(cudaDeviceSynchronize());
+    return diversity_stats(out, reset != 0);
+}
+
 RB3_EXPORT int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                                    int32_t min_len, int64_t min_occ, const rb3_opts *o, rb3_smem *out, int64_t cap,
                                    int64_t *n_out, void *stream) {

@@ -30,6 +30,10 @@ constexpr unsigned DV_FULL = 0xffffffffu;
 constexpr size_t DV_WARP_BYTES = (size_t)DV_CAP * (3 * 8 + 3 * 4 + 1);  // 16-byte multiple
 static_assert(DV_WARP_BYTES % 16 == 0, "per-warp table must keep 16-byte alignment");
 
+// Rank-all reads (two per extended cell) and cells entered, summed over
+// queries since the last reset.
+__device__ unsigned long long g_dv_stats[2];
+
 struct DvParams {
     int32_t a, b, q, e, W, redundancy;
 };
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
     int32_t cH = 0, cE = DV_NEG;
     int ncur = m > 0 ? 1 : 0;
     bool overflow = false;
+    unsigned long long n_ext = 0, n_cells = 0;  // warp-uniform counts
 
     for (int64_t i = m - 1; i >= 0 && ncur > 0 && !overflow; --i) {
         const int c = q[q0 + i];
@@ -162,6 +167,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
         {
             int64_t xk[4] = {0, 0, 0, 0}, xkp[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
             if (lane < ncur) dv_children<NS>(V, ck, ckp, cs, xk, xkp, xs);
+            n_ext += ncur;
             for (int t = 0; t < ncur && !overflow; ++t) {
                 const int32_t h = __shfl_sync(DV_FULL, cH, t);
 #pragma unroll
@@ -200,6 +206,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
                 }
                 any |= __ballot_sync(DV_FULL, act) != 0;
                 unsigned todo = __ballot_sync(DV_FULL, act && fv > 0);
+                n_ext += __popc(todo);
                 __syncwarp();
                 while (todo && !overflow) {
                     const int t = __ffs(todo) - 1;
@@ -217,6 +224,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
             if (!any) break;
             if (pass > DV_CAP) overflow = true;  // a chain cannot be longer than the table
         }
+        n_cells += tn;
         if (overflow) break;
         // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
         const int keep = min(tn, p.W);
@@ -272,6 +280,10 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
         __syncwarp();  // every lane is done with the table before the next step refills it
     }
 
+    if (lane == 0) {
+        atomicAdd(&g_dv_stats[0], 2 * n_ext);
+        atomicAdd(&g_dv_stats[1], n_cells);
+    }
     if (overflow) {
         if (lane == 0) n_out[qi] = -1;
         return;
@@ -301,6 +313,18 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
 }
 
 }  // namespace
+
+int diversity_stats(int64_t out[2], bool reset) {
+    unsigned long long h[2];
+    RB3_CUDA_TRY(cudaMemcpyFromSymbol(h, g_dv_stats, sizeof(h)));
+    out[0] = (int64_t)h[0];
+    out[1] = (int64_t)h[1];
+    if (reset) {
+        const unsigned long long z[2] = {0, 0};
+        RB3_CUDA_TRY(cudaMemcpyToSymbol(g_dv_stats, z, sizeof(z)));
+    }
+    return RB3_OK;
+}
 
 int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
                    const int32_t prm[6], int64_t *out, int64_t *n_out, cudaStream_t st) {

@@ -64,6 +64,7 @@ def lib():
             "rb3_merge_opts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rb3_append_batches": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
             "rb3_backward_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+            "rb3_diversity_stats": (ctypes.c_int, [_vp, _i32]),
             "rb3_haplotype_diversity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
                                                        _vp, _vp, _vp]),
             "rb3_mem_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _i64,
@@ -240,6 +241,14 @@ def rb3_haplotype_diversity(idx: Index, q, qoff, a: int = 1, b: int = 3, gap_ope
     _check(lib().rb3_haplotype_diversity(idx.handle, _ptr(q), _ptr(qoff), nq, a, b, gap_open, gap_ext, W,
                                          int(redundancy), _ptr(out), _ptr(n_out), _stream(stream)))
     return out, n_out
+
+
+def rb3_diversity_stats(reset: bool = False) -> dict:
+    """Rank-all reads and table cells of rb3_haplotype_diversity since the
+    last reset."""
+    out = np.zeros(2, dtype=np.int64)
+    _check(lib().rb3_diversity_stats(_ptr(out), int(reset)))
+    return {"rank_reads": int(out[0]), "cells": int(out[1])}
 
 
 def rb3_mem_search_opts(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opts=None, out=None, cap=None,
