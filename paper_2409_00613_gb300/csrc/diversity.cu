@@ -23,12 +23,16 @@
 namespace rb3 {
 namespace {
 
-constexpr int DV_WARPS = 2;     // queries per CTA
-constexpr int DV_CAP = 2048;    // cells one query step may hold
+// Two table sizes: every query first runs with small tables (eight warps a
+// CTA, two CTAs an SM); the queries whose step outgrew it run again with the
+// large one (two warps a CTA).
+constexpr int DV_CAP_S = 384, DV_WARPS_S = 8;
+constexpr int DV_CAP_L = 2048, DV_WARPS_L = 2;
 constexpr int32_t DV_NEG = -(1 << 30);
 constexpr unsigned DV_FULL = 0xffffffffu;
-constexpr size_t DV_WARP_BYTES = (size_t)DV_CAP * (3 * 8 + 3 * 4 + 1);  // 16-byte multiple
-static_assert(DV_WARP_BYTES % 16 == 0, "per-warp table must keep 16-byte alignment");
+__host__ __device__ constexpr size_t dv_warp_bytes(int cap) { return (size_t)cap * (3 * 8 + 3 * 4 + 1); }
+static_assert(dv_warp_bytes(DV_CAP_S) % 16 == 0 && dv_warp_bytes(DV_CAP_L) % 16 == 0,
+              "per-warp tables must keep 16-byte alignment");
 
 // Rank-all reads (two per extended cell) and cells entered, summed over
 // queries since the last reset.
@@ -45,15 +49,15 @@ struct DvTab {
     uint8_t *flag;  // bit 0: to be extended by deletions; bit 1: taken into the band
 };
 
-__device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
+template <int CAP> __device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
     DvTab t;
     t.k = reinterpret_cast<int64_t *>(base);
-    t.kp = t.k + DV_CAP;
-    t.s = t.kp + DV_CAP;
-    t.H = reinterpret_cast<int32_t *>(t.s + DV_CAP);
-    t.E = t.H + DV_CAP;
-    t.F = t.E + DV_CAP;
-    t.flag = reinterpret_cast<uint8_t *>(t.F + DV_CAP);
+    t.kp = t.k + CAP;
+    t.s = t.kp + CAP;
+    t.H = reinterpret_cast<int32_t *>(t.s + CAP);
+    t.E = t.H + CAP;
+    t.F = t.E + CAP;
+    t.flag = reinterpret_cast<uint8_t *>(t.F + CAP);
     return t;
 }
 
@@ -96,6 +100,7 @@ __device__ __forceinline__ int dv_find(const DvTab &T, int tn, int64_t k, int64_
 // Raises the cell (k, k', s) to H = max(H, h), E = max(E, ev), F = max(F, fv),
 // adding it when absent; a cell whose H or F rises is marked for deletion
 // extension.  Warp-uniform; returns the new cell count.
+template <int CAP>
 __device__ __forceinline__ int dv_upsert(const DvTab &T, int tn, int64_t k, int64_t kp, int64_t s, int32_t h,
                                          int32_t ev, int32_t fv, int lane, bool &overflow) {
     const int j = dv_find(T, tn, k, kp, s, lane);
@@ -116,7 +121,7 @@ __device__ __forceinline__ int dv_upsert(const DvTab &T, int tn, int64_t k, int6
         __syncwarp();
         return tn;
     }
-    if (tn >= DV_CAP) {
+    if (tn >= CAP) {
         overflow = true;
         return tn;
     }
@@ -142,15 +147,18 @@ __device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, i
     return s1 < s2;
 }
 
-template <int NS>
-__global__ void __launch_bounds__(32 * DV_WARPS)
-    k_diversity(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff, int64_t nq, DvParams p,
-                int64_t *__restrict__ out, int64_t *__restrict__ n_out) {
+// Queries sel[0 .. nsel) (all nsel = nq of them when sel is null), one warp each.
+template <int NS, int CAP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
+    k_diversity(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff,
+                const int64_t *__restrict__ sel, int64_t nsel, DvParams p, int64_t *__restrict__ out,
+                int64_t *__restrict__ n_out) {
     extern __shared__ __align__(16) uint8_t dv_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t qi = (int64_t)blockIdx.x * DV_WARPS + w;
-    if (qi >= nq) return;  // the whole warp leaves together
-    const DvTab T = dv_tab(dv_smem + (size_t)w * DV_WARP_BYTES);
+    const int64_t wi = (int64_t)blockIdx.x * WARPS + w;
+    if (wi >= nsel) return;  // the whole warp leaves together
+    const int64_t qi = sel ? sel[wi] : wi;
+    const DvTab T = dv_tab<CAP>(dv_smem + (size_t)w * dv_warp_bytes(CAP));
     const int64_t q0 = qoff[qi], m = qoff[qi + 1] - q0;
 
     // lane r holds the r-th kept cell; before any symbol only the root (H = 0)
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
                     const int64_t kp = __shfl_sync(DV_FULL, xkp[a - 1], t);
                     const int64_t s = __shfl_sync(DV_FULL, xs[a - 1], t);
                     const int32_t g = h + (a == c ? p.a : -p.b);
-                    if (s > 0 && g > 0 && !overflow) tn = dv_upsert(T, tn, k, kp, s, g, DV_NEG, DV_NEG, lane, overflow);
+                    if (s > 0 && g > 0 && !overflow) tn = dv_upsert<CAP>(T, tn, k, kp, s, g, DV_NEG, DV_NEG, lane, overflow);
                 }
             }
         }
@@ -188,7 +196,7 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
                 const int64_t k = __shfl_sync(DV_FULL, ck, t);
                 const int64_t kp = __shfl_sync(DV_FULL, ckp, t);
                 const int64_t s = __shfl_sync(DV_FULL, cs, t);
-                if (e1 > 0) tn = dv_upsert(T, tn, k, kp, s, e1, e1, DV_NEG, lane, overflow);
+                if (e1 > 0) tn = dv_upsert<CAP>(T, tn, k, kp, s, e1, e1, DV_NEG, lane, overflow);
             }
         }
         // deletion: a text symbol against a gap, until no cell is left to extend
@@ -217,12 +225,12 @@ __global__ void __launch_bounds__(32 * DV_WARPS)
                         const int64_t k = __shfl_sync(DV_FULL, yk[a], t);
                         const int64_t kp = __shfl_sync(DV_FULL, ykp[a], t);
                         const int64_t s = __shfl_sync(DV_FULL, ys[a], t);
-                        if (s > 0 && !overflow) tn = dv_upsert(T, tn, k, kp, s, f, DV_NEG, f, lane, overflow);
+                        if (s > 0 && !overflow) tn = dv_upsert<CAP>(T, tn, k, kp, s, f, DV_NEG, f, lane, overflow);
                     }
                 }
             }
             if (!any) break;
-            if (pass > DV_CAP) overflow = true;  // a chain cannot be longer than the table
+            if (pass > CAP) overflow = true;  // a chain cannot be longer than the table
         }
         n_cells += tn;
         if (overflow) break;
@@ -326,18 +334,37 @@ int diversity_stats(int64_t out[2], bool reset) {
     return RB3_OK;
 }
 
+template <int NS, int CAP, int WARPS>
+static int dv_launch(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *sel, int64_t nsel,
+                     const DvParams &p, int64_t *out, int64_t *n_out, cudaStream_t st) {
+    const size_t smem = WARPS * dv_warp_bytes(CAP);
+    auto kern = k_diversity<NS, CAP, WARPS>;
+    RB3_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)((nsel + WARPS - 1) / WARPS);
+    RB3_LAUNCH(kern, grid, 32 * WARPS, smem, st, occ_view(idx), q, qoff, sel, nsel, p, out, n_out);
+    return RB3_OK;
+}
+
 int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
                    const int32_t prm[6], int64_t *out, int64_t *n_out, cudaStream_t st) {
     RB3_TRY(check_codes(q, total_q, st));
     if (nq == 0) return RB3_OK;
     const DvParams p{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5]};
-    const size_t smem = DV_WARPS * DV_WARP_BYTES;
-    const unsigned grid = (unsigned)((nq + DV_WARPS - 1) / DV_WARPS);
     Phase ph("search.diversity", st);
-    RB3_WITH_NS(idx->D, RB3_CUDA_TRY(cudaFuncSetAttribute(k_diversity<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)smem));
-                RB3_LAUNCH(k_diversity<NS>, grid, 32 * DV_WARPS, smem, st, occ_view(idx), q, qoff, nq, p, out, n_out));
-    return RB3_OK;
+    RB3_WITH_NS(idx->D, RB3_TRY((dv_launch<NS, DV_CAP_S, DV_WARPS_S>(idx, q, qoff, nullptr, nq, p, out, n_out, st))));
+    // the queries that outgrew the small table, again with the large one
+    std::vector<int64_t> n(nq), sel;
+    RB3_CUDA_TRY(cudaMemcpyAsync(n.data(), n_out, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < nq; ++i)
+        if (n[i] < 0) sel.push_back(i);
+    if (sel.empty()) return RB3_OK;
+    DevBuf ds;
+    RB3_TRY(ds.alloc(sizeof(int64_t) * sel.size(), st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(ds.p, sel.data(), sizeof(int64_t) * sel.size(), cudaMemcpyHostToDevice, st));
+    RB3_WITH_NS(idx->D, RB3_TRY((dv_launch<NS, DV_CAP_L, DV_WARPS_L>(idx, q, qoff, ds.as<int64_t>(),
+                                                                     (int64_t)sel.size(), p, out, n_out, st))));
+    return RB3_OK;  // ds is freed in stream order after the launch
 }
 
 }  // namespace rb3
