@@ -24,9 +24,9 @@ namespace rb3 {
 namespace {
 
 // Two table sizes: every query first runs with small tables (eight warps a
-// CTA, two CTAs an SM); the queries whose step outgrew it run again with the
+// CTA, three CTAs an SM at D = 32); the queries whose step outgrew it run again with the
 // large one (two warps a CTA).
-constexpr int DV_CAP_S = 384, DV_WARPS_S = 8;
+constexpr int DV_CAP_S = 256, DV_WARPS_S = 8;
 constexpr int DV_CAP_L = 2048, DV_WARPS_L = 2;
 constexpr int32_t DV_NEG = -(1 << 30);
 constexpr unsigned DV_FULL = 0xffffffffu;
