@@ -67,11 +67,22 @@ def check_all(B, got, n_got, q, qoff, a, b, go, ge, W, red):
 @pytest.mark.parametrize("layout", ["d32", "d64", "rle512"])
 @pytest.mark.parametrize("scores", SCORES)
 def test_diversity_vs_oracle(layout, scores):
+    run_layout(layout, scores)
+
+
+@pytest.mark.parametrize("layout", ["d128", "d256", "rle4096"])
+def test_diversity_other_layouts(layout):
+    """The remaining rank layouts under two score sets."""
+    for scores in (SCORES[0], SCORES[2]):
+        run_layout(layout, scores)
+
+
+def run_layout(layout, scores):
     import torch
     import paper_2409_00613_gb300 as rb
     a, b, go, ge, W = scores
     S, B = index_case()
-    D = 64 if layout == "d64" else 32
+    D = int(layout[1:]) if layout.startswith("d") else 32
     dev = torch.device("cuda:0")
     off = S.offsets
     half = off[3]
@@ -79,8 +90,8 @@ def test_diversity_vs_oracle(layout, scores):
                              opts={"occ_interval": D})
     rb.rb3_merge(idx, rb.rb3_build_batch(torch.from_numpy(S.seq[half:].copy()).to(dev), S.lens[3:].copy(),
                                          opts={"occ_interval": D}))
-    if layout == "rle512":
-        idx = rb.rb3_index_compress(idx, 512)
+    if layout.startswith("rle"):
+        idx = rb.rb3_index_compress(idx, int(layout[3:]))
     q, qoff = diversity_queries(S, 812 + a + 7 * W, 120)
     for red in (True, False):
         got, n_got = rb.rb3_haplotype_diversity(idx, q, qoff, a, b, go, ge, W, red)
