@@ -9,8 +9,8 @@
 // lane; a step's candidates go into a table of the warp's own in shared memory
 // (found by a warp-wide compare, written by lane 0).  Only candidates with a
 // positive score enter the table: a cell whose H never rises above 0 extends
-// nothing (a match, an insertion or a deletion from it stays below 0), so the
-// cells with H > 0 and their scores are those of the full recurrence.
+// nothing (a match, an insertion or a deletion from it stays at or below 0),
+// so the cells with H > 0 and their scores are those of the full recurrence.
 //   match / mismatch  H(child) = H + a or H - b (N in P mismatches everything)
 //   insertion         E = max(H - q, E) - e, same node, next query position
 //   deletion          F(child) = max(H - q, F) - e, same query position, until
@@ -24,8 +24,8 @@ namespace rb3 {
 namespace {
 
 // Two table sizes: every query first runs with small tables (eight warps a
-// CTA, three CTAs an SM at D = 32); the queries whose step outgrew it run again with the
-// large one (two warps a CTA).
+// CTA, three CTAs an SM at D = 32); the queries whose step outgrew theirs run
+// again with the large one (two warps a CTA).
 constexpr int DV_CAP_S = 256, DV_WARPS_S = 8;
 constexpr int DV_CAP_L = 2048, DV_WARPS_L = 2;
 constexpr int32_t DV_NEG = -(1 << 30);
