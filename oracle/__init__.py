@@ -85,6 +85,9 @@ def lib():
         L.orc_diversity.argtypes = [_u8p, ctypes.c_int64, _u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i64p,
                                     ctypes.c_int64]
+        L.orc_bwasw.restype = ctypes.c_int64
+        L.orc_bwasw.argtypes = [_u8p, ctypes.c_int64, _u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p, ctypes.c_int64]
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -269,6 +272,25 @@ def haplotype_diversity(B, P, a: int = 1, b: int = 3, q: int = 5, e: int = 2, W:
     out = np.empty((max(n, 1), 4), dtype=np.int64)
     L.orc_diversity(pb, len(B), pp, len(P), a, b, q, e, W, int(redundancy), out.ctypes.data_as(_i64p), n)
     return out[:n].copy()
+
+
+def bwasw(B, P, a: int = 1, b: int = 3, q: int = 5, e: int = 2, W: int = 25) -> np.ndarray:
+    """Section "Finding inexact matches with BWA-SW": Algorithm 5 between the
+    prefix DAWG of P (built from the BWT of the one-string text P$) and that
+    of the indexed text; (N, 6) int64 records (uk, us, k, k', s, H): a query
+    node (the SA interval (uk, us) of its strings in P$) and a text node with
+    H > 0, the band of W cells per query node (0: no band), sorted by query
+    node, then H descending, k, k', s."""
+    B, pb = _u8(B)
+    P = np.asarray(P, dtype=np.uint8)
+    BP, pbp = _u8(bwt(concat(P, np.array([len(P)], np.int64), False)))
+    L = lib()
+    n = L.orc_bwasw(pb, len(B), pbp, len(BP), a, b, q, e, W, None, 0)
+    out = np.empty((max(n, 1), 6), dtype=np.int64)
+    L.orc_bwasw(pb, len(B), pbp, len(BP), a, b, q, e, W, out.ctypes.data_as(_i64p), n)
+    out = out[:n]
+    order = np.lexsort((out[:, 4], out[:, 3], out[:, 2], -out[:, 5], out[:, 1], out[:, 0]))
+    return out[order].copy()
 
 
 def occ_brute(T, P) -> int:

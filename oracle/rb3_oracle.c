@@ -607,6 +607,130 @@ int64_t orc_diversity(const uint8_t *B, int64_t n, const uint8_t *P, int64_t m, 
     return nout;
 }
 
+/* ------------------------------------------------------------------------
+ * Section "Finding inexact matches with BWA-SW": Algorithm 5 between the prefix
+ * DAWG of a query P, stored explicitly (nodes are the SA intervals (k, s) of
+ * P's substrings in the BWT BP of the one-string text P$, an edge x -> cx for
+ * every symbol c A..N with cx in P), and the prefix DAWG of the indexed text,
+ * walked implicitly by BackwardExt (nodes are bi-intervals, children by A..T).
+ * Query nodes are taken in a topological order (Kahn's algorithm over the
+ * edges); the pair of roots starts with H = 0 and is extended although H is
+ * not positive; every other cell is kept while H > 0.  Scores, gaps, node
+ * identity, the deletion closure and the band (W, 0 = none, after the
+ * deletions of each query node) are those of orc_diversity.
+ * Writes (uk, us, k, k', s, H) for every kept cell of every query node but
+ * the root (at most cap records) and returns their number.
+ * Test infrastructure: small inputs, lists searched linearly.
+ * ---------------------------------------------------------------------- */
+typedef struct { int64_t k, s; } pnode_t;
+
+int64_t orc_bwasw(const uint8_t *B, int64_t n, const uint8_t *BP, int64_t np, int64_t a, int64_t b, int64_t q,
+                  int64_t e, int64_t W, int64_t *out, int64_t cap)
+{
+    orc_rank_t *r = rank_new(B, n), *rp = rank_new(BP, np);
+    /* the query DAWG: nodes by breadth-first BackwardExt from the root */
+    int64_t nn = 1, ncap = 64, ne = 0, ecap = 64;
+    pnode_t *nodes = (pnode_t *)malloc(sizeof(pnode_t) * ncap);
+    int64_t(*edge)[3] = (int64_t(*)[3])malloc(sizeof(int64_t[3]) * ecap); /* from, to, symbol */
+    nodes[0].k = 0;
+    nodes[0].s = np;
+    for (int64_t u = 0; u < nn; ++u)
+        for (int c = 1; c <= 5; ++c) {
+            const int64_t lo = pi_B(rp, c, nodes[u].k), hi = pi_B(rp, c, nodes[u].k + nodes[u].s);
+            if (hi == lo) continue;
+            int64_t v = 0;
+            while (v < nn && !(nodes[v].k == lo && nodes[v].s == hi - lo)) ++v;
+            if (v == nn) {
+                if (nn == ncap) nodes = (pnode_t *)realloc(nodes, sizeof(pnode_t) * (ncap *= 2));
+                nodes[nn].k = lo;
+                nodes[nn].s = hi - lo;
+                ++nn;
+            }
+            if (ne == ecap) edge = (int64_t(*)[3])realloc(edge, sizeof(int64_t[3]) * (ecap *= 2));
+            edge[ne][0] = u;
+            edge[ne][1] = v;
+            edge[ne][2] = c;
+            ++ne;
+        }
+    /* a topological order (Kahn) */
+    int64_t *indeg = (int64_t *)calloc((size_t)nn, sizeof(int64_t)), *order = (int64_t *)malloc(sizeof(int64_t) * nn);
+    for (int64_t i = 0; i < ne; ++i) ++indeg[edge[i][1]];
+    int64_t no = 0;
+    order[no++] = 0;
+    for (int64_t h = 0; h < no; ++h)
+        for (int64_t i = 0; i < ne; ++i)
+            if (edge[i][0] == order[h] && --indeg[edge[i][1]] == 0) order[no++] = edge[i][1];
+    /* cells of every query node */
+    dlist_t *cells = (dlist_t *)calloc((size_t)nn, sizeof(dlist_t));
+    int64_t ri = dlist_get(&cells[0], (biint_t){0, 0, n});
+    cells[0].c[ri].H = 0;
+    int64_t nout = 0;
+    for (int64_t h = 1; h < no; ++h) {
+        const int64_t u = order[h];
+        dlist_t *nxt = &cells[u];
+        for (int64_t i = 0; i < ne; ++i) {
+            if (edge[i][1] != u) continue;
+            const dlist_t *pre = &cells[edge[i][0]];
+            const int c = (int)edge[i][2];
+            for (int64_t t = 0; t < pre->n; ++t) { /* match or mismatch */
+                const dcell_t cc = pre->c[t];
+                for (int x = 1; x <= 4; ++x) {
+                    biint_t v = backward_ext(r, (biint_t){cc.k, cc.kp, cc.s}, x);
+                    if (v.s == 0) continue;
+                    int64_t j = dlist_get(nxt, v);
+                    nxt->c[j].H = dmax(nxt->c[j].H, cc.H + (x == c ? a : -b));
+                }
+            }
+            for (int64_t t = 0; t < pre->n; ++t) { /* insertion: the query symbol against a gap */
+                const dcell_t cc = pre->c[t];
+                const int64_t ev = dmax(cc.H - q, cc.E) - e;
+                int64_t j = dlist_get(nxt, (biint_t){cc.k, cc.kp, cc.s});
+                nxt->c[j].E = dmax(nxt->c[j].E, ev);
+                nxt->c[j].H = dmax(nxt->c[j].H, nxt->c[j].E);
+            }
+        }
+        for (int changed = 1; changed;) { /* deletion, to the closure */
+            changed = 0;
+            for (int64_t t = 0; t < nxt->n; ++t) {
+                if (nxt->c[t].H <= 0) continue;
+                for (int x = 1; x <= 4; ++x) {
+                    const dcell_t cc = nxt->c[t];
+                    biint_t v = backward_ext(r, (biint_t){cc.k, cc.kp, cc.s}, x);
+                    if (v.s == 0) continue;
+                    const int64_t fv = dmax(cc.H - q, cc.F) - e;
+                    int64_t j = dlist_get(nxt, v);
+                    if (fv > nxt->c[j].F) {
+                        nxt->c[j].F = fv;
+                        nxt->c[j].H = dmax(nxt->c[j].H, fv);
+                        changed = 1;
+                    }
+                }
+            }
+        }
+        int64_t kept = 0; /* the cells: H > 0 */
+        for (int64_t t = 0; t < nxt->n; ++t)
+            if (nxt->c[t].H > 0) nxt->c[kept++] = nxt->c[t];
+        nxt->n = kept;
+        qsort(nxt->c, (size_t)nxt->n, sizeof(dcell_t), dcell_cmp);
+        if (W > 0 && nxt->n > W) nxt->n = W; /* the band */
+        for (int64_t t = 0; t < nxt->n; ++t, ++nout)
+            if (nout < cap) {
+                int64_t *o = out + 6 * nout;
+                o[0] = nodes[u].k; o[1] = nodes[u].s;
+                o[2] = nxt->c[t].k; o[3] = nxt->c[t].kp; o[4] = nxt->c[t].s; o[5] = nxt->c[t].H;
+            }
+    }
+    for (int64_t u = 0; u < nn; ++u) free(cells[u].c);
+    free(cells);
+    free(indeg);
+    free(order);
+    free(edge);
+    free(nodes);
+    rank_free(rp);
+    rank_free(r);
+    return nout;
+}
+
 int64_t orc_smem_mt(const uint8_t *B, int64_t n, const uint8_t *q, const int64_t *qoff, int64_t nq,
                     int64_t ell, int64_t smin, int64_t *out, int64_t cap, int nthreads)
 {

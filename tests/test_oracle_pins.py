@@ -609,3 +609,92 @@ def test_diversity_degenerate_queries():
     top = oracle.haplotype_diversity(B, P, a=2)[0]
     assert top[3] == 2 * len(P)
     assert (top[0], top[2]) == (oracle.lo_brute(T, P), oracle.occ_brute(T, P))
+
+
+# ---- Section "Finding inexact matches with BWA-SW" (Algorithm 5, DAWG to DAWG) ----
+
+def py_bwasw(T, strings, P, a, b, q, e):
+    """Pair by pair: for every distinct substring x of P and y of the
+    double-strand text T (of the list `strings`), the pruned end-to-end score
+    of x against y (py_diversity with x as the query), keyed by x's SA
+    interval in the text P$ and y's bi-interval, the best pair of each key
+    kept."""
+    TP = oracle.concat(enc(P), np.array([len(P)]), False)
+    xs = {P[i:j] for i in range(len(P)) for j in range(i + 1, len(P) + 1)}
+    cells = {}
+    for x in xs:
+        ukey = (oracle.lo_brute(TP, enc(x)), oracle.occ_brute(TP, enc(x)))
+        for key, h in diversity_from_strings(T, py_diversity(strings, x, a, b, q, e)).items():
+            k = ukey + key
+            cells[k] = max(cells.get(k, -(1 << 40)), h)
+    return cells
+
+
+@pytest.mark.parametrize("scores", [(1, 3, 5, 2), (2, 1, 2, 1), (3, 2, 1, 1)])
+def test_bwasw_unbanded_equals_pair_brute_force(scores):
+    """No band: every (query node, text node) cell with H > 0 equals the best
+    pruned score over the string pairs of that pair of intervals."""
+    a, b, q, e = scores
+    g = synth.rng(880 + a + 10 * b)
+    n_cells = 0
+    for trial in range(6):
+        S, strs = rand_list(g, int(g.integers(1, 3)), 16, n_frac=0.03, allow_empty=False)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        m = int(g.integers(1, 7))
+        if g.random() < 0.6 and len(S.seq) > m:
+            st = int(g.integers(0, len(S.seq) - m))
+            P = S.seq[st:st + m].copy()
+            P[P == 0] = 1
+            if g.random() < 0.5:
+                P[int(g.integers(0, m))] = int(g.integers(1, 6))
+        else:
+            P = synth.random_bases(g, m)
+        got = oracle.bwasw(B, P, a, b, q, e, W=0)
+        want = py_bwasw(T, strs, dec(P), a, b, q, e)
+        assert {tuple(r[:5]): r[5] for r in got.tolist()} == want
+        n_cells += len(got)
+    assert n_cells >= 10
+
+
+def test_bwasw_band_and_worked_example():
+    """Band: at most W cells per query node, none above its unbanded score.
+    The section's example text CAAGCAG with query AGCA: the query node of
+    AGCA (which also holds AG and AGC, occurring once in P) reaches AGCA in the
+    text with 4a, and the node of A reaches the text's A with a."""
+    g = synth.rng(885)
+    S = synth.pangenome(seed=886, founder_len=200, n_hap=4, batch=4)
+    T = oracle.concat(S.seq, S.lens, True)
+    B = oracle.bwt(T)
+    for _ in range(4):
+        P = S.seq[int(g.integers(0, 300)):][:12].copy()
+        P[P == 0] = 1
+        full = {tuple(r[:5]): r[5] for r in oracle.bwasw(B, P, W=0).tolist()}
+        for W in (1, 4):
+            band = oracle.bwasw(B, P, W=W)
+            per_node = {}
+            for r in band.tolist():
+                per_node[(r[0], r[1])] = per_node.get((r[0], r[1]), 0) + 1
+                assert tuple(r[:5]) in full and r[5] <= full[tuple(r[:5])]
+            assert max(per_node.values()) <= W
+    text = "CAAGCAG"
+    T = oracle.concat(enc(text), np.array([7]), True)
+    B = oracle.bwt(T)
+    TP = oracle.concat(enc("AGCA"), np.array([4]), False)
+    got = {tuple(r[:5]): r[5] for r in oracle.bwasw(B, enc("AGCA"), 3, 3, 5, 2, W=0).tolist()}
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+    def key(x, y):
+        rc = "".join(comp[c] for c in reversed(y))
+        return (oracle.lo_brute(TP, enc(x)), oracle.occ_brute(TP, enc(x)), oracle.lo_brute(T, enc(y)),
+                oracle.lo_brute(T, enc(rc)), oracle.occ_brute(T, enc(y)))
+
+    assert got[key("AGCA", "AGCA")] == 12
+    assert got[key("A", "A")] == 3
+    assert key("AG", "AGCA")[:2] == key("AGCA", "AGCA")[:2]
+    # an N in the query is a node of its own DAWG that mismatches every text symbol
+    # (ANCA against AGCA stays positive from the end: 3, 6, 3, 6)
+    got = {tuple(r[:5]): r[5] for r in oracle.bwasw(B, enc("ANCA"), 3, 3, 5, 2, W=0).tolist()}
+    assert got == py_bwasw(T, [text], "ANCA", 3, 3, 5, 2)
+    TP = oracle.concat(enc("ANCA"), np.array([4]), False)
+    assert got[key("ANCA", "AGCA")] == 3 * 3 - 3
