@@ -540,8 +540,8 @@ def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W
                                "unit": "G req/s", "frac": round(res["rank_reads_G_per_s"] / probe_g, 4),
                                "what": "rank-all reads counted by the kernel over its CUDA-event time; ceiling: "
                                        "the random-read probe of the merge walk's roofline"}
-    except rb.RB3Error as e:
-        res["error"] = str(e)
+    except (rb.RB3Error, RuntimeError) as e:  # a side leg: record the failure, keep the bench line
+        res["error"] = f"{type(e).__name__}: {e}"
     return res
 
 
