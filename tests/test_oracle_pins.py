@@ -698,3 +698,25 @@ def test_bwasw_band_and_worked_example():
     assert got == py_bwasw(T, [text], "ANCA", 3, 3, 5, 2)
     TP = oracle.concat(enc("ANCA"), np.array([4]), False)
     assert got[key("ANCA", "AGCA")] == 3 * 3 - 3
+
+
+def test_bwasw_node_of_whole_query_equals_linear_runs():
+    """The query node holding all of P also holds every prefix of P that
+    occurs once in P (same SA interval in P$); its cells are, text node by
+    text node, the best of the linear-query runs of those strings."""
+    g = synth.rng(890)
+    for trial in range(10):
+        S, _ = rand_list(g, int(g.integers(1, 3)), 30, allow_empty=False)
+        T = oracle.concat(S.seq, S.lens, True)
+        B = oracle.bwt(T)
+        P = synth.random_bases(g, int(g.integers(3, 9)))
+        TP = oracle.concat(P, np.array([len(P)]), False)
+        node = (oracle.lo_brute(TP, P), 1)
+        members = [P[:j] for j in range(1, len(P) + 1) if oracle.occ_brute(TP, P[:j]) == 1]
+        assert all(oracle.lo_brute(TP, x) == node[0] for x in members)
+        want = {}
+        for x in members:
+            for r in oracle.haplotype_diversity(B, x, 3, 2, 1, 1, W=0, redundancy=False).tolist():
+                want[tuple(r[:3])] = max(want.get(tuple(r[:3]), -1), r[3])
+        got = {tuple(r[2:5]): r[5] for r in oracle.bwasw(B, P, 3, 2, 1, 1, W=0).tolist() if (r[0], r[1]) == node}
+        assert got == want
