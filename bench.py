@@ -370,6 +370,8 @@ def run_rb3(args, rank, world, local_rank):
         out["served_full"] = served_full(rb, torch, st, dev, opts)
     if rank == 0 and not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_sample(S)
+        if "haplotype_diversity" in out:
+            out["haplotype_diversity"]["cpu_baseline"] = diversity_cpu_sample(S)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -543,6 +545,32 @@ def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W
     except (rb.RB3Error, RuntimeError) as e:  # a side leg: record the failure, keep the bench line
         res["error"] = f"{type(e).__name__}: {e}"
     return res
+
+
+def diversity_cpu_sample(S, window: int = 20_000, k: int = 51, nq: int = 300, W: int = 25):
+    """The oracle's haplotype diversity on a bounded sample of the same
+    workload: the double-strand BWT (naive sort, untimed) of the first
+    `window` bp of every haplotype, and `nq` sliding k-mers of one haplotype's
+    window with 1% substitutions, default scores; one thread."""
+    import oracle
+    off = S.offsets
+    wins = [S.seq[off[h]:off[h] + min(window, S.lens[h])] for h in range(len(S.lens))]
+    lens = np.array([len(w) for w in wins], dtype=np.int64)
+    B = oracle.bwt(oracle.concat(np.concatenate(wins), lens, True))
+    g = synth.rng(synth.SEED_BASE + 78)
+    win = wins[int(g.integers(0, len(wins)))][:nq + k - 1].copy()
+    win[win == 0] = 1
+    sub = g.random(len(win)) < 0.01
+    win[sub] = (win[sub] % 4) + 1
+    n = len(win) - k + 1
+    t = time.perf_counter()
+    for i in range(n):
+        oracle.haplotype_diversity(B, win[i:i + k], 1, 3, 5, 2, W=W)
+    dt = time.perf_counter() - t
+    return {"value": round(n / dt, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} sliding {k}-mers of one haplotype's first {window} bp with 1% substitutions against "
+                      f"the oracle's double-strand BWT of the first {window} bp of all {len(wins)} haplotypes "
+                      f"({len(B)} symbols): {dt:.2f} s"}
 
 
 def mem_search(rb, torch, S, idx, args, st, dev):
