@@ -371,7 +371,10 @@ def run_rb3(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_sample(S)
         if "haplotype_diversity" in out:
-            out["haplotype_diversity"]["cpu_baseline"] = diversity_cpu_sample(S)
+            try:  # a side leg: a failure is recorded, the bench line still printed
+                out["haplotype_diversity"]["cpu_baseline"] = diversity_cpu_sample(S)
+            except (RuntimeError, OSError, ValueError) as e:
+                out["haplotype_diversity"]["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
