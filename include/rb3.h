@@ -1,7 +1,7 @@
 /*
  * rb3.h -- C ABI of librb3.so: GB300 (sm_103a) multi-string double-strand BWT
- * construction by batch build + merge, and backward / SMEM search on the
- * result.  The method is H. Li, "BWT construction and search at the terabase
+ * construction by batch build + merge, and backward / SMEM search and local
+ * haplotype diversity on the result.  The method is H. Li, "BWT construction and search at the terabase
  * scale" (arXiv 2409.00613); each call cites the passage that defines what it
  * computes.  All arithmetic is integer and exact.
  *
@@ -20,8 +20,8 @@
  *    the call returns.
  *  Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
  *    Every device operation is enqueued on it.  Calls whose result size is
- *    data dependent (build, merge, mem_search) synchronize that stream before
- *    they return; the others return once the work is enqueued when all their
+ *    data dependent (build, merge, mem_search, haplotype_diversity)
+ *    synchronize that stream before they return; the others return once the work is enqueued when all their
  *    outputs are device memory.
  *  Ownership.  The library owns every rb3_index and its scratch memory
  *    (stream-ordered cudaMallocAsync); callers own every output buffer.
