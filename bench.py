@@ -497,12 +497,9 @@ def run_length_bench(rb, torch, S, idx, args, st, dev, chunk_len):
     return res
 
 
-def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W=25):
-    """Local haplotype diversity of sliding k-mers of a new sample (a window
-    of one haplotype with 1% substitutions), one k-mer per query, default
-    scores, on the finished index: queries/s, and the kernel's rank-all reads
-    per second against the random-read probe (each read is a dependent random
-    32-byte access at D = 32)."""
+def diversity_kmers(S, k=51, n_kmers=20_000):
+    """The diversity leg's queries: the n_kmers sliding k-mers of a window of
+    one haplotype with 1% substitutions (a new sample), back to back."""
     g = synth.rng(synth.SEED_BASE + 77)
     off = S.offsets
     h = int(g.integers(0, len(S.lens)))
@@ -515,6 +512,17 @@ def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W
     starts = np.arange(nq, dtype=np.int64)
     q = win[starts[:, None] + np.arange(k)].reshape(-1).astype(np.uint8)
     qoff = np.arange(nq + 1, dtype=np.int64) * k
+    return q, qoff
+
+
+def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W=25):
+    """Local haplotype diversity of sliding k-mers of a new sample (a window
+    of one haplotype with 1% substitutions), one k-mer per query, default
+    scores, on the finished index: queries/s, and the kernel's rank-all reads
+    per second against the random-read probe (each read is a dependent random
+    32-byte access at D = 32)."""
+    q, qoff = diversity_kmers(S, k, n_kmers)
+    nq = len(qoff) - 1
     dq, doff = torch.from_numpy(q).to(dev), torch.from_numpy(qoff).to(dev)
     out = torch.empty((nq, W, 4), dtype=torch.int64, device=dev)
     n_out = torch.empty(nq, dtype=torch.int64, device=dev)

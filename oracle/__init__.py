@@ -85,6 +85,10 @@ def lib():
         L.orc_diversity.argtypes = [_u8p, ctypes.c_int64, _u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i64p,
                                     ctypes.c_int64]
+        L.orc_diversity_many.restype = None
+        L.orc_diversity_many.argtypes = [_u8p, ctypes.c_int64, _u8p, _i64p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                         _i64p, _i64p]
         L.orc_bwasw.restype = ctypes.c_int64
         L.orc_bwasw.argtypes = [_u8p, ctypes.c_int64, _u8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p, ctypes.c_int64]
@@ -272,6 +276,22 @@ def haplotype_diversity(B, P, a: int = 1, b: int = 3, q: int = 5, e: int = 2, W:
     out = np.empty((max(n, 1), 4), dtype=np.int64)
     L.orc_diversity(pb, len(B), pp, len(P), a, b, q, e, W, int(redundancy), out.ctypes.data_as(_i64p), n)
     return out[:n].copy()
+
+
+def haplotype_diversity_many(B, q, qoff, a: int = 1, b: int = 3, gq: int = 5, e: int = 2, W: int = 25,
+                             redundancy: bool = True):
+    """haplotype_diversity for every query q[qoff[i]:qoff[i+1]] with one
+    rank table over B (W >= 1): (out (nq, W, 4), n_out (nq,))."""
+    assert W >= 1
+    B, pb = _u8(B)
+    q, pq = _u8(q)
+    qoff, po = _i64(qoff)
+    nq = len(qoff) - 1
+    out = np.zeros((max(nq, 1), W, 4), dtype=np.int64)
+    n_out = np.zeros(max(nq, 1), dtype=np.int64)
+    lib().orc_diversity_many(pb, len(B), pq, po, nq, a, b, gq, e, W, int(redundancy), out.ctypes.data_as(_i64p),
+                             n_out.ctypes.data_as(_i64p))
+    return out[:nq], n_out[:nq]
 
 
 def bwasw(B, P, a: int = 1, b: int = 3, q: int = 5, e: int = 2, W: int = 25) -> np.ndarray:

@@ -526,10 +526,9 @@ static int dcell_cmp(const void *pa, const void *pb)
 
 static int64_t dmax(int64_t x, int64_t y) { return x > y ? x : y; }
 
-int64_t orc_diversity(const uint8_t *B, int64_t n, const uint8_t *P, int64_t m, int64_t a, int64_t b, int64_t q,
-                      int64_t e, int64_t W, int redundancy, int64_t *out, int64_t cap)
+static int64_t diversity_one(const orc_rank_t *r, int64_t n, const uint8_t *P, int64_t m, int64_t a, int64_t b,
+                             int64_t q, int64_t e, int64_t W, int redundancy, int64_t *out, int64_t cap)
 {
-    orc_rank_t *r = rank_new(B, n);
     dlist_t cur = {0, 0, 0}, nxt = {0, 0, 0};
     biint_t root = {0, 0, n};
     int64_t ri = dlist_get(&cur, root);
@@ -603,8 +602,29 @@ int64_t orc_diversity(const uint8_t *B, int64_t n, const uint8_t *P, int64_t m, 
     free(kept);
     free(cur.c);
     free(nxt.c);
+    return nout;
+}
+
+int64_t orc_diversity(const uint8_t *B, int64_t n, const uint8_t *P, int64_t m, int64_t a, int64_t b, int64_t q,
+                      int64_t e, int64_t W, int redundancy, int64_t *out, int64_t cap)
+{
+    orc_rank_t *r = rank_new(B, n);
+    const int64_t nout = diversity_one(r, n, P, m, a, b, q, e, W, redundancy, out, cap);
     rank_free(r);
     return nout;
+}
+
+/* orc_diversity for the queries q[qoff[i] .. qoff[i+1]), one rank table for
+ * all of them: query i's records (at most W, W >= 1) at out + 4*W*i, their
+ * number in n_out[i]. */
+void orc_diversity_many(const uint8_t *B, int64_t n, const uint8_t *qs, const int64_t *qoff, int64_t nq, int64_t a,
+                        int64_t b, int64_t q, int64_t e, int64_t W, int redundancy, int64_t *out, int64_t *n_out)
+{
+    orc_rank_t *r = rank_new(B, n);
+    for (int64_t i = 0; i < nq; ++i)
+        n_out[i] = diversity_one(r, n, qs + qoff[i], qoff[i + 1] - qoff[i], a, b, q, e, W, redundancy,
+                                 out + 4 * W * i, W);
+    rank_free(r);
 }
 
 /* ------------------------------------------------------------------------

@@ -2,8 +2,9 @@
 50 haplotypes, batches of 10, both strands, ~500 Msym), in the configuration
 bench.py times (default options), against the oracle's own incremental build
 (naive sort per haplotype + Algorithm 1 merges), plus the LF-decode certificate;
-MEM search on the finished index checked on a sample of the 1 M queries; and a
-reduced instance of the uneven-genome workload (clusters, N-runs)."""
+MEM search on the finished index checked on a sample of the 1 M queries,
+haplotype diversity on a sample of the bench's sliding k-mers, and a reduced
+instance of the uneven-genome workload (clusters, N-runs)."""
 import os
 
 import numpy as np
@@ -71,6 +72,30 @@ def test_pangenome_full_mem_search_sample(pangenome_full):
     # backward search on the same sample
     lohi = rb.rb3_backward_search(idx, sub.q, sub.qoff)
     assert np.array_equal(lohi, oracle.backward_search(want, sub.q, sub.qoff))
+
+
+def test_pangenome_full_diversity_sample(pangenome_full):
+    """Haplotype diversity in the configuration bench.py times (the 20,000
+    sliding 51-mers of its leg, default scores, W = 25, filter on) on the
+    finished index; 200 sampled queries against the oracle on its own BWT."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    S, idx, want = pangenome_full
+    q, qoff = bench.diversity_kmers(S)
+    out, n = rb.rb3_haplotype_diversity(idx, torch.from_numpy(q).to(DEV), torch.from_numpy(qoff).to(DEV), 1, 3, 5,
+                                        2, 25, True, out=torch.empty((len(qoff) - 1, 25, 4), dtype=torch.int64,
+                                                                     device=DEV),
+                                        n_out=torch.empty(len(qoff) - 1, dtype=torch.int64, device=DEV))
+    out, n = out.cpu().numpy(), n.cpu().numpy()
+    sample = np.sort(synth.rng(11).choice(len(n), size=200, replace=False))
+    sq = np.concatenate([q[qoff[i]:qoff[i + 1]] for i in sample])
+    soff = np.arange(len(sample) + 1, dtype=np.int64) * 51
+    ref, nref = oracle.haplotype_diversity_many(want, sq, soff, 1, 3, 5, 2, 25, True)
+    assert np.array_equal(n[sample], nref)
+    for j, i in enumerate(sample):
+        assert np.array_equal(out[i, :n[i]], ref[j, :nref[j]]), i
+    assert (n > 0).mean() > 0.5
 
 
 def test_uneven_genomes_reduced():

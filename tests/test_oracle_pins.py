@@ -720,3 +720,21 @@ def test_bwasw_node_of_whole_query_equals_linear_runs():
                 want[tuple(r[:3])] = max(want.get(tuple(r[:3]), -1), r[3])
         got = {tuple(r[2:5]): r[5] for r in oracle.bwasw(B, P, 3, 2, 1, 1, W=0).tolist() if (r[0], r[1]) == node}
         assert got == want
+
+
+def test_diversity_many_equals_one_by_one():
+    """The batched entry (one rank table) gives each query's records as the
+    one-query call does."""
+    g = synth.rng(895)
+    S = synth.pangenome(seed=896, founder_len=400, n_hap=4, batch=4)
+    B = oracle.bwt(oracle.concat(S.seq, S.lens, True))
+    pats = [np.zeros(0, np.uint8)] + [S.seq[s:s + 25].copy() for s in g.integers(0, len(S.seq) - 25, 30)]
+    for p in pats:
+        p[p == 0] = 1
+    q = np.concatenate(pats)
+    qoff = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.int64)
+    for W in (1, 5, 25):
+        out, n = oracle.haplotype_diversity_many(B, q, qoff, W=W)
+        for i, p in enumerate(pats):
+            want = oracle.haplotype_diversity(B, p, W=W)
+            assert n[i] == len(want) and np.array_equal(out[i, :n[i]], want)
