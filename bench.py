@@ -3,15 +3,18 @@
 
 Workload (default): the pangenome merge -- a 5 Mb uniform-random founder, 50
 haplotypes with 0.1% SNPs and 0.01% indels, both strands (~500 M symbols),
-built incrementally in batches of 10 haplotypes.  Batch 0 is built before the
-timed region; each timed step builds the next batch's BWT on the device and
-merges it into the running index (step k uses batch 1 + (k mod 4)); the steps
-run through rb3_append_batches, which builds batch k+1 while batch k merges.  value =
-new symbols per second (Msym/s) over the K timed steps, inputs resident in HBM.
-After the timed steps the index holds all 50 haplotypes (for K = 4) and is
-searched for SMEMs (>= 31 bp) of 1 M queries (lognormal lengths, median 150 bp;
-90% from the haplotypes with 1% substitutions, 10% random) -- reported as
-`mem_search` (Mbp/s) beside the plain one-query-per-thread form.
+built incrementally in batches of 10 haplotypes: batch 0 is built, batches 1-4
+are each built on the device and merged into the index of the batches before
+them (100, 200, 300, 400 Msym).  Timed step k is merge step k mod 4 of such a
+pass; every pass starts from its own batch-0 index, built before the timed
+region, so every timed step is a step of the workload whatever K.  The steps of
+a pass run through rb3_append_batches, which builds batch k+1 while batch k
+merges.  value = new symbols per second (Msym/s) over the K timed steps, inputs
+resident in HBM.  The finished index (all 50 haplotypes) is then searched for
+SMEMs (>= 31 bp) of 1 M queries (lognormal lengths, median 150 bp; 90% from the
+haplotypes with 1% substitutions, 10% random) -- reported as `mem_search`
+(Mbp/s) beside the plain one-query-per-thread form -- and a batch already in
+the index is merged again (`merge_of_indexed_batch`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rb3|reference]
 
@@ -45,13 +48,24 @@ METRIC = "BWT-merge Msymbols/s"
 
 # DRAM traffic per launch of the kernel the roofline reports, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the four
-# timed merges of the default workload, averaged:
+# merges of one pass of the default workload, averaged:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
 #       -k regex:k_merge_walk -s 3 -c 4 python bench.py --no-cpu --no-serve --no-search --no-plain
-#       --warmup 3 --steps 4 --seg-len 642
-# Keyed by (kernel, Occ interval, founder bp, merge form); reported only for
-# that workload.  Must be taken again (or removed) whenever the kernel changes.
-NCU_TRAFFIC = {("k.merge_walk", 32, 5_000_000, 0): 10.11e9}
+#       --warmup 3 --steps 4
+# Keyed by (kernel, Occ interval, founder bp, merge form, digest of the merge
+# kernel's sources): a change to the kernel's source drops the figure (null)
+# until it is captured again.  Every timed step is a step of one pass, so the
+# per-launch average does not depend on the number of steps (a multiple of 4).
+NCU_TRAFFIC: dict = {}
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("merge.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2409_00613_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -185,18 +199,20 @@ def run_rb3(args, rank, world, local_rank):
     S = synth.pangenome(seed=synth.SEED_BASE + 1 + 1000 * rank, founder_len=founder, n_hap=50, batch=10)
     off = S.offsets
     batches = S.batches
-    dev_batches, host_batches = [], []
+    dev_batches = []
     for (a, b) in batches:
         seq = S.seq[off[a]:off[b]]
-        lens = S.lens[a:b].copy()
-        dev_batches.append((torch.from_numpy(seq.copy()).to(dev), lens))
-        pinned = torch.empty(len(seq), dtype=torch.uint8, pin_memory=True)
-        pinned.numpy()[:] = seq
-        host_batches.append((pinned, lens))
+        dev_batches.append((torch.from_numpy(seq.copy()).to(dev), S.lens[a:b].copy()))
     ds = [int(2 * (lens.sum() + len(lens))) for (_, lens) in dev_batches]
     opts = {"occ_interval": args.occ, "seg_len": args.seg_len, "walk_ctas_per_sm": args.walk_ctas,
             "merge_form": args.merge_form}
-    step_batch = [1 + (k % (len(batches) - 1)) for k in range(args.steps)]
+    # The workload is one pass: batch 0 built, batches 1..4 built and merged into
+    # an index of 100, 200, 300, 400 Msym.  Timed step k is merge step k mod 4 of
+    # a pass; every pass starts from its own batch-0 index, built before the
+    # timed region, so that every timed step is a step of the workload whatever K.
+    n_merge = len(batches) - 1
+    step_batch = [1 + (k % n_merge) for k in range(args.steps)]
+    groups = [list(range(g0, min(g0 + n_merge, args.steps))) for g0 in range(0, args.steps, n_merge)]
 
     def barrier():
         torch.cuda.synchronize()
@@ -204,14 +220,28 @@ def run_rb3(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    # the K timed steps' batches, back to back (device, and pinned host for e2e)
-    step_seq = np.concatenate([S.seq[off[batches[b][0]]:off[batches[b][1]]] for b in step_batch])
-    step_lens = np.concatenate([S.lens[batches[b][0]:batches[b][1]] for b in step_batch]).astype(np.int64)
-    step_ends = np.cumsum([batches[b][1] - batches[b][0] for b in step_batch]).astype(np.int64)
-    step_dev = torch.from_numpy(step_seq).to(dev)
-    step_host = torch.empty(len(step_seq), dtype=torch.uint8, pin_memory=True)
-    step_host.numpy()[:] = step_seq
+    # batches 1..4 back to back (device, and pinned host for e2e); pass g reads
+    # the prefix holding its steps' batches
+    s1 = off[batches[1][0]]
+    all_seq = S.seq[s1:off[batches[-1][1]]]
+    merge_dev = torch.from_numpy(all_seq.copy()).to(dev)
+    merge_host = torch.empty(len(all_seq), dtype=torch.uint8, pin_memory=True)
+    merge_host.numpy()[:] = all_seq
+
+    def group_args(g):
+        bs = [step_batch[k] for k in g]  # 1, 2, ... in order
+        a, b = batches[bs[0]][0], batches[bs[-1]][1]
+        nbytes = int(off[b] - off[a])
+        lens = S.lens[a:b].astype(np.int64)
+        ends = np.cumsum([batches[x][1] - batches[x][0] for x in bs]).astype(np.int64)
+        return nbytes, lens, ends
+
     new_syms = int(sum(ds[b] for b in step_batch))
+
+    def fresh_base():
+        x = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+        rb.rb3_drop_build_data(x)
+        return x
 
     # ---- device memory of one batch build (peak of the library's allocations, untimed) ----
     torch.cuda.synchronize()
@@ -226,27 +256,32 @@ def run_rb3(args, rank, world, local_rank):
               "what": "peak of the library's device allocations during one batch build, above what was in use "
                       "before it, per indexed symbol; the batch's index itself (D = 32)"}
     # ---- autotune the merge's segment length on batch 1 into batch 0 (untimed) ----
-    idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
     tune = {}
     if not args.seg_len:
+        idx = fresh_base()
         src = rb.rb3_build_batch(*dev_batches[1], opts=opts, stream=st)
         best, tms = rb.rb3_tune_merge(idx, src, opts, stream=st)
         src.free()
+        idx.free()
         opts["seg_len"] = int(best.seg_len)
         tune = {"seg_len": int(best.seg_len), "walk_ms": round(tms, 3),
                 "candidates": "default L0 = n2/(SMs*512) and L0/2, 2*L0, 4*L0"}
-    # ---- warm-up: W batches appended to a batch-0 index ----
-    wb = [1 + w % (len(batches) - 1) for w in range(args.warmup)]
-    if wb:
-        wseq = torch.from_numpy(np.concatenate([S.seq[off[batches[b][0]]:off[batches[b][1]]] for b in wb])).to(dev)
-        wlens = np.concatenate([S.lens[batches[b][0]:batches[b][1]] for b in wb]).astype(np.int64)
-        wends = np.cumsum([batches[b][1] - batches[b][0] for b in wb]).astype(np.int64)
-        rb.rb3_append_batches(idx, wseq, wlens, wends, opts, stream=st)
-        del wseq
-    idx.free()
-    # ---- timed: fresh batch-0 index (untimed), then the K steps' batches, each
-    # built and merged, builds overlapping merges ----
-    idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+
+    def run_groups(bases, src, host):
+        for g, x in zip(groups, bases):
+            nbytes, lens, ends = group_args(g)
+            rb.rb3_append_batches(x, src[:nbytes], lens, ends, opts, stream=st)
+
+    # ---- warm-up: W steps of the same schedule, untimed ----
+    if args.warmup:
+        wgroups = [list(range(g0, min(g0 + n_merge, args.warmup))) for g0 in range(0, args.warmup, n_merge)]
+        for g in wgroups:
+            x = fresh_base()
+            nbytes, lens, ends = group_args(g)
+            rb.rb3_append_batches(x, merge_dev[:nbytes], lens, ends, opts, stream=st)
+            x.free()
+    # ---- timed: ceil(K/4) passes, each into its own batch-0 index (built untimed) ----
+    bases = [fresh_base() for _ in groups]
     barrier()
     rb.rb3_profile_reset()
     rb.rb3_profile_enable(True)
@@ -258,7 +293,7 @@ def run_rb3(args, rank, world, local_rank):
     t1 = torch.cuda.Event(enable_timing=True)
     barrier()
     t0.record(st)
-    rb.rb3_append_batches(idx, step_dev, step_lens, step_ends, opts, stream=st)
+    run_groups(bases, merge_dev, False)
     t1.record(st)
     barrier()
     ms = t0.elapsed_time(t1)
@@ -266,19 +301,31 @@ def run_rb3(args, rank, world, local_rank):
     clk = clocks.stop()
     rb.rb3_profile_enable(False)
     prof = rb.rb3_profile_read()
+    walk_launch_ms = [round(d, 3) for (nm, _, d) in rb.rb3_profile_timeline() if nm == "k.merge_walk"]
     wstats = rb.rb3_walk_stats()
+    # the index the searches use: the last pass, completed (untimed) if K is not a multiple of 4
+    idx = bases[-1]
+    done = len(groups[-1])
+    if done < n_merge:
+        rest = [b for b in range(1 + done, len(batches))]
+        a, b = batches[rest[0]][0], batches[rest[-1]][1]
+        rb.rb3_append_batches(idx, torch.from_numpy(S.seq[off[a]:off[b]].copy()).to(dev),
+                              S.lens[a:b].astype(np.int64),
+                              np.cumsum([batches[x][1] - batches[x][0] for x in rest]).astype(np.int64), opts,
+                              stream=st)
+    for x in bases[:-1]:
+        x.free()
     info = rb.rb3_index_info(idx)
     ms, total_syms = aggregate_ranks(ms, new_syms, world, dev)
     value = total_syms / (ms * 1e3)
 
-    # ---- the same steps one at a time (build, then merge): no overlap ----
-    seq_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    # ---- one pass one step at a time (build, then merge): no overlap ----
+    seq_idx = fresh_base()
     barrier()
     a_ev = torch.cuda.Event(enable_timing=True)
     b_ev = torch.cuda.Event(enable_timing=True)
     a_ev.record(st)
-    for k in range(args.steps):
-        b = step_batch[k]
+    for b in range(1, len(batches)):
         src = rb.rb3_build_batch(dev_batches[b][0], dev_batches[b][1], opts=opts, stream=st)
         rb.rb3_merge_opts(seq_idx, src, opts, stream=st)
         src.free()
@@ -289,16 +336,17 @@ def run_rb3(args, rank, world, local_rank):
     seq_idx.free()
 
     # ---- e2e: the public call on pinned host buffers (h2d inside the call) ----
-    e2e_idx = rb.rb3_build_batch(dev_batches[0][0], dev_batches[0][1], opts=opts, stream=st)
+    e2e_bases = [fresh_base() for _ in groups]
     barrier()
     e0 = time.perf_counter()
-    rb.rb3_append_batches(e2e_idx, step_host, step_lens, step_ends, opts, stream=st)  # reads merged counts back
+    run_groups(e2e_bases, merge_host, True)  # each call reads the merged counts back
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - e0) * 1e3
-    e2e_idx.free()
+    for x in e2e_bases:
+        x.free()
+    h2d = sum(group_args(g)[0] + 8 * len(group_args(g)[1]) for g in groups)
     e2e = {"value": round(new_syms / (e_ms * 1e3), 3), "unit": "Msym/s",
-           "h2d_bytes_per_step": int((len(step_seq) + 8 * len(step_lens)) // max(1, args.steps)),
-           "d2h_bytes_per_step": 96}
+           "h2d_bytes_per_step": int(h2d // max(1, args.steps)), "d2h_bytes_per_step": 96}
 
     # ---- roofline of the dominant kernel (live CUDA events of the timed region) ----
     hbm, peak_kind = peaks()
@@ -312,7 +360,9 @@ def run_rb3(args, rank, world, local_rank):
         achieved = kbytes / (kms * 1e-3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": NCU_TRAFFIC.get((top, info["occ_interval"], founder, args.merge_form)),
+                "traffic": (NCU_TRAFFIC.get((top, info["occ_interval"], founder, args.merge_form, kernel_digest()))
+                            if args.steps % n_merge == 0 else None),
+                "kernel_digest": kernel_digest(),
                 "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),
                 "launches": kcalls, "share_of_step": round(kms / ms, 4)}
         if top == "k.merge_walk" and info["occ_interval"] == 32:
@@ -339,16 +389,25 @@ def run_rb3(args, rank, world, local_rank):
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "founder_bp": founder, "haplotypes": 50, "batch_haplotypes": 10,
                       "new_symbols_per_gpu": new_syms, "final_index_symbols": info["n"],
+                      "index_symbols_before_step": [int(sum(ds[:b])) for b in step_batch[:n_merge]],
+                      "passes": len(groups),
+                      "schedule": "timed step k builds batch 1 + (k mod 4) and merges it into the index of "
+                                  "batches 0..(k mod 4); every 4 steps a fresh batch-0 index (built untimed)",
                       "occ_interval": info["occ_interval"], "seg_len": opts["seg_len"],
                       "l2": "inputs larger than L2 (batch ~100 Msym text + 100-500 MB index per step)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "phases_ms": phases,
+           "walk_ms_per_step": walk_launch_ms,
            "autotune": tune, "memory": memory,
-           "one_by_one": {"ms_per_step": round(seq_ms / args.steps, 3),
-                          "value": round(new_syms / (seq_ms * 1e3), 3), "unit": "Msym/s",
+           "one_by_one": {"ms_per_step": round(seq_ms / n_merge, 3),
+                          "value": round(sum(ds[1:]) / (seq_ms * 1e3), 3), "unit": "Msym/s",
                           "equal_output": same,
-                          "note": "each step's build then its merge, no overlap (the timed value overlaps "
-                                  "the next batch's build with the current merge)"}}
+                          "note": "one pass, each step's build then its merge, no overlap (the timed value "
+                                  "overlaps the next batch's build with the current merge)"}}
+
+    # ---- a batch whose haplotypes are already in the index ----
+    if rank == 0:
+        out["merge_of_indexed_batch"] = indexed_batch_merge(rb, torch, dev_batches, opts, st, ds)
 
     # ---- comparison with the plain one-walk-per-string form on one merge ----
     if not args.no_plain and rank == 0:
@@ -381,6 +440,40 @@ def run_rb3(args, rank, world, local_rank):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def indexed_batch_merge(rb, torch, dev_batches, opts, st, ds):
+    """The merge of a batch whose haplotypes the index already holds (batch 1
+    into the index of batches 0-1: every new string equals an indexed one to
+    its sentinel), beside the merge of a fresh batch (batch 2) into the same
+    index; both outputs checked equal to the index built the other way round."""
+    res = {"what": "batch 1 (10 haplotypes already indexed) merged into the index of batches 0-1, against batch 2 "
+                   "(fresh haplotypes) into the same index; walk = k.merge_walk's CUDA-event time",
+           "new_symbols": ds[1]}
+    for name, b in (("indexed", 1), ("fresh", 2)):
+        base = rb.rb3_build_batch(*dev_batches[0], opts=opts, stream=st)
+        rb.rb3_drop_build_data(base)
+        one = rb.rb3_build_batch(*dev_batches[1], opts=opts, stream=st)
+        rb.rb3_merge_opts(base, one, opts, stream=st)
+        one.free()
+        src = rb.rb3_build_batch(*dev_batches[b], opts=opts, stream=st)
+        torch.cuda.synchronize()
+        rb.rb3_profile_reset()
+        rb.rb3_profile_enable(True)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rb.rb3_merge_opts(base, src, opts, stream=st)
+        e.record(st)
+        torch.cuda.synchronize()
+        rb.rb3_profile_enable(False)
+        prof = rb.rb3_profile_read()
+        res[f"{name}_merge_ms"] = round(a.elapsed_time(e), 3)
+        res[f"{name}_walk_ms"] = round(prof.get("k.merge_walk", (float("nan"),))[0], 3)
+        src.free()
+        base.free()
+    res["indexed_over_fresh_walk"] = round(res["indexed_walk_ms"] / res["fresh_walk_ms"], 2)
+    return res
 
 
 def plain_vs_segmented(rb, torch, dev_batches, opts, st, ds):
@@ -714,7 +807,9 @@ def cpu_sample(S, window: int = 5_000_000):
     B1 = oracle.bwt(oracle.concat(a, np.array([len(a)]), True))
     n2, dt, _ = oracle_step(oracle, B1, b)
     return {"value": round(n2 / dt / 1e6, 4), "unit": "Msym/s", "cores": 2, "kind": "oracle",
-            "host_cores": os.cpu_count(),
+            "host_cores": os.cpu_count(), "b1_symbols": int(len(B1)), "b2_symbols": int(n2),
+            "b1_note": "the workload's steps merge 100 Msym batches into 100-400 Msym indexes; this sample's index "
+                       "is one haplotype window (10 Msym), so its rank table is far smaller",
             "sample": f"build (naive suffix sort, 1 thread) of the double-strand BWT of a {len(b)} bp window of "
                       f"haplotype 10 and Algorithm 1 merge (2 walks, 2 threads) into that of haplotype 0's window: "
                       f"{n2} new symbols in {dt:.2f} s"}

@@ -218,7 +218,9 @@ int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const int64_t *q
  * q, qoff and out must be device pointers (out may be NULL when cap = 0).
  * Limits: at most 131,072 queries per call, and at most 524,288 query chunks
  * (a query of L bases counts max(1, ceil(L/256)) chunks); larger calls return
- * RB3_E_INVAL without doing any work.  The scratch is a file-scope device
+ * RB3_E_INVAL without doing any work.  qoff must not decrease and no query may
+ * reach 2^31 bases: such a qoff is refused with RB3_E_INVAL before any search
+ * kernel runs.  The scratch is a file-scope device
  * array of 4,726,868 bytes that every GPU which loads the library holds until
  * the process exits; the library allocates nothing else for this call.  The
  * first call on a device looks up that array's device address

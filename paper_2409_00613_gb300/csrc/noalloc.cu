@@ -29,7 +29,7 @@ constexpr int64_t NA_QITEMS = 0;                                // [NA_MAX_QUERI
 constexpr int64_t NA_RCNT = NA_QITEMS + NA_MAX_QUERIES + 1;     // [NA_MAX_CHUNKS + 1] SMEMs per chunk
 constexpr int64_t NA_ROFF = NA_RCNT + NA_MAX_CHUNKS + 1;        // [NA_MAX_CHUNKS + 1] output offsets
 constexpr int64_t NA_PART = NA_ROFF + NA_MAX_CHUNKS + 1;        // [NA_PARTS]
-constexpr int64_t NA_MISC = NA_PART + NA_PARTS;                 // [16]: word 0 = bad-symbol flag
+constexpr int64_t NA_MISC = NA_PART + NA_PARTS;                 // [16]: word 0 = bad-symbol flag, 1 = bad-qoff flag
 constexpr int64_t NA_WORDS = NA_MISC + 16;                      // 4,726,868 bytes in all
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
@@ -64,8 +64,13 @@ __global__ void k_na_check(const uint8_t *__restrict__ q, int64_t b, int64_t e, 
 }
 
 // chunks of query i (at least one); entry nq is 0 so that the scan's last
-// value is the total
-__global__ void k_na_qitems(const int64_t *__restrict__ qoff, int64_t nq, uint32_t *__restrict__ qitems) {
+// value is the total.  A query whose offsets run backwards, or whose length
+// does not fit the records' 32-bit start / end, sets *bad_qoff (the host
+// refuses the call before any search kernel runs); with non-decreasing
+// offsets every query lies inside [qoff[0], qoff[nq]), the range the symbol
+// check covers.
+__global__ void k_na_qitems(const int64_t *__restrict__ qoff, int64_t nq, uint32_t *__restrict__ qitems,
+                            uint32_t *__restrict__ bad_qoff) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > nq) return;
     if (i == nq) {
@@ -73,6 +78,10 @@ __global__ void k_na_qitems(const int64_t *__restrict__ qoff, int64_t nq, uint32
         return;
     }
     int64_t len = qoff[i + 1] - qoff[i];
+    if (len < 0 || len >= ((int64_t)1 << 31)) {
+        atomicOr(bad_qoff, 1u);
+        len = 0;
+    }
     qitems[i] = (uint32_t)(len <= NA_CHUNK ? 1 : (len + NA_CHUNK - 1) / NA_CHUNK);
 }
 
@@ -148,25 +157,37 @@ static int mem_search_noalloc(const rb3_index *idx, const uint8_t *q, const int6
     uint32_t *ws = nullptr;
     RB3_TRY(noalloc_scratch(&ws));
     uint32_t *qitems = ws + NA_QITEMS, *rcnt = ws + NA_RCNT, *roff = ws + NA_ROFF, *part = ws + NA_PART;
-    uint32_t *bad = ws + NA_MISC;
+    uint32_t *bad = ws + NA_MISC, *bad_qoff = ws + NA_MISC + 1;
     int64_t ends[2] = {0, 0};
     RB3_CUDA_TRY(cudaMemcpyAsync(&ends[0], qoff, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     RB3_CUDA_TRY(cudaMemcpyAsync(&ends[1], qoff + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    RB3_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(uint32_t), st));
+    RB3_CUDA_TRY(cudaMemsetAsync(bad, 0, 2 * sizeof(uint32_t), st));
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     RB3_CHECK_ARG(ends[0] >= 0 && ends[1] >= ends[0], "bad qoff");
     RB3_CHECK_ARG(ends[1] == ends[0] || q != nullptr, "q is NULL");
+    // every chunk holds at most NA_CHUNK bases, so more bases than this are more
+    // chunks than the limit (checked here, before the per-query counts are added
+    // up in 32 bits)
+    if (ends[1] - ends[0] > NA_MAX_CHUNKS * NA_CHUNK) {
+        set_error("rb3_mem_search_noalloc: %lld query bases, more than the limit of %lld chunks of %lld bases",
+                  (long long)(ends[1] - ends[0]), (long long)NA_MAX_CHUNKS, (long long)NA_CHUNK);
+        return RB3_E_INVAL;
+    }
     if (ends[1] > ends[0]) {
         unsigned grid = nb_for(ends[1] - ends[0], 256);
         if (grid > (unsigned)num_sms() * 8) grid = (unsigned)num_sms() * 8;
         RB3_LAUNCH(k_na_check, grid, 256, 0, st, q, ends[0], ends[1], bad);
     }
-    RB3_LAUNCH(k_na_qitems, nb_for(nq + 1, 256), 256, 0, st, qoff, nq, qitems);
+    RB3_LAUNCH(k_na_qitems, nb_for(nq + 1, 256), 256, 0, st, qoff, nq, qitems, bad_qoff);
     RB3_TRY(scan_u32_ws(qitems, qitems, nq + 1, false, part, NA_PARTS, st));
-    uint32_t hv[2] = {0, 0};
+    uint32_t hv[3] = {0, 0, 0};
     RB3_CUDA_TRY(cudaMemcpyAsync(&hv[0], qitems + nq, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    RB3_CUDA_TRY(cudaMemcpyAsync(&hv[1], bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&hv[1], bad, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hv[2]) {
+        set_error("rb3_mem_search_noalloc: qoff decreases, or a query is 2^31 bases or longer");
+        return RB3_E_INVAL;
+    }
     if (hv[1]) {
         set_error("query symbol outside 1..5 (A,C,G,T,N codes)");
         return RB3_E_INVAL;
