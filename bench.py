@@ -80,8 +80,10 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--seg-len", type=int, default=0)
+    p.add_argument("--seed-cap", type=int, default=0, help="merge: ForwardExt steps of a segment seed (0 = default)")
     p.add_argument("--merge-form", type=int, default=0,
-                   help="0: segment tops at content anchors (default); 2: segment tops every L symbols")
+                   help="0: bounded seeds, segment tops at content anchors (default); 2: bounded seeds, tops every "
+                        "L symbols; 3: uncapped seeds with the takeover chain, anchored tops")
     p.add_argument("--walk-ctas", type=int, default=0, help="merge walk CTAs per SM (0 = library default)")
     p.add_argument("--occ", type=int, default=32)
     p.add_argument("--no-serve", action="store_true")
@@ -205,7 +207,7 @@ def run_rb3(args, rank, world, local_rank):
         dev_batches.append((torch.from_numpy(seq.copy()).to(dev), S.lens[a:b].copy()))
     ds = [int(2 * (lens.sum() + len(lens))) for (_, lens) in dev_batches]
     opts = {"occ_interval": args.occ, "seg_len": args.seg_len, "walk_ctas_per_sm": args.walk_ctas,
-            "merge_form": args.merge_form}
+            "merge_form": args.merge_form, "seed_cap": args.seed_cap}
     # The workload is one pass: batch 0 built, batches 1..4 built and merged into
     # an index of 100, 200, 300, 400 Msym.  Timed step k is merge step k mod 4 of
     # a pass; every pass starts from its own batch-0 index, built before the
@@ -264,8 +266,9 @@ def run_rb3(args, rank, world, local_rank):
         src.free()
         idx.free()
         opts["seg_len"] = int(best.seg_len)
-        tune = {"seg_len": int(best.seg_len), "walk_ms": round(tms, 3),
-                "candidates": "default L0 = n2/(SMs*512) and L0/2, 2*L0, 4*L0"}
+        opts["seed_cap"] = int(best.seed_cap)
+        tune = {"seg_len": int(best.seg_len), "seed_cap": int(best.seed_cap), "walk_ms": round(tms, 3),
+                "candidates": "L in {L0/2, L0, 2 L0, 4 L0} (L0 = n2/(SMs*512)) x seed cap in {L, 2L, 4L}"}
 
     def run_groups(bases, src, host):
         for g, x in zip(groups, bases):
@@ -378,7 +381,7 @@ def run_rb3(args, rank, world, local_rank):
                 "per_launch": req / max(1, kcalls), "G_per_s": round(per_s / 1e9, 2),
                 "probe_G_per_s": round(probe_m / 1e3, 2), "frac": round(per_s / (probe_m * 1e6), 3),
                 "seeds": wstats["seeds"], "seed_block_reads": wstats["seed_block_reads"],
-                "walk_block_reads": wstats["walk_block_reads"], "taken_over": wstats["taken_over"],
+                "walk_block_reads": wstats["walk_block_reads"], "walked_again": wstats["walked_again"],
                 "what": "lane-level rank block reads of the seeds and walk steps plus the walk's pos writes, "
                         "counted by the kernel, over its CUDA-event time; ceiling: rb3_probe_random_gather, "
                         "32-byte dependent random reads, 2048 threads per SM, 8 GiB buffer"}
@@ -415,12 +418,12 @@ def run_rb3(args, rank, world, local_rank):
 
     # ---- MEM search on the finished index ----
     if not args.no_search and rank == 0:
-        out["mem_search"] = mem_search(rb, torch, S, idx, args, st, dev)
+        probe = (roof or {}).get("random_requests", {}).get("probe_G_per_s")
+        out["mem_search"] = mem_search(rb, torch, S, idx, args, st, dev, probe)
         if not args.no_serve:
             out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
         out["run_length"] = run_length_bench(rb, torch, S, idx, args, st, dev,
                                              out["mem_search"]["autotune_chunk_len"])
-        probe = (roof or {}).get("random_requests", {}).get("probe_G_per_s")
         out["haplotype_diversity"] = diversity_bench(rb, torch, S, idx, st, dev, probe)
     idx.free()
     if not args.no_search and rank == 0:
@@ -677,7 +680,7 @@ def diversity_cpu_sample(S, window: int = 20_000, k: int = 51, nq: int = 300, W:
                       f"({len(B)} symbols): {dt:.2f} s"}
 
 
-def mem_search(rb, torch, S, idx, args, st, dev):
+def mem_search(rb, torch, S, idx, args, st, dev, probe_g=None):
     Q = synth.mem_queries(S, nq=args.queries)
     q = torch.from_numpy(Q.q).to(dev)
     qoff = torch.from_numpy(Q.qoff).to(dev)
@@ -696,6 +699,10 @@ def mem_search(rb, torch, S, idx, args, st, dev):
         reps = 2 if form == 0 else 1
         _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up
         torch.cuda.synchronize()
+        if form == 0:
+            rb.rb3_search_stats(reset=True)
+            rb.rb3_profile_reset()
+            rb.rb3_profile_enable(True)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
@@ -707,6 +714,23 @@ def mem_search(rb, torch, S, idx, args, st, dev):
         res[key] = round(bp / (ms * 1e3), 2)
         res[key.replace("value", "ms")] = round(ms, 3)
         res["smems"] = int(n)
+        if form == 0:
+            rb.rb3_profile_enable(False)
+            kms = rb.rb3_profile_read().get("k.smem_steps", (ms * reps, reps, 0))[0] / reps
+            ss = rb.rb3_search_stats(reset=True)
+            reads, ext = ss["block_reads"] / reps, ss["extensions"] / reps
+            rate = reads / (kms * 1e-3) / 1e9
+            hbm, peak_kind = peaks()
+            res["roofline"] = {
+                "kernel": "k.smem_steps", "bound": "random_requests", "achieved": round(rate, 3),
+                "peak": probe_g, "unit": "G req/s", "frac": round(rate / probe_g, 4) if probe_g else None,
+                "kernel_ms": round(kms, 3), "extensions_per_base": round(ext / bp, 3),
+                "block_reads_per_base": round(reads / bp, 3),
+                "bytes_per_base": round(32 * reads / bp, 1),
+                "hbm_frac": round(32 * reads / (kms * 1e-3) / 1e9 / hbm, 4), "hbm_peak_kind": peak_kind,
+                "what": "Occ block reads (one 32-byte request each at D = 32) counted by the kernel over its "
+                        "CUDA-event time; ceiling: the random-read probe (32-byte dependent reads); hbm_frac: "
+                        "those bytes per second against the copy peak"}
     res["speedup_vs_plain"] = round(res["value"] / res["plain_value"], 2)
     return res
 

@@ -76,11 +76,15 @@ typedef struct {
     int32_t occ_interval;  /* D, symbols per Occ block: 32, 64, 128 or 256 (default 32) */
     int32_t single_strand; /* 0: index both strands (the paper's default, Section "Methods"); 1: forward only */
     int64_t seg_len;       /* merge: walk segment length L (default: autotuned) */
-    int64_t seed_cap;      /* merge: most ForwardExt steps spent on one segment seed (default 4*L) */
-    int32_t merge_form;    /* 0: segmented batched walk, segment tops moved to content anchors (within
-                              +-L/4 of every L-th position, so the batch's homologous segments start at
-                              the same locus and walk side by side); 1: plain Algorithm 1, one walk per
-                              string; 2: segmented walk with tops every L symbols from the string end */
+    int64_t seed_cap;      /* merge: ForwardExt steps after which a segment seed stops and leaves its
+                              candidates (at most 63 suffixes) to the resolve pass; merge_form 3: most
+                              steps of a seed, then the walk from above takes the segment (default 2*L;
+                              single strand: the seed's backward-search window, default 4*L) */
+    int32_t merge_form;    /* 0: segmented batched walk with bounded seeds, segment tops moved to content
+                              anchors (within +-L/4 of every L-th position, so the batch's homologous
+                              segments start at the same locus and walk side by side); 1: plain
+                              Algorithm 1, one walk per string; 2: as 0 with tops every L symbols from
+                              the string end; 3: as 0 with uncapped seeds and the takeover chain */
     int32_t search_form;   /* 0: chunked work-stealing SMEM search, one extension per lane per step;
                               1: plain, one query per thread; 2: chunked, each lane looping on its own */
     int64_t chunk_len;     /* SMEM: query chunk length (default 256) */
@@ -131,11 +135,42 @@ int rb3_index_empty(const rb3_opts *o, rb3_index **out);
 /* Algorithm 1 (AppendBWT): dst := BWT(strings of dst, then strings of src).
  * The sentinels of src rank after those of dst (the walk starts at l = m1).
  * src is unchanged.  With src's build data the new strings are walked in
- * exact segments (seeded by ForwardExt of Algorithm 3); without it, or with
- * merge_form = 1, one walk per string as in the paper.  The result is the same
- * bit for bit.  rb3_merge uses default options. */
+ * segments seeded by ForwardExt (Algorithm 3): a seed that has not resolved
+ * after seed_cap steps leaves the few suffixes it still ties with as
+ * candidates, the segment walks them all at once, and a pass down each string
+ * picks the true one, so the walk's depth does not grow with the length of a
+ * match with the index; without the build data, or with merge_form = 1, one
+ * walk per string as in the paper.  The result is the same bit for bit.
+ * rb3_merge uses default options.  RB3_E_CUDA (dst unchanged) if the walk's
+ * own consistency check fails. */
 int rb3_merge(rb3_index *dst, const rb3_index *src, void *stream);
 int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_opts *o, void *stream);
+
+/* The merge in parts, for merging on several GPUs (each holding a copy of dst
+ * and src).  Algorithm 1's walks are independent given B1 (Section "BWT
+ * construction": the merge is parallel over the strings of B2), so the input
+ * strings of src can be split among parts; every part computes the merged
+ * rows of its strings' suffixes, the parts' arrays are added up (all-reduce),
+ * and every part applies the whole array to its own copy of dst.
+ *
+ * rb3_merge_partition (host only; no GPU): owner[i] in [0, parts) for each of
+ * the n_seq input strings (lengths len), longest first to the part with the
+ * fewest symbols so far; deterministic, so every part computes the same.
+ * rb3_merge_positions: pos[k] (device, src->n entries, caller-owned) = the row
+ * of the merged index that B2 row k goes to (k + l of Algorithm 1), written for
+ * the rows of the input strings with owner[i] == part (both strands) and 0 for
+ * every other row, so that the parts' arrays sum to the whole; owner = NULL
+ * writes every row.  With an empty dst the part owning string 0 writes every
+ * row.  Options as rb3_merge_opts.  dst and src are not modified.
+ * rb3_merge_apply: dst := the merge of src into dst at the rows pos (host or
+ * device, src->n entries); pos must increase and lie in [0, n(dst) + n(src)),
+ * else RB3_E_INVAL and dst is unchanged.  rb3_merge equals
+ * rb3_merge_positions (owner NULL) then rb3_merge_apply.  Plain layouts only
+ * (RB3_E_INVAL for a run-length index). */
+int rb3_merge_partition(const int64_t *len, int64_t n_seq, int32_t parts, int32_t *owner);
+int rb3_merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts *o, const int32_t *owner,
+                        int32_t part, int64_t *pos, void *stream);
+int rb3_merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, void *stream);
 
 /* The build loop of Section "Methods": for each batch of strings, build its
  * BWT (as rb3_build_batch) and merge it into dst (as rb3_merge), in order.
@@ -327,10 +362,20 @@ int rb3_index_bytes(const rb3_index *idx, int64_t *device_bytes, int64_t *runs);
  * since the last reset, added up by the walks as they finish: out[0] seeds
  * run, out[1] Occ block reads of the seeds (one per ForwardExt whose two ends
  * share a block, else two), out[2] block reads of the walk steps (one per new
- * symbol), out[3] segments taken over from above.  At D = 32 a block read is
+ * symbol, plus one per position walked a second time), out[3] positions walked
+ * a second time from their segment's resolved top (merge_form 0 and 2), or
+ * segments taken over from above (merge_form 3).  At D = 32 a block read is
  * one 32-byte memory request.  reset != 0 zeroes them after the read.
  * Synchronizes the device. */
 int rb3_walk_stats(int64_t *out, int32_t reset);
+
+/* Counts of the step-machine SMEM search (rb3_mem_search's default form,
+ * Algorithm 4 over the extensions of Algorithm 3) since the last reset, added
+ * up by its warps as they finish: out[0] extensions (BackwardExt or
+ * ForwardExt), out[1] Occ block reads (one per extension whose two interval
+ * ends share a block, else two; at D = 32 a block read is one 32-byte memory
+ * request).  reset != 0 zeroes them after the read.  Synchronizes the device. */
+int rb3_search_stats(int64_t *out, int32_t reset);
 
 /* Self-test of the bounded device-side waits (the radix sort's look-back wait,
  * the same device function): one thread waits on a flag that nothing sets,

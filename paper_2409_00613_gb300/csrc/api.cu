@@ -5,6 +5,8 @@
 #include <map>
 #include <mutex>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace rb3 {
@@ -281,6 +283,12 @@ RB3_EXPORT int rb3_walk_stats(int64_t *out, int32_t reset) {
     return walk_stats(out, reset != 0);
 }
 
+RB3_EXPORT int rb3_search_stats(int64_t *out, int32_t reset) {
+    g_err.clear();
+    RB3_CHECK_ARG(out != nullptr, "NULL argument");
+    return search_stats(out, reset != 0);
+}
+
 RB3_EXPORT int rb3_selftest_wait(int32_t limit, void *stream) {
     g_err.clear();
     RB3_CHECK_ARG(limit >= 1 && limit <= (1 << 20), "limit must be in [1, 2^20]");
@@ -367,6 +375,60 @@ RB3_EXPORT int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_op
 
 RB3_EXPORT int rb3_merge(rb3_index *dst, const rb3_index *src, void *stream) {
     return rb3_merge_opts(dst, src, nullptr, stream);
+}
+
+// Longest string first, each to the part with the fewest symbols so far
+// (ties: the lower part); host only.
+RB3_EXPORT int rb3_merge_partition(const int64_t *len, int64_t n_seq, int32_t parts, int32_t *owner) {
+    g_err.clear();
+    RB3_CHECK_ARG(n_seq >= 0 && parts >= 1, "n_seq < 0 or parts < 1");
+    if (n_seq == 0) return RB3_OK;
+    RB3_CHECK_ARG(len && owner, "NULL argument");
+    for (int64_t i = 0; i < n_seq; ++i) RB3_CHECK_ARG(len[i] >= 0, "negative length");
+    std::vector<int64_t> ord(n_seq);
+    for (int64_t i = 0; i < n_seq; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return len[a] > len[b]; });
+    std::vector<int64_t> load(parts, 0);
+    for (int64_t i : ord) {
+        int32_t best = 0;
+        for (int32_t p = 1; p < parts; ++p)
+            if (load[p] < load[best]) best = p;
+        owner[i] = best;
+        load[best] += len[i] + 1;
+    }
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts *o,
+                                   const int32_t *owner, int32_t part, int64_t *pos, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(dst && src, "NULL index");
+    RB3_CHECK_ARG(dst != src, "dst and src must differ");
+    RB3_CHECK_ARG(!dst->rle && !src->rle, "merge positions need plain-layout indexes");
+    RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
+                  "cannot merge a single-strand index with a double-strand one");
+    if (src->n == 0) return RB3_OK;
+    RB3_CHECK_ARG(pos != nullptr && is_device_ptr(pos), "pos must be a device pointer");
+    rb3_opts opts;
+    rb3_opts_default(&opts);
+    if (o) opts = *o;
+    cudaStream_t st = (cudaStream_t)stream;
+    RB3_TRY(merge_positions(dst, src, opts, st, pos, nullptr, owner, part));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(dst && src, "NULL index");
+    if (src->n == 0) return merge_apply(dst, src, nullptr, nullptr, (cudaStream_t)stream);
+    RB3_CHECK_ARG(pos != nullptr, "NULL pos");
+    cudaStream_t st = (cudaStream_t)stream;
+    InArg dp;
+    RB3_TRY(dp.set(pos, sizeof(int64_t) * src->n, st));
+    RB3_TRY(merge_apply(dst, src, static_cast<const int64_t *>(dp.dev), nullptr, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
 }
 
 RB3_EXPORT int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,

@@ -811,9 +811,16 @@ int build_batch_impl(const uint8_t *seq_dev, const int64_t *lens_host, int64_t n
 int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
 int wait_selftest(int limit, cudaStream_t st);
 int walk_stats(int64_t out[4], bool reset);
-int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos);
+int search_stats(int64_t out[2], bool reset);
+int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos,
+                    unsigned int *err_dev = nullptr, const int32_t *owner = nullptr, int32_t part = 0);
+// The scatter-merge of src into dst at the given merged rows pos (device,
+// src->n entries, as merge_positions writes them for every part).
+int merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, const unsigned int *walk_err,
+                cudaStream_t st);
 // Autotuner memory (tune.cu): 0 when nothing was tuned for this input shape.
 int64_t tuned_seg_len(const rb3_index *dst, const rb3_index *src);
+int64_t tuned_seed_cap(const rb3_index *dst, const rb3_index *src);
 int64_t tuned_chunk_len(const rb3_index *idx, int64_t nq, int64_t total_q);
 int append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *lens, int64_t n_seq, const int64_t *batch_end,
                    int64_t n_batches, const rb3_opts &o, cudaStream_t caller);

@@ -34,11 +34,14 @@ namespace cg = cooperative_groups;
 namespace rb3 {
 
 // ---- plain Algorithm 1 walk --------------------------------------------------
+// own (optional): own[i] != 0 for the new strings this call walks (string i
+// starts at B2 row i, its sentinel's row); the others are left alone.
 template <int NS1, int NS2>
-__global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, int64_t *__restrict__ pos,
-                             unsigned int *__restrict__ err) {
+__global__ void k_walk_plain(OccView B1, OccView B2, int64_t m1, int64_t m2, const uint8_t *__restrict__ own,
+                             int64_t *__restrict__ pos, unsigned int *__restrict__ err) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m2) return;
+    if (own && !own[i]) return;
     int64_t k = i, l = m1;
     for (int64_t steps = 0;; ++steps) {
         int a = sym_at(B2, k);
@@ -211,6 +214,340 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
                 bnd = nx >= 0 ? w_hi[nx] : lo;
             }
             if (--p < lo) break;
+            a = an;
+            k = kn;
+        }
+    }
+}
+
+// ---- segmented walk with bounded seeds: candidate tops, resolved afterwards ----------
+// The takeover chain above is exact but its depth is the longest stretch of a
+// new string that the index already holds (one dependent rank per symbol):
+// when a new string equals an indexed one to its sentinel, every seed runs to
+// the string end and the walk from above crosses the whole string.  Here no
+// segment waits for another:
+//  (1) k_walk_seeded: every segment's seed stops after `cap` extensions (and
+//      once its interval holds at most CAND_MAX B1 suffixes).  Its bi-interval
+//      (k, k', s) then says that the s B1 suffixes of rows [k, k+s) share the
+//      seed's prefix with X, so l(X) is one of the s + 1 values k .. k+s.  The
+//      segment walks all of them at once: the values stay s + 1 consecutive
+//      rows' images under pi_{B1}(a, .), which is monotone and grows by
+//      [B1[r] = a] from row r to r + 1, so they are held as the smallest value
+//      v and a mask M (bit j - 1 set iff candidate j's value is candidate
+//      j - 1's plus one).  One step reads the block of v (the rank) and the
+//      symbols of rows v .. v + popcount(M) - 1, nearly always in the same
+//      32-byte block: a step costs what a one-value step costs.  When M becomes
+//      0 every candidate has the same value, which is then exact, and pos is
+//      written from there on.  The segment stores its candidates' values at
+//      its lower end (v, M).
+//  (2) k_seg_resolve: one warp per string runs down its segments from the
+//      sentinel (exact): the true value at the top of segment w + 1 is the
+//      value of w's true candidate at w's lower end.  Each step is a popcount
+//      and a compare; a segment whose seed was exact has one candidate, and an
+//      inconsistent value (outside the next segment's candidates) is reported.
+//  (3) k_rewalk: each segment whose walk did not converge before its end walks
+//      its unwritten positions again from its true top value.
+// Depth: cap + the longest segment, twice, plus the resolve pass; it does not
+// grow with the length of a match.  A seed whose interval still holds more
+// than CAND_MAX suffixes after cap extensions extends on until it holds at
+// most CAND_MAX (or resolves): content held by more than CAND_MAX copies is
+// the remaining case whose depth grows with the match.
+constexpr int CAND_MAX = 63;  // candidates k .. k+s, s <= 63: the mask fits 64 bits
+
+// bit t of the result = [B[r0 + t] == a] for t < d (1 <= d <= 63, r0 + d <= n);
+// higher bits are unspecified.  D = 32: up to three blocks' planes; D >= 64:
+// up to two 64-symbol payload sectors.
+template <int NS>
+__device__ __forceinline__ uint64_t eq_bits(const OccView &v, int64_t r0, int d, int a) {
+    if constexpr (NS == 0) {
+        const uint8_t *b = v.blocks + (r0 >> 5) * 32;
+        const int o = (int)(r0 & 31);
+        uint64_t e = (uint64_t)(s32_match(ld_sec64(b), a) >> o);
+        int got = 32 - o;
+        if (d > got) {
+            e |= (uint64_t)s32_match(ld_sec64(b + 32), a) << got;
+            got += 32;
+            if (d > got) e |= (uint64_t)s32_match(ld_sec64(b + 64), a) << got;
+        }
+        return e;
+    } else {
+        const int D = 64 * NS;
+        auto sec_of = [&](int64_t r) {
+            return v.blocks + (r >> v.log2D) * (int64_t)v.bb + HEADER_BYTES + 32 * ((int)(r & (D - 1)) >> 6);
+        };
+        auto match64 = [&](const Sec &s) {
+            const uint64_t p0 = sec_plane(s, 0), p1 = sec_plane(s, 1), p2 = sec_plane(s, 2);
+            return ((a & 1) ? p0 : ~p0) & ((a & 2) ? p1 : ~p1) & ((a & 4) ? p2 : ~p2);
+        };
+        const int bit = (int)(r0 & 63);
+        uint64_t e = match64(ld_sec64(sec_of(r0))) >> bit;
+        const int got = 64 - bit;
+        if (d > got) e |= match64(ld_sec64(sec_of((r0 | 63) + 1))) << got;
+        return e;
+    }
+}
+
+// Bits of e deposited, in order, at the set bits of m (bit t of e goes to the
+// t-th set bit of m).
+__device__ __forceinline__ uint64_t deposit_bits(uint64_t e, uint64_t m) {
+    uint64_t r = 0;
+    while (m) {
+        const uint64_t b = m & (~m + 1ull);
+        if (e & 1ull) r |= b;
+        e >>= 1;
+        m ^= b;
+    }
+    return r;
+}
+
+// Candidate seed over a double-strand B1: ForwardExt along X = T2[x, send)$
+// until the count is 0 (exact: the k field), X's sentinel (exact: k +
+// occ(Q$)), or, after cap extensions, an interval of at most CAND_MAX rows
+// (candidates k .. k+s).  Returns k; *s_out = 0 when exact.
+template <int NS>
+__device__ __forceinline__ int64_t seed_forward_cand(const OccView &B1, const uint8_t *__restrict__ T2, int64_t x,
+                                                     int64_t send, int64_t cap, int *s_out, uint32_t *reads) {
+    BiInt q = {0, 0, B1.n};
+    int a = T2[x];
+    const int lg = NS == 0 ? 5 : B1.log2D;
+    for (int64_t t = 0;; ++t) {
+        const int64_t p = x + t;
+        if (p == send) {
+            *reads += 2;
+            *s_out = 0;
+            return q.k + (rank1<NS>(B1, 0, q.kp + q.s) - rank1<NS>(B1, 0, q.kp));
+        }
+        if (t >= cap && q.s <= CAND_MAX) {
+            *s_out = (int)q.s;
+            return q.k;
+        }
+        const int an = T2[p + 1];
+        *reads += ((q.kp + q.s) >> lg) == (q.kp >> lg) ? 1u : 2u;
+        const BiInt y = forward_ext<NS>(B1, q, a);
+        if (y.s == 0) {
+            *s_out = 0;
+            return y.k;
+        }
+        q = y;
+        a = an;
+    }
+}
+
+// Candidate seed over any B1 (single strand: no ForwardExt): the SA interval
+// [lo, hi) of T2[x, y), y = min(x + c, send), by backward search; exact once
+// the interval is empty (l = lo) or when y = send (from the sentinel, l = m1);
+// else the candidates are lo .. hi if hi - lo <= CAND_MAX, otherwise the
+// window doubles.
+template <int NS>
+__device__ __forceinline__ int64_t seed_backward_cand(const OccView &B1, int64_t m1, const uint8_t *__restrict__ T2,
+                                                      int64_t x, int64_t send, int64_t cap, int *s_out,
+                                                      uint32_t *reads) {
+    for (int64_t c = cap > 0 ? cap : 1;; c *= 2) {
+        const int64_t y = x + c < send ? x + c : send;
+        bool exact = y == send;
+        int64_t lo = exact ? m1 : 0, hi = exact ? m1 : B1.n;
+        for (int64_t p = y - 1; p >= x; --p) {
+            const int a = T2[p];
+            *reads += exact ? 1u : 2u;
+            if (exact) {
+                lo = C_of(B1, a) + rank1<NS>(B1, a, lo);
+                hi = lo;
+            } else {
+                BlockLd<NS> bl = block_load<NS>(B1, lo), bh = block_load<NS>(B1, hi);
+                lo = C_of(B1, a) + block_rank<NS>(bl, a);
+                hi = C_of(B1, a) + block_rank<NS>(bh, a);
+                exact = lo == hi;
+            }
+        }
+        if (exact || hi - lo <= CAND_MAX) {
+            *s_out = exact ? 0 : (int)(hi - lo);
+            return lo;
+        }
+    }
+}
+
+// Walk counters of the bounded-seed form: [0] seeds, [1] seed block reads,
+// [2] block reads of walk steps (both passes), [3] positions walked again.
+template <int NS, bool DS>
+__global__ void __launch_bounds__(WALK_THREADS, 32)
+    k_walk_seeded(OccView B1, int64_t m1, const uint8_t *__restrict__ T2, const int32_t *__restrict__ isa2,
+                  const int64_t *__restrict__ w_hi, const int64_t *__restrict__ w_send,
+                  const int64_t *__restrict__ w_sstart, const int32_t *__restrict__ w_next,
+                  const int32_t *__restrict__ order, int64_t nw, int64_t cap, unsigned long long *__restrict__ next,
+                  int64_t *__restrict__ pos, int64_t *__restrict__ seg_lo, int32_t *__restrict__ seg_n,
+                  int64_t *__restrict__ bot_v, uint64_t *__restrict__ bot_m, int64_t *__restrict__ unw_lo,
+                  unsigned int *__restrict__ err) {
+    uint32_t n_seed = 0, r_seed = 0, r_walk = 0;
+    for (;;) {
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        const int64_t idx = (int64_t)base + grp.thread_rank();
+        if (idx >= nw) {
+            cg::coalesced_group out = cg::coalesced_threads();
+            const unsigned long long c0 = cg::reduce(out, (unsigned long long)n_seed, cg::plus<unsigned long long>());
+            const unsigned long long c1 = cg::reduce(out, (unsigned long long)r_seed, cg::plus<unsigned long long>());
+            const unsigned long long c2 = cg::reduce(out, (unsigned long long)r_walk, cg::plus<unsigned long long>());
+            if (out.thread_rank() == 0) {
+                atomicAdd(&g_walk_stats[0], c0);
+                atomicAdd(&g_walk_stats[1], c1);
+                atomicAdd(&g_walk_stats[2], c2);
+            }
+            break;
+        }
+        const int32_t w = order[idx];
+        const int64_t hi = w_hi[w], send = w_send[w], lo = w_sstart[w];
+        const int32_t nx = w_next[w];
+        const int64_t bnd = nx >= 0 ? w_hi[nx] : lo;
+        int64_t v;
+        int s = 0;
+        if (hi == send) {  // top segment: starts at the string's sentinel, row isa2[hi]
+            v = m1;
+            const int64_t k = isa2[hi];
+            pos[k] = k + v;
+        } else {
+            ++n_seed;
+            v = DS ? seed_forward_cand<NS>(B1, T2, hi, send, cap, &s, &r_seed)
+                   : seed_backward_cand<NS>(B1, m1, T2, hi, send, cap, &s, &r_seed);
+        }
+        seg_lo[w] = v;
+        seg_n[w] = s;
+        uint64_t M = s ? (s == 64 ? ~0ull : ((1ull << s) - 1ull)) : 0ull;
+        int64_t unw = M ? bnd : hi;  // lowest position not written (hi: none)
+        int64_t p = hi - 1;
+        if (p >= lo) {
+            int a = T2[p];
+            int64_t k = isa2[p];
+            for (;;) {
+                int an = 0;
+                int64_t kn = 0;
+                if (p > bnd) {
+                    an = T2[p - 1];
+                    kn = isa2[p - 1];
+                }
+                ++r_walk;
+                if (M == 0) {
+                    v = C_of(B1, a) + rank1<NS>(B1, a, v);
+                    pos[k] = k + v;
+                } else {
+                    const int d = __popcll(M);
+                    if (v + d > B1.n) {  // candidates are rows of B1: cannot happen on valid inputs
+                        atomicOr(err, 2u);
+                        break;
+                    }
+                    const int64_t vn = C_of(B1, a) + rank1<NS>(B1, a, v);
+                    M = deposit_bits(eq_bits<NS>(B1, v, d, a), M);
+                    v = vn;
+                    if (M == 0) {  // the candidates met: exact from here down
+                        pos[k] = k + v;
+                        unw = p + 1;
+                    }
+                }
+                if (--p < bnd) break;
+                a = an;
+                k = kn;
+            }
+        }
+        bot_v[w] = v;
+        bot_m[w] = M;
+        unw_lo[w] = unw;
+    }
+}
+
+// One warp per string: the true candidate of every segment, from the sentinel
+// down.  top_l[w] = the exact l at segment w's top.
+__global__ void k_seg_resolve(const int32_t *__restrict__ segoff, int64_t ns, const int64_t *__restrict__ seg_lo,
+                              const int32_t *__restrict__ seg_n, const int64_t *__restrict__ bot_v,
+                              const uint64_t *__restrict__ bot_m, int64_t *__restrict__ top_l,
+                              unsigned int *__restrict__ err) {
+    const int64_t sidx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sidx >= ns) return;  // the warp leaves together
+    const int64_t w0 = segoff[sidx], w1 = segoff[sidx + 1];
+    int j = 0;  // true candidate at the top of the next segment (the top segment is exact)
+    bool bad = false;
+    for (int64_t b = w0; b < w1; b += 32) {
+        const int64_t w = b + lane;
+        const bool act = w < w1;
+        const int64_t lo = act ? seg_lo[w] : 0;
+        const int n = act ? seg_n[w] : 0;
+        const int64_t bv = act ? bot_v[w] : 0;
+        const uint64_t bm = act ? bot_m[w] : 0ull;
+        int64_t lo_nx = __shfl_down_sync(0xffffffffu, lo, 1);
+        int n_nx = __shfl_down_sync(0xffffffffu, n, 1);
+        if (lane == 31 && w + 1 < w1) {
+            lo_nx = seg_lo[w + 1];
+            n_nx = seg_n[w + 1];
+        }
+        const bool has_nx = w + 1 < w1;
+        // offset of the bottom values against the next segment's first candidate,
+        // clamped far enough outside [0, 63] that a bad value stays outside
+        int64_t o = bv - lo_nx;
+        o = o < -128 ? -128 : (o > 128 ? 128 : o);
+        const int oc = has_nx ? (int)o : 0;
+        const int cnt = w1 - b < 32 ? (int)(w1 - b) : 32;
+        int myj = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const int oi = __shfl_sync(0xffffffffu, oc, i);
+            const int ni = __shfl_sync(0xffffffffu, n_nx, i);
+            const uint64_t mi = __shfl_sync(0xffffffffu, bm, i);
+            const bool hn = __shfl_sync(0xffffffffu, has_nx, i);
+            if (lane == i) myj = j;
+            if (hn) {
+                const int val = oi + __popcll(mi & prefix_mask(j));
+                if (val < 0 || val > ni) bad = true;
+                j = val < 0 ? 0 : (val > ni ? ni : val);
+            }
+        }
+        if (act) top_l[w] = lo + myj;
+    }
+    if (bad && lane == 0) atomicOr(err, 1u);
+}
+
+// Positions [unw_lo[w], hi) of every segment, walked from the exact top value.
+template <int NS>
+__global__ void __launch_bounds__(WALK_THREADS, 32)
+    k_rewalk(OccView B1, const uint8_t *__restrict__ T2, const int32_t *__restrict__ isa2,
+             const int64_t *__restrict__ w_hi, const int64_t *__restrict__ unw_lo, const int64_t *__restrict__ top_l,
+             const int32_t *__restrict__ order, int64_t nw, unsigned long long *__restrict__ next,
+             int64_t *__restrict__ pos) {
+    uint32_t r_walk = 0, r_again = 0;
+    for (;;) {
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        const int64_t idx = (int64_t)base + grp.thread_rank();
+        if (idx >= nw) {
+            cg::coalesced_group out = cg::coalesced_threads();
+            const unsigned long long c2 = cg::reduce(out, (unsigned long long)r_walk, cg::plus<unsigned long long>());
+            const unsigned long long c3 = cg::reduce(out, (unsigned long long)r_again, cg::plus<unsigned long long>());
+            if (out.thread_rank() == 0) {
+                atomicAdd(&g_walk_stats[2], c2);
+                atomicAdd(&g_walk_stats[3], c3);
+            }
+            break;
+        }
+        const int32_t w = order[idx];
+        const int64_t hi = w_hi[w], u = unw_lo[w];
+        if (u >= hi) continue;
+        int64_t l = top_l[w];
+        int64_t p = hi - 1;
+        int a = T2[p];
+        int64_t k = isa2[p];
+        for (;;) {
+            int an = 0;
+            int64_t kn = 0;
+            if (p > u) {
+                an = T2[p - 1];
+                kn = isa2[p - 1];
+            }
+            l = C_of(B1, a) + rank1<NS>(B1, a, l);
+            pos[k] = k + l;
+            ++r_walk;
+            ++r_again;
+            if (--p < u) break;
             a = an;
             k = kn;
         }
@@ -563,31 +900,31 @@ __global__ void k_span_bases(const int64_t *__restrict__ tbase, int64_t rows, in
 }
 
 template <int NS1>
-static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
-                               unsigned int *err, cudaStream_t st) {
+static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, const uint8_t *own,
+                               int64_t *pos, unsigned int *err, cudaStream_t st) {
     unsigned grid = nb_for(m2, 32);
     if (D2 == 32) {
         auto kern = k_walk_plain<NS1, 0>;
-        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, own, pos, err);
     } else if (D2 == 64) {
         auto kern = k_walk_plain<NS1, 1>;
-        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, own, pos, err);
     } else if (D2 == 128) {
         auto kern = k_walk_plain<NS1, 2>;
-        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, own, pos, err);
     } else {
         auto kern = k_walk_plain<NS1, 4>;
-        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, pos, err);
+        RB3_LAUNCH(kern, grid, 32, 0, st, V1, V2, m1, m2, own, pos, err);
     }
     return RB3_OK;
 }
 
-static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, int64_t *pos,
-                             unsigned int *err, cudaStream_t st) {
-    if (D1 == 32) return launch_walk_plain_1<0>(D2, V1, V2, m1, m2, pos, err, st);
-    if (D1 == 64) return launch_walk_plain_1<1>(D2, V1, V2, m1, m2, pos, err, st);
-    if (D1 == 128) return launch_walk_plain_1<2>(D2, V1, V2, m1, m2, pos, err, st);
-    return launch_walk_plain_1<4>(D2, V1, V2, m1, m2, pos, err, st);
+static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, const uint8_t *own,
+                             int64_t *pos, unsigned int *err, cudaStream_t st) {
+    if (D1 == 32) return launch_walk_plain_1<0>(D2, V1, V2, m1, m2, own, pos, err, st);
+    if (D1 == 64) return launch_walk_plain_1<1>(D2, V1, V2, m1, m2, own, pos, err, st);
+    if (D1 == 128) return launch_walk_plain_1<2>(D2, V1, V2, m1, m2, own, pos, err, st);
+    return launch_walk_plain_1<4>(D2, V1, V2, m1, m2, own, pos, err, st);
 }
 
 // Segment w of the plan: string s with segoff[s] <= w < segoff[s+1], r = w -
@@ -630,7 +967,8 @@ __device__ int64_t anchor_top(const uint8_t *__restrict__ T2, int64_t n2, int64_
     return top;
 }
 
-__global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int32_t *__restrict__ segoff, int64_t ns,
+__global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int64_t *__restrict__ str_start,
+                           const int32_t *__restrict__ segoff, int64_t ns,
                            int64_t L, int64_t nw, const uint8_t *__restrict__ T2, int64_t n2,
                            int64_t *__restrict__ w_hi, int64_t *__restrict__ w_send,
                            int64_t *__restrict__ w_sstart, int32_t *__restrict__ w_next, uint32_t *__restrict__ key,
@@ -644,7 +982,7 @@ __global__ void k_seg_fill(const int64_t *__restrict__ str_end, const int32_t *_
         else hi = mid;
     }
     const int64_t s = lo, r = w - segoff[s], R = segoff[s + 1] - segoff[s];
-    const int64_t end = str_end[s], start = s == 0 ? 0 : str_end[s - 1] + 1;
+    const int64_t end = str_end[s], start = str_start[s];
     w_hi[w] = (T2 && r > 0) ? anchor_top(T2, n2, start, end - r * L, L) : end - r * L;
     w_send[w] = end;
     w_sstart[w] = start;
@@ -660,26 +998,55 @@ __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
 
 // pos[k] = merged row of every B2 row k (the walk of Algorithm 1), into a
 // caller-provided array of src->n entries; dst and src are not modified.
-int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos) {
+//
+// merge_form 0 (default) and 2: bounded seeds and candidate tops (k_walk_seeded,
+// k_seg_resolve, k_rewalk), segment tops at content anchors (0) or every L
+// symbols (2); 3: anchored tops with uncapped seeds and the takeover chain
+// (k_merge_walk); 1: plain Algorithm 1.  A consistency failure of the resolve
+// pass is reported through *err_dev (bit 0: a segment's true value fell outside
+// the next segment's candidates; bit 1: a candidate past B1's end) when given,
+// else checked here before returning.
+//
+// owner (host, optional): owner[i] = the part that walks input string i of src
+// (both of its strands); only the rows of strings with owner == part are
+// written, every other entry of pos is set to 0, so that the parts' pos
+// arrays add up to the whole.  With an empty dst, the part that owns string 0
+// writes every row.
+int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos,
+                    unsigned int *err_dev, const int32_t *owner, int32_t part) {
     RB3_CHECK_ARG(!dst->rle && !src->rle, "the merge walk reads plain-layout indexes only");
     const int64_t n1 = dst->n, n2 = src->n;
     if (n2 == 0) return RB3_OK;
     OccView V1 = occ_view(dst), V2 = occ_view(src);
     const int64_t m1 = dst->m, m2 = src->m;
+    // DS string s (the strings of src's text, in order) is input string s / 2, or s
+    // with a single strand
+    const int per = src->single_strand ? 1 : 2;
+    auto owned = [&](int64_t s) { return owner == nullptr || owner[s / per] == part; };
+    if (owner) RB3_CUDA_TRY(cudaMemsetAsync(pos, 0, sizeof(int64_t) * n2, st));
     {
         Phase ph("merge.walk", st);
-        bool segmented = (o.merge_form == 0 || o.merge_form == 2) && src->text && src->isa;
+        const bool chain = o.merge_form == 3;
+        bool segmented = (o.merge_form == 0 || o.merge_form == 2 || chain) && src->text && src->isa;
         if (n1 == 0) {
             // empty B1: every l is 0 (there are no older suffixes), pos[k] = k
-            RB3_LAUNCH(k_iota, nb_for(n2, 256), 256, 0, st, pos, n2);
+            if (owned(0)) RB3_LAUNCH(k_iota, nb_for(n2, 256), 256, 0, st, pos, n2);
         } else if (!segmented) {
-            DevBuf err;
+            DevBuf err, own;
             RB3_TRY(err.alloc(sizeof(unsigned int), st));
             RB3_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(unsigned int), st));
+            std::vector<uint8_t> own_h;
+            if (owner) {
+                own_h.resize(m2);
+                for (int64_t s = 0; s < m2; ++s) own_h[s] = owned(s) ? 1 : 0;
+                RB3_TRY(own.alloc(m2, st));
+                RB3_CUDA_TRY(cudaMemcpyAsync(own.p, own_h.data(), m2, cudaMemcpyHostToDevice, st));
+            }
             {
                 // per new symbol: two ranks (B2 row, B1 l) and an 8 B pos
                 Phase pk("k.walk_plain", st, (double)n2 * (rank_bytes(src->D) + rank_bytes(dst->D) + 8.0));
-                RB3_TRY(launch_walk_plain(dst->D, src->D, V1, V2, m1, m2, pos, err.as<unsigned int>(), st));
+                RB3_TRY(launch_walk_plain(dst->D, src->D, V1, V2, m1, m2, owner ? own.as<uint8_t>() : nullptr, pos,
+                                          err.as<unsigned int>(), st));
             }
             unsigned int herr = 0;
             RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
@@ -699,17 +1066,27 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 if (L < 512) L = 512;
                 if (L > 16384) L = 16384;
             }
-            // double strand: seeds are self-limiting (claimed from above), so no cap
-            // unless asked; single strand: the backward seed looks cap symbols ahead
-            int64_t cap = o.seed_cap > 0 ? o.seed_cap : (dst->single_strand ? 4 * L : (int64_t)1 << 62);
-            // segments per string (host, one number per string); the segments
-            // themselves and their order are laid out on the device
-            const int64_t ns = (int64_t)src->str_end.size();
+            // chain form, double strand: seeds are self-limiting (claimed from above), so
+            // no cap unless asked; single strand: the backward seed looks cap symbols
+            // ahead.  Bounded form: 2L extensions (4L symbols ahead, single strand).
+            int64_t cap = o.seed_cap > 0 ? o.seed_cap : (chain ? 0 : tuned_seed_cap(dst, src));
+            if (cap <= 0) cap = dst->single_strand ? 4 * L : (chain ? (int64_t)1 << 62 : 2 * L);
+            // the strings walked here (all, or the part's), and segments per string
+            // (host, one number per string); the segments themselves and their
+            // order are laid out on the device
+            std::vector<int64_t> s_end, s_start;
+            for (int64_t s = 0; s < (int64_t)src->str_end.size(); ++s)
+                if (owned(s)) {
+                    s_end.push_back(src->str_end[s]);
+                    s_start.push_back(s == 0 ? 0 : src->str_end[s - 1] + 1);
+                }
+            const int64_t ns = (int64_t)s_end.size();
+            if (ns == 0) return RB3_OK;  // nothing of this part's
             std::vector<int32_t> segoff(ns + 1, 0);
             int64_t nw = 0, maxr = 0;
             for (int64_t s = 0; s < ns; ++s) {
-                const int64_t start = s == 0 ? 0 : src->str_end[s - 1] + 1;
-                const int64_t len = src->str_end[s] - start;
+                const int64_t start = s_start[s];
+                const int64_t len = s_end[s] - start;
                 const int64_t R = len > L ? (len + L - 1) / L : 1;
                 if (R - 1 > maxr) maxr = R - 1;
                 nw += R;
@@ -719,27 +1096,29 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 }
                 segoff[s + 1] = (int32_t)nw;
             }
-            DevBuf plan, sk0, sk1, sv1, ends;
+            DevBuf plan, sk0, sk1, sv1, ends, cand;
             size_t bytes = sizeof(int64_t) * (3 * nw) + sizeof(int32_t) * (3 * nw) + sizeof(unsigned long long) + 64;
             RB3_TRY(plan.alloc(bytes, st));
             RB3_TRY(sk0.alloc(sizeof(uint32_t) * nw, st));
             RB3_TRY(sk1.alloc(sizeof(uint32_t) * nw, st));
             RB3_TRY(sv1.alloc(sizeof(uint32_t) * nw, st));
-            RB3_TRY(ends.alloc(sizeof(int64_t) * ns + sizeof(int32_t) * (ns + 1), st));
+            RB3_TRY(ends.alloc(sizeof(int64_t) * 2 * ns + sizeof(int32_t) * (ns + 1), st));
             int64_t *d_hi = plan.as<int64_t>(), *d_send = d_hi + nw, *d_sstart = d_send + nw;
             int32_t *d_next = reinterpret_cast<int32_t *>(d_sstart + nw), *d_state = d_next + nw, *d_order = d_state + nw;
             unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(
                 (reinterpret_cast<uintptr_t>(d_order + nw) + 15) & ~uintptr_t(15));
-            int64_t *d_end = ends.as<int64_t>();
-            int32_t *d_segoff = reinterpret_cast<int32_t *>(d_end + ns);
-            RB3_CUDA_TRY(cudaMemcpyAsync(d_end, src->str_end.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
+            int64_t *d_end = ends.as<int64_t>(), *d_start = d_end + ns;
+            int32_t *d_segoff = reinterpret_cast<int32_t *>(d_start + ns);
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_end, s_end.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(d_start, s_start.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, st));
             RB3_CUDA_TRY(cudaMemcpyAsync(d_segoff, segoff.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, st));
             // order: by rank from the string end, then string (a stable sort by rank of
             // the segments in string order), so homologous segments of the batch's
             // strings run side by side
             uint32_t *ord_v0 = reinterpret_cast<uint32_t *>(d_order);
-            RB3_LAUNCH(k_seg_fill, nb_for(nw, 256), 256, 0, st, d_end, d_segoff, ns, L, nw,
-                       o.merge_form == 0 ? src->text : (const uint8_t *)nullptr, src->n, d_hi, d_send, d_sstart,
+            RB3_LAUNCH(k_seg_fill, nb_for(nw, 256), 256, 0, st, d_end, d_start, d_segoff, ns, L, nw,
+                       (o.merge_form == 0 || chain) ? src->text : (const uint8_t *)nullptr, src->n, d_hi, d_send,
+                       d_sstart,
                        d_next, sk0.as<uint32_t>(), ord_v0);
             if (maxr > 0) {
                 bool alt = false;
@@ -748,56 +1127,141 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 if (alt)
                     RB3_CUDA_TRY(cudaMemcpyAsync(ord_v0, sv1.p, sizeof(uint32_t) * nw, cudaMemcpyDeviceToDevice, st));
             }
-            RB3_CUDA_TRY(cudaMemsetAsync(d_state, 0, sizeof(int32_t) * nw, st));
             RB3_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st));
-            {
+            // the persistent walks: cps x 256 threads per SM (default 8, of which
+            // registers let half be resident at once), in one-warp CTAs
+            const int cps = o.walk_ctas_per_sm > 0 ? (o.walk_ctas_per_sm < 8 ? o.walk_ctas_per_sm : 8) : 8;
+            const int64_t resident = (int64_t)num_sms() * 256 * cps;
+            const int64_t threads = nw < resident ? nw : resident;
+            const unsigned grid = nb_for(threads, WALK_THREADS);
+            if (chain) {
+                RB3_CUDA_TRY(cudaMemsetAsync(d_state, 0, sizeof(int32_t) * nw, st));
                 // per new symbol: 1 B text, 4 B ISA, one rank, 8 B pos (seed steps not counted)
                 Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
-                // the walk is persistent: cps x 256 threads per SM (default 8, of which
-                // registers let half be resident at once)
-                const int cps = o.walk_ctas_per_sm > 0 ? (o.walk_ctas_per_sm < 8 ? o.walk_ctas_per_sm : 8) : 8;
-                int64_t resident = (int64_t)num_sms() * 256 * cps;
-                int64_t threads = nw < resident ? nw : resident;
-                unsigned grid = nb_for(threads, WALK_THREADS);
                 if (dst->single_strand)
-                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
-                                                   src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
-                                                   cap, d_ctr, pos));
+                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
+                                                         src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_state,
+                                                         d_order, nw, cap, d_ctr, pos));
                 else
-                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1, src->text,
-                                                   src->isa, d_hi, d_send, d_sstart, d_next, d_state, d_order, nw,
-                                                   cap, d_ctr, pos));
+                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
+                                                         src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_state,
+                                                         d_order, nw, cap, d_ctr, pos));
+            } else {
+                // per segment: first candidate, candidate count, values and mask at the lower
+                // end, lowest unwritten position, exact top value; a flag word and a counter
+                RB3_TRY(cand.alloc(sizeof(int64_t) * 5 * nw + sizeof(int32_t) * nw + 64, st));
+                int64_t *c_lo = cand.as<int64_t>(), *c_bv = c_lo + nw, *c_unw = c_bv + nw, *c_top = c_unw + nw;
+                uint64_t *c_bm = reinterpret_cast<uint64_t *>(c_top + nw);
+                int32_t *c_n = reinterpret_cast<int32_t *>(c_bm + nw);
+                unsigned long long *c_ctr = reinterpret_cast<unsigned long long *>(
+                    (reinterpret_cast<uintptr_t>(c_n + nw) + 15) & ~uintptr_t(15));
+                unsigned int *c_err = reinterpret_cast<unsigned int *>(c_ctr + 1);
+                RB3_CUDA_TRY(cudaMemsetAsync(c_ctr, 0, sizeof(unsigned long long) + sizeof(unsigned int), st));
+                unsigned int *errp = err_dev ? err_dev : c_err;
+                {
+                    // per new symbol: 1 B text, 4 B ISA, one rank, 8 B pos (seed steps and the
+                    // second walk of unconverged positions not counted)
+                    Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
+                    if (dst->single_strand)
+                        RB3_WITH_NS_PLAIN(dst->D,
+                                          RB3_LAUNCH((k_walk_seeded<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
+                                                     src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
+                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, errp));
+                    else
+                        RB3_WITH_NS_PLAIN(dst->D,
+                                          RB3_LAUNCH((k_walk_seeded<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
+                                                     src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
+                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, errp));
+                }
+                {
+                    Phase pr("k.seg_resolve", st);
+                    RB3_LAUNCH(k_seg_resolve, nb_for(ns * 32, 128), 128, 0, st, d_segoff, ns, c_lo, c_n, c_bv, c_bm,
+                               c_top, errp);
+                }
+                {
+                    Phase pr("k.rewalk", st);
+                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_rewalk<NS>), grid, WALK_THREADS, 0, st, V1, src->text,
+                                                         src->isa, d_hi, c_unw, c_top, d_order, nw, c_ctr, pos));
+                }
+                if (!err_dev) {
+                    unsigned int herr = 0;
+                    RB3_CUDA_TRY(cudaMemcpyAsync(&herr, c_err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+                    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (herr) {
+                        set_error("merge: segment seeds and walks disagree (flags %u)", herr);
+                        return RB3_E_CUDA;
+                    }
+                }
             }
         }
     }
     return RB3_OK;
 }
 
-int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
+static int merge_check(const rb3_index *dst, const rb3_index *src) {
     RB3_CHECK_ARG(dst != src, "dst and src must differ");
     RB3_CHECK_ARG(!dst->rle && !src->rle, "a run-length index is read-only (merge plain indexes, then compress)");
     RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
                   "cannot merge a single-strand index with a double-strand one");
-    if (src->n == 0) return RB3_OK;
-    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
-    if (nM >= (int64_t(1) << 40)) {
+    if ((dst->n + src->n) >= (int64_t(1) << 40)) {
         set_error("merged index would exceed 2^40 symbols");
         return RB3_E_INVAL;
     }
+    return RB3_OK;
+}
+
+int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
+    RB3_TRY(merge_check(dst, src));
+    if (src->n == 0) return RB3_OK;
+    DevBuf posb, errb;
+    RB3_TRY(posb.alloc(sizeof(int64_t) * src->n, st));
+    RB3_TRY(errb.alloc(sizeof(unsigned int), st));
+    RB3_CUDA_TRY(cudaMemsetAsync(errb.p, 0, sizeof(unsigned int), st));
+    RB3_TRY(merge_positions(dst, src, o, st, posb.as<int64_t>(), errb.as<unsigned int>()));
+    return merge_apply(dst, src, posb.as<int64_t>(), errb.as<unsigned int>(), st);
+}
+
+// pos[k] < pos[k+1], 0 <= pos[0], pos[n2-1] < n1 + n2: the rows of a stable
+// interleave of B1 and B2 (bit 2 of *bad otherwise).
+__global__ void k_check_pos(const int64_t *__restrict__ pos, int64_t n2, int64_t nM, unsigned int *__restrict__ bad) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n2) return;
+    const int64_t p = pos[k];
+    if (p < 0 || p >= nM || (k + 1 < n2 && pos[k + 1] <= p)) atomicOr(bad, 4u);
+}
+
+int merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, const unsigned int *walk_err,
+                cudaStream_t st) {
+    RB3_TRY(merge_check(dst, src));
+    if (src->n == 0) return RB3_OK;
+    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
     // output layout: D of dst (or of src when dst is empty)
     int D = n1 ? dst->D : src->D;
     int log2D = ilog2(D), bb = block_bytes_for(D);
     int64_t nbM = nM / D + 1;
     int64_t ntiles = (nbM * D + MT - 1) / MT;
-    DevBuf posb, kst, Mb, tbase;
-    RB3_TRY(posb.alloc(sizeof(int64_t) * n2, st));
+    DevBuf kst, Mb, tbase, errb;
+    RB3_TRY(errb.alloc(sizeof(unsigned int), st));
+    if (walk_err)
+        RB3_CUDA_TRY(cudaMemcpyAsync(errb.p, walk_err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+    else
+        RB3_CUDA_TRY(cudaMemsetAsync(errb.p, 0, sizeof(unsigned int), st));
     RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
     RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
     RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
-    int64_t *pos = posb.as<int64_t>();
     OccView V1 = occ_view(dst), V2 = occ_view(src);
     const int64_t m1 = dst->m, m2 = src->m;
-    RB3_TRY(merge_positions(dst, src, o, st, pos));
+    if (!walk_err) {
+        // positions from the caller: a valid interleave, or nothing is written
+        RB3_LAUNCH(k_check_pos, nb_for(n2, 256), 256, 0, st, pos, n2, nM, errb.as<unsigned int>());
+        unsigned int herr = 0;
+        RB3_CUDA_TRY(cudaMemcpyAsync(&herr, errb.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+        RB3_CUDA_TRY(cudaStreamSynchronize(st));
+        if (herr) {
+            set_error("merge: pos is not an increasing list of rows of the merged index");
+            return RB3_E_INVAL;
+        }
+    }
     {
         Phase ph("merge.scatter", st);
         RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst.as<int64_t>());
@@ -836,6 +1300,22 @@ int merge_impl(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStre
         const int64_t rows = gbase_rows(nM);
         RB3_TRY(dev_alloc((void **)&gb, sizeof(int64_t) * 5 * rows, st));
         RB3_LAUNCH(k_span_bases, nb_for(rows * 5, 128), 128, 0, st, tbase.as<int64_t>(), rows, gb);
+    }
+    // the walk's own consistency check (segment seeds against the walks from above),
+    // before dst is touched
+    {
+        unsigned int herr = 0;
+        RB3_CUDA_TRY(cudaMemcpyAsync(&herr, errb.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+        RB3_CUDA_TRY(cudaStreamSynchronize(st));
+        if (herr) {
+            if (gb) dev_free(gb, st);
+            if (smp.sdir) dev_free(smp.sdir, st);
+            if (smp.svals) dev_free(smp.svals, st);
+            smp.sdir = nullptr;
+            smp.svals = nullptr;
+            set_error("merge: segment seeds and walks disagree (flags %u); dst unchanged", herr);
+            return RB3_E_CUDA;
+        }
     }
     // install
     free_samples(dst);

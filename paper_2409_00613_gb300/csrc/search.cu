@@ -110,6 +110,11 @@ __global__ void __launch_bounds__(256) k_smem_chunked(OccView V, const uint8_t *
 // extensions, same records as smem_range.
 enum : int { SM_ITEM = 0, SM_B1, SM_F, SM_CHK, SM_B2, SM_DONE };
 
+// Counts of the step-machine search since the last reset (rb3_search_stats):
+// [0] extensions (BackwardExt or ForwardExt), [1] Occ block reads (one per
+// extension whose two interval ends share a block, else two).
+__device__ unsigned long long g_search_stats[2];
+
 template <int NS> __device__ __forceinline__ BiInt ext_dir(const OccView &V, BiInt x, int a, bool fwd) {
     const BiInt xi = fwd ? BiInt{x.kp, x.k, x.s} : x;
     const BiInt y = backward_ext<NS>(V, xi, fwd ? comp_sym(a) : a);
@@ -132,6 +137,8 @@ __global__ void __launch_bounds__(256) k_smem_steps(OccView V, const uint8_t *__
     int64_t qi = 0, len = 0, x0 = 0, x1 = 0, i = 0, j = 0, e = 0, nxt = 0;
     bool first = false;
     BiInt x = {0, 0, V.n};
+    uint32_t n_ext = 0, n_reads = 0;  // this lane's counts (rb3_search_stats)
+    const int lg = V.log2D;
     for (;;) {
         // lanes without a chunk take the next ones (one atomic per warp)
         const unsigned need = __ballot_sync(0xffffffffu, phase == SM_ITEM);
@@ -168,10 +175,24 @@ __global__ void __launch_bounds__(256) k_smem_steps(OccView V, const uint8_t *__
                 }
             }
         }
-        if (__ballot_sync(0xffffffffu, phase != SM_DONE) == 0) break;
+        if (__ballot_sync(0xffffffffu, phase != SM_DONE) == 0) {
+            // the warp leaves together: one atomic per counter
+            const unsigned long long e = __reduce_add_sync(0xffffffffu, n_ext);
+            const unsigned long long r = __reduce_add_sync(0xffffffffu, n_reads);
+            if (lane == 0) {
+                atomicAdd(&g_search_stats[0], e);
+                atomicAdd(&g_search_stats[1], r);
+            }
+            break;
+        }
         if (phase == SM_ITEM || phase == SM_DONE) continue;
         // one extension per lane
         const int64_t at = phase == SM_CHK ? x0 - 1 : j;
+        {
+            const int64_t lo = phase == SM_F ? x.kp : x.k;  // the interval the extension ranks
+            ++n_ext;
+            n_reads += ((lo + x.s) >> lg) == (lo >> lg) ? 1u : 2u;
+        }
         const BiInt y = ext_dir<NS>(V, x, P[at], phase == SM_F);
         bool to_start = false, after_f = false;
         if (phase == SM_B1) {
@@ -270,6 +291,17 @@ __global__ void k_smem_gather(const rb3_smem *__restrict__ in, const uint32_t *_
 }
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int search_stats(int64_t out[2], bool reset) {
+    unsigned long long h[2];
+    RB3_CUDA_TRY(cudaMemcpyFromSymbol(h, g_search_stats, sizeof(h)));
+    for (int i = 0; i < 2; ++i) out[i] = (int64_t)h[i];
+    if (reset) {
+        const unsigned long long z[2] = {0, 0};
+        RB3_CUDA_TRY(cudaMemcpyToSymbol(g_search_stats, z, sizeof(z)));
+    }
+    return RB3_OK;
+}
 
 int check_codes(const uint8_t *q, int64_t n, cudaStream_t st) {
     if (n <= 0) return RB3_OK;

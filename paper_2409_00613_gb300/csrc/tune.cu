@@ -1,6 +1,8 @@
 // Autotuner.  The merge's segment length trades seed work against walk
-// parallelism, and the SMEM search's chunk length trades load balance against
-// the chunks' extra first steps; the best values depend on the inputs' shape.
+// parallelism, its seed cap trades seed work against candidate walks and
+// second walks of unconverged segments, and the SMEM search's chunk length
+// trades load balance against the chunks' extra first steps; the best values
+// depend on the inputs' shape.
 // rb3_tune_merge / rb3_tune_search time candidates on the caller's own inputs
 // (the merge's walk phase runs into scratch, so the index is not modified) and
 // remember the winner per input shape: device, Occ interval, strand mode and
@@ -76,6 +78,12 @@ Key search_key(const rb3_index *idx, int64_t nq, int64_t total_q) {
 
 int64_t tuned_seg_len(const rb3_index *dst, const rb3_index *src) { return lookup(merge_key(dst, src)); }
 
+int64_t tuned_seed_cap(const rb3_index *dst, const rb3_index *src) {
+    Key k = merge_key(dst, src);
+    std::get<0>(k) = 2;
+    return lookup(k);
+}
+
 int64_t tuned_chunk_len(const rb3_index *idx, int64_t nq, int64_t total_q) {
     return lookup(search_key(idx, nq, total_q));
 }
@@ -102,26 +110,42 @@ int tune_merge(const rb3_index *dst, const rb3_index *src, const rb3_opts &base,
     RB3_TRY(pos.alloc(sizeof(int64_t) * src->n, st));
     int64_t L0 = src->n / ((int64_t)num_sms() * 512);
     if (L0 < 512) L0 = 512;
-    std::vector<int64_t> cand;
-    for (int64_t L : {L0 / 2, L0, 2 * L0, 4 * L0})
-        if (L >= 256 && L <= 65536) cand.push_back(L);
+    // segment lengths around the default, each with seed caps of 1, 2 and 4
+    // segment lengths (the bounded-seed forms; the chain form takes no cap)
+    std::vector<std::pair<int64_t, int64_t>> cand;
     rb3_opts o = base;
-    if (o.merge_form != 2) o.merge_form = 0;  // tune the segmented walk (nominal or anchored tops)
+    if (o.merge_form != 2 && o.merge_form != 3) o.merge_form = 0;  // a segmented form
+    for (int64_t L : {L0 / 2, L0, 2 * L0, 4 * L0}) {
+        if (L < 256 || L > 65536) continue;
+        if (base.seed_cap > 0 || o.merge_form == 3)
+            cand.push_back({L, base.seed_cap});
+        else
+            for (int64_t c : {L, 2 * L, 4 * L}) cand.push_back({L, c});
+    }
     o.seg_len = L0;
+    o.seed_cap = base.seed_cap;
     RB3_TRY(merge_positions(dst, src, o, st, pos.as<int64_t>()));  // warm-up
     float bestt = 1e30f;
-    int64_t bestL = L0;
-    for (int64_t L : cand) {
-        o.seg_len = L;
+    int64_t bestL = L0, bestC = base.seed_cap;
+    for (const auto &lc : cand) {
+        o.seg_len = lc.first;
+        o.seed_cap = lc.second;
         float t = 0.f;
         RB3_TRY(time_ms(st, &t, [&] { return merge_positions(dst, src, o, st, pos.as<int64_t>()); }));
         if (t < bestt) {
             bestt = t;
-            bestL = L;
+            bestL = lc.first;
+            bestC = lc.second;
         }
     }
-    store(merge_key(dst, src), bestL);
+    Key k = merge_key(dst, src);
+    store(k, bestL);
+    if (bestC > 0 && o.merge_form != 3) {
+        std::get<0>(k) = 2;
+        store(k, bestC);
+    }
     best->seg_len = bestL;
+    best->seed_cap = bestC;
     if (best_ms) *best_ms = bestt;
     return RB3_OK;
 }

@@ -62,6 +62,9 @@ def lib():
             "rb3_index_empty": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
             "rb3_merge": (ctypes.c_int, [_vp, _vp, _vp]),
             "rb3_merge_opts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rb3_merge_partition": (ctypes.c_int, [_vp, _i64, _i32, _vp]),
+            "rb3_merge_positions": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+            "rb3_merge_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rb3_append_batches": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
             "rb3_backward_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
             "rb3_diversity_stats": (ctypes.c_int, [_vp, _i32]),
@@ -83,6 +86,7 @@ def lib():
             "rb3_device_peak": (ctypes.c_int, [ctypes.POINTER(_i64), _i32]),
             "rb3_selftest_wait": (ctypes.c_int, [_i32, _vp]),
             "rb3_walk_stats": (ctypes.c_int, [_vp, _i32]),
+            "rb3_search_stats": (ctypes.c_int, [_vp, _i32]),
             "rb3_index_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "rb3_index_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
             "rb3_index_free": (None, [_vp]),
@@ -211,6 +215,46 @@ def rb3_merge_opts(dst: Index, src: Index, opts=None, stream=None):
     _check(lib().rb3_merge_opts(dst.handle, src.handle, ctypes.byref(o) if o else None, _stream(stream)))
 
 
+def rb3_merge_partition(lens, parts: int) -> np.ndarray:
+    """owner[i] in [0, parts) of every input string (host only; see include/rb3.h)."""
+    lens = np.ascontiguousarray(lens, dtype=np.int64)
+    owner = np.zeros(len(lens), dtype=np.int32)
+    _check(lib().rb3_merge_partition(_ptr(lens), len(lens), int(parts), _ptr(owner)))
+    return owner
+
+
+def rb3_merge_positions(dst: Index, src: Index, pos, owner=None, part: int = 0, opts=None, stream=None):
+    """Writes into the device tensor pos the merged rows of src's rows owned by `part`
+    (every row when owner is None), 0 elsewhere."""
+    o = _opts(opts)
+    own = None if owner is None else np.ascontiguousarray(owner, dtype=np.int32)
+    _check(lib().rb3_merge_positions(dst.handle, src.handle, ctypes.byref(o) if o else None, _ptr(own), int(part),
+                                     _ptr(pos), _stream(stream)))
+    return pos
+
+
+def rb3_merge_apply(dst: Index, src: Index, pos, stream=None):
+    _check(lib().rb3_merge_apply(dst.handle, src.handle, _ptr(pos), _stream(stream)))
+
+
+def rb3_merge_sharded(dst: Index, src: Index, lens, opts=None, group=None, stream=None):
+    """The merge split over the ranks of a torch.distributed group, each rank
+    holding its own copy of dst and src on its GPU: the ranks walk their share
+    of src's input strings (lengths lens), add up their position arrays with one
+    all-reduce, and each applies the whole array to its copy of dst."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    owner = rb3_merge_partition(lens, world)
+    n2 = rb3_index_info(src)["n"]
+    pos = torch.zeros(n2, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+    rb3_merge_positions(dst, src, pos, owner, rank, opts, stream)
+    dist.all_reduce(pos, op=dist.ReduceOp.SUM, group=group)
+    torch.cuda.synchronize()  # the all-reduce's stream may differ from `stream`
+    rb3_merge_apply(dst, src, pos, stream)
+
+
 def rb3_append_batches(dst: Index, seq, lens, batch_end, opts=None, stream=None):
     """Build each batch and merge it into dst, builds overlapping merges."""
     o = _opts(opts)
@@ -332,7 +376,14 @@ def rb3_walk_stats(reset: bool = False) -> dict:
     """Counts of the merge walks since the last reset (see include/rb3.h)."""
     v = (_i64 * 4)()
     _check(lib().rb3_walk_stats(v, int(reset)))
-    return {"seeds": v[0], "seed_block_reads": v[1], "walk_block_reads": v[2], "taken_over": v[3]}
+    return {"seeds": v[0], "seed_block_reads": v[1], "walk_block_reads": v[2], "walked_again": v[3]}
+
+
+def rb3_search_stats(reset: bool = False) -> dict:
+    """Counts of the step-machine SMEM search since the last reset (see include/rb3.h)."""
+    v = (_i64 * 2)()
+    _check(lib().rb3_search_stats(v, int(reset)))
+    return {"extensions": v[0], "block_reads": v[1]}
 
 
 def rb3_selftest_wait(limit: int, stream=None):

@@ -81,6 +81,22 @@ def _substitute(g, s: np.ndarray, rate: float) -> np.ndarray:
     return s
 
 
+def _substitute_sparse(g, s: np.ndarray, rate: float) -> np.ndarray:
+    """Like _substitute, with the substituted positions drawn directly (a
+    binomial count of uniform positions, repeats merged) instead of one
+    uniform number per base: the same law up to the rare repeats, and cheap on
+    megabase strings."""
+    n = int(g.binomial(len(s), rate)) if len(s) else 0
+    idx = np.unique(g.integers(0, len(s), size=n)) if n else np.zeros(0, np.int64)
+    if len(idx):
+        old = s[idx]
+        ok = old <= 4
+        idx, old = idx[ok], old[ok]
+        shift = g.integers(1, 4, size=len(idx), dtype=np.uint8)
+        s[idx] = ((old - 1 + shift) % 4 + 1).astype(np.uint8)
+    return s
+
+
 def _trunc_geometric(g, size: int, p: float = 0.5, hi: int = 10) -> np.ndarray:
     out = g.geometric(p, size=size)
     bad = out > hi
@@ -159,7 +175,7 @@ def uneven(seed: int = SEED_BASE + 2, n_founders: int = 20, founder_len: int = 7
     for i in range(n_genomes):
         f = founders[(i // per_cluster) % n_founders]
         st = int(g.integers(0, founder_len - L[i] + 1))
-        s = _substitute(g, f[st:st + L[i]].copy(), sub)
+        s = _substitute_sparse(g, f[st:st + L[i]].copy(), sub)
         nr = int(round(n_frac * L[i] / mean_run))
         if nr:
             rl = g.integers(nrun[0], nrun[1] + 1, size=nr)

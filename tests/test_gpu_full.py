@@ -3,8 +3,10 @@
 bench.py times (default options), against the oracle's own incremental build
 (naive sort per haplotype + Algorithm 1 merges), plus the LF-decode certificate;
 MEM search on the finished index checked on a sample of the 1 M queries,
-haplotype diversity on a sample of the bench's sliding k-mers, and a reduced
-instance of the uneven-genome workload (clusters, N-runs)."""
+haplotype diversity on a sample of the bench's sliding k-mers, the
+uneven-genome workload (clusters, N-runs) reduced (against the oracle's
+build) and at its size (certified), and the ~6 Gsym served index (certified,
+and pinned by backward-search additivity)."""
 import os
 
 import numpy as np
@@ -19,6 +21,25 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 DEV = torch.device("cuda:0")
 FIELDS = ("qid", "start", "end", "k", "kp", "s")
 NTH = os.cpu_count() or 4
+
+
+def host_memory_bytes() -> int:
+    """Memory this process may still use on the host: MemAvailable, capped by
+    the cgroup limit when there is one."""
+    avail = 0
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as f:
+                v = f.read().strip()
+            if v != "max":
+                avail = min(avail, int(v))
+        except (OSError, ValueError):
+            pass
+    return avail
 
 
 def gpu_incremental(S, opts=None):
@@ -110,6 +131,33 @@ def test_uneven_genomes_reduced():
     assert oracle.certify(codes, oracle.concat(S.seq, S.lens, True), nthreads=NTH) == 0
 
 
+def test_uneven_genomes_full():
+    """The uneven-genome workload at its size: 2,000 genomes in 20 clusters
+    (lognormal lengths, median 3 Mb, 1% substitutions, 0.5% N-runs of 10-100),
+    both strands (~12.8 Gsym), appended in 32 batches of 64 genomes through
+    rb3_append_batches; the finished BWT is certified by the oracle's LF-decode
+    certificate against the text (too large for its naive sort), and its symbol
+    counts checked."""
+    need = 60 << 30  # strings, exported BWT, text, certificate's marks and rank table
+    if host_memory_bytes() < need:
+        pytest.skip(f"needs {need >> 30} GiB of host memory for the certificate")
+    S = synth.uneven()
+    off = S.offsets
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    idx = rb.rb3_index_empty()
+    seq = torch.from_numpy(S.seq).to(DEV)
+    rb.rb3_append_batches(idx, seq, S.lens.copy(), ends)
+    del seq
+    info = rb.rb3_index_info(idx)
+    assert info["n"] == S.ds_symbols() and info["m"] == 2 * len(S.lens) == 4000
+    codes = rb.rb3_export(idx)
+    idx.free()
+    T = oracle.concat(S.seq, S.lens, True)
+    del S, off
+    assert list(oracle.counts(codes)) == list(oracle.counts(T))
+    assert oracle.certify(codes, T, nthreads=NTH) == 0
+
+
 def test_occ32_index_past_2_to_32():
     """D = 32 keeps 32-bit counts relative to 2^32-symbol spans.  The served
     index (150 Mb founder, 20 haplotypes, batches of 4: ~6 Gsym) crosses 2^32
@@ -132,6 +180,11 @@ def test_occ32_index_past_2_to_32():
         parts.append(part)
     info = rb.rb3_index_info(idx)
     assert info["n"] == S.ds_symbols() > 2**32 and info["occ_interval"] == 32
+    # the whole BWT certified against the text by the oracle's LF-decode certificate
+    if host_memory_bytes() >= (30 << 30):
+        codes = rb.rb3_export(idx)
+        assert oracle.certify(codes, oracle.concat(S.seq, S.lens, True), nthreads=NTH) == 0
+        del codes
     g = synth.rng(4242)
     pats = [np.array([c], np.uint8) for c in range(1, 6)]
     for _ in range(4000):

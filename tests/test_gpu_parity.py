@@ -87,7 +87,7 @@ def test_random_lists_batches(D, both):
                 idx = part
             else:
                 mopts = dict(opts, seg_len=int(g.integers(3, 64)), seed_cap=int(g.integers(1, 20)),
-                             merge_form=2 * (trial % 2))
+                             merge_form=(0, 2, 3)[trial % 3])
                 rb.rb3_merge_opts(idx, part, mopts)
         check_index(idx, ref_bwt(S, 0, n_str, both), D)
 
@@ -304,17 +304,20 @@ def test_bounded_wait_times_out_and_context_survives():
 
 def test_walk_stats_count_every_new_symbol_once():
     """The walk's counters: one rank read per new symbol except the strings'
-    sentinels (n2 - m2), whatever the segment length; seeds at most one per
-    segment below a sentinel."""
+    sentinels (n2 - m2), plus one per position walked a second time from a
+    resolved segment top, whatever the segment length and seed cap; seeds at
+    most one per segment below a sentinel."""
     S = synth.pangenome(seed=93, founder_len=30_000, n_hap=6, batch=3)
-    for L in (50, 700):
+    for L, cap in ((50, 0), (700, 0), (50, 8), (700, 100000)):
         idx = build(S, 0, 3)
         src = build(S, 3, 6)
         info = rb.rb3_index_info(src)
         rb.rb3_walk_stats(reset=True)
-        rb.rb3_merge_opts(idx, src, {"seg_len": L})
+        rb.rb3_merge_opts(idx, src, {"seg_len": L, "seed_cap": cap})
         st = rb.rb3_walk_stats(reset=True)
-        assert st["walk_block_reads"] == info["n"] - info["m"], st
+        assert st["walk_block_reads"] - st["walked_again"] == info["n"] - info["m"], st
+        if cap == 100000:
+            assert st["walked_again"] == 0, st  # every seed resolved: nothing to walk again
         # both strands of each haplotype are strings of len + 1 symbols, cut every L from their end
         seeds_max = 2 * sum(-(-(int(l) + 1) // L) - 1 for l in S.lens[3:6])
         assert 0 < st["seeds"] <= seeds_max, (st, seeds_max)
@@ -446,3 +449,69 @@ def test_locate_errors_and_save_load(tmp_path):
     assert np.array_equal(rb.rb3_locate(back, rows), rb.rb3_locate(idx, rows))
     T = oracle.concat(S.seq, S.lens, True)
     assert np.array_equal(rb.rb3_locate(back, rows), oracle.locate(T, oracle.suffix_array(T), rows))
+
+
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
+def test_merge_in_parts_equals_the_oracle(form):
+    """The merge split into parts (as over several GPUs, here one after the
+    other on one): each part's rows are Algorithm 1's positions of its own
+    strings' suffixes and 0 elsewhere, the parts add up to the oracle's whole
+    position array, and applying it gives the oracle's merged BWT."""
+    g = synth.rng(4300 + form)
+    S = synth.random_strings(g, 17, 900, n_frac=0.02, allow_empty=True)
+    a, b = 6, 17
+    B1 = ref_bwt(S, 0, a)
+    sub = S.subset(a, b)
+    T2 = oracle.concat(sub.seq, sub.lens, True)
+    SA2 = oracle.suffix_array(T2)
+    _, want = oracle.merge(B1, oracle.bwt_from_sa(T2, SA2), want_pos=True)
+    string_of_row = np.searchsorted(np.flatnonzero(T2 == 0), SA2) // 2
+    opts = {"merge_form": form, "seg_len": 40, "seed_cap": 8}
+    for parts in (1, 2, 3):
+        dst, src = build(S, 0, a), build(S, a, b)
+        owner = rb.rb3_merge_partition(S.lens[a:b], parts)
+        total = torch.zeros(len(T2), dtype=torch.int64, device=DEV)
+        for p in range(parts):
+            pos = torch.full((len(T2),), -7, dtype=torch.int64, device=DEV)
+            rb.rb3_merge_positions(dst, src, pos, owner, p, opts)
+            got = pos.cpu().numpy()
+            mine = owner[string_of_row] == p
+            assert np.array_equal(got[mine], want[mine]) and not got[~mine].any(), (parts, p)
+            total += pos
+        assert np.array_equal(total.cpu().numpy(), want)
+        rb.rb3_merge_apply(dst, src, total)
+        check_index(dst, ref_bwt(S, 0, b))
+    # into an empty index: the part owning string 0 writes every row
+    empty, src = rb.rb3_index_empty(), build(S, a, b)
+    owner = rb.rb3_merge_partition(S.lens[a:b], 2)
+    total = torch.zeros(len(T2), dtype=torch.int64, device=DEV)
+    for p in range(2):
+        pos = torch.empty(len(T2), dtype=torch.int64, device=DEV)
+        rb.rb3_merge_positions(empty, src, pos, owner, p, opts)
+        total += pos
+    rb.rb3_merge_apply(empty, src, total.cpu().numpy())  # host pos
+    check_index(empty, ref_bwt(S, a, b))
+
+
+def test_merge_apply_refuses_bad_positions():
+    g = synth.rng(4400)
+    S = synth.random_strings(g, 8, 300, allow_empty=False)
+    dst, src = build(S, 0, 4), build(S, 4, 8)
+    before = rb.rb3_export(dst)
+    n2 = rb.rb3_index_info(src)["n"]
+    pos = torch.zeros(n2, dtype=torch.int64, device=DEV)
+    rb.rb3_merge_positions(dst, src, pos)
+    for bad in ("dup", "neg", "past"):
+        p = pos.clone()
+        if bad == "dup":
+            p[5] = p[4]
+        elif bad == "neg":
+            p[0] = -1
+        else:
+            p[-1] = rb.rb3_index_info(dst)["n"] + n2
+        with pytest.raises(rb.RB3Error) as e:
+            rb.rb3_merge_apply(dst, src, p)
+        assert e.value.code == rb.RB3_E_INVAL
+        assert np.array_equal(rb.rb3_export(dst), before)
+    rb.rb3_merge_apply(dst, src, pos)
+    check_index(dst, ref_bwt(S))
