@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
 //      0 every candidate has the same value, which is then exact, and pos is
 //      written from there on.  The segment stores its candidates' values at
 //      its lower end (v, M).
-//  (2) k_seg_resolve: one warp per string runs down its segments from the
-//      sentinel (exact): the true value at the top of segment w + 1 is the
-//      value of w's true candidate at w's lower end.  Each step is a popcount
-//      and a compare; a segment whose seed was exact has one candidate, and an
-//      inconsistent value (outside the next segment's candidates) is reported.
+//  (2) the resolve pass (k_res_chunk, k_res_carry, k_res_apply): the true
+//      value at the top of segment w + 1 is the value of w's true candidate at
+//      w's lower end, starting from the sentinel (exact); a scan along each
+//      string of maps between candidate indexes (below).  An inconsistent
+//      value (outside the next segment's candidates) is reported.
 //  (3) k_rewalk: each segment whose walk did not converge before its end walks
 //      its unwritten positions again from its true top value.
 // Depth: cap + the longest segment, twice, plus the resolve pass; it does not
@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 32) k_merge_walk(OccView B1, int
 // most CAND_MAX (or resolves): content held by more than CAND_MAX copies is
 // the remaining case whose depth grows with the match.
 constexpr int CAND_MAX = 63;  // candidates k .. k+s, s <= 63: the mask fits 64 bits
+constexpr int REWALK_CK = 64;  // positions between checkpoints of the candidate walk (a power of two)
 
 // bit t of the result = [B[r0 + t] == a] for t < d (1 <= d <= 63, r0 + d <= n);
 // higher bits are unspecified.  D = 32: up to three blocks' planes; D >= 64:
@@ -376,6 +377,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
                   const int32_t *__restrict__ order, int64_t nw, int64_t cap, unsigned long long *__restrict__ next,
                   int64_t *__restrict__ pos, int64_t *__restrict__ seg_lo, int32_t *__restrict__ seg_n,
                   int64_t *__restrict__ bot_v, uint64_t *__restrict__ bot_m, int64_t *__restrict__ unw_lo,
+                  int64_t *__restrict__ ck_v, uint64_t *__restrict__ ck_m, int ck_per_seg,
                   unsigned int *__restrict__ err) {
     uint32_t n_seed = 0, r_seed = 0, r_walk = 0;
     for (;;) {
@@ -413,6 +415,10 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
         }
         seg_lo[w] = v;
         seg_n[w] = s;
+        if (hi - bnd >= (int64_t)ck_per_seg * REWALK_CK) {  // the plan bounds every segment below this
+            atomicOr(err, 8u);
+            continue;
+        }
         uint64_t M = s ? (s == 64 ? ~0ull : ((1ull << s) - 1ull)) : 0ull;
         int64_t unw = M ? bnd : hi;  // lowest position not written (hi: none)
         int64_t p = hi - 1;
@@ -442,6 +448,14 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
                     if (M == 0) {  // the candidates met: exact from here down
                         pos[k] = k + v;
                         unw = p + 1;
+                    } else if (((hi - p) & (REWALK_CK - 1)) == 0) {
+                        // checkpoint t: the candidates' values at p = hi - t * REWALK_CK, from
+                        // which the second walk restarts once the true candidate is known
+                        const int64_t t = (hi - p) / REWALK_CK;
+                        if (t < ck_per_seg) {
+                            ck_v[(int64_t)w * ck_per_seg + t] = v;
+                            ck_m[(int64_t)w * ck_per_seg + t] = M;
+                        }
                     }
                 }
                 if (--p < bnd) break;
@@ -455,71 +469,160 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
     }
 }
 
-// One warp per string: the true candidate of every segment, from the sentinel
-// down.  top_l[w] = the exact l at segment w's top.
-__global__ void k_seg_resolve(const int32_t *__restrict__ segoff, int64_t ns, const int64_t *__restrict__ seg_lo,
-                              const int32_t *__restrict__ seg_n, const int64_t *__restrict__ bot_v,
-                              const uint64_t *__restrict__ bot_m, int64_t *__restrict__ top_l,
-                              unsigned int *__restrict__ err) {
-    const int64_t sidx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (sidx >= ns) return;  // the warp leaves together
-    const int64_t w0 = segoff[sidx], w1 = segoff[sidx + 1];
-    int j = 0;  // true candidate at the top of the next segment (the top segment is exact)
-    bool bad = false;
-    for (int64_t b = w0; b < w1; b += 32) {
-        const int64_t w = b + lane;
-        const bool act = w < w1;
-        const int64_t lo = act ? seg_lo[w] : 0;
-        const int n = act ? seg_n[w] : 0;
-        const int64_t bv = act ? bot_v[w] : 0;
-        const uint64_t bm = act ? bot_m[w] : 0ull;
-        int64_t lo_nx = __shfl_down_sync(0xffffffffu, lo, 1);
-        int n_nx = __shfl_down_sync(0xffffffffu, n, 1);
-        if (lane == 31 && w + 1 < w1) {
-            lo_nx = seg_lo[w + 1];
-            n_nx = seg_n[w + 1];
-        }
-        const bool has_nx = w + 1 < w1;
-        // offset of the bottom values against the next segment's first candidate,
-        // clamped far enough outside [0, 63] that a bad value stays outside
-        int64_t o = bv - lo_nx;
-        o = o < -128 ? -128 : (o > 128 ? 128 : o);
-        const int oc = has_nx ? (int)o : 0;
-        const int cnt = w1 - b < 32 ? (int)(w1 - b) : 32;
-        int myj = 0;
-        for (int i = 0; i < cnt; ++i) {
-            const int oi = __shfl_sync(0xffffffffu, oc, i);
-            const int ni = __shfl_sync(0xffffffffu, n_nx, i);
-            const uint64_t mi = __shfl_sync(0xffffffffu, bm, i);
-            const bool hn = __shfl_sync(0xffffffffu, has_nx, i);
-            if (lane == i) myj = j;
-            if (hn) {
-                const int val = oi + __popcll(mi & prefix_mask(j));
-                if (val < 0 || val > ni) bad = true;
-                j = val < 0 ? 0 : (val > ni ? ni : val);
-            }
-        }
-        if (act) top_l[w] = lo + myj;
-    }
-    if (bad && lane == 0) atomicOr(err, 1u);
+// ---- the resolve pass: which candidate of every segment top is the true one ----
+// The true candidate j(w+1) at segment w+1's top is F_w(j(w)), where F_w maps a
+// candidate index at w's top to the index, among w+1's candidates, of its value
+// at w's lower end: F_w(j) = clamp(o + popcount(m & low_j), 0, n_{w+1}), o =
+// (w's lowest bottom value) - (w+1's first candidate), m = w's bottom mask.
+// Values outside w+1's candidates belong to false candidates only, so clamping
+// them changes nothing that matters, and keeps F_w monotone with steps of 0 or
+// 1: F_w is then (c, M): F(j) = c + popcount(M & low_j).  Such maps compose
+// into maps of the same kind (G after F: c = G(F.c), M = the bits of G.M from
+// F.c on, deposited at the set bits of F.M), so the j of every segment is an
+// inclusive scan of the maps along its string, started from j = 0 at the
+// string's top (its sentinel's value is exact):
+//   k_res_chunk: one warp per chunk of up to 32 segments of one string, a warp
+//     scan of the composition; prefix maps per segment, the chunk's aggregate;
+//   k_res_carry: one warp per string, the chunks' aggregates in order (32
+//     loaded at once, applied one after another): each chunk's entry j;
+//   k_res_apply: one thread per segment, its j from its chunk's entry j and
+//     the prefix map before it; top_l = first candidate + j, and the check
+//     that the true value lies among the next segment's candidates.
+struct CandMap {
+    int c;
+    uint64_t M;
+};
+
+__device__ __forceinline__ int cmap_at(const CandMap &f, int j) { return f.c + __popcll(f.M & prefix_mask(j)); }
+
+// g after f
+__device__ __forceinline__ CandMap cmap_then(const CandMap &f, const CandMap &g) {
+    CandMap h;
+    h.c = cmap_at(g, f.c);
+    h.M = deposit_bits(f.c < 64 ? (g.M >> f.c) : 0ull, f.M);
+    return h;
 }
 
-// Positions [unw_lo[w], hi) of every segment, walked from the exact top value.
+// F_w in (c, M) form from o, m and the next segment's candidate count nn
+__device__ __forceinline__ CandMap cmap_of(int64_t o, uint64_t m, int nn) {
+    CandMap f;
+    f.c = o < 0 ? 0 : (o > nn ? nn : (int)o);
+    // the t-th set bit of m moves the raw value from o + t to o + t + 1: it is a
+    // step of the clamped map iff 0 <= o + t and o + t + 1 <= nn
+    uint64_t r = 0;
+    int64_t t = 0;
+    while (m) {
+        const uint64_t b = m & (~m + 1ull);
+        if (o + t >= 0 && o + t + 1 <= nn) r |= b;
+        m ^= b;
+        ++t;
+    }
+    f.M = r;
+    return f;
+}
+
+__device__ __forceinline__ CandMap cmap_shfl_up(const CandMap &f, int d) {
+    CandMap g;
+    g.c = __shfl_up_sync(0xffffffffu, f.c, d);
+    g.M = __shfl_up_sync(0xffffffffu, f.M, d);
+    return g;
+}
+
+// chunk q: segments [ch_w0[q], ch_w0[q] + ch_cnt[q]) of one string; seg_last[w]
+// set for the last segment of a string (it has no next segment)
+__global__ void k_res_chunk(const int32_t *__restrict__ ch_w0, const int32_t *__restrict__ ch_cnt, int64_t nch,
+                            const int64_t *__restrict__ seg_lo, const int32_t *__restrict__ seg_n,
+                            const int64_t *__restrict__ bot_v, const uint64_t *__restrict__ bot_m,
+                            const uint8_t *__restrict__ seg_last, int32_t *__restrict__ pre_c,
+                            uint64_t *__restrict__ pre_m, int32_t *__restrict__ agg_c, uint64_t *__restrict__ agg_m) {
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nch) return;  // the warp leaves together
+    const int64_t w = (int64_t)ch_w0[q] + lane;
+    const int cnt = ch_cnt[q];
+    CandMap f = {0, 0ull};
+    if (lane < cnt && !seg_last[w]) f = cmap_of(bot_v[w] - seg_lo[w + 1], bot_m[w], seg_n[w + 1]);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const CandMap g = cmap_shfl_up(f, d);
+        if (lane >= d) f = cmap_then(g, f);
+    }
+    if (lane < cnt) {
+        pre_c[w] = f.c;
+        pre_m[w] = f.M;
+    }
+    if (lane == cnt - 1) {
+        agg_c[q] = f.c;
+        agg_m[q] = f.M;
+    }
+}
+
+// string s: chunks [choff[s], choff[s+1]); entry[q] = the true candidate at the
+// top of chunk q's first segment
+__global__ void k_res_carry(const int32_t *__restrict__ choff, int64_t ns, const int32_t *__restrict__ agg_c,
+                            const uint64_t *__restrict__ agg_m, int32_t *__restrict__ entry) {
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= ns) return;
+    const int64_t q0 = choff[s], q1 = choff[s + 1];
+    int j = 0;
+    for (int64_t b = q0; b < q1; b += 32) {
+        const int64_t q = b + lane;
+        CandMap f = {0, 0ull};
+        if (q < q1) f = CandMap{agg_c[q], agg_m[q]};
+        const int cnt = q1 - b < 32 ? (int)(q1 - b) : 32;
+        int mine = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const int ci = __shfl_sync(0xffffffffu, f.c, i);
+            const uint64_t mi = __shfl_sync(0xffffffffu, f.M, i);
+            if (lane == i) mine = j;
+            j = ci + __popcll(mi & prefix_mask(j));
+        }
+        if (q < q1) entry[q] = mine;
+    }
+}
+
+__global__ void k_res_apply(const int32_t *__restrict__ seg_chunk, const int32_t *__restrict__ ch_w0, int64_t nw,
+                            const int32_t *__restrict__ entry, const int32_t *__restrict__ pre_c,
+                            const uint64_t *__restrict__ pre_m, const int64_t *__restrict__ seg_lo,
+                            const int32_t *__restrict__ seg_n, const int64_t *__restrict__ bot_v,
+                            const uint64_t *__restrict__ bot_m, const uint8_t *__restrict__ seg_last,
+                            int64_t *__restrict__ top_l, unsigned int *__restrict__ err) {
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int32_t q = seg_chunk[w];
+    const int e = entry[q];
+    const int j = w == ch_w0[q] ? e : cmap_at(CandMap{pre_c[w - 1], pre_m[w - 1]}, e);
+    top_l[w] = seg_lo[w] + j;
+    bool bad = j < 0 || j > seg_n[w];
+    if (!seg_last[w]) {  // the true value at the lower end must be one of the next top's candidates
+        const int64_t v = bot_v[w] + __popcll(bot_m[w] & prefix_mask(j)) - seg_lo[w + 1];
+        bad |= v < 0 || v > seg_n[w + 1];
+    }
+    if (bad) atomicOr(err, 1u);
+}
+
+// Positions [unw_lo[w], hi) of every segment, walked again from the exact
+// value: in pieces of REWALK_CK positions, piece t starting at hi - t *
+// REWALK_CK from the top value (t = 0) or from checkpoint t of the candidate
+// walk, so that the pieces run side by side instead of one chain per segment.
+// Unit u = (order position u / ck_per_seg, piece u % ck_per_seg).
 template <int NS>
 __global__ void __launch_bounds__(WALK_THREADS, 32)
     k_rewalk(OccView B1, const uint8_t *__restrict__ T2, const int32_t *__restrict__ isa2,
              const int64_t *__restrict__ w_hi, const int64_t *__restrict__ unw_lo, const int64_t *__restrict__ top_l,
-             const int32_t *__restrict__ order, int64_t nw, unsigned long long *__restrict__ next,
-             int64_t *__restrict__ pos) {
+             const int64_t *__restrict__ seg_lo, const int64_t *__restrict__ ck_v, const uint64_t *__restrict__ ck_m,
+             int ck_per_seg, const int32_t *__restrict__ order, int64_t nw, unsigned long long *__restrict__ next,
+             int64_t *__restrict__ pos, unsigned int *__restrict__ err) {
     uint32_t r_walk = 0, r_again = 0;
+    const int64_t nu = nw * ck_per_seg;
     for (;;) {
         cg::coalesced_group grp = cg::coalesced_threads();
         unsigned long long base = 0;
         if (grp.thread_rank() == 0) base = atomicAdd(next, (unsigned long long)grp.size());
         base = grp.shfl(base, 0);
         const int64_t idx = (int64_t)base + grp.thread_rank();
-        if (idx >= nw) {
+        if (idx >= nu) {
             cg::coalesced_group out = cg::coalesced_threads();
             const unsigned long long c2 = cg::reduce(out, (unsigned long long)r_walk, cg::plus<unsigned long long>());
             const unsigned long long c3 = cg::reduce(out, (unsigned long long)r_again, cg::plus<unsigned long long>());
@@ -529,17 +632,30 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
             }
             break;
         }
-        const int32_t w = order[idx];
+        const int32_t w = order[idx / ck_per_seg];
+        const int64_t t = idx % ck_per_seg;
         const int64_t hi = w_hi[w], u = unw_lo[w];
-        if (u >= hi) continue;
-        int64_t l = top_l[w];
-        int64_t p = hi - 1;
+        const int64_t top = hi - t * REWALK_CK;  // this piece walks [max(u, top - REWALK_CK), top)
+        if (top <= u) continue;
+        const int64_t stop = top - REWALK_CK > u ? top - REWALK_CK : u;
+        int64_t l;
+        if (t == 0) {
+            l = top_l[w];
+        } else {
+            const int j = (int)(top_l[w] - seg_lo[w]);
+            l = ck_v[(int64_t)w * ck_per_seg + t] + __popcll(ck_m[(int64_t)w * ck_per_seg + t] & prefix_mask(j));
+        }
+        if (l < 0 || l > B1.n) {  // a value of B1's rows; anything else is reported, never read with
+            atomicOr(err, 16u);
+            continue;
+        }
+        int64_t p = top - 1;
         int a = T2[p];
         int64_t k = isa2[p];
         for (;;) {
             int an = 0;
             int64_t kn = 0;
-            if (p > u) {
+            if (p > stop) {
                 an = T2[p - 1];
                 kn = isa2[p - 1];
             }
@@ -547,7 +663,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 32)
             pos[k] = k + l;
             ++r_walk;
             ++r_again;
-            if (--p < u) break;
+            if (--p < stop) break;
             a = an;
             k = kn;
         }
@@ -1000,7 +1116,7 @@ __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
 // caller-provided array of src->n entries; dst and src are not modified.
 //
 // merge_form 0 (default) and 2: bounded seeds and candidate tops (k_walk_seeded,
-// k_seg_resolve, k_rewalk), segment tops at content anchors (0) or every L
+// the resolve pass, k_rewalk), segment tops at content anchors (0) or every L
 // symbols (2); 3: anchored tops with uncapped seeds and the takeover chain
 // (k_merge_walk); 1: plain Algorithm 1.  A consistency failure of the resolve
 // pass is reported through *err_dev (bit 0: a segment's true value fell outside
@@ -1149,10 +1265,15 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
             } else {
                 // per segment: first candidate, candidate count, values and mask at the lower
                 // end, lowest unwritten position, exact top value; a flag word and a counter
-                RB3_TRY(cand.alloc(sizeof(int64_t) * 5 * nw + sizeof(int32_t) * nw + 64, st));
+                // checkpoints of the candidate walks every REWALK_CK positions: a
+                // segment holds at most L + 2 (anchor window) + 1 positions
+                const int ck_per_seg = (int)((L + 2 * (L * RB3_ANCHOR_W / 100) + 2) / REWALK_CK + 1);
+                RB3_TRY(cand.alloc(sizeof(int64_t) * (5 + 2 * (size_t)ck_per_seg) * nw + sizeof(int32_t) * nw + 64, st));
                 int64_t *c_lo = cand.as<int64_t>(), *c_bv = c_lo + nw, *c_unw = c_bv + nw, *c_top = c_unw + nw;
                 uint64_t *c_bm = reinterpret_cast<uint64_t *>(c_top + nw);
-                int32_t *c_n = reinterpret_cast<int32_t *>(c_bm + nw);
+                int64_t *c_ckv = reinterpret_cast<int64_t *>(c_bm + nw);
+                uint64_t *c_ckm = reinterpret_cast<uint64_t *>(c_ckv + (size_t)ck_per_seg * nw);
+                int32_t *c_n = reinterpret_cast<int32_t *>(c_ckm + (size_t)ck_per_seg * nw);
                 unsigned long long *c_ctr = reinterpret_cast<unsigned long long *>(
                     (reinterpret_cast<uintptr_t>(c_n + nw) + 15) & ~uintptr_t(15));
                 unsigned int *c_err = reinterpret_cast<unsigned int *>(c_ctr + 1);
@@ -1166,22 +1287,58 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                         RB3_WITH_NS_PLAIN(dst->D,
                                           RB3_LAUNCH((k_walk_seeded<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
                                                      src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
-                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, errp));
+                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, c_ckv, c_ckm,
+                                                     ck_per_seg, errp));
                     else
                         RB3_WITH_NS_PLAIN(dst->D,
                                           RB3_LAUNCH((k_walk_seeded<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
                                                      src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
-                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, errp));
+                                                     cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, c_ckv, c_ckm,
+                                                     ck_per_seg, errp));
                 }
                 {
+                    // chunks of up to 32 segments of one string (host: from the
+                    // segments per string), the string's chunks, each segment's chunk
+                    std::vector<int32_t> h_w0, h_cnt, h_choff(ns + 1, 0), h_segch(nw);
+                    std::vector<uint8_t> h_last(nw, 0);
+                    for (int64_t s2 = 0; s2 < ns; ++s2) {
+                        for (int64_t w = segoff[s2]; w < segoff[s2 + 1]; w += 32) {
+                            const int64_t c = segoff[s2 + 1] - w < 32 ? segoff[s2 + 1] - w : 32;
+                            for (int64_t i = 0; i < c; ++i) h_segch[w + i] = (int32_t)h_w0.size();
+                            h_w0.push_back((int32_t)w);
+                            h_cnt.push_back((int32_t)c);
+                        }
+                        h_choff[s2 + 1] = (int32_t)h_w0.size();
+                        h_last[segoff[s2 + 1] - 1] = 1;
+                    }
+                    const int64_t nch = (int64_t)h_w0.size();
+                    DevBuf rs;
+                    RB3_TRY(rs.alloc(sizeof(int32_t) * (4 * nch + ns + 1 + 2 * nw) + sizeof(uint64_t) * (nw + nch) +
+                                         nw + 64,
+                                     st));
+                    uint64_t *r_prem = rs.as<uint64_t>(), *r_aggm = r_prem + nw;
+                    int32_t *r_prec = reinterpret_cast<int32_t *>(r_aggm + nch), *r_aggc = r_prec + nw,
+                            *r_entry = r_aggc + nch, *r_w0 = r_entry + nch, *r_cnt = r_w0 + nch, *r_choff = r_cnt + nch,
+                            *r_segch = r_choff + ns + 1;
+                    uint8_t *r_last = reinterpret_cast<uint8_t *>(r_segch + nw);
+                    RB3_CUDA_TRY(cudaMemcpyAsync(r_w0, h_w0.data(), sizeof(int32_t) * nch, cudaMemcpyHostToDevice, st));
+                    RB3_CUDA_TRY(cudaMemcpyAsync(r_cnt, h_cnt.data(), sizeof(int32_t) * nch, cudaMemcpyHostToDevice, st));
+                    RB3_CUDA_TRY(
+                        cudaMemcpyAsync(r_choff, h_choff.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, st));
+                    RB3_CUDA_TRY(cudaMemcpyAsync(r_segch, h_segch.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
+                    RB3_CUDA_TRY(cudaMemcpyAsync(r_last, h_last.data(), nw, cudaMemcpyHostToDevice, st));
                     Phase pr("k.seg_resolve", st);
-                    RB3_LAUNCH(k_seg_resolve, nb_for(ns * 32, 128), 128, 0, st, d_segoff, ns, c_lo, c_n, c_bv, c_bm,
-                               c_top, errp);
+                    RB3_LAUNCH(k_res_chunk, nb_for(nch * 32, 128), 128, 0, st, r_w0, r_cnt, nch, c_lo, c_n, c_bv, c_bm,
+                               r_last, r_prec, r_prem, r_aggc, r_aggm);
+                    RB3_LAUNCH(k_res_carry, nb_for(ns * 32, 128), 128, 0, st, r_choff, ns, r_aggc, r_aggm, r_entry);
+                    RB3_LAUNCH(k_res_apply, nb_for(nw, 256), 256, 0, st, r_segch, r_w0, nw, r_entry, r_prec, r_prem,
+                               c_lo, c_n, c_bv, c_bm, r_last, c_top, errp);
                 }
                 {
                     Phase pr("k.rewalk", st);
                     RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_rewalk<NS>), grid, WALK_THREADS, 0, st, V1, src->text,
-                                                         src->isa, d_hi, c_unw, c_top, d_order, nw, c_ctr, pos));
+                                                         src->isa, d_hi, c_unw, c_top, c_lo, c_ckv, c_ckm, ck_per_seg,
+                                                         d_order, nw, c_ctr, pos, errp));
                 }
                 if (!err_dev) {
                     unsigned int herr = 0;
