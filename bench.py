@@ -87,6 +87,9 @@ def parse():
     p.add_argument("--walk-ctas", type=int, default=0, help="merge walk CTAs per SM (0 = library default)")
     p.add_argument("--occ", type=int, default=32)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--uneven-genomes", type=int, default=256,
+                   help="uneven-genome leg: the first N genomes (batches of 64) of the 2,000-genome workload, "
+                        "layout autotuned (0 = skip)")
     p.add_argument("--serve-full", action="store_true",
                    help="also build the served index (20 haplotypes of a 150 Mb founder, ~6 Gsym) and serve on it")
     return p.parse_args()
@@ -430,6 +433,8 @@ def run_rb3(args, rank, world, local_rank):
         out["locate"] = locate_bench(rb, torch, S, args, st, dev, opts, batches, off)
     if args.serve_full and rank == 0:
         out["served_full"] = served_full(rb, torch, st, dev, opts)
+    if args.uneven_genomes and rank == 0:
+        out["uneven"] = uneven_bench(rb, torch, st, dev, args.uneven_genomes)
     if rank == 0 and not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_sample(S)
         if "haplotype_diversity" in out:
@@ -736,50 +741,83 @@ def mem_search(rb, torch, S, idx, args, st, dev, probe_g=None):
 
 
 def _serve_trace(rb, srv, arr, Q):
-    """Open-loop replay: submit each request at its arrival time, collect
-    completions; latency = completion time - scheduled arrival time."""
-    n = Q.nq
-    qs = [Q.q[Q.qoff[i]:Q.qoff[i + 1]] for i in range(n)]
-    t0 = time.monotonic_ns() + 20_000_000
-    sched = t0 + (arr * 1e9).astype(np.int64)
-    done = []
-    i = 0
-    while i < n or len(done) < n:
-        now = time.monotonic_ns()
-        while i < n and sched[i] <= now:
-            rb.rb3_server_submit(srv, qs[i], i)
-            i += 1
-        if i < n:
-            wait_us = int(max(0, min(2000, (sched[i] - time.monotonic_ns()) // 1000)))
-        else:
-            wait_us = 20000
-        c = rb.rb3_server_poll(srv, 8192, wait_us)
-        for r in c:
-            done.append((int(r["tag"]), int(r["t_done_ns"]), int(r["batch_requests"])))
-            rb.rb3_server_take(srv, r["req_id"], int(r["n_smem"]))
-    lat = np.array([(td - sched[tag]) / 1e6 for tag, td, _ in done])
-    last = max(td for _, td, _ in done)
+    """Open-loop replay on the library's native submitter: each request
+    submitted at its arrival time; latency = completion time - scheduled
+    arrival time."""
+    done, batch = rb.rb3_server_replay(srv, Q.q, Q.qoff, arr)
+    lat = (done - arr) * 1e3
     bp = int(Q.qoff[-1])
     return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "Mbp_per_s": round(bp / ((last - t0) / 1e9) / 1e6, 1),
-            "mean_batch": round(float(np.mean([b for _, _, b in done])), 2)}
+            "Mbp_per_s": round(bp / float(done.max()) / 1e6, 1), "mean_batch": round(float(batch.mean()), 2)}
 
 
-def served(rb, S, idx, index_desc, rates=(2000, 10000, 50000), n_cap=10000):
-    """Poisson arrivals, query lengths log-uniform in [100, 100000] bp with 0.1-5%
-    substitutions (the served workload's request law); continuous batching (4
-    slots) against the plain server (one request at a time, one slot)."""
+SERVE_RATES = (2000, 5000, 10000, 20000, 50000, 100000, 200000, 500000, 1000000)
+
+
+def served(rb, S, idx, index_desc, rates=SERVE_RATES, n_cap=20000, unbatched_max_rate=10000):
+    """The served workload's request law (query lengths log-uniform in [100,
+    100000] bp with 0.1-5% substitutions) replayed as Poisson arrivals at each
+    rate, up to and past saturation (min(rate x 1 s, 20,000) requests of one
+    request set per rate): continuous batching (4 slots) with the step-machine
+    search, the same with the plain one-query-per-thread kernel (equal output),
+    and no batching (one request per micro-batch, one slot) at the low rates."""
     res = {"index": index_desc, "requests": "Poisson arrivals; lengths log-uniform 100 bp-100 kb; "
                                             "0.1-5% substitutions; SMEMs >= 31 bp", "rates": {}}
+    _, Qall = synth.served_requests(S, rate=2000.0, n_req=n_cap)
+    forms = (("batched", dict(slots=4)), ("batched_plain_kernel", dict(slots=4, search_form=1)),
+             ("unbatched", dict(slots=1, max_batch_requests=1)))
     for rate in rates:
-        n = min(n_cap, int(rate))
-        arr, Q = synth.served_requests(S, rate=float(rate), n_req=n)
+        n = int(min(n_cap, max(1000, rate)))
+        Q = Qall.subset(np.arange(n))
+        arr = np.cumsum(synth.rng(synth.SEED_BASE + 40 + rate).exponential(1.0 / rate, size=n))
         row = {"n_requests": n, "offered_Mbp_per_s": round(float(Q.qoff[-1]) / arr[-1] / 1e6, 1)}
-        for name, kw in (("batched", dict(slots=4)), ("plain", dict(slots=1, max_batch_requests=1))):
+        for name, kw in forms:
+            if name == "unbatched" and rate > unbatched_max_rate:
+                continue
             srv = rb.rb3_server_create(idx, **kw)
             row[name] = _serve_trace(rb, srv, arr, Q)
             srv.close()
         res["rates"][str(rate)] = row
+    return res
+
+
+def uneven_bench(rb, torch, st, dev, n_genomes):
+    """The uneven-genome workload (2,000 bacterial-like genomes in 20 clusters,
+    lognormal lengths, 1% substitutions, 0.5% N-runs; batches of 64 genomes),
+    its first n_genomes: rb3_tune_build picks the Occ interval, segment length
+    and seed cap on batches 0-1 (untimed); then every batch is appended to an
+    empty index through rb3_append_batches (timed, CUDA events), Msym/s."""
+    S = synth.uneven(n_genomes=n_genomes)
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    seq = torch.from_numpy(S.seq).to(dev)
+    res = {"workload": f"uneven genomes: the first {n_genomes} of 2000 (20 clusters, lognormal median 3 Mb, "
+                       "1% substitutions, 0.5% N-runs 10-100), batches of 64, both strands",
+           "genomes": n_genomes, "batches": len(ends), "symbols": S.ds_symbols()}
+    if len(ends) < 2:
+        res["error"] = "needs two batches"
+        return res
+    t = time.perf_counter()
+    best, table = rb.rb3_tune_build(seq, S.lens, ends, stream=st)
+    res["autotune"] = {"occ_interval": int(best.occ_interval), "seg_len": int(best.seg_len),
+                       "seed_cap": int(best.seed_cap), "walk_ctas_per_sm": int(best.walk_ctas_per_sm) or 8,
+                       "candidates": [{"D": d, "build_merge_ms": round(ms, 2), "index_mib": round(mb, 1)}
+                                      for d, ms, mb in table],
+                       "tune_s": round(time.perf_counter() - t, 2),
+                       "what": "batch 1 built and merged into batch 0 at each D; the fastest whose projected "
+                               "index fits (no budget given)"}
+    idx = rb.rb3_index_empty(best)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    rb.rb3_append_batches(idx, seq, S.lens, ends, best, stream=st)
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    info = rb.rb3_index_info(idx)
+    res.update({"value": round(info["n"] / (ms * 1e3), 1), "unit": "Msym/s", "ms": round(ms, 1),
+                "index_symbols": info["n"], "index_bytes": rb.rb3_index_bytes(idx)["device_bytes"]})
+    idx.free()
     return res
 
 

@@ -284,7 +284,8 @@ typedef struct {
     int64_t min_occ;            /* occurrence threshold (default 1) */
     int64_t max_batch_bases;    /* query bases per micro-batch (default 8 Mi) */
     int64_t max_batch_requests; /* requests per micro-batch (default 4096; 1 = no batching) */
-    int64_t reserved[4];
+    int64_t search_form;        /* rb3_opts.search_form of the micro-batches' search (default 0) */
+    int64_t reserved[3];
 } rb3_server_opts;
 
 typedef struct {
@@ -304,12 +305,22 @@ int rb3_server_poll(rb3_server *s, rb3_completion *out, int64_t cap, int64_t *n,
 /* Copies a completed request's SMEMs (start-ordered) and releases them. */
 int rb3_server_take(rb3_server *s, int64_t req_id, rb3_smem *out, int64_t cap, int64_t *n);
 int64_t rb3_server_batches(rb3_server *s);
+/* Open-loop load generator on native threads: submits query i (q[qoff[i] ..
+ * qoff[i+1]), host memory) at t0 + arrival_ns[i] (non-decreasing, relative to
+ * a start t0 a few ms after the call), collects every completion and drops its
+ * records; done_ns[i] = its completion time - t0 (latency = done_ns[i] -
+ * arrival_ns[i]) and, if batch is not NULL, batch[i] = the size of the
+ * micro-batch it ran in.  Returns when all n have completed, or at the first
+ * error.  Do not submit or poll from other threads meanwhile. */
+int rb3_server_replay(rb3_server *s, const uint8_t *q, const int64_t *qoff, int64_t n, const int64_t *arrival_ns,
+                      int64_t *done_ns, int32_t *batch);
 void rb3_server_destroy(rb3_server *s);
 
 /* ---- Autotuner (no counterpart in the paper; tunes this build's knobs) ----
  * rb3_tune_merge times the merge's walk phase (into scratch: dst and src are
- * not modified) for several segment lengths around the default and writes the
- * fastest into best->seg_len; rb3_tune_search times the chunked SMEM search
+ * not modified) for several segment lengths around the default, each with seed
+ * caps of 1, 2 and 4 segment lengths (unless base->seed_cap is set), and
+ * writes the fastest into best->seg_len and best->seed_cap; rb3_tune_search times the chunked SMEM search
  * (q, qoff: device) for several chunk lengths and writes best->chunk_len.  The
  * choice is remembered per input shape (device, D, strand mode, log2 size
  * classes) and used by rb3_merge / rb3_mem_search when their knob is 0; with
@@ -319,6 +330,20 @@ int rb3_tune_merge(const rb3_index *dst, const rb3_index *src, const rb3_opts *b
                    void *stream);
 int rb3_tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t min_len,
                     int64_t min_occ, const rb3_opts *base, rb3_opts *best, double *best_ms, void *stream);
+
+/* Layout autotuner for a whole incremental build (the input of
+ * rb3_append_batches: seq host or device, len, batch_end): builds batch 1 and
+ * merges it into batch 0 at the Occ intervals D = 32, 64 and 128, each with
+ * rb3_tune_merge's segment length and seed cap, and writes into *best the
+ * fastest D whose projected index (every batch's symbols at D's bytes per
+ * symbol: 1, 1 and 0.75) fits index_mb MiB (0 = no limit; if none fits, the
+ * smallest), with its seg_len and seed_cap.  cand_ms[3] / cand_mb[3]
+ * (optional) receive each D's build + merge time and projected index MiB.
+ * Needs two batches; allocates and frees its own indexes; synchronizes the
+ * stream. */
+int rb3_tune_build(const uint8_t *seq, const int64_t *len, int64_t n_seq, const int64_t *batch_end, int64_t n_batches,
+                   const rb3_opts *base, int64_t index_mb, rb3_opts *best, double *cand_ms, double *cand_mb,
+                   void *stream);
 
 /* Unpacks B into codes (n bytes, one symbol per byte) and, when occ != NULL,
  * writes occ[j*6 + a] = rank_B(a, j*D) for j = 0 .. n/D (Table 1). */

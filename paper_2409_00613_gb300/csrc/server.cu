@@ -10,6 +10,7 @@
 // free up, so several micro-batches overlap on the device; memory is bounded by
 // slots x budget.  Results do not depend on the batching: a query's SMEMs are
 // a function of the query and the index only.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -67,6 +68,7 @@ static void server_worker(rb3_server *S) {
     std::vector<rb3_smem> h_out;
     rb3_opts so;
     rb3_opts_default(&so);
+    so.search_form = (int32_t)S->o.search_form;
     for (;;) {
         std::vector<rb3_server::Req> batch;
         {
@@ -197,6 +199,7 @@ RB3_EXPORT int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o,
     RB3_CHECK_ARG(opt.min_len >= 1 && opt.min_occ >= 1, "min_len and min_occ must be >= 1");
     RB3_CHECK_ARG(opt.slots >= 1 && opt.slots <= 64, "slots must be in [1, 64]");
     RB3_CHECK_ARG(opt.max_batch_bases >= 1 && opt.max_batch_requests >= 1, "batch limits must be >= 1");
+    RB3_CHECK_ARG(opt.search_form >= 0 && opt.search_form <= 2, "search_form must be 0, 1 or 2");
     rb3_server *S = new rb3_server();
     S->idx = idx;
     S->o = opt;
@@ -265,6 +268,56 @@ RB3_EXPORT int rb3_server_take(rb3_server *S, int64_t req_id, rb3_smem *out, int
 }
 
 RB3_EXPORT int64_t rb3_server_batches(rb3_server *S) { return S ? S->batches.load() : 0; }
+
+// Open-loop replay of an arrival trace from native threads: a submitter thread
+// submits request i at t0 + arrival_ns[i] (sleeping until shortly before, then
+// spinning), while the calling thread collects the completions and drops their
+// records; done_ns[i] = completion time - t0 (CLOCK_MONOTONIC), batch[i] =
+// size of its micro-batch.
+RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t *qoff, int64_t n,
+                                 const int64_t *arrival_ns, int64_t *done_ns, int32_t *batch) {
+    set_error("%s", "");
+    RB3_CHECK_ARG(S && qoff && arrival_ns && done_ns && n >= 0, "bad argument");
+    for (int64_t i = 0; i < n; ++i) {
+        RB3_CHECK_ARG(qoff[i + 1] >= qoff[i] && (i == 0 || arrival_ns[i] >= arrival_ns[i - 1]),
+                      "qoff and arrival_ns must not decrease");
+        done_ns[i] = -1;
+    }
+    RB3_CHECK_ARG(n == 0 || qoff[n] == qoff[0] || q, "q is NULL");
+    const int64_t t0 = now_ns() + 2000000;
+    std::atomic<int> sub_err{RB3_OK};
+    std::thread submitter([&] {
+        for (int64_t i = 0; i < n && sub_err.load() == RB3_OK; ++i) {
+            const int64_t target = t0 + arrival_ns[i];
+            for (int64_t now = now_ns(); now < target; now = now_ns())
+                if (target - now > 60000) std::this_thread::sleep_for(std::chrono::nanoseconds(target - now - 40000));
+            int64_t id = 0;
+            const int r = rb3_server_submit(S, q + qoff[i], qoff[i + 1] - qoff[i], i, &id);
+            if (r != RB3_OK) sub_err.store(r);
+        }
+    });
+    int64_t got = 0;
+    int status = RB3_OK;
+    std::vector<rb3_completion> c(4096);
+    while (got < n && sub_err.load() == RB3_OK) {
+        int64_t k = 0;
+        status = rb3_server_poll(S, c.data(), (int64_t)c.size(), &k, 20000);
+        if (status != RB3_OK) break;
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (int64_t j = 0; j < k; ++j) {
+            const int64_t i = c[j].tag;
+            if (i >= 0 && i < n) {
+                done_ns[i] = c[j].t_done_ns - t0;
+                if (batch) batch[i] = c[j].batch_requests;
+            }
+            S->results.erase(c[j].req_id);
+            ++got;
+        }
+    }
+    submitter.join();
+    if (status == RB3_OK && sub_err.load() != RB3_OK) status = sub_err.load();
+    return status;
+}
 
 RB3_EXPORT void rb3_server_destroy(rb3_server *S) {
     if (!S) return;

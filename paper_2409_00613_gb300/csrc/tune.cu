@@ -12,6 +12,7 @@
 // file and read back by later processes.
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <functional>
 #include <map>
 #include <mutex>
@@ -191,9 +192,118 @@ int tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, con
     return RB3_OK;
 }
 
+// Layout tuner for a whole incremental build (rb3_tune_build): batch 1 built
+// and merged into batch 0 at each Occ interval D, each with the merge tuner's
+// segment length and seed cap; the fastest D whose projected index fits the
+// budget wins.  Bytes per symbol of a plain index: block bytes / D (32 B per 32
+// symbols at D = 32, 64 B per 64, 96 B per 128).
+static const int kTuneD[3] = {32, 64, 128};
+
+int tune_build(const uint8_t *seq_dev, const std::vector<int64_t> &lens, const std::vector<int64_t> &ends,
+               const rb3_opts &base, int64_t index_mb, rb3_opts *best, double cand_ms[3], double cand_mb[3],
+               cudaStream_t st) {
+    *best = base;
+    if (ends.size() < 2 || ends[0] == 0 || ends[1] == ends[0]) return RB3_OK;  // needs two non-empty batches
+    int64_t off1 = 0, total_sym = 0;
+    for (int64_t i = 0; i < ends[0]; ++i) off1 += lens[i];
+    for (size_t i = 0; i < lens.size(); ++i) total_sym += (lens[i] + 1) * (base.single_strand ? 1 : 2);
+    float bestt = 1e30f, smallest = 1e30f;
+    int bestD = kDefaultOccInterval, smallD = kDefaultOccInterval;
+    rb3_opts bo = base;
+    for (int c = 0; c < 3; ++c) {
+        const int D = kTuneD[c];
+        rb3_opts o = base;
+        o.occ_interval = D;
+        o.seg_len = 0;
+        o.seed_cap = 0;
+        rb3_index *A = new rb3_index(), *B = new rb3_index();
+        auto done = [&](int r) {
+            rb3_index_free(A);
+            rb3_index_free(B);
+            return r;
+        };
+        cudaGetDevice(&A->device);
+        B->device = A->device;
+        int r = build_batch_impl(seq_dev, lens.data(), ends[0], o, st, A);
+        float tb = 0.f;
+        if (r == RB3_OK)
+            r = time_ms(st, &tb, [&] {
+                return build_batch_impl(seq_dev + off1, lens.data() + ends[0], ends[1] - ends[0], o, st, B);
+            });
+        rb3_opts tuned = o;
+        double walk_ms = 0;
+        if (r == RB3_OK) r = tune_merge(A, B, o, &tuned, &walk_ms, st);
+        float tm = 0.f;
+        if (r == RB3_OK) r = time_ms(st, &tm, [&] { return merge_impl(A, B, tuned, st); });
+        if (r != RB3_OK) return done(r);
+        const double mb = (double)total_sym * block_bytes_for(D) / D / 1048576.0;
+        cand_ms[c] = (double)(tb + tm);
+        cand_mb[c] = mb;
+        if ((index_mb <= 0 || mb <= (double)index_mb) && tb + tm < bestt) {
+            bestt = tb + tm;
+            bestD = D;
+            bo = tuned;
+        }
+        if (mb < smallest) {
+            smallest = (float)mb;
+            smallD = D;
+            if (bestt >= 1e30f) bo = tuned;
+        }
+        done(RB3_OK);
+    }
+    if (bestt >= 1e30f) bestD = smallD;  // nothing fits: the smallest layout
+    *best = bo;
+    best->occ_interval = bestD;
+    return RB3_OK;
+}
+
 }  // namespace rb3
 
 using namespace rb3;
+
+RB3_EXPORT int rb3_tune_build(const uint8_t *seq, const int64_t *len, int64_t n_seq, const int64_t *batch_end,
+                              int64_t n_batches, const rb3_opts *base, int64_t index_mb, rb3_opts *best,
+                              double *cand_ms, double *cand_mb, void *stream) {
+    set_error("%s", "");
+    RB3_CHECK_ARG(best && len && batch_end && n_seq >= 0 && n_batches >= 2, "bad argument (two batches needed)");
+    rb3_opts o;
+    rb3_opts_default(&o);
+    if (base) o = *base;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> lens(n_seq), ends(n_batches);
+    if (is_device_ptr(len)) RB3_CUDA_TRY(cudaMemcpy(lens.data(), len, sizeof(int64_t) * n_seq, cudaMemcpyDeviceToHost));
+    else memcpy(lens.data(), len, sizeof(int64_t) * n_seq);
+    if (is_device_ptr(batch_end))
+        RB3_CUDA_TRY(cudaMemcpy(ends.data(), batch_end, sizeof(int64_t) * n_batches, cudaMemcpyDeviceToHost));
+    else memcpy(ends.data(), batch_end, sizeof(int64_t) * n_batches);
+    int64_t prev = 0;
+    for (int64_t b = 0; b < n_batches; ++b) {
+        RB3_CHECK_ARG(ends[b] >= prev && ends[b] <= n_seq, "batch_end must be non-decreasing and <= n_seq");
+        prev = ends[b];
+    }
+    int64_t two = 0;
+    for (int64_t i = 0; i < ends[1]; ++i) {
+        RB3_CHECK_ARG(lens[i] >= 0, "negative string length");
+        two += lens[i];
+    }
+    RB3_CHECK_ARG(two == 0 || seq != nullptr, "seq is NULL");
+    // the first two batches on the device
+    const uint8_t *sd = seq;
+    DevBuf copy;
+    if (two > 0 && !is_device_ptr(seq)) {
+        RB3_TRY(copy.alloc((size_t)two, st));
+        RB3_CUDA_TRY(cudaMemcpyAsync(copy.p, seq, (size_t)two, cudaMemcpyHostToDevice, st));
+        sd = copy.as<uint8_t>();
+    }
+    double ms[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
+    RB3_TRY(tune_build(sd, lens, ends, o, index_mb, best, ms, mb, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < 3; ++c) {
+        if (cand_ms) cand_ms[c] = ms[c];
+        if (cand_mb) cand_mb[c] = mb[c];
+    }
+    return RB3_OK;
+}
 
 RB3_EXPORT int rb3_tune_merge(const rb3_index *dst, const rb3_index *src, const rb3_opts *base, rb3_opts *best,
                               double *best_ms, void *stream) {

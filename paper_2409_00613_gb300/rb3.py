@@ -34,7 +34,7 @@ class rb3_opts(ctypes.Structure):
 class rb3_server_opts(ctypes.Structure):
     _fields_ = [("min_len", ctypes.c_int32), ("slots", ctypes.c_int32), ("min_occ", ctypes.c_int64),
                 ("max_batch_bases", ctypes.c_int64), ("max_batch_requests", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("search_form", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
 
 
 COMPLETION_DTYPE = np.dtype([("req_id", "<i8"), ("tag", "<i8"), ("n_smem", "<i8"), ("status", "<i4"),
@@ -101,6 +101,7 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(_i64)]),
             "rb3_launch_count": (_i64, []),
             "rb3_tune_merge": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+            "rb3_tune_build": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp]),
             "rb3_tune_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp,
                                                ctypes.POINTER(ctypes.c_double), _vp]),
             "rb3_server_opts_default": (None, [_vp]),
@@ -108,6 +109,7 @@ def lib():
             "rb3_server_submit": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(_i64)]),
             "rb3_server_poll": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64), _i32]),
             "rb3_server_take": (ctypes.c_int, [_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)]),
+            "rb3_server_replay": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
             "rb3_server_batches": (_i64, [_vp]),
             "rb3_server_destroy": (None, [_vp]),
             "rb3_probe_random_gather": (ctypes.c_int, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double),
@@ -346,6 +348,19 @@ def rb3_tune_merge(dst: Index, src: Index, opts=None, stream=None):
     return best, ms.value
 
 
+def rb3_tune_build(seq, lens, batch_end, opts=None, index_mb: int = 0, stream=None):
+    """(best rb3_opts, [(D, build+merge ms, projected index MiB)]) for an incremental build."""
+    o = _opts(opts) or rb3_opts_default()
+    lens_a = np.ascontiguousarray(lens, dtype=np.int64) if not hasattr(lens, "data_ptr") else lens
+    ends = np.ascontiguousarray(batch_end, dtype=np.int64)
+    best = rb3_opts()
+    ms = (ctypes.c_double * 3)()
+    mb = (ctypes.c_double * 3)()
+    _check(lib().rb3_tune_build(_ptr(seq), _ptr(lens_a), _len(lens_a), _ptr(ends), len(ends), ctypes.byref(o),
+                                int(index_mb), ctypes.byref(best), ms, mb, _stream(stream)))
+    return best, [(D, ms[i], mb[i]) for i, D in enumerate((32, 64, 128))]
+
+
 def rb3_tune_search(idx: Index, q, qoff, min_len: int, min_occ: int = 1, opts=None, stream=None):
     """(best rb3_opts, ms) of the chunked SMEM search on these (device) queries."""
     o = _opts(opts) or rb3_opts_default()
@@ -547,6 +562,19 @@ def rb3_server_take(srv: Server, req_id: int, n_smem: int) -> np.ndarray:
     n = _i64()
     _check(lib().rb3_server_take(srv.handle, int(req_id), out.ctypes.data, len(out), ctypes.byref(n)))
     return out[:n.value]
+
+
+def rb3_server_replay(srv: Server, q, qoff, arrival_s):
+    """Open-loop replay (native threads): (done_s, batch) per request, relative to the
+    trace start; latency = done_s - arrival_s."""
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    qoff = np.ascontiguousarray(qoff, dtype=np.int64)
+    arr = np.ascontiguousarray(np.round(np.asarray(arrival_s) * 1e9), dtype=np.int64)
+    n = len(qoff) - 1
+    done = np.empty(n, dtype=np.int64)
+    batch = np.empty(n, dtype=np.int32)
+    _check(lib().rb3_server_replay(srv.handle, _ptr(q), _ptr(qoff), n, _ptr(arr), _ptr(done), _ptr(batch)))
+    return done / 1e9, batch
 
 
 def rb3_server_batches(srv: Server) -> int:

@@ -515,3 +515,21 @@ def test_merge_apply_refuses_bad_positions():
         assert np.array_equal(rb.rb3_export(dst), before)
     rb.rb3_merge_apply(dst, src, pos)
     check_index(dst, ref_bwt(S))
+
+
+def test_tune_build_picks_a_layout_and_the_result_is_exact():
+    """rb3_tune_build on the first two batches of an uneven-genome input: a D
+    among 32/64/128 with its segment length and seed cap; appending every batch
+    with those options gives the oracle's BWT; a budget below every layout's
+    projected index gives the smallest layout (D = 128)."""
+    S = synth.uneven(n_founders=3, founder_len=60_000, n_genomes=12, per_cluster=4, median=30_000, sigma=0.3,
+                     lo=10_000, hi=60_000, batch=4)
+    ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
+    best, table = rb.rb3_tune_build(S.seq, S.lens, ends)
+    assert best.occ_interval in (32, 64, 128) and best.seg_len > 0 and best.seed_cap > 0
+    assert [d for d, _, _ in table] == [32, 64, 128] and all(ms > 0 for _, ms, _ in table)
+    idx = rb.rb3_index_empty(best)
+    rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens, ends, best)
+    check_index(idx, ref_bwt(S), best.occ_interval)
+    small, table = rb.rb3_tune_build(torch.from_numpy(S.seq.copy()).to(DEV), S.lens, ends, index_mb=1)
+    assert small.occ_interval == 128 and table[2][2] < table[0][2]

@@ -76,3 +76,44 @@ def test_server_rejects_bad_symbols():
     with pytest.raises(rb.RB3Error):
         rb.rb3_server_submit(srv, np.array([1, 2, 0], np.uint8))
     srv.close()
+
+
+def test_server_plain_kernel_same_records():
+    """Micro-batches run with the one-query-per-thread kernel (search_form 1)
+    give the same records as the default form."""
+    S, idx = _index()
+    _, Q = synth.served_requests(S, rate=1000.0, n_req=80, lo=100, hi=20_000)
+    ref, _ = rb.rb3_mem_search(idx, Q.q, Q.qoff, 31, 1)
+    srv = rb.rb3_server_create(idx, slots=3, search_form=1, max_batch_bases=100_000)
+    tags = {rb.rb3_server_submit(srv, Q.q[Q.qoff[i]:Q.qoff[i + 1]], i): i for i in range(Q.nq)}
+    for c in _collect(srv, Q.nq):
+        assert c["status"] == 0
+        recs = rb.rb3_server_take(srv, c["req_id"], c["n_smem"])
+        want = ref[ref["qid"] == tags[c["req_id"]]]
+        for f in FIELDS:
+            assert np.array_equal(recs[f], want[f])
+    srv.close()
+    with pytest.raises(rb.RB3Error):
+        rb.rb3_server_create(idx, search_form=7)
+
+
+def test_server_replay_open_loop():
+    """The native replay submits every request at its arrival time and
+    reports each completion after its arrival; an impossible rate (all at
+    once) still completes, in micro-batches of more than one request."""
+    S, idx = _index()
+    _, Q = synth.served_requests(S, rate=1000.0, n_req=400, lo=100, hi=20_000)
+    for rate in (2000.0, 1e9):
+        arr = np.cumsum(synth.rng(5).exponential(1.0 / rate, size=Q.nq))
+        srv = rb.rb3_server_create(idx, slots=4)
+        done, batch = rb.rb3_server_replay(srv, Q.q, Q.qoff, arr)
+        srv.close()
+        assert (done >= arr).all() and (batch >= 1).all()
+        if rate > 1e6:
+            assert batch.max() > 1
+    with pytest.raises(rb.RB3Error):
+        srv = rb.rb3_server_create(idx)
+        try:
+            rb.rb3_server_replay(srv, Q.q, Q.qoff, arr[::-1].copy())
+        finally:
+            srv.close()
