@@ -518,18 +518,24 @@ def test_merge_apply_refuses_bad_positions():
 
 
 def test_tune_build_picks_a_layout_and_the_result_is_exact():
-    """rb3_tune_build on the first two batches of an uneven-genome input: a D
-    among 32/64/128 with its segment length and seed cap; appending every batch
-    with those options gives the oracle's BWT; a budget below every layout's
-    projected index gives the smallest layout (D = 128)."""
-    S = synth.uneven(n_founders=3, founder_len=60_000, n_genomes=12, per_cluster=4, median=30_000, sigma=0.3,
-                     lo=10_000, hi=60_000, batch=4)
+    """rb3_tune_build on the first two batches of an uneven-genome input: the
+    fastest D among 32/64/128 with its segment length and seed cap; appending
+    every batch with those options gives the oracle's BWT; a budget that only
+    the D = 128 layout fits (1 MiB for ~1.2 Msym: 1.14 MiB at D = 32 or 64,
+    0.86 at 128) gives D = 128."""
+    S = synth.uneven(n_founders=3, founder_len=60_000, n_genomes=12, per_cluster=4, median=50_000, sigma=0.0,
+                     lo=50_000, hi=50_000, batch=4)
     ends = np.array([b for (_, b) in S.batches], dtype=np.int64)
     best, table = rb.rb3_tune_build(S.seq, S.lens, ends)
-    assert best.occ_interval in (32, 64, 128) and best.seg_len > 0 and best.seed_cap > 0
     assert [d for d, _, _ in table] == [32, 64, 128] and all(ms > 0 for _, ms, _ in table)
+    assert best.occ_interval == min(table, key=lambda t: t[1])[0]
+    assert best.seg_len > 0 and best.seed_cap > 0
     idx = rb.rb3_index_empty(best)
     rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens, ends, best)
     check_index(idx, ref_bwt(S), best.occ_interval)
     small, table = rb.rb3_tune_build(torch.from_numpy(S.seq.copy()).to(DEV), S.lens, ends, index_mb=1)
-    assert small.occ_interval == 128 and table[2][2] < table[0][2]
+    assert table[2][2] <= 1 < table[0][2] and table[0][2] == table[1][2]
+    assert small.occ_interval == 128
+    idx = rb.rb3_index_empty(small)
+    rb.rb3_append_batches(idx, torch.from_numpy(S.seq.copy()).to(DEV), S.lens, ends, small)
+    check_index(idx, ref_bwt(S), 128)
