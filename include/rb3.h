@@ -192,6 +192,29 @@ int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int64_t *len, i
 int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                         int64_t *lo_hi, void *stream);
 
+/* BWA-SW between two prefix DAWGs (Section "Finding inexact matches with
+ * BWA-SW", Algorithm 5): for every query P = q[qoff[i] .. qoff[i+1]), its
+ * prefix DAWG -- a node is the SA interval (uk, us) of a substring of P in the
+ * BWT of the one-string, one-strand text P$ (strings with one interval are one
+ * node), an edge x -> cx for every symbol c of A..N that keeps the interval
+ * non-empty -- against the indexed text's (a node is a bi-interval (k, k', s);
+ * its children its BackwardExt by A, C, G, T), the query's nodes in a
+ * topological order.  The cells of a query node gather, over its in-edges
+ * (u, c), the four children of each kept cell of u (match +a when the text
+ * symbol is c, else -b; N matches nothing) and the cell itself (insertion,
+ * E = max(H - gap_open, E) - gap_ext), then deletions to the closure (F of a
+ * child = max(H - gap_open, F) - gap_ext); the W cells of largest H are kept
+ * (ties: smaller k, k', s).  The root's cell is the whole text with H = 0.
+ * out: 7 int64 per record (qid, uk, us, k, k', s, H), every kept cell with
+ * H > 0 of every query node but the root, sorted by (qid, uk, us, then H
+ * descending, k, k', s); host or device memory, caller-owned.  If more than
+ * cap records exist, *n_out holds the number and RB3_E_CAPACITY is returned.
+ * Queries of at most 2047 bases; W in 1..32; scores as
+ * rb3_haplotype_diversity; a double-strand index of any layout.
+ * RB3_E_CAPACITY also when a query node left more than 2048 candidate cells. */
+int rb3_bwasw(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a, int32_t b,
+              int32_t gap_open, int32_t gap_ext, int32_t W, int64_t *out, int64_t cap, int64_t *n_out, void *stream);
+
 /* Local haplotype diversity (Section "Estimating local haplotype diversity"):
  * Algorithm 5 (the revised BWA-SW of Section "Finding inexact matches with
  * BWA-SW") on the graph of each linear query q[qoff[i] .. qoff[i+1]), walked
@@ -210,8 +233,9 @@ int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *q
  * RB3_E_INVAL: a symbol outside 1..5, W outside 1..32, a < 1, b < 0,
  * gap_open < 0, gap_ext < 1, a score above 65536, a query longer than
  * 2^29 / a, or a single-strand index.  RB3_E_CAPACITY when a query symbol
- * left more than 2048 candidate cells: that query's n_out is -1, every other
- * query's result is written. */
+ * left more than 2048 candidate cells, or its deletion chain ran longer than
+ * that table: that query's n_out is -1, every other query's result is
+ * written. */
 int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a,
                             int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W, int32_t redundancy,
                             int64_t *out, int64_t *n_out, void *stream);

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librb3.so")
 SOURCES = ["api.cu", "sort.cu", "build.cu", "merge.cu", "search.cu", "locate.cu", "rle.cu", "probe.cu", "noalloc.cu",
-           "pipeline.cu", "server.cu", "tune.cu", "diversity.cu"]
+           "pipeline.cu", "server.cu", "tune.cu", "diversity.cu", "bwasw.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-Xptxas", "-v"]
 

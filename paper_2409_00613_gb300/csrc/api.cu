@@ -460,6 +460,45 @@ RB3_EXPORT int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const
     return RB3_OK;
 }
 
+RB3_EXPORT int rb3_bwasw(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a,
+                         int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W, int64_t *out, int64_t cap,
+                         int64_t *n_out, void *stream) {
+    g_err.clear();
+    RB3_CHECK_ARG(idx != nullptr && n_out != nullptr, "NULL argument");
+    *n_out = 0;
+    RB3_CHECK_ARG(nq >= 0 && cap >= 0, "negative size");
+    RB3_CHECK_ARG(!idx->single_strand, "BWA-SW needs a double-strand index");
+    RB3_CHECK_ARG(a >= 1 && b >= 0 && gap_open >= 0 && gap_ext >= 1, "scores: a >= 1, b >= 0, q >= 0, e >= 1");
+    RB3_CHECK_ARG(a <= 65536 && b <= 65536 && gap_open <= 65536 && gap_ext <= 65536, "a score above 65536");
+    RB3_CHECK_ARG(W >= 1 && W <= 32, "W must be in 1..32");
+    if (nq == 0) return RB3_OK;
+    RB3_CHECK_ARG(qoff != nullptr && (cap == 0 || out != nullptr), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> qo;
+    RB3_TRY(read_i64(qoff, nq + 1, qo, st));
+    RB3_TRY(check_qoff(qo));
+    RB3_CHECK_ARG(qo[nq] == qo[0] || q != nullptr, "q is NULL");
+    for (int64_t i = 0; i < nq; ++i) RB3_CHECK_ARG(qo[i + 1] - qo[i] <= 2047, "BWA-SW queries are at most 2047 bases");
+    InArg dq, doff;
+    RB3_TRY(dq.set(q, (size_t)qo[nq], st));
+    RB3_TRY(doff.set(qoff, sizeof(int64_t) * (nq + 1), st));
+    const bool dev_out = cap == 0 || is_device_ptr(out);
+    DevBuf ob;
+    int64_t *o = out;
+    if (!dev_out) {
+        RB3_TRY(ob.alloc(sizeof(int64_t) * 7 * (size_t)cap, st));
+        o = ob.as<int64_t>();
+    }
+    const int32_t prm[5] = {a, b, gap_open, gap_ext, W};
+    const int r = bwasw_impl(idx, static_cast<const uint8_t *>(dq.dev), static_cast<const int64_t *>(doff.dev), qo, nq,
+                             prm, o, cap, n_out, st);
+    if (r != RB3_OK) return r;
+    if (!dev_out && *n_out > 0)
+        RB3_CUDA_TRY(cudaMemcpyAsync(out, o, sizeof(int64_t) * 7 * (size_t)*n_out, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    return RB3_OK;
+}
+
 RB3_EXPORT int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq,
                                        int32_t a, int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W,
                                        int32_t redundancy, int64_t *out, int64_t *n_out, void *stream) {
@@ -504,7 +543,8 @@ RB3_EXPORT int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, c
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     for (int64_t i = 0; i < nq; ++i)
         if (counts[i] < 0) {
-            set_error("query %lld: a step left more than 2048 candidate cells", (long long)i);
+            set_error("query %lld: a step left more than 2048 candidate cells, or its deletion chain outran "
+                      "the 2048-cell table", (long long)i);
             return RB3_E_CAPACITY;
         }
     return RB3_OK;

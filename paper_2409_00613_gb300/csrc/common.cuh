@@ -833,6 +833,11 @@ int check_codes(const uint8_t *q, int64_t n, cudaStream_t st);
 int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int64_t total_q,
                    const int32_t prm[6], int64_t *out, int64_t *n_out, cudaStream_t st);
 int diversity_stats(int64_t out[2], bool reset);
+// BWA-SW between the prefix DAWG of every query and the text's (prm = a, b, q,
+// e, W); records of 7 int64 (qid, uk, us, k, k', s, H) sorted by (qid, uk, us,
+// band rank); q, qoff device pointers, qo the offsets on the host.
+int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const std::vector<int64_t> &qo, int64_t nq,
+               const int32_t prm[5], int64_t *out, int64_t cap, int64_t *n_out, cudaStream_t st);
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);

@@ -101,6 +101,7 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(_i64)]),
             "rb3_launch_count": (_i64, []),
             "rb3_tune_merge": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+            "rb3_bwasw": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _vp]),
             "rb3_tune_build": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _vp]),
             "rb3_tune_search": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _i64, _vp, _vp,
                                                ctypes.POINTER(ctypes.c_double), _vp]),
@@ -272,6 +273,27 @@ def rb3_backward_search(idx: Index, q, qoff, nq=None, lo_hi=None, stream=None):
         lo_hi = np.empty((nq, 2), dtype=np.int64)
     _check(lib().rb3_backward_search(idx.handle, _ptr(q), _ptr(qoff), nq, _ptr(lo_hi), _stream(stream)))
     return lo_hi
+
+
+def rb3_bwasw(idx: Index, q, qoff, a: int = 1, b: int = 3, gap_open: int = 5, gap_ext: int = 2, W: int = 25,
+              cap=None, nq=None, out=None, stream=None):
+    """BWA-SW of every query's prefix DAWG against the index (see include/rb3.h):
+    (N, 7) int64 records (qid, uk, us, k, k', s, H) sorted by (qid, uk, us, band
+    rank).  Grows a host output buffer once when cap is not given."""
+    nq = _len(qoff) - 1 if nq is None else nq
+    n_out = _i64(0)
+    if cap is None:
+        cap = 1 << 16
+    for _ in range(2):
+        buf = np.empty((max(cap, 1), 7), dtype=np.int64) if out is None else out
+        code = lib().rb3_bwasw(idx.handle, _ptr(q), _ptr(qoff), nq, int(a), int(b), int(gap_open), int(gap_ext),
+                               int(W), _ptr(buf), int(cap), ctypes.byref(n_out), _stream(stream))
+        if code == RB3_E_CAPACITY and out is None and n_out.value > cap:
+            cap = n_out.value
+            continue
+        _check(code)
+        return buf[:n_out.value] if out is None else n_out.value
+    _check(code)
 
 
 def rb3_haplotype_diversity(idx: Index, q, qoff, a: int = 1, b: int = 3, gap_open: int = 5, gap_ext: int = 2,
