@@ -428,6 +428,7 @@ def run_rb3(args, rank, world, local_rank):
         out["run_length"] = run_length_bench(rb, torch, S, idx, args, st, dev,
                                              out["mem_search"]["autotune_chunk_len"])
         out["haplotype_diversity"] = diversity_bench(rb, torch, S, idx, st, dev, probe)
+        out["bwasw"] = bwasw_bench(rb, torch, S, idx, st, dev)
     idx.free()
     if not args.no_search and rank == 0:
         out["locate"] = locate_bench(rb, torch, S, args, st, dev, opts, batches, off)
@@ -654,6 +655,34 @@ def diversity_bench(rb, torch, S, idx, st, dev, probe_g, k=51, n_kmers=20_000, W
                                "unit": "G req/s", "frac": round(res["rank_reads_G_per_s"] / probe_g, 4),
                                "what": "rank-all reads counted by the kernel over its CUDA-event time; ceiling: "
                                        "the random-read probe of the merge walk's roofline"}
+    except (rb.RB3Error, RuntimeError) as e:  # a side leg: record the failure, keep the bench line
+        res["error"] = f"{type(e).__name__}: {e}"
+    return res
+
+
+def bwasw_bench(rb, torch, S, idx, st, dev, nq=2000, L=150):
+    """BWA-SW between query DAWGs and the finished index (Algorithm 5 with
+    the query as a DAWG): nq queries of L bp from the haplotypes with 2%
+    substitutions, default scores, W = 25; queries/s and records."""
+    Q = synth.mem_queries(S, seed=synth.SEED_BASE + 79, nq=nq, median=L, sigma=0.0, lo=L, hi=L, sub=0.02,
+                          random_frac=0.0)
+    dq, doff = torch.from_numpy(Q.q).to(dev), torch.from_numpy(Q.qoff).to(dev)
+    cap = nq * 2 * (L + 1) * 25
+    out = torch.empty((cap, 7), dtype=torch.int64, device=dev)
+    res = {"workload": f"{nq} queries of {L} bp from the haplotypes with 2% substitutions, scores a=1 b=3 q=5 e=2, "
+                       "W=25, on the finished index", "unit": "queries/s"}
+    try:
+        n = rb.rb3_bwasw(idx, dq, doff, 1, 3, 5, 2, 25, cap=cap, out=out, stream=st)  # warm-up
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        n = rb.rb3_bwasw(idx, dq, doff, 1, 3, 5, 2, 25, cap=cap, out=out, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res.update({"value": round(nq / (ms * 1e-3), 1), "ms": round(ms, 3), "records": int(n),
+                    "records_per_query": round(n / nq, 1)})
     except (rb.RB3Error, RuntimeError) as e:  # a side leg: record the failure, keep the bench line
         res["error"] = f"{type(e).__name__}: {e}"
     return res
