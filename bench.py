@@ -50,13 +50,15 @@ METRIC = "BWT-merge Msymbols/s"
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the four
 # merges of one pass of the default workload, averaged:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
-#       -k regex:k_merge_walk -s 3 -c 4 python bench.py --no-cpu --no-serve --no-search --no-plain
-#       --warmup 3 --steps 4
-# Keyed by (kernel, Occ interval, founder bp, merge form, digest of the merge
-# kernel's sources): a change to the kernel's source drops the figure (null)
+#       -k regex:k_walk_seeded -s 3 -c 4 python bench.py --steps 4 --warmup 3 --no-serve --no-cpu --no-search
+#       --no-plain --uneven-genomes 0 --seg-len 1284 --seed-cap 1284
+# (the knobs the autotuner picks for this workload; k.merge_walk is k_walk_seeded's phase)
+# Keyed by (kernel, Occ interval, founder bp, merge form, segment length, seed
+# cap, digest of the merge kernel's sources): a change to the kernel's source
+# or other knobs drops the figure (null)
 # until it is captured again.  Every timed step is a step of one pass, so the
 # per-launch average does not depend on the number of steps (a multiple of 4).
-NCU_TRAFFIC: dict = {}
+NCU_TRAFFIC: dict = {("k.merge_walk", 32, 5_000_000, 0, 1284, 1284, "84c09aac0f177e7c"): 5.99e9}
 
 
 def kernel_digest() -> str:
@@ -366,7 +368,8 @@ def run_rb3(args, rank, world, local_rank):
         achieved = kbytes / (kms * 1e-3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": (NCU_TRAFFIC.get((top, info["occ_interval"], founder, args.merge_form, kernel_digest()))
+                "traffic": (NCU_TRAFFIC.get((top, info["occ_interval"], founder, args.merge_form, opts["seg_len"],
+                                             opts["seed_cap"], kernel_digest()))
                             if args.steps % n_merge == 0 else None),
                 "kernel_digest": kernel_digest(),
                 "algo_bytes_per_launch": kbytes / max(1, kcalls), "avg_launch_ms": kms / max(1, kcalls),

@@ -211,7 +211,9 @@ int rb3_backward_search(const rb3_index *idx, const uint8_t *q, const int64_t *q
  * cap records exist, *n_out holds the number and RB3_E_CAPACITY is returned.
  * Queries of at most 2047 bases; W in 1..32; scores as
  * rb3_haplotype_diversity; a double-strand index of any layout.
- * RB3_E_CAPACITY also when a query node left more than 2048 candidate cells. */
+ * RB3_E_CAPACITY also when a query node left more than 65,534 candidate cells
+ * (the deletion closure of a long exact match holds about a dozen cells per
+ * unit of score on a pangenome). */
 int rb3_bwasw(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a, int32_t b,
               int32_t gap_open, int32_t gap_ext, int32_t W, int64_t *out, int64_t cap, int64_t *n_out, void *stream);
 
@@ -233,9 +235,8 @@ int rb3_bwasw(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64
  * RB3_E_INVAL: a symbol outside 1..5, W outside 1..32, a < 1, b < 0,
  * gap_open < 0, gap_ext < 1, a score above 65536, a query longer than
  * 2^29 / a, or a single-strand index.  RB3_E_CAPACITY when a query symbol
- * left more than 2048 candidate cells, or its deletion chain ran longer than
- * that table: that query's n_out is -1, every other query's result is
- * written. */
+ * left more than 65,534 candidate cells: that query's n_out is -1, every
+ * other query's result is written. */
 int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, int64_t nq, int32_t a,
                             int32_t b, int32_t gap_open, int32_t gap_ext, int32_t W, int32_t redundancy,
                             int64_t *out, int64_t *n_out, void *stream);

@@ -12,20 +12,41 @@ namespace dv {
 
 constexpr int32_t DV_NEG = -(1 << 30);
 constexpr unsigned DV_FULL = 0xffffffffu;
-__host__ __device__ constexpr size_t dv_warp_bytes(int cap) { return (size_t)cap * (3 * 8 + 3 * 4 + 1); }
+constexpr int DV_CAP_G = 65534;  // cells of the global-memory tier (indexes + 1 fit 16 bits)
+
+// Hash slots of a table of cap cells: twice the next power of two.
+__host__ __device__ constexpr int dv_hash_slots(int cap) {
+    int h = 1;
+    while (h < cap) h <<= 1;
+    return 2 * h;
+}
+// A table of cap cells (structure of arrays: k, k', s, H, E, F, a worklist
+// ring of cell indexes, a flag byte) and its hash index (cell index + 1, 0 =
+// empty; open addressing with linear probing), rounded to 16 bytes.
+__host__ __device__ constexpr size_t dv_warp_bytes(int cap) {
+    return ((size_t)cap * (3 * 8 + 3 * 4 + 2 + 1) + (size_t)dv_hash_slots(cap) * 2 + 15) / 16 * 16;
+}
 
 struct DvParams {
     int32_t a, b, q, e, W, redundancy;
 };
 
-// One warp's cells, structure of arrays.
+// One warp's cells.
 struct DvTab {
     int64_t *k, *kp, *s;
     int32_t *H, *E, *F;
-    uint8_t *flag;  // bit 0: to be extended by deletions; bit 1: taken into the band
+    unsigned short *queue;  // worklist ring of the cells to extend by deletions
+    uint8_t *flag;          // bit 0: in the worklist; bit 1: taken into the band
+    unsigned short *slot;   // hash index over (k, k', s)
+};
+
+// The table's counters (warp-uniform): cells, worklist head and tail.
+struct DvSt {
+    int tn, qh, qt;
 };
 
 template <int CAP> __device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
+    static_assert(CAP % 2 == 0 && CAP <= DV_CAP_G, "cell count: even, indexes + 1 in 16 bits");
     DvTab t;
     t.k = reinterpret_cast<int64_t *>(base);
     t.kp = t.k + CAP;
@@ -33,8 +54,53 @@ template <int CAP> __device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
     t.H = reinterpret_cast<int32_t *>(t.s + CAP);
     t.E = t.H + CAP;
     t.F = t.E + CAP;
-    t.flag = reinterpret_cast<uint8_t *>(t.F + CAP);
+    t.queue = reinterpret_cast<unsigned short *>(t.F + CAP);
+    t.flag = reinterpret_cast<uint8_t *>(t.queue + CAP);
+    t.slot = reinterpret_cast<unsigned short *>(t.flag + CAP);  // CAP is even: 2-byte aligned
     return t;
+}
+
+__device__ __forceinline__ uint32_t dv_hash(int64_t k, int64_t kp, int64_t s);
+
+// Clears the whole hash index (a table in memory not yet used).
+template <int CAP> __device__ __forceinline__ void dv_clear_all(const DvTab &T, DvSt &st, int lane) {
+    for (int i = lane; i < dv_hash_slots(CAP); i += 32) T.slot[i] = 0;
+    st.tn = st.qh = st.qt = 0;
+    __syncwarp();
+}
+
+// Empties the table (the warp together).  Small hash indexes are cleared
+// whole; a large one only at the slots of the st.tn cells in use (each cell's
+// slot found first, then all cleared, so no probe crosses a cleared slot).
+template <int CAP> __device__ __forceinline__ void dv_clear(const DvTab &T, DvSt &st, int lane) {
+    constexpr int HS = dv_hash_slots(CAP);
+    if (HS <= 8192 || st.tn * 4 > HS) {
+        for (int i = lane; i < HS; i += 32) T.slot[i] = 0;
+    } else {
+        for (int j0 = 0; j0 < st.tn; j0 += 32) {
+            const int j = j0 + lane;
+            uint32_t pos = 0;
+            if (j < st.tn) {
+                pos = dv_hash(T.k[j], T.kp[j], T.s[j]) & (HS - 1);
+                while (T.slot[pos] != (unsigned short)(j + 1)) pos = (pos + 1) & (HS - 1);
+            }
+            __syncwarp();
+            if (j < st.tn) T.slot[pos] = 0;
+            __syncwarp();
+        }
+    }
+    st.tn = 0;
+    st.qh = 0;
+    st.qt = 0;
+    __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t dv_hash(int64_t k, int64_t kp, int64_t s) {
+    uint64_t x = (uint64_t)k * 0x9E3779B97F4A7C15ull ^ (uint64_t)kp * 0xC2B2AE3D27D4EB4Full ^
+                 (uint64_t)s * 0x165667B19E3779F9ull;
+    x ^= x >> 29;
+    x *= 0xBF58476D1CE4E5B9ull;
+    return (uint32_t)(x >> 32);
 }
 
 // BackwardExt (Algorithm 3) of (k, k', s) by A, C, G and T at once, from the
@@ -62,56 +128,83 @@ __device__ __forceinline__ void dv_children(const OccView &V, int64_t k, int64_t
     }
 }
 
-// Finds (k, k', s) among the first tn cells: its index or -1 (warp-uniform).
-__device__ __forceinline__ int dv_find(const DvTab &T, int tn, int64_t k, int64_t kp, int64_t s, int lane) {
-    for (int j0 = 0; j0 < tn; j0 += 32) {
-        const int j = j0 + lane;
-        const bool hit = j < tn && T.s[j] == s && T.k[j] == k && T.kp[j] == kp;
-        const unsigned m = __ballot_sync(DV_FULL, hit);
-        if (m) return j0 + __ffs(m) - 1;
-    }
-    return -1;
-}
-
-// Raises the cell (k, k', s) to H = max(H, h), E = max(E, ev), F = max(F, fv),
-// adding it when absent; a cell whose H or F rises is marked for deletion
-// extension.  Warp-uniform; returns the new cell count.
+// Raises the cells offered by the lanes with `want` -- (k, k', s) to H =
+// max(H, h), E = max(E, ev), F = max(F, fv) -- adding those absent; a cell
+// that is new, or whose H or F rises, joins the worklist unless it is in it.
+// Lanes offering the same cell are combined first (the maxima, one leader),
+// so the leaders hold distinct keys: each looks its key up in the hash index,
+// raises the cell it finds, or, absent, takes a new cell (numbered in lane
+// order after st.tn) and claims a free slot for it.  Called by the whole warp;
+// st stays warp-uniform; sets overflow, changing nothing, when the new cells
+// do not fit.
 template <int CAP>
-__device__ __forceinline__ int dv_upsert(const DvTab &T, int tn, int64_t k, int64_t kp, int64_t s, int32_t h,
-                                         int32_t ev, int32_t fv, int lane, bool &overflow) {
-    const int j = dv_find(T, tn, k, kp, s, lane);
-    if (j >= 0) {
-        if (lane == 0) {
-            bool up = false;
-            if (ev > T.E[j]) T.E[j] = ev;
-            if (fv > T.F[j]) {
-                T.F[j] = fv;
-                up = true;
+__device__ __forceinline__ void dv_upsert_batch(const DvTab &T, DvSt &st, bool want, int64_t k, int64_t kp, int64_t s,
+                                                int32_t h, int32_t ev, int32_t fv, int lane, bool &overflow) {
+    const unsigned vm = __ballot_sync(DV_FULL, want);
+    if (!vm) return;
+    const unsigned g = __match_any_sync(DV_FULL, k) & __match_any_sync(DV_FULL, kp) & __match_any_sync(DV_FULL, s) & vm;
+    if (want) {
+        h = __reduce_max_sync(g, h);
+        ev = __reduce_max_sync(g, ev);
+        fv = __reduce_max_sync(g, fv);
+    }
+    const bool lead = want && (__ffs(g) - 1) == lane;
+    constexpr uint32_t HM = dv_hash_slots(CAP) - 1;
+    uint32_t pos = dv_hash(k, kp, s) & HM;
+    int found = -1;
+    if (lead) {
+        for (;;) {
+            const int sl = T.slot[pos];
+            if (sl == 0) break;
+            const int j = sl - 1;
+            if (T.s[j] == s && T.k[j] == k && T.kp[j] == kp) {
+                found = j;
+                break;
             }
-            if (h > T.H[j]) {
-                T.H[j] = h;
-                up = true;
-            }
-            if (up) T.flag[j] |= 1;
+            pos = (pos + 1) & HM;
         }
-        __syncwarp();
-        return tn;
-    }
-    if (tn >= CAP) {
-        overflow = true;
-        return tn;
-    }
-    if (lane == 0) {
-        T.k[tn] = k;
-        T.kp[tn] = kp;
-        T.s[tn] = s;
-        T.H[tn] = h;
-        T.E[tn] = ev;
-        T.F[tn] = fv;
-        T.flag[tn] = 1;
     }
     __syncwarp();
-    return tn + 1;
+    const unsigned nm = __ballot_sync(DV_FULL, lead && found < 0);
+    const int nnew = __popc(nm);
+    if (st.tn + nnew > CAP) {
+        overflow = true;
+        return;
+    }
+    int cell = -1;  // the cell to put on the worklist
+    if (lead && found >= 0) {
+        bool up = false;
+        if (ev > T.E[found]) T.E[found] = ev;
+        if (fv > T.F[found]) {
+            T.F[found] = fv;
+            up = true;
+        }
+        if (h > T.H[found]) {
+            T.H[found] = h;
+            up = true;
+        }
+        if (up && !(T.flag[found] & 1)) {
+            T.flag[found] |= 1;
+            cell = found;
+        }
+    } else if (lead) {
+        const int j = st.tn + __popc(nm & ((1u << lane) - 1u));
+        T.k[j] = k;
+        T.kp[j] = kp;
+        T.s[j] = s;
+        T.H[j] = h;
+        T.E[j] = ev;
+        T.F[j] = fv;
+        T.flag[j] = 1;
+        cell = j;
+        // a free slot from where the lookup stopped (other leaders may take some)
+        while (atomicCAS(&T.slot[pos], (unsigned short)0, (unsigned short)(j + 1)) != 0) pos = (pos + 1) & HM;
+    }
+    const unsigned pm = __ballot_sync(DV_FULL, cell >= 0);
+    if (cell >= 0) T.queue[(st.qt + __popc(pm & ((1u << lane) - 1u))) % CAP] = (unsigned short)cell;
+    st.tn += nnew;
+    st.qt += __popc(pm);
+    __syncwarp();
 }
 
 // Band order: larger H first, then smaller k, k', s.
@@ -123,6 +216,34 @@ __device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, i
     return s1 < s2;
 }
 
+
+// The deletion closure: cells are taken off the worklist 32 at a time; each
+// with H or F still giving a positive F to its children extends them (F =
+// max(H - q, F) - e); a child that is new or whose H or F rises joins the
+// worklist again.  The recurrences are monotone, so the closure is the same in
+// any order.
+template <int NS, int CAP>
+__device__ __forceinline__ void dv_close(const OccView &V, const DvTab &T, DvSt &st, const DvParams &p, int lane,
+                                         bool &overflow, unsigned long long &n_ext) {
+    while (!overflow && st.qh < st.qt) {
+        const int cnt = st.qt - st.qh < 32 ? st.qt - st.qh : 32;
+        int32_t fv = DV_NEG;
+        int64_t yk[4] = {0, 0, 0, 0}, ykp[4] = {0, 0, 0, 0}, ys[4] = {0, 0, 0, 0};
+        if (lane < cnt) {
+            const int j = T.queue[(st.qh + lane) % CAP];
+            T.flag[j] &= (uint8_t)~1u;
+            fv = max(T.H[j] - p.q, T.F[j]) - p.e;
+            if (fv > 0) dv_children<NS>(V, T.k[j], T.kp[j], T.s[j], yk, ykp, ys);
+        }
+        st.qh += cnt;
+        const bool ext = lane < cnt && fv > 0;
+        n_ext += __popc(__ballot_sync(DV_FULL, ext));
+        __syncwarp();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            if (!overflow) dv_upsert_batch<CAP>(T, st, ext && ys[a] > 0, yk[a], ykp[a], ys[a], fv, DV_NEG, fv, lane, overflow);
+    }
+}
 
 }  // namespace dv
 }  // namespace rb3

@@ -543,8 +543,7 @@ RB3_EXPORT int rb3_haplotype_diversity(const rb3_index *idx, const uint8_t *q, c
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     for (int64_t i = 0; i < nq; ++i)
         if (counts[i] < 0) {
-            set_error("query %lld: a step left more than 2048 candidate cells, or its deletion chain outran "
-                      "the 2048-cell table", (long long)i);
+            set_error("query %lld: a step left more than 65534 candidate cells", (long long)i);
             return RB3_E_CAPACITY;
         }
     return RB3_OK;

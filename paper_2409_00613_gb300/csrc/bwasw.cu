@@ -44,7 +44,7 @@ constexpr int BW_MAXN = 2 * BW_NP;    // the SA intervals of P$'s substrings: be
 constexpr int BW_HASH = 8192;         // node hash slots (a power of two, twice the nodes)
 constexpr int BW_THREADS = 256;
 constexpr int BW_PER = BW_NP / BW_THREADS;
-constexpr int BW_CAP_S = 256, BW_WARPS_S = 8;  // cell tables, as the linear-query kernel
+constexpr int BW_CAP_S = 256, BW_WARPS_S = 6;  // cell tables, as the linear-query kernel
 constexpr int BW_CAP_L = 2048, BW_WARPS_L = 2;
 static_assert(dv_warp_bytes(BW_CAP_S) % 16 == 0 && dv_warp_bytes(BW_CAP_L) % 16 == 0, "table alignment");
 
@@ -387,16 +387,20 @@ struct Kept {
     int32_t *n;  // [nodes] kept cells of the node
 };
 
-template <int NS, int CAP, int WARPS>
+// GM: the tables in global memory (gtab, one per warp of the launch).
+template <int NS, int CAP, int WARPS, bool GM>
 __global__ void __launch_bounds__(32 * WARPS)
     k_bwasw(OccView V, const int64_t *__restrict__ sel, int64_t nsel, const int64_t *__restrict__ nbase,
-            const int64_t *__restrict__ ebase, QDawg G, DvParams p, Kept K, int32_t *__restrict__ overflow) {
+            const int64_t *__restrict__ ebase, QDawg G, DvParams p, Kept K, int32_t *__restrict__ overflow,
+            uint8_t *__restrict__ gtab) {
     extern __shared__ __align__(16) uint8_t bw_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t wi = (int64_t)blockIdx.x * WARPS + w;
     if (wi >= nsel) return;  // the whole warp leaves together
     const int64_t ci = sel ? sel[wi] : wi;
-    const DvTab T = dv_tab<CAP>(bw_smem + (size_t)w * dv_warp_bytes(CAP));
+    const DvTab T = dv_tab<CAP>(GM ? gtab + (size_t)wi * dv_warp_bytes(CAP) : bw_smem + (size_t)w * dv_warp_bytes(CAP));
+    DvSt st{0, 0, 0};
+    dv_clear_all<CAP>(T, st, lane);
     const int64_t nb = nbase[ci], eb = ebase[ci];
     const int nn = G.nn[ci];
     const int32_t *ioff = G.in_off + nb + ci;
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(32 * WARPS)
     bool over = false;
     unsigned long long n_ext = 0;
     for (int v = 1; v < nn && !over; ++v) {
-        int tn = 0;
+        dv_clear<CAP>(T, st, lane);
         for (int e = ioff[v]; e < ioff[v + 1] && !over; ++e) {
             const int u = G.in_pred[eb + e], c = G.in_c[eb + e];
             const int cnt = K.n[nb + u];
@@ -432,60 +436,20 @@ __global__ void __launch_bounds__(32 * WARPS)
             int64_t xk[4] = {0, 0, 0, 0}, xkp[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
             if (lane < cnt) dv_children<NS>(V, ck, ckp, cs, xk, xkp, xs);
             n_ext += cnt;
-            for (int t = 0; t < cnt && !over; ++t) {
-                const int32_t h = __shfl_sync(DV_FULL, cH, t);
 #pragma unroll
-                for (int a = 1; a <= 4; ++a) {
-                    const int64_t k = __shfl_sync(DV_FULL, xk[a - 1], t);
-                    const int64_t kp = __shfl_sync(DV_FULL, xkp[a - 1], t);
-                    const int64_t s = __shfl_sync(DV_FULL, xs[a - 1], t);
-                    const int32_t g = h + (a == c ? p.a : -p.b);
-                    if (s > 0 && g > 0 && !over) tn = dv_upsert<CAP>(T, tn, k, kp, s, g, DV_NEG, DV_NEG, lane, over);
-                }
+            for (int a = 1; a <= 4; ++a) {
+                const int32_t g = cH + (a == c ? p.a : -p.b);
+                if (!over)
+                    dv_upsert_batch<CAP>(T, st, lane < cnt && xs[a - 1] > 0 && g > 0, xk[a - 1], xkp[a - 1],
+                                         xs[a - 1], g, DV_NEG, DV_NEG, lane, over);
             }
             // insertion: the query symbol against a gap, the text node unchanged
             const int32_t ev = max(cH - p.q, cE) - p.e;
-            for (int t = 0; t < cnt && !over; ++t) {
-                const int32_t e1 = __shfl_sync(DV_FULL, ev, t);
-                const int64_t k = __shfl_sync(DV_FULL, ck, t);
-                const int64_t kp = __shfl_sync(DV_FULL, ckp, t);
-                const int64_t s = __shfl_sync(DV_FULL, cs, t);
-                if (e1 > 0) tn = dv_upsert<CAP>(T, tn, k, kp, s, e1, e1, DV_NEG, lane, over);
-            }
+            if (!over) dv_upsert_batch<CAP>(T, st, lane < cnt && ev > 0, ck, ckp, cs, ev, ev, DV_NEG, lane, over);
         }
         // deletion: a text symbol against a gap, until no cell is left to extend
-        for (int pass = 0; !over; ++pass) {
-            bool any = false;
-            for (int j0 = 0; j0 < tn && !over; j0 += 32) {
-                const int j = j0 + lane;
-                const bool act = j < tn && (T.flag[j] & 1);
-                int32_t fv = DV_NEG;
-                int64_t yk[4] = {0, 0, 0, 0}, ykp[4] = {0, 0, 0, 0}, ys[4] = {0, 0, 0, 0};
-                if (act) {
-                    fv = max(T.H[j] - p.q, T.F[j]) - p.e;
-                    if (fv > 0) dv_children<NS>(V, T.k[j], T.kp[j], T.s[j], yk, ykp, ys);
-                    T.flag[j] &= (uint8_t)~1u;
-                }
-                any |= __ballot_sync(DV_FULL, act) != 0;
-                unsigned todo = __ballot_sync(DV_FULL, act && fv > 0);
-                n_ext += __popc(todo);
-                __syncwarp();
-                while (todo && !over) {
-                    const int t = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const int32_t f = __shfl_sync(DV_FULL, fv, t);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int64_t k = __shfl_sync(DV_FULL, yk[a], t);
-                        const int64_t kp = __shfl_sync(DV_FULL, ykp[a], t);
-                        const int64_t s = __shfl_sync(DV_FULL, ys[a], t);
-                        if (s > 0 && !over) tn = dv_upsert<CAP>(T, tn, k, kp, s, f, DV_NEG, f, lane, over);
-                    }
-                }
-            }
-            if (!any) break;
-            if (pass > CAP) over = true;  // a chain cannot be longer than the table
-        }
+        dv_close<NS, CAP>(V, T, st, p, lane, over, n_ext);
+        const int tn = st.tn;
         if (over) break;
         // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
         const int keep = min(tn, W);
@@ -583,10 +547,26 @@ template <int NS, int CAP, int WARPS>
 int bw_launch(const rb3_index *idx, const int64_t *sel, int64_t nsel, const int64_t *nbase, const int64_t *ebase,
               const QDawg &G, const DvParams &p, const Kept &K, int32_t *overflow, cudaStream_t st) {
     const size_t smem = WARPS * dv_warp_bytes(CAP);
-    auto kern = k_bwasw<NS, CAP, WARPS>;
+    auto kern = k_bwasw<NS, CAP, WARPS, false>;
     RB3_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RB3_LAUNCH(kern, nb_for(nsel, WARPS), 32 * WARPS, smem, st, occ_view(idx), sel, nsel, nbase, ebase, G, p, K,
-               overflow);
+               overflow, (uint8_t *)nullptr);
+    return RB3_OK;
+}
+
+// The global-memory tier: one warp per CTA, at most BW_GM_WARPS tables at once.
+constexpr int64_t BW_GM_WARPS = 1024;
+template <int NS>
+int bw_launch_gm(const rb3_index *idx, const int64_t *sel, int64_t nsel, const int64_t *nbase, const int64_t *ebase,
+                 const QDawg &G, const DvParams &p, const Kept &K, int32_t *overflow, cudaStream_t st) {
+    const int64_t nw = nsel < BW_GM_WARPS ? nsel : BW_GM_WARPS;
+    DevBuf tab;
+    RB3_TRY(tab.alloc(dv_warp_bytes(DV_CAP_G) * (size_t)nw, st));
+    for (int64_t b = 0; b < nsel; b += nw) {
+        const int64_t n = nsel - b < nw ? nsel - b : nw;
+        RB3_LAUNCH((k_bwasw<NS, DV_CAP_G, 1, true>), (unsigned)n, 32, 0, st, occ_view(idx), sel + b, n, nbase, ebase,
+                   G, p, K, overflow, tab.as<uint8_t>());
+    }
     return RB3_OK;
 }
 
@@ -676,12 +656,25 @@ int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, cons
                                                                      d_nbase, d_ebase, G, p, K, d_over, st))));
             RB3_CUDA_TRY(cudaMemcpyAsync(over.data(), d_over, sizeof(int32_t) * cq, cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int64_t> sel2;
             for (int64_t i = 0; i < cq; ++i)
-                if (over[i]) {
-                    set_error("bwasw: query %lld left more than %d candidate cells at a node", (long long)(q0 + i),
-                              BW_CAP_L);
-                    return RB3_E_CAPACITY;
-                }
+                if (over[i]) sel2.push_back(i);
+            if (!sel2.empty()) {  // the global-memory tier
+                DevBuf bsel2;
+                RB3_TRY(bsel2.alloc(sizeof(int64_t) * sel2.size(), st));
+                RB3_CUDA_TRY(
+                    cudaMemcpyAsync(bsel2.p, sel2.data(), sizeof(int64_t) * sel2.size(), cudaMemcpyHostToDevice, st));
+                RB3_WITH_NS(idx->D, RB3_TRY((bw_launch_gm<NS>(idx, bsel2.as<int64_t>(), (int64_t)sel2.size(), d_nbase,
+                                                              d_ebase, G, p, K, d_over, st))));
+                RB3_CUDA_TRY(cudaMemcpyAsync(over.data(), d_over, sizeof(int32_t) * cq, cudaMemcpyDeviceToHost, st));
+                RB3_CUDA_TRY(cudaStreamSynchronize(st));
+                for (int64_t i = 0; i < cq; ++i)
+                    if (over[i]) {
+                        set_error("bwasw: query %lld left more than %d candidate cells at a node", (long long)(q0 + i),
+                                  DV_CAP_G);
+                        return RB3_E_CAPACITY;
+                    }
+            }
         }
         unsigned int herr = 0;
         RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));

@@ -25,10 +25,11 @@ namespace {
 
 using namespace dv;
 
-// Two table sizes: every query first runs with small tables (eight warps a
-// CTA, three CTAs an SM at D = 32); the queries whose step outgrew theirs run
-// again with the large one (two warps a CTA).
-constexpr int DV_CAP_S = 256, DV_WARPS_S = 8;
+// Three table sizes: every query first runs with small tables (six warps a
+// CTA, three CTAs an SM); the queries whose step outgrew theirs run again
+// with the large one (2,048 cells, two warps a CTA), and those that outgrew
+// that with a table of 65,534 cells in global memory.
+constexpr int DV_CAP_S = 256, DV_WARPS_S = 6;
 constexpr int DV_CAP_L = 2048, DV_WARPS_L = 2;
 static_assert(dv_warp_bytes(DV_CAP_S) % 16 == 0 && dv_warp_bytes(DV_CAP_L) % 16 == 0,
               "per-warp tables must keep 16-byte alignment");
@@ -37,17 +38,21 @@ static_assert(dv_warp_bytes(DV_CAP_S) % 16 == 0 && dv_warp_bytes(DV_CAP_L) % 16 
 __device__ unsigned long long g_dv_stats[2];
 
 // Queries sel[0 .. nsel) (all nsel = nq of them when sel is null), one warp each.
-template <int NS, int CAP, int WARPS>
+// GM: the tables in global memory (gtab, one per warp of the launch), for the
+// queries that outgrew the shared-memory ones.
+template <int NS, int CAP, int WARPS, bool GM>
 __global__ void __launch_bounds__(32 * WARPS)
     k_diversity(OccView V, const uint8_t *__restrict__ q, const int64_t *__restrict__ qoff,
                 const int64_t *__restrict__ sel, int64_t nsel, DvParams p, int64_t *__restrict__ out,
-                int64_t *__restrict__ n_out) {
+                int64_t *__restrict__ n_out, uint8_t *__restrict__ gtab) {
     extern __shared__ __align__(16) uint8_t dv_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t wi = (int64_t)blockIdx.x * WARPS + w;
     if (wi >= nsel) return;  // the whole warp leaves together
     const int64_t qi = sel ? sel[wi] : wi;
-    const DvTab T = dv_tab<CAP>(dv_smem + (size_t)w * dv_warp_bytes(CAP));
+    const DvTab T = dv_tab<CAP>(GM ? gtab + (size_t)wi * dv_warp_bytes(CAP) : dv_smem + (size_t)w * dv_warp_bytes(CAP));
+    DvSt st{0, 0, 0};
+    dv_clear_all<CAP>(T, st, lane);
     const int64_t q0 = qoff[qi], m = qoff[qi + 1] - q0;
 
     // lane r holds the r-th kept cell; before any symbol only the root (H = 0)
@@ -59,68 +64,28 @@ __global__ void __launch_bounds__(32 * WARPS)
 
     for (int64_t i = m - 1; i >= 0 && ncur > 0 && !overflow; --i) {
         const int c = q[q0 + i];
-        int tn = 0;
-        // match / mismatch: the children of every kept cell
+        dv_clear<CAP>(T, st, lane);
+        // match / mismatch: the children of every kept cell (lane t: cell t's child by a)
         {
             int64_t xk[4] = {0, 0, 0, 0}, xkp[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
             if (lane < ncur) dv_children<NS>(V, ck, ckp, cs, xk, xkp, xs);
             n_ext += ncur;
-            for (int t = 0; t < ncur && !overflow; ++t) {
-                const int32_t h = __shfl_sync(DV_FULL, cH, t);
 #pragma unroll
-                for (int a = 1; a <= 4; ++a) {
-                    const int64_t k = __shfl_sync(DV_FULL, xk[a - 1], t);
-                    const int64_t kp = __shfl_sync(DV_FULL, xkp[a - 1], t);
-                    const int64_t s = __shfl_sync(DV_FULL, xs[a - 1], t);
-                    const int32_t g = h + (a == c ? p.a : -p.b);
-                    if (s > 0 && g > 0 && !overflow) tn = dv_upsert<CAP>(T, tn, k, kp, s, g, DV_NEG, DV_NEG, lane, overflow);
-                }
+            for (int a = 1; a <= 4; ++a) {
+                const int32_t g = cH + (a == c ? p.a : -p.b);
+                if (!overflow)
+                    dv_upsert_batch<CAP>(T, st, lane < ncur && xs[a - 1] > 0 && g > 0, xk[a - 1], xkp[a - 1],
+                                         xs[a - 1], g, DV_NEG, DV_NEG, lane, overflow);
             }
         }
         // insertion: the query symbol against a gap, the node unchanged
         {
             const int32_t ev = max(cH - p.q, cE) - p.e;
-            for (int t = 0; t < ncur && !overflow; ++t) {
-                const int32_t e1 = __shfl_sync(DV_FULL, ev, t);
-                const int64_t k = __shfl_sync(DV_FULL, ck, t);
-                const int64_t kp = __shfl_sync(DV_FULL, ckp, t);
-                const int64_t s = __shfl_sync(DV_FULL, cs, t);
-                if (e1 > 0) tn = dv_upsert<CAP>(T, tn, k, kp, s, e1, e1, DV_NEG, lane, overflow);
-            }
+            if (!overflow) dv_upsert_batch<CAP>(T, st, lane < ncur && ev > 0, ck, ckp, cs, ev, ev, DV_NEG, lane, overflow);
         }
         // deletion: a text symbol against a gap, until no cell is left to extend
-        for (int pass = 0; !overflow; ++pass) {
-            bool any = false;
-            for (int j0 = 0; j0 < tn && !overflow; j0 += 32) {
-                const int j = j0 + lane;
-                const bool act = j < tn && (T.flag[j] & 1);
-                int32_t fv = DV_NEG;
-                int64_t yk[4] = {0, 0, 0, 0}, ykp[4] = {0, 0, 0, 0}, ys[4] = {0, 0, 0, 0};
-                if (act) {
-                    fv = max(T.H[j] - p.q, T.F[j]) - p.e;
-                    if (fv > 0) dv_children<NS>(V, T.k[j], T.kp[j], T.s[j], yk, ykp, ys);
-                    T.flag[j] &= (uint8_t)~1u;
-                }
-                any |= __ballot_sync(DV_FULL, act) != 0;
-                unsigned todo = __ballot_sync(DV_FULL, act && fv > 0);
-                n_ext += __popc(todo);
-                __syncwarp();
-                while (todo && !overflow) {
-                    const int t = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const int32_t f = __shfl_sync(DV_FULL, fv, t);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int64_t k = __shfl_sync(DV_FULL, yk[a], t);
-                        const int64_t kp = __shfl_sync(DV_FULL, ykp[a], t);
-                        const int64_t s = __shfl_sync(DV_FULL, ys[a], t);
-                        if (s > 0 && !overflow) tn = dv_upsert<CAP>(T, tn, k, kp, s, f, DV_NEG, f, lane, overflow);
-                    }
-                }
-            }
-            if (!any) break;
-            if (pass > CAP) overflow = true;  // a chain cannot be longer than the table
-        }
+        dv_close<NS, CAP>(V, T, st, p, lane, overflow, n_ext);
+        const int tn = st.tn;
         n_cells += tn;
         if (overflow) break;
         // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
@@ -227,10 +192,27 @@ template <int NS, int CAP, int WARPS>
 static int dv_launch(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *sel, int64_t nsel,
                      const DvParams &p, int64_t *out, int64_t *n_out, cudaStream_t st) {
     const size_t smem = WARPS * dv_warp_bytes(CAP);
-    auto kern = k_diversity<NS, CAP, WARPS>;
+    auto kern = k_diversity<NS, CAP, WARPS, false>;
     RB3_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)((nsel + WARPS - 1) / WARPS);
-    RB3_LAUNCH(kern, grid, 32 * WARPS, smem, st, occ_view(idx), q, qoff, sel, nsel, p, out, n_out);
+    RB3_LAUNCH(kern, grid, 32 * WARPS, smem, st, occ_view(idx), q, qoff, sel, nsel, p, out, n_out,
+               (uint8_t *)nullptr);
+    return RB3_OK;
+}
+
+// The global-memory tier: one warp per CTA, at most DV_GM_WARPS tables at once.
+constexpr int64_t DV_GM_WARPS = 1024;
+template <int NS>
+static int dv_launch_gm(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *sel, int64_t nsel,
+                        const DvParams &p, int64_t *out, int64_t *n_out, cudaStream_t st) {
+    const int64_t nw = nsel < DV_GM_WARPS ? nsel : DV_GM_WARPS;
+    DevBuf tab;
+    RB3_TRY(tab.alloc(dv_warp_bytes(DV_CAP_G) * (size_t)nw, st));
+    for (int64_t b = 0; b < nsel; b += nw) {
+        const int64_t n = nsel - b < nw ? nsel - b : nw;
+        RB3_LAUNCH((k_diversity<NS, DV_CAP_G, 1, true>), (unsigned)n, 32, 0, st, occ_view(idx), q, qoff, sel + b, n, p,
+                   out, n_out, tab.as<uint8_t>());
+    }
     return RB3_OK;
 }
 
@@ -253,7 +235,19 @@ int diversity_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, 
     RB3_CUDA_TRY(cudaMemcpyAsync(ds.p, sel.data(), sizeof(int64_t) * sel.size(), cudaMemcpyHostToDevice, st));
     RB3_WITH_NS(idx->D, RB3_TRY((dv_launch<NS, DV_CAP_L, DV_WARPS_L>(idx, q, qoff, ds.as<int64_t>(),
                                                                      (int64_t)sel.size(), p, out, n_out, st))));
-    return RB3_OK;  // ds is freed in stream order after the launch
+    // those that outgrew the large table too, with the global-memory one
+    RB3_CUDA_TRY(cudaMemcpyAsync(n.data(), n_out, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int64_t> sel2;
+    for (int64_t i = 0; i < nq; ++i)
+        if (n[i] < 0) sel2.push_back(i);
+    if (sel2.empty()) return RB3_OK;
+    DevBuf ds2;
+    RB3_TRY(ds2.alloc(sizeof(int64_t) * sel2.size(), st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(ds2.p, sel2.data(), sizeof(int64_t) * sel2.size(), cudaMemcpyHostToDevice, st));
+    RB3_WITH_NS(idx->D, RB3_TRY((dv_launch_gm<NS>(idx, q, qoff, ds2.as<int64_t>(), (int64_t)sel2.size(), p, out,
+                                                  n_out, st))));
+    return RB3_OK;  // ds and ds2 are freed in stream order after the launches
 }
 
 }  // namespace rb3

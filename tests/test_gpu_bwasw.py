@@ -119,3 +119,19 @@ def test_bwasw_longest_query_and_refusals(text):
     with pytest.raises(rb.RB3Error) as e:
         rb.rb3_bwasw(idx, q, qoff, cap=3, out=out)
     assert e.value.code == rb.RB3_E_CAPACITY
+
+
+def test_bwasw_node_overflow_is_reported():
+    """The query X of the diversity overflow text outgrows every cell table at
+    the node of the whole of X: RB3_E_CAPACITY."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "dv", os.path.join(os.path.dirname(os.path.abspath(__file__)), "test_gpu_diversity.py"))
+    dvmod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(dvmod)
+    seq, lens, X = dvmod.overflow_text()
+    idx = rb.rb3_build_batch(torch.from_numpy(seq).to(DEV), lens)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_bwasw(idx, X, np.array([0, 20], np.int64), 5, 3, 0, 1, 4)
+    assert e.value.code == rb.RB3_E_CAPACITY

@@ -141,15 +141,43 @@ def test_diversity_paper_example_and_refusals():
     assert e.value.code == rb.RB3_E_INVAL
 
 
+def overflow_text():
+    """65,536 strings: every 8-mer over ACGT followed by one random 20-mer X.
+    After the whole of X (a = 5, q = 0, e = 1: H = 100), deleting text symbols
+    to its left keeps every left extension of up to 99 symbols positive, and X
+    is preceded by all 4^8 contexts: the closure reaches 4 + 16 + ... + 4^8 >
+    65,534 distinct nodes at that step, beyond the largest table."""
+    g = synth.rng(814)
+    X = synth.random_bases(g, 20)
+    ctx = (np.arange(65536)[:, None] >> (2 * np.arange(8)[::-1])[None, :]) & 3
+    seq = np.concatenate([ctx.astype(np.uint8) + 1, np.tile(X, (65536, 1))], axis=1).reshape(-1)
+    return seq.astype(np.uint8), np.full(65536, 28, np.int64), X
+
+
 def test_diversity_table_overflow_is_reported():
-    """Free gap opens (a = 2, q = 0, e = 1) on an exact 1400-symbol window that
-    starts at offset 4000 of a random 8000-symbol string: after the window's
-    last k symbols its own cell scores 2k, and deleting text symbols one by
-    one to its left keeps every left extension of up to 2k - 1 symbols
-    positive, each a distinct node; past k = 1024 one step holds more than
-    the 2048 cells of the table.  That query reports -1 and RB3_E_CAPACITY;
-    the short queries beside it (at most about 900 cells a step in the
-    oracle) are still exact."""
+    """The query X on overflow_text() outgrows every table (the small, the
+    large and the 65,534-cell one in global memory): it reports -1 and
+    RB3_E_CAPACITY; the query beside it keeps its result (all N: no cell
+    scores above 0, since every extension mismatches and gaps only lower the
+    root's 0)."""
+    import torch
+    import paper_2409_00613_gb300 as rb
+    dev = torch.device("cuda:0")
+    seq, lens, X = overflow_text()
+    idx = rb.rb3_build_batch(torch.from_numpy(seq).to(dev), lens)
+    q = np.concatenate([X, np.full(9, 5, np.uint8)])
+    qoff = np.array([0, 20, 29], np.int64)
+    out = np.zeros((2, 4, 4), np.int64)
+    n = np.full(2, 7, np.int64)
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_haplotype_diversity(idx, q, qoff, 5, 3, 0, 1, 4, True, out=out, n_out=n)
+    assert e.value.code == rb.RB3_E_CAPACITY
+    assert n[0] == -1 and n[1] == 0
+
+
+def test_diversity_large_tables_exact():
+    """Queries whose steps outgrow the 256-cell and 2,048-cell tables (a long
+    exact window with free gap opens) are answered exactly by the next table."""
     import torch
     import paper_2409_00613_gb300 as rb
     dev = torch.device("cuda:0")
@@ -157,17 +185,10 @@ def test_diversity_table_overflow_is_reported():
     T = synth.random_bases(g, 8000)
     idx = rb.rb3_build_batch(torch.from_numpy(T).to(dev), np.array([8000], np.int64))
     B = oracle.bwt(oracle.concat(T, np.array([8000]), True))
-    short = [T[100:112].copy(), T[2000:2015].copy()]
-    pats = [short[0], T[4000:5400].copy(), short[1]]
+    pats = [T[4000:4300].copy(), T[4000:5400].copy(), T[100:112].copy()]
     q = np.concatenate(pats)
-    qoff = np.array([0, 12, 1412, 1427], np.int64)
-    out = np.zeros((3, 4, 4), np.int64)
-    n = np.zeros(3, np.int64)
-    with pytest.raises(rb.RB3Error) as e:
-        rb.rb3_haplotype_diversity(idx, q, qoff, 2, 3, 0, 1, 4, True, out=out, n_out=n)
-    assert e.value.code == rb.RB3_E_CAPACITY
-    assert n[1] == -1
-    for i in (0, 2):
-        want = oracle.haplotype_diversity(B, short[i // 2], 2, 3, 0, 1, W=4)
-        assert len(want) > 0
-        assert n[i] == len(want) and np.array_equal(out[i, :n[i]], want)
+    qoff = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.int64)
+    out, n = rb.rb3_haplotype_diversity(idx, q, qoff, 2, 3, 0, 1, 4, True)
+    for i, p in enumerate(pats):
+        want = oracle.haplotype_diversity(B, p, 2, 3, 0, 1, W=4)
+        assert n[i] == len(want) and np.array_equal(out[i, :n[i]], want), i
