@@ -207,6 +207,11 @@ __device__ __forceinline__ void dv_upsert_batch(const DvTab &T, DvSt &st, bool w
     __syncwarp();
 }
 
+// x[a] for a warp-uniform a in 0..3, by selects (the array stays in registers).
+__device__ __forceinline__ int64_t dv_pick(const int64_t x[4], int a) {
+    return a == 0 ? x[0] : (a == 1 ? x[1] : (a == 2 ? x[2] : x[3]));
+}
+
 // Band order: larger H first, then smaller k, k', s.
 __device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, int64_t s1, int32_t h2, int64_t k2,
                                           int64_t kp2, int64_t s2) {
@@ -239,9 +244,12 @@ __device__ __forceinline__ void dv_close(const OccView &V, const DvTab &T, DvSt 
         const bool ext = lane < cnt && fv > 0;
         n_ext += __popc(__ballot_sync(DV_FULL, ext));
         __syncwarp();
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            if (!overflow) dv_upsert_batch<CAP>(T, st, ext && ys[a] > 0, yk[a], ykp[a], ys[a], fv, DV_NEG, fv, lane, overflow);
+        // one call site for the four children (a smaller kernel: the upsert is long)
+#pragma unroll 1
+        for (int a = 0; a < 4 && !overflow; ++a) {
+            const int64_t k = dv_pick(yk, a), kp = dv_pick(ykp, a), s = dv_pick(ys, a);
+            dv_upsert_batch<CAP>(T, st, ext && s > 0, k, kp, s, fv, DV_NEG, fv, lane, overflow);
+        }
     }
 }
 

@@ -70,12 +70,11 @@ __global__ void __launch_bounds__(32 * WARPS)
             int64_t xk[4] = {0, 0, 0, 0}, xkp[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
             if (lane < ncur) dv_children<NS>(V, ck, ckp, cs, xk, xkp, xs);
             n_ext += ncur;
-#pragma unroll
-            for (int a = 1; a <= 4; ++a) {
+#pragma unroll 1
+            for (int a = 1; a <= 4 && !overflow; ++a) {
                 const int32_t g = cH + (a == c ? p.a : -p.b);
-                if (!overflow)
-                    dv_upsert_batch<CAP>(T, st, lane < ncur && xs[a - 1] > 0 && g > 0, xk[a - 1], xkp[a - 1],
-                                         xs[a - 1], g, DV_NEG, DV_NEG, lane, overflow);
+                const int64_t k = dv_pick(xk, a - 1), kp = dv_pick(xkp, a - 1), s = dv_pick(xs, a - 1);
+                dv_upsert_batch<CAP>(T, st, lane < ncur && s > 0 && g > 0, k, kp, s, g, DV_NEG, DV_NEG, lane, overflow);
             }
         }
         // insertion: the query symbol against a gap, the node unchanged

@@ -93,8 +93,10 @@ def test_bwasw_other_layouts(text, layout):
 def test_bwasw_longest_query_and_refusals(text):
     S, idx, B = text
     g = synth.rng(9100)
-    st = int(g.integers(0, len(S.seq) - 2047))
-    p = S.seq[st:st + 2047].copy()
+    off = S.offsets
+    h = int(g.integers(0, len(S.lens)))
+    st = int(off[h] + g.integers(0, S.lens[h] - 2047 + 1))
+    p = S.seq[st:st + 2047].copy()  # inside one haplotype
     recs = rb.rb3_bwasw(idx, p, np.array([0, 2047], np.int64), 1, 3, 5, 2, 25)
     # the whole query occurs: the node of P itself holds its exact match, H = 2047 a
     assert recs[:, 6].max() == 2047 and (recs[:, 6] > 0).all()
