@@ -5,6 +5,9 @@
 // query-DAWG kernel (BWA-SW).
 #pragma once
 
+#include <climits>
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace rb3 {
@@ -219,6 +222,36 @@ __device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, i
     if (k1 != k2) return k1 < k2;
     if (kp1 != kp2) return kp1 < kp2;
     return s1 < s2;
+}
+
+// The band of a table of at most 32 cells: lane r returns the index of the
+// r-th cell in band order (-1 past tn).  A bitonic sort across the warp, one
+// cell per lane (cells are distinct, so the order is total).
+__device__ __forceinline__ int dv_band_small(const DvTab &T, int tn, int lane) {
+    const bool v = lane < tn;
+    int32_t h = v ? T.H[lane] : INT32_MIN;
+    int64_t k = v ? T.k[lane] : INT64_MAX, kp = v ? T.kp[lane] : INT64_MAX, s = v ? T.s[lane] : INT64_MAX;
+    int idx = v ? lane : -1;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            const int32_t oh = __shfl_xor_sync(DV_FULL, h, j);
+            const int64_t ok = __shfl_xor_sync(DV_FULL, k, j), okp = __shfl_xor_sync(DV_FULL, kp, j),
+                          os = __shfl_xor_sync(DV_FULL, s, j);
+            const int oi = __shfl_xor_sync(DV_FULL, idx, j);
+            // the lower lane of a pair keeps the earlier cell in an ascending run, the later one in a descending run
+            const bool lower = (lane & j) == 0, asc = (lane & size) == 0;
+            const bool other_first = oi >= 0 && (idx < 0 || dv_before(oh, ok, okp, os, h, k, kp, s));
+            if (other_first == (lower == asc)) {
+                h = oh;
+                k = ok;
+                kp = okp;
+                s = os;
+                idx = oi;
+            }
+        }
+    return idx;
 }
 
 

@@ -450,9 +450,21 @@ __global__ void __launch_bounds__(32 * WARPS)
         dv_close<NS, CAP>(V, T, st, p, lane, over, n_ext);
         const int tn = st.tn;
         if (over) break;
-        // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
+        // the band: a warp sort when the table fits the lanes, else W rounds of a
+        // warp-wide argmin in band order over the cells not yet taken
         const int keep = min(tn, W);
-        for (int r = 0; r < keep; ++r) {
+        if (tn <= 32) {
+            const int j = dv_band_small(T, tn, lane);
+            if (lane < keep) {
+                const int64_t at = (nb + v) * W + lane;
+                K.k[at] = T.k[j];
+                K.kp[at] = T.kp[j];
+                K.s[at] = T.s[j];
+                K.H[at] = T.H[j];
+                K.E[at] = T.E[j];
+            }
+        }
+        for (int r = 0; r < keep && tn > 32; ++r) {
             int bj = -1;
             int32_t bH = 0;
             int64_t bk = 0, bkp = 0, bs = 0;

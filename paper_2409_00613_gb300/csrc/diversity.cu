@@ -87,11 +87,22 @@ __global__ void __launch_bounds__(32 * WARPS)
         const int tn = st.tn;
         n_cells += tn;
         if (overflow) break;
-        // the band: W rounds of a warp-wide argmin in band order over the cells not yet taken
+        // the band: a warp sort when the table fits the lanes, else W rounds of a
+        // warp-wide argmin in band order over the cells not yet taken
         const int keep = min(tn, p.W);
         int64_t nk = 0, nkp = 0, ns = 0;
         int32_t nH = 0, nE = DV_NEG;
-        for (int r = 0; r < keep; ++r) {
+        if (tn <= 32) {
+            const int j = dv_band_small(T, tn, lane);
+            if (lane < keep) {
+                nk = T.k[j];
+                nkp = T.kp[j];
+                ns = T.s[j];
+                nH = T.H[j];
+                nE = T.E[j];
+            }
+        }
+        for (int r = 0; r < keep && tn > 32; ++r) {
             int bj = -1;
             int32_t bH = 0;
             int64_t bk = 0, bkp = 0, bs = 0;
