@@ -620,7 +620,7 @@ int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, cons
             ++q1;
         }
         const int64_t cq = q1 - q0;
-        DevBuf bq, bn, bi, be, bk, bkey, bval, bkey2, bval2, bcnt, boff, bsel;
+        DevBuf bq, bn, bi, be, bk, bkey, bval, bkey2, bval2, bcnt, boff;
         RB3_TRY(bq.alloc(sizeof(int64_t) * (2 * cq + nodes) + sizeof(int32_t) * cq, st));
         int64_t *d_nbase = bq.as<int64_t>(), *d_ebase = d_nbase + cq, *d_nodeq = d_ebase + cq;
         int32_t *d_over = reinterpret_cast<int32_t *>(d_nodeq + nodes);
@@ -651,41 +651,42 @@ int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, cons
         K.E = K.H + nodes * W;
         K.n = K.E + nodes * W;
         RB3_CUDA_TRY(cudaMemsetAsync(K.n, 0, sizeof(int32_t) * nodes, st));
-        RB3_WITH_NS(idx->D, RB3_TRY((bw_launch<NS, BW_CAP_S, BW_WARPS_S>(idx, nullptr, cq, d_nbase, d_ebase, G, p, K,
-                                                                         d_over, st))));
+        // every query starts at the table size its best possible score suggests (a
+        // deletion closure holds about a dozen cells per unit of score), and one that
+        // outgrows its table runs again, from its start, with the next size
+        std::vector<int64_t> tier[3];
+        for (int64_t i = 0; i < cq; ++i) {
+            const int64_t best = (qo[q0 + i + 1] - qo[q0 + i]) * (int64_t)p.a;
+            tier[best <= 16 ? 0 : (best <= 160 ? 1 : 2)].push_back(i);
+        }
         std::vector<int32_t> over(cq);
-        RB3_CUDA_TRY(cudaMemcpyAsync(over.data(), d_over, sizeof(int32_t) * cq, cudaMemcpyDeviceToHost, st));
-        RB3_CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<int64_t> sel;
-        for (int64_t i = 0; i < cq; ++i)
-            if (over[i]) sel.push_back(i);
-        if (!sel.empty()) {
-            RB3_TRY(bsel.alloc(sizeof(int64_t) * sel.size(), st));
-            RB3_CUDA_TRY(cudaMemcpyAsync(bsel.p, sel.data(), sizeof(int64_t) * sel.size(), cudaMemcpyHostToDevice, st));
-            RB3_WITH_NS(idx->D,
-                        RB3_TRY((bw_launch<NS, BW_CAP_L, BW_WARPS_L>(idx, bsel.as<int64_t>(), (int64_t)sel.size(),
-                                                                     d_nbase, d_ebase, G, p, K, d_over, st))));
+        DevBuf bs[3];
+        for (int t = 0; t < 3; ++t) {
+            if (tier[t].empty()) continue;
+            RB3_TRY(bs[t].alloc(sizeof(int64_t) * tier[t].size(), st));
+            RB3_CUDA_TRY(
+                cudaMemcpyAsync(bs[t].p, tier[t].data(), sizeof(int64_t) * tier[t].size(), cudaMemcpyHostToDevice, st));
+            const int64_t *ds = bs[t].as<int64_t>();
+            const int64_t ns = (int64_t)tier[t].size();
+            if (t == 0)
+                RB3_WITH_NS(idx->D, RB3_TRY((bw_launch<NS, BW_CAP_S, BW_WARPS_S>(idx, ds, ns, d_nbase, d_ebase, G, p, K,
+                                                                                 d_over, st))));
+            else if (t == 1)
+                RB3_WITH_NS(idx->D, RB3_TRY((bw_launch<NS, BW_CAP_L, BW_WARPS_L>(idx, ds, ns, d_nbase, d_ebase, G, p, K,
+                                                                                 d_over, st))));
+            else
+                RB3_WITH_NS(idx->D, RB3_TRY((bw_launch_gm<NS>(idx, ds, ns, d_nbase, d_ebase, G, p, K, d_over, st))));
             RB3_CUDA_TRY(cudaMemcpyAsync(over.data(), d_over, sizeof(int32_t) * cq, cudaMemcpyDeviceToHost, st));
             RB3_CUDA_TRY(cudaStreamSynchronize(st));
-            std::vector<int64_t> sel2;
-            for (int64_t i = 0; i < cq; ++i)
-                if (over[i]) sel2.push_back(i);
-            if (!sel2.empty()) {  // the global-memory tier
-                DevBuf bsel2;
-                RB3_TRY(bsel2.alloc(sizeof(int64_t) * sel2.size(), st));
-                RB3_CUDA_TRY(
-                    cudaMemcpyAsync(bsel2.p, sel2.data(), sizeof(int64_t) * sel2.size(), cudaMemcpyHostToDevice, st));
-                RB3_WITH_NS(idx->D, RB3_TRY((bw_launch_gm<NS>(idx, bsel2.as<int64_t>(), (int64_t)sel2.size(), d_nbase,
-                                                              d_ebase, G, p, K, d_over, st))));
-                RB3_CUDA_TRY(cudaMemcpyAsync(over.data(), d_over, sizeof(int32_t) * cq, cudaMemcpyDeviceToHost, st));
-                RB3_CUDA_TRY(cudaStreamSynchronize(st));
-                for (int64_t i = 0; i < cq; ++i)
-                    if (over[i]) {
+            for (int64_t i : tier[t])
+                if (over[i]) {
+                    if (t == 2) {
                         set_error("bwasw: query %lld left more than %d candidate cells at a node", (long long)(q0 + i),
                                   DV_CAP_G);
                         return RB3_E_CAPACITY;
                     }
-            }
+                    tier[t + 1].push_back(i);
+                }
         }
         unsigned int herr = 0;
         RB3_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));

@@ -840,7 +840,8 @@ int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, cons
                const int32_t prm[5], int64_t *out, int64_t cap, int64_t *n_out, cudaStream_t st);
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
-                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st);
+                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st,
+                    bool codes_checked = false);
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
 int rle_export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st);
 // Merge of any two layouts: a run-length input is merged through a plain copy,

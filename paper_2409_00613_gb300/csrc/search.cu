@@ -332,8 +332,8 @@ int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *
 
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
-                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st) {
-    RB3_TRY(check_codes(q, total_q, st));
+                    rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st, bool codes_checked) {
+    if (!codes_checked) RB3_TRY(check_codes(q, total_q, st));
     *n_out = 0;
     if (nq == 0) return RB3_OK;
     OccView V = occ_view(idx);

@@ -116,15 +116,16 @@ static void server_worker(rb3_server *S) {
             r = dev_alloc((void **)&d_out, sizeof(rb3_smem) * (size_t)out_cap, st);
         }
         if (r == RB3_OK) {
+            // the symbols were checked by rb3_server_submit
             r = mem_search_impl(S->idx, d_q, d_off, h_off, nq, total, S->o.min_len, S->o.min_occ, so, d_out, out_cap,
-                                &n, st);
+                                &n, st, true);
             if (r == RB3_E_CAPACITY) {  // grow once to the size reported and rerun
                 dev_free(d_out, st);
                 out_cap = n + 4096;
                 r = dev_alloc((void **)&d_out, sizeof(rb3_smem) * (size_t)out_cap, st);
                 if (r == RB3_OK)
                     r = mem_search_impl(S->idx, d_q, d_off, h_off, nq, total, S->o.min_len, S->o.min_occ, so, d_out,
-                                        out_cap, &n, st);
+                                        out_cap, &n, st, true);
             }
         }
         if (r == RB3_OK) {
