@@ -26,8 +26,9 @@ __host__ __device__ constexpr int dv_hash_slots(int cap) {
 // A table of cap cells (structure of arrays: k, k', s, H, E, F, a worklist
 // ring of cell indexes, a flag byte) and its hash index (cell index + 1, 0 =
 // empty; open addressing with linear probing), rounded to 16 bytes.
+constexpr int DV_HIST = 256;  // score bins of the band selection
 __host__ __device__ constexpr size_t dv_warp_bytes(int cap) {
-    return ((size_t)cap * (3 * 8 + 3 * 4 + 2 + 1) + (size_t)dv_hash_slots(cap) * 2 + 15) / 16 * 16;
+    return DV_HIST * 4 + ((size_t)cap * (3 * 8 + 3 * 4 + 2 + 1) + (size_t)dv_hash_slots(cap) * 2 + 15) / 16 * 16;
 }
 
 struct DvParams {
@@ -41,6 +42,7 @@ struct DvTab {
     unsigned short *queue;  // worklist ring of the cells to extend by deletions
     uint8_t *flag;          // bit 0: in the worklist; bit 1: taken into the band
     unsigned short *slot;   // hash index over (k, k', s)
+    uint32_t *hist;         // [DV_HIST] scratch of the band selection
 };
 
 // The table's counters (warp-uniform): cells, worklist head and tail.
@@ -60,6 +62,7 @@ template <int CAP> __device__ __forceinline__ DvTab dv_tab(uint8_t *base) {
     t.queue = reinterpret_cast<unsigned short *>(t.F + CAP);
     t.flag = reinterpret_cast<uint8_t *>(t.queue + CAP);
     t.slot = reinterpret_cast<unsigned short *>(t.flag + CAP);  // CAP is even: 2-byte aligned
+    t.hist = reinterpret_cast<uint32_t *>(base + dv_warp_bytes(CAP) - DV_HIST * 4);
     return t;
 }
 
@@ -224,14 +227,13 @@ __device__ __forceinline__ bool dv_before(int32_t h1, int64_t k1, int64_t kp1, i
     return s1 < s2;
 }
 
-// The band of a table of at most 32 cells: lane r returns the index of the
-// r-th cell in band order (-1 past tn).  A bitonic sort across the warp, one
-// cell per lane (cells are distinct, so the order is total).
-__device__ __forceinline__ int dv_band_small(const DvTab &T, int tn, int lane) {
-    const bool v = lane < tn;
-    int32_t h = v ? T.H[lane] : INT32_MIN;
-    int64_t k = v ? T.k[lane] : INT64_MAX, kp = v ? T.kp[lane] : INT64_MAX, s = v ? T.s[lane] : INT64_MAX;
-    int idx = v ? lane : -1;
+// Lanes each holding a cell index (or -1) end up holding them in band order
+// (-1 last): a bitonic sort across the warp (cells are distinct, so the order
+// is total).
+__device__ __forceinline__ int dv_sort_lanes(const DvTab &T, int idx, int lane) {
+    const bool v = idx >= 0;
+    int32_t h = v ? T.H[idx] : INT32_MIN;
+    int64_t k = v ? T.k[idx] : INT64_MAX, kp = v ? T.kp[idx] : INT64_MAX, s = v ? T.s[idx] : INT64_MAX;
 #pragma unroll
     for (int size = 2; size <= 32; size <<= 1)
 #pragma unroll
@@ -254,6 +256,135 @@ __device__ __forceinline__ int dv_band_small(const DvTab &T, int tn, int lane) {
     return idx;
 }
 
+// Band by rounds: round r takes the first cell in band order among those of
+// list[0 .. n) (list = null: cells 0 .. n) not yet taken (flag bit 1); lane
+// r returns round r's cell.
+__device__ __forceinline__ int dv_band_rounds(const DvTab &T, const unsigned short *list, int n, int keep,
+                                              int lane) {
+    int mine = -1;
+    for (int r = 0; r < keep; ++r) {
+        int bj = -1;
+        int32_t bH = 0;
+        int64_t bk = 0, bkp = 0, bs = 0;
+        for (int x = lane; x < n; x += 32) {
+            const int j = list ? list[x] : x;
+            if (T.flag[j] & 2) continue;
+            if (bj < 0 || dv_before(T.H[j], T.k[j], T.kp[j], T.s[j], bH, bk, bkp, bs)) {
+                bj = j;
+                bH = T.H[j];
+                bk = T.k[j];
+                bkp = T.kp[j];
+                bs = T.s[j];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const int oj = __shfl_xor_sync(DV_FULL, bj, off);
+            const int32_t oH = __shfl_xor_sync(DV_FULL, bH, off);
+            const int64_t ok = __shfl_xor_sync(DV_FULL, bk, off);
+            const int64_t okp = __shfl_xor_sync(DV_FULL, bkp, off);
+            const int64_t os = __shfl_xor_sync(DV_FULL, bs, off);
+            if (oj >= 0 && (bj < 0 || dv_before(oH, ok, okp, os, bH, bk, bkp, bs))) {
+                bj = oj;
+                bH = oH;
+                bk = ok;
+                bkp = okp;
+                bs = os;
+            }
+        }
+        // keys are distinct, so every lane holds the same cell
+        if (lane == r) mine = bj;
+        __syncwarp();
+        if (lane == 0) T.flag[bj] |= 2;
+        __syncwarp();
+    }
+    return mine;
+}
+
+// The band: the W <= 32 cells of largest H (ties: smaller k, k', s) of the
+// table's tn cells; lane r returns the r-th (-1 past min(tn, W)).  A table that
+// fits the lanes is sorted across the warp.  A larger one: the largest H, a
+// histogram of how far below it every H lies (DV_HIST bins), the bin b where
+// the count from the top reaches W; the cells above bin b (fewer than W) are
+// all in the band and are sorted across the warp, and the cells of bin b (one
+// score) fill the remaining places by (k, k', s) -- sorted across the warp
+// when they fit the lanes, else by rounds.  When the top DV_HIST scores hold
+// fewer than W cells, or bin b holds more cells than the list can take, the
+// band is taken by rounds over the whole table.
+template <int CAP> __device__ __forceinline__ int dv_band(const DvTab &T, int tn, int W, int lane) {
+    const int keep = tn < W ? tn : W;
+    if (tn <= 32) {
+        const int j = dv_sort_lanes(T, lane < tn ? lane : -1, lane);
+        return lane < keep ? j : -1;
+    }
+    int32_t mh = INT32_MIN;
+    for (int j = lane; j < tn; j += 32) mh = max(mh, T.H[j]);
+    mh = __reduce_max_sync(DV_FULL, mh);
+    for (int i = lane; i < DV_HIST; i += 32) T.hist[i] = 0;
+    __syncwarp();
+    for (int j = lane; j < tn; j += 32) {
+        const int64_t d = (int64_t)mh - T.H[j];
+        if (d < DV_HIST) atomicAdd(&T.hist[d], 1u);
+    }
+    __syncwarp();
+    // bins 8 a lane: the first bin where the count from the top reaches W
+    constexpr int PB = DV_HIST / 32;
+    uint32_t c[PB], lt = 0;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+        c[i] = T.hist[lane * PB + i];
+        lt += c[i];
+    }
+    uint32_t incl = lt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(DV_FULL, incl, d);
+        if (lane >= d) incl += u;
+    }
+    uint32_t before = incl - lt;  // cells in the bins of lower lanes
+    int bstar = -1;
+    uint32_t above = 0;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+        if (bstar < 0 && before + c[i] >= (uint32_t)W) {
+            bstar = lane * PB + i;
+            above = before;
+        }
+        before += c[i];
+    }
+    const unsigned found = __ballot_sync(DV_FULL, bstar >= 0);
+    if (!found) return dv_band_rounds(T, nullptr, tn, keep, lane);
+    const int src = __ffs(found) - 1;
+    bstar = __shfl_sync(DV_FULL, bstar, src);
+    const int nabove = (int)__shfl_sync(DV_FULL, above, src);
+    const int nties = (int)T.hist[bstar];
+    if (nties > CAP - 32) return dv_band_rounds(T, nullptr, tn, keep, lane);
+    // the cells above bin b to list[0 ..), those of bin b to list[32 ..)
+    unsigned short *list = T.queue;
+    int na = 0, nt = 0;
+    for (int j0 = 0; j0 < tn; j0 += 32) {
+        const int j = j0 + lane;
+        const int64_t d = j < tn ? (int64_t)mh - T.H[j] : DV_HIST;
+        const unsigned ma = __ballot_sync(DV_FULL, d < bstar), mt = __ballot_sync(DV_FULL, d == bstar);
+        const unsigned lt_mask = (1u << lane) - 1u;
+        if (d < bstar) list[na + __popc(ma & lt_mask)] = (unsigned short)j;
+        if (d == bstar) list[32 + nt + __popc(mt & lt_mask)] = (unsigned short)j;
+        na += __popc(ma);
+        nt += __popc(mt);
+    }
+    __syncwarp();
+    const int ia = dv_sort_lanes(T, lane < nabove ? (int)list[lane] : -1, lane);
+    const int need = keep - nabove;  // places for bin b's cells
+    int it;
+    if (nties <= 32) {
+        it = dv_sort_lanes(T, lane < nties ? (int)list[32 + lane] : -1, lane);
+    } else {
+        it = dv_band_rounds(T, list + 32, nties, need, lane);
+    }
+    // lane r: the r-th cell above bin b, else bin b's (r - nabove)-th
+    const int from_t = __shfl_sync(DV_FULL, it, (lane - nabove) & 31);
+    return lane < nabove ? ia : (lane < keep ? from_t : -1);
+}
 
 // The deletion closure: cells are taken off the worklist 32 at a time; each
 // with H or F still giving a positive F to its children extends them (F =

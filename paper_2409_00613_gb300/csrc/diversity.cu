@@ -87,13 +87,12 @@ __global__ void __launch_bounds__(32 * WARPS)
         const int tn = st.tn;
         n_cells += tn;
         if (overflow) break;
-        // the band: a warp sort when the table fits the lanes, else W rounds of a
-        // warp-wide argmin in band order over the cells not yet taken
+        // the band (a warp sort, or a score histogram and sorts of what it singles out)
         const int keep = min(tn, p.W);
         int64_t nk = 0, nkp = 0, ns = 0;
         int32_t nH = 0, nE = DV_NEG;
-        if (tn <= 32) {
-            const int j = dv_band_small(T, tn, lane);
+        {
+            const int j = dv_band<CAP>(T, tn, p.W, lane);
             if (lane < keep) {
                 nk = T.k[j];
                 nkp = T.kp[j];
@@ -101,47 +100,6 @@ __global__ void __launch_bounds__(32 * WARPS)
                 nH = T.H[j];
                 nE = T.E[j];
             }
-        }
-        for (int r = 0; r < keep && tn > 32; ++r) {
-            int bj = -1;
-            int32_t bH = 0;
-            int64_t bk = 0, bkp = 0, bs = 0;
-            for (int j = lane; j < tn; j += 32) {
-                if (T.flag[j] & 2) continue;
-                if (bj < 0 || dv_before(T.H[j], T.k[j], T.kp[j], T.s[j], bH, bk, bkp, bs)) {
-                    bj = j;
-                    bH = T.H[j];
-                    bk = T.k[j];
-                    bkp = T.kp[j];
-                    bs = T.s[j];
-                }
-            }
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                const int oj = __shfl_xor_sync(DV_FULL, bj, off);
-                const int32_t oH = __shfl_xor_sync(DV_FULL, bH, off);
-                const int64_t ok = __shfl_xor_sync(DV_FULL, bk, off);
-                const int64_t okp = __shfl_xor_sync(DV_FULL, bkp, off);
-                const int64_t os = __shfl_xor_sync(DV_FULL, bs, off);
-                if (oj >= 0 && (bj < 0 || dv_before(oH, ok, okp, os, bH, bk, bkp, bs))) {
-                    bj = oj;
-                    bH = oH;
-                    bk = ok;
-                    bkp = okp;
-                    bs = os;
-                }
-            }
-            // keys are distinct, so every lane holds the same best cell
-            if (lane == r) {
-                nk = bk;
-                nkp = bkp;
-                ns = bs;
-                nH = bH;
-                nE = T.E[bj];
-            }
-            __syncwarp();
-            if (lane == 0) T.flag[bj] |= 2;
-            __syncwarp();
         }
         ck = nk;
         ckp = nkp;

@@ -140,11 +140,13 @@ static void server_worker(rb3_server *S) {
         // split records by query (sorted by (qid, start)), publish
         std::vector<std::vector<rb3_smem>> per(nq);
         if (r == RB3_OK)
-            for (int64_t i = 0; i < n; ++i) {
-                rb3_smem x = h_out[i];
-                const int64_t qi = x.qid;
-                x.qid = 0;
-                per[qi].push_back(x);
+            for (int64_t i = 0; i < n;) {  // each request's records are contiguous
+                const int64_t qi = h_out[i].qid;
+                int64_t j = i + 1;
+                while (j < n && h_out[j].qid == qi) ++j;
+                per[qi].assign(h_out.begin() + i, h_out.begin() + j);
+                for (auto &x : per[qi]) x.qid = 0;
+                i = j;
             }
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -213,11 +215,12 @@ RB3_EXPORT int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o,
 RB3_EXPORT int rb3_server_submit(rb3_server *S, const uint8_t *q, int64_t len, int64_t tag, int64_t *req_id) {
     RB3_CHECK_ARG(S && (len == 0 || q) && len >= 0, "bad argument");
     RB3_CHECK_ARG(len < (int64_t(1) << 31), "query longer than 2^31 - 1");
-    for (int64_t i = 0; i < len; ++i)
-        if (q[i] < 1 || q[i] > 5) {
-            set_error("query symbol outside 1..5 (A,C,G,T,N codes)");
-            return RB3_E_INVAL;
-        }
+    unsigned bad = 0;  // branch-free, so the compiler vectorizes the check
+    for (int64_t i = 0; i < len; ++i) bad |= (unsigned)((uint8_t)(q[i] - 1u) > 4u);
+    if (bad) {
+        set_error("query symbol outside 1..5 (A,C,G,T,N codes)");
+        return RB3_E_INVAL;
+    }
     rb3_server::Req r;
     r.tag = tag;
     r.q.assign(q, q + len);
