@@ -430,6 +430,7 @@ def run_rb3(args, rank, world, local_rank):
             out["mem_search"]["served"] = served(rb, S, idx, "pangenome-merge index (500 Msym)")
         out["run_length"] = run_length_bench(rb, torch, S, idx, args, st, dev,
                                              out["mem_search"]["autotune_chunk_len"])
+        out["run_length"]["merge_into"] = rle_merge_bench(rb, torch, dev_batches, opts, st, ds)
         out["haplotype_diversity"] = diversity_bench(rb, torch, S, idx, st, dev, probe)
         out["bwasw"] = bwasw_bench(rb, torch, S, idx, st, dev)
     idx.free()
@@ -485,6 +486,50 @@ def indexed_batch_merge(rb, torch, dev_batches, opts, st, ds):
         src.free()
         base.free()
     res["indexed_over_fresh_walk"] = round(res["indexed_walk_ms"] / res["fresh_walk_ms"], 2)
+    return res
+
+
+def rle_merge_bench(rb, torch, dev_batches, opts, st, ds, span=2048):
+    """The last batch (100 Msym) merged into the index of the batches before it
+    (400 Msym), held plain (D = 32) and run-length encoded (span 2048, merged
+    into directly): each merge's time (CUDA events around the call) and the
+    peak of the library's device allocations during it above what was in use
+    before; the two merged BWTs compared on the device."""
+    last = len(dev_batches) - 1
+    P = rb.rb3_build_batch(*dev_batches[0], opts=opts, stream=st)
+    rb.rb3_drop_build_data(P)
+    for b in range(1, last):
+        src = rb.rb3_build_batch(*dev_batches[b], opts=opts, stream=st)
+        rb.rb3_merge_opts(P, src, opts, stream=st)
+        src.free()
+    R = rb.rb3_index_compress(P, span, stream=st)
+    res = {"what": f"batch {last} ({ds[last]} symbols) merged into the index of batches 0-{last - 1} "
+                   f"({sum(ds[:last])} symbols), plain D = 32 and run-length span {span}; peak = the library's "
+                   "device allocations during the call above those before it", "span": span}
+    for name, dst in (("plain", P), ("run_length", R)):
+        src = rb.rb3_build_batch(*dev_batches[last], opts=opts, stream=st)
+        before = rb.rb3_index_bytes(dst)["device_bytes"]
+        torch.cuda.synchronize()
+        base = rb.rb3_device_peak(reset=True)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rb.rb3_merge_opts(dst, src, opts, stream=st)
+        e.record(st)
+        torch.cuda.synchronize()
+        res[name] = {"merge_ms": round(a.elapsed_time(e), 3), "index_bytes_before": before,
+                     "index_bytes_after": rb.rb3_index_bytes(dst)["device_bytes"],
+                     "peak_above_before_bytes": rb.rb3_device_peak() - base}
+        src.free()
+    n = rb.rb3_index_info(P)["n"]
+    cp = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cr = torch.empty(n, dtype=torch.uint8, device="cuda")
+    rb.rb3_export(P, codes=cp, stream=st)
+    rb.rb3_export(R, codes=cr, stream=st)
+    torch.cuda.synchronize()
+    res["equal_output"] = bool(torch.equal(cp, cr))
+    P.free()
+    R.free()
     return res
 
 
@@ -731,12 +776,15 @@ def mem_search(rb, torch, S, idx, args, st, dev, probe_g=None):
     ns = min(Q.nq, 100_000)
     best, tms = rb.rb3_tune_search(idx, q[:int(Q.qoff[ns])], qoff[:ns + 1], 31, 1, stream=st)
     res["autotune_chunk_len"] = int(best.chunk_len)
-    for form, key in ((0, "value"), (2, "loops_value"), (1, "plain_value")):
-        o = {"search_form": form, "chunk_len": int(best.chunk_len)}
+    res["autotune_hot_depth"] = int(best.hot_depth)
+    for form, key, hot in ((0, "value", int(best.hot_depth)), (0, "no_hot_table_value", -1),
+                           (2, "loops_value", 0), (1, "plain_value", 0)):
+        o = {"search_form": form, "chunk_len": int(best.chunk_len), "hot_depth": hot}
+        main = key == "value"
         reps = 2 if form == 0 else 1
         _, n = rb.rb3_mem_search_opts(idx, q, qoff, 31, 1, o, out=out, cap=cap, stream=st)  # warm-up
         torch.cuda.synchronize()
-        if form == 0:
+        if main:
             rb.rb3_search_stats(reset=True)
             rb.rb3_profile_reset()
             rb.rb3_profile_enable(True)
@@ -751,7 +799,7 @@ def mem_search(rb, torch, S, idx, args, st, dev, probe_g=None):
         res[key] = round(bp / (ms * 1e3), 2)
         res[key.replace("value", "ms")] = round(ms, 3)
         res["smems"] = int(n)
-        if form == 0:
+        if main:
             rb.rb3_profile_enable(False)
             kms = rb.rb3_profile_read().get("k.smem_steps", (ms * reps, reps, 0))[0] / reps
             ss = rb.rb3_search_stats(reset=True)
@@ -765,9 +813,9 @@ def mem_search(rb, torch, S, idx, args, st, dev, probe_g=None):
                 "block_reads_per_base": round(reads / bp, 3),
                 "bytes_per_base": round(32 * reads / bp, 1),
                 "hbm_frac": round(32 * reads / (kms * 1e-3) / 1e9 / hbm, 4), "hbm_peak_kind": peak_kind,
-                "what": "Occ block reads (one 32-byte request each at D = 32) counted by the kernel over its "
-                        "CUDA-event time; ceiling: the random-read probe (32-byte dependent reads); hbm_frac: "
-                        "those bytes per second against the copy peak"}
+                "what": "Occ block reads (one 32-byte request each at D = 32; a hot-level table read counts "
+                        "as one) counted by the kernel over its CUDA-event time; ceiling: the random-read probe "
+                        "(32-byte dependent reads); hbm_frac: those bytes per second against the copy peak"}
     res["speedup_vs_plain"] = round(res["value"] / res["plain_value"], 2)
     return res
 

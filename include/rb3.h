@@ -97,7 +97,15 @@ typedef struct {
                               batch is cut into runs of whole strings whose build footprint (estimated at
                               RB3_BUILD_BYTES_PER_SYMBOL per indexed symbol) fits it; a string that alone
                               exceeds it is built by itself.  Results do not depend on the cut. */
-    int32_t reserved[5];
+    int32_t hot_depth;     /* SMEM search (search_form 0): depth K of the hot-level table, the SA
+                              bi-intervals of every A/C/G/T string of length 1..K (32 bytes each, 4^K
+                              strings at depth K), built once per index on the device and kept with it.
+                              A backward extension that starts from the whole index looks its first
+                              symbols up there (as many as the FindSMEM loop will take, at most K, when
+                              they hold no N and the looked-up interval still occurs >= min_occ times)
+                              instead of extending symbol by symbol; the records are the same.
+                              0: autotuned, else log4(n) - 3 clamped to 0..10; -1: no table; 1..12. */
+    int32_t reserved[4];
 } rb3_opts;
 
 /* Device bytes a batch build holds at its peak per indexed symbol (both strands
@@ -165,8 +173,9 @@ int rb3_merge_opts(rb3_index *dst, const rb3_index *src, const rb3_opts *o, void
  * rb3_merge_apply: dst := the merge of src into dst at the rows pos (host or
  * device, src->n entries); pos must increase and lie in [0, n(dst) + n(src)),
  * else RB3_E_INVAL and dst is unchanged.  rb3_merge equals
- * rb3_merge_positions (owner NULL) then rb3_merge_apply.  Plain layouts only
- * (RB3_E_INVAL for a run-length index). */
+ * rb3_merge_positions (owner NULL) then rb3_merge_apply.  dst may be
+ * run-length encoded (the walk ranks its spans; rb3_merge_apply rewrites them);
+ * src must be plain (RB3_E_INVAL otherwise). */
 int rb3_merge_partition(const int64_t *len, int64_t n_seq, int32_t parts, int32_t *owner);
 int rb3_merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts *o, const int32_t *owner,
                         int32_t part, int64_t *pos, void *stream);
@@ -310,7 +319,9 @@ typedef struct {
     int64_t max_batch_bases;    /* query bases per micro-batch (default 8 Mi) */
     int64_t max_batch_requests; /* requests per micro-batch (default 4096; 1 = no batching) */
     int64_t search_form;        /* rb3_opts.search_form of the micro-batches' search (default 0) */
-    int64_t reserved[3];
+    int64_t hot_depth;          /* rb3_opts.hot_depth of the micro-batches' search (default 0); the
+                                   table is built when the server is created */
+    int64_t reserved[2];
 } rb3_server_opts;
 
 typedef struct {
@@ -346,7 +357,8 @@ void rb3_server_destroy(rb3_server *s);
  * not modified) for several segment lengths around the default, each with seed
  * caps of 1, 2 and 4 segment lengths (unless base->seed_cap is set), and
  * writes the fastest into best->seg_len and best->seed_cap; rb3_tune_search times the chunked SMEM search
- * (q, qoff: device) for several chunk lengths and writes best->chunk_len.  The
+ * (q, qoff: device) for several chunk lengths and writes best->chunk_len, then (unless
+ * base->hot_depth is set) for hot-level depths -1, 6, 8 and 10 and writes best->hot_depth.  The
  * choice is remembered per input shape (device, D, strand mode, log2 size
  * classes) and used by rb3_merge / rb3_mem_search when their knob is 0; with
  * RB3_TUNE_FILE set it is also persisted there.  best_ms (optional) receives
@@ -395,11 +407,14 @@ int rb3_index_info(const rb3_index *idx, int64_t *n, int64_t *m, int64_t *C, int
  * position.  The copy keeps src's sampled suffix array; src is unchanged.
  * rb3_backward_search, rb3_mem_search (all forms), rb3_mem_search_noalloc,
  * the server, rb3_locate, rb3_export (occ rows = the span headers),
- * rb3_index_save / rb3_index_load take it.  rb3_merge / rb3_merge_opts take it
- * on either side and rb3_append_batches as dst: a run-length input is expanded
- * to a transient plain D = 32 copy (one byte per symbol), merged, and a
- * run-length dst is re-encoded at its span (dst unchanged on failure);
- * rb3_tune_merge rejects it (RB3_E_INVAL).
+ * rb3_index_save / rb3_index_load take it.  It can be merged into directly:
+ * rb3_merge / rb3_merge_opts / rb3_append_batches / rb3_merge_positions /
+ * rb3_tune_merge take it as dst, the walk ranking its spans, and the merge
+ * rewrites every span from its old runs and the batch's symbols at their merged
+ * rows (no plain copy of dst; the result is run-length at the same span, dst
+ * unchanged on failure).  As src of rb3_merge a run-length index is expanded to
+ * a transient plain D = 32 copy (one byte per symbol); rb3_merge_positions and
+ * rb3_tune_merge refuse it as src (RB3_E_INVAL).
  * RB3_E_INVAL for a bad span or a src that is already run-length encoded. */
 int rb3_index_compress(const rb3_index *src, int32_t span, void *stream, rb3_index **out);
 
@@ -436,7 +451,9 @@ int rb3_selftest_wait(int32_t limit, void *stream);
 
 /* The high-water mark of device memory in use by this library's stream-ordered
  * allocations (the device's default memory pool) since the last reset, in
- * bytes; reset != 0 sets it back to the memory in use now.  Host-side query. */
+ * bytes; reset != 0 sets the mark back to the memory in use now and returns
+ * that (so a later call minus it is what a call in between added at its
+ * peak).  Host-side query. */
 int rb3_device_peak(int64_t *used_high, int32_t reset);
 
 /* Frees the batch text and inverse suffix array kept by rb3_build_batch. */

@@ -234,6 +234,7 @@ static void free_index(rb3_index *x) {
     dev_free(x->isa, st);
     free_samples(x);
     cudaStreamSynchronize(st);
+    free_hot(x);
     delete x;
 }
 
@@ -304,12 +305,14 @@ RB3_EXPORT int rb3_device_peak(int64_t *used_high, int32_t reset) {
     cudaMemPool_t pool;
     RB3_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
     uint64_t v = 0;
-    RB3_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
-    *used_high = (int64_t)v;
     if (reset) {
-        uint64_t zero = 0;  // resets the mark to the memory in use now
+        uint64_t zero = 0;  // resets the mark to the memory in use now, which is returned
         RB3_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+        RB3_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+    } else {
+        RB3_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
     }
+    *used_high = (int64_t)v;
     return RB3_OK;
 }
 
@@ -404,7 +407,7 @@ RB3_EXPORT int rb3_merge_positions(const rb3_index *dst, const rb3_index *src, c
     g_err.clear();
     RB3_CHECK_ARG(dst && src, "NULL index");
     RB3_CHECK_ARG(dst != src, "dst and src must differ");
-    RB3_CHECK_ARG(!dst->rle && !src->rle, "merge positions need plain-layout indexes");
+    RB3_CHECK_ARG(!src->rle, "the batch merged in must be a plain index");
     RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
                   "cannot merge a single-strand index with a double-strand one");
     if (src->n == 0) return RB3_OK;
@@ -572,6 +575,7 @@ RB3_EXPORT int rb3_mem_search_opts(const rb3_index *idx, const uint8_t *q, const
     rb3_opts opts;
     rb3_opts_default(&opts);
     if (o) opts = *o;
+    RB3_CHECK_ARG(opts.hot_depth >= -1 && opts.hot_depth <= HOT_MAX, "hot_depth must be -1..12");
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<int64_t> qo;
     RB3_TRY(read_i64(qoff, nq + 1, qo, st));

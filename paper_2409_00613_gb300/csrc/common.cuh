@@ -61,6 +61,17 @@ struct rb3_index {
     int32_t *isa = nullptr;    // device, n entries
     std::vector<int64_t> str_end;  // host: position of the sentinel ending DS string i
     int device = 0;
+    // hot-level table of the SMEM search (device, built on first use by
+    // rb3::hot_table and owned here): the bi-intervals of every A/C/G/T string
+    // of length 1..hot_k, valid while n and the rank arrays are those it was
+    // built from (hot_n, hot_src).  A table replaced by a deeper one stays in
+    // hot_old until the index is freed (a search on another stream may still
+    // read it).
+    mutable void *hot = nullptr;
+    mutable int32_t hot_k = 0;
+    mutable int64_t hot_n = -1;
+    mutable const void *hot_src = nullptr;
+    mutable std::vector<void *> hot_old;
 };
 
 namespace rb3 {
@@ -838,18 +849,35 @@ int diversity_stats(int64_t out[2], bool reset);
 // band rank); q, qoff device pointers, qo the offsets on the host.
 int bwasw_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const std::vector<int64_t> &qo, int64_t nq,
                const int32_t prm[5], int64_t *out, int64_t cap, int64_t *n_out, cudaStream_t st);
+// Hot-level table: entry hot_off(L) + w is the bi-interval of the string of
+// length L whose base-4 digits (A..T = 0..3, first symbol most significant)
+// spell w, as BackwardExt computes it from the whole index, last symbol first.
+struct alignas(32) HotEnt {
+    int64_t k, kp, s, pad;
+};
+__host__ __device__ __forceinline__ int64_t hot_off(int L) { return ((int64_t(1) << (2 * L)) - 4) / 3; }
+constexpr int HOT_MAX = 12;
+// The table of depth K for idx (built or rebuilt on stream st, which it then
+// synchronizes, when the index has none of that depth or has changed since).
+int hot_table(const rb3_index *idx, int K, cudaStream_t st, const HotEnt **out);
+// The depth a search uses: o.hot_depth, else the tuned one, else log4(n) - 3
+// clamped to 0..10 (0: no table).
+int hot_depth_for(const rb3_index *idx, const rb3_opts &o, int64_t nq, int64_t total_q);
+void free_hot(rb3_index *x);
+int64_t tuned_hot_depth(const rb3_index *idx, int64_t nq, int64_t total_q);
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st,
                     bool codes_checked = false);
 int export_impl(const rb3_index *idx, uint8_t *codes_dev, int64_t *occ_dev, cudaStream_t st);
 int rle_export_impl(const rb3_index *x, uint8_t *codes, int64_t *occ, cudaStream_t st);
-// Merge of any two layouts: a run-length input is merged through a plain copy,
-// and a run-length dst is re-encoded (same span) after the merge.
+// Merge of any two layouts: a run-length src is merged through a plain copy of
+// it; a run-length dst is merged into directly (its spans rewritten).
 int merge_any(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st);
-int rle_plain_copy(const rb3_index *x, cudaStream_t st, rb3_index **out);
-int rle_recompress_into(rb3_index *dst, const rb3_index *plain, int span, cudaStream_t st);
 int rle_check_impl(const rb3_index *x, cudaStream_t st);
+// The run-length arrays of a run-length dst merged with a plain src at rows pos.
+int rle_merge_arrays(const rb3_index *dst, const rb3_index *src, const int64_t *pos, cudaStream_t st,
+                     rb3_index *out);
 // Sampled suffix array of a batch from its SA (builder) and of a merge (from pos).
 int sample_batch(rb3_index *x, const int32_t *SA, cudaStream_t st);
 int sample_merge(const rb3_index *dst, const rb3_index *src, const int64_t *pos, const int64_t *kstart,
@@ -866,25 +894,6 @@ int finalize_counts(rb3_index *idx, cudaStream_t st);
             constexpr int NS = NS_RLE;           \
             __VA_ARGS__;                         \
         } else if ((D) == 32) {                  \
-            constexpr int NS = 0;                \
-            __VA_ARGS__;                         \
-        } else if ((D) == 64) {                  \
-            constexpr int NS = 1;                \
-            __VA_ARGS__;                         \
-        } else if ((D) == 128) {                 \
-            constexpr int NS = 2;                \
-            __VA_ARGS__;                         \
-        } else {                                 \
-            constexpr int NS = 4;                \
-            __VA_ARGS__;                         \
-        }                                        \
-    } while (0)
-
-// The same over the plain layouts only (kernels that never see a run-length
-// index: the merge, whose callers reject one first).
-#define RB3_WITH_NS_PLAIN(D, ...)                \
-    do {                                         \
-        if ((D) == 32) {                         \
             constexpr int NS = 0;                \
             __VA_ARGS__;                         \
         } else if ((D) == 64) {                  \

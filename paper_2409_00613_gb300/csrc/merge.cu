@@ -257,10 +257,33 @@ constexpr int REWALK_CK = 64;  // positions between checkpoints of the candidate
 
 // bit t of the result = [B[r0 + t] == a] for t < d (1 <= d <= 63, r0 + d <= n);
 // higher bits are unspecified.  D = 32: up to three blocks' planes; D >= 64:
-// up to two 64-symbol payload sectors.
+// up to two 64-symbol payload sectors; run-length: the runs over [r0, r0 + d),
+// decoded from the last mark before r0 (two spans at most).
 template <int NS>
 __device__ __forceinline__ uint64_t eq_bits(const OccView &v, int64_t r0, int d, int a) {
-    if constexpr (NS == 0) {
+    if constexpr (NS == NS_RLE) {
+        const int64_t rend = r0 + d;
+        uint64_t e = 0;
+        for (int64_t r = r0; r < rend;) {
+            const int64_t sp = r >> v.log2D, s0 = sp << v.log2D;
+            int64_t slen = v.n - s0;
+            if (slen > ((int64_t)1 << v.log2D)) slen = (int64_t)1 << v.log2D;
+            int64_t base[SIGMA], pos;
+            uint64_t acc[2];
+            RunRd rd;
+            rd.init(rle_start(v, sp, r - s0, base, &pos, acc));
+            while (pos < slen && s0 + pos < rend) {
+                int b;
+                int64_t len;
+                rd.run(&b, &len);
+                const int64_t lo = s0 + pos > r0 ? s0 + pos : r0, hi = s0 + pos + len < rend ? s0 + pos + len : rend;
+                if (b == a && hi > lo) e |= ((1ull << (hi - lo)) - 1ull) << (lo - r0);
+                pos += len;
+            }
+            r = s0 + slen;
+        }
+        return e;
+    } else if constexpr (NS == 0) {
         const uint8_t *b = v.blocks + (r0 >> 5) * 32;
         const int o = (int)(r0 & 31);
         uint64_t e = (uint64_t)(s32_match(ld_sec64(b), a) >> o);
@@ -1037,6 +1060,7 @@ static int launch_walk_plain_1(int D2, OccView V1, OccView V2, int64_t m1, int64
 
 static int launch_walk_plain(int D1, int D2, OccView V1, OccView V2, int64_t m1, int64_t m2, const uint8_t *own,
                              int64_t *pos, unsigned int *err, cudaStream_t st) {
+    if (D1 > 256) return launch_walk_plain_1<NS_RLE>(D2, V1, V2, m1, m2, own, pos, err, st);
     if (D1 == 32) return launch_walk_plain_1<0>(D2, V1, V2, m1, m2, own, pos, err, st);
     if (D1 == 64) return launch_walk_plain_1<1>(D2, V1, V2, m1, m2, own, pos, err, st);
     if (D1 == 128) return launch_walk_plain_1<2>(D2, V1, V2, m1, m2, own, pos, err, st);
@@ -1130,7 +1154,7 @@ __global__ void k_iota(int64_t *__restrict__ pos, int64_t n) {
 // writes every row.
 int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st, int64_t *pos,
                     unsigned int *err_dev, const int32_t *owner, int32_t part) {
-    RB3_CHECK_ARG(!dst->rle && !src->rle, "the merge walk reads plain-layout indexes only");
+    RB3_CHECK_ARG(!src->rle, "the batch merged in must be a plain index");
     const int64_t n1 = dst->n, n2 = src->n;
     if (n2 == 0) return RB3_OK;
     OccView V1 = occ_view(dst), V2 = occ_view(src);
@@ -1255,11 +1279,11 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 // per new symbol: 1 B text, 4 B ISA, one rank, 8 B pos (seed steps not counted)
                 Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
                 if (dst->single_strand)
-                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
                                                          src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_state,
                                                          d_order, nw, cap, d_ctr, pos));
                 else
-                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_merge_walk<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
                                                          src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_state,
                                                          d_order, nw, cap, d_ctr, pos));
             } else {
@@ -1284,13 +1308,13 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                     // second walk of unconverged positions not counted)
                     Phase pw("k.merge_walk", st, (double)n2 * (13.0 + rank_bytes(dst->D)));
                     if (dst->single_strand)
-                        RB3_WITH_NS_PLAIN(dst->D,
+                        RB3_WITH_NS(dst->D,
                                           RB3_LAUNCH((k_walk_seeded<NS, false>), grid, WALK_THREADS, 0, st, V1, m1,
                                                      src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
                                                      cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, c_ckv, c_ckm,
                                                      ck_per_seg, errp));
                     else
-                        RB3_WITH_NS_PLAIN(dst->D,
+                        RB3_WITH_NS(dst->D,
                                           RB3_LAUNCH((k_walk_seeded<NS, true>), grid, WALK_THREADS, 0, st, V1, m1,
                                                      src->text, src->isa, d_hi, d_send, d_sstart, d_next, d_order, nw,
                                                      cap, d_ctr, pos, c_lo, c_n, c_bv, c_bm, c_unw, c_ckv, c_ckm,
@@ -1336,7 +1360,7 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
                 }
                 {
                     Phase pr("k.rewalk", st);
-                    RB3_WITH_NS_PLAIN(dst->D, RB3_LAUNCH((k_rewalk<NS>), grid, WALK_THREADS, 0, st, V1, src->text,
+                    RB3_WITH_NS(dst->D, RB3_LAUNCH((k_rewalk<NS>), grid, WALK_THREADS, 0, st, V1, src->text,
                                                          src->isa, d_hi, c_unw, c_top, c_lo, c_ckv, c_ckm, ck_per_seg,
                                                          d_order, nw, c_ctr, pos, errp));
                 }
@@ -1357,7 +1381,7 @@ int merge_positions(const rb3_index *dst, const rb3_index *src, const rb3_opts &
 
 static int merge_check(const rb3_index *dst, const rb3_index *src) {
     RB3_CHECK_ARG(dst != src, "dst and src must differ");
-    RB3_CHECK_ARG(!dst->rle && !src->rle, "a run-length index is read-only (merge plain indexes, then compress)");
+    RB3_CHECK_ARG(!src->rle, "the batch merged in must be a plain index");
     RB3_CHECK_ARG(dst->single_strand == src->single_strand || dst->n == 0,
                   "cannot merge a single-strand index with a double-strand one");
     if ((dst->n + src->n) >= (int64_t(1) << 40)) {
@@ -1387,13 +1411,63 @@ __global__ void k_check_pos(const int64_t *__restrict__ pos, int64_t n2, int64_t
     if (p < 0 || p >= nM || (k + 1 < n2 && pos[k + 1] <= p)) atomicOr(bad, 4u);
 }
 
+// A run-length dst: the merged spans are written from its runs and src's
+// symbols (rle_merge_arrays), with the sampled suffix array merged as for a
+// plain one; dst is replaced only when everything succeeded.
+static int merge_apply_rle(rb3_index *dst, const rb3_index *src, const int64_t *pos, const unsigned int *errb,
+                           int64_t *kst, int64_t ntiles, cudaStream_t st) {
+    const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
+    struct Owned {
+        rb3_index *p = new rb3_index();
+        ~Owned() {
+            if (p) rb3_index_free(p);
+        }
+    } R;
+    RB3_TRY(rle_merge_arrays(dst, src, pos, st, R.p));
+    const bool keep_samples = src->sa_s > 0 && src->sdir && (n1 == 0 || (dst->sa_s == src->sa_s && dst->sdir));
+    if (keep_samples) {
+        Phase ph("merge.sample", st);
+        RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst);
+        if (n1 == 0) {
+            const int64_t nw = n2 / 64 + 1;
+            RB3_TRY(dev_alloc((void **)&R.p->sdir, sizeof(uint64_t) * 2 * nw, st));
+            RB3_TRY(dev_alloc((void **)&R.p->svals, sizeof(uint64_t) * (src->n_samples > 0 ? src->n_samples : 1), st));
+            RB3_CUDA_TRY(cudaMemcpyAsync(R.p->sdir, src->sdir, sizeof(uint64_t) * 2 * nw, cudaMemcpyDeviceToDevice, st));
+            if (src->n_samples > 0)
+                RB3_CUDA_TRY(cudaMemcpyAsync(R.p->svals, src->svals, sizeof(uint64_t) * src->n_samples,
+                                             cudaMemcpyDeviceToDevice, st));
+            R.p->n_samples = src->n_samples;
+        } else {
+            RB3_TRY(sample_merge(dst, src, pos, kst, ntiles, nM, MT, R.p, st));
+        }
+        R.p->sa_s = src->sa_s;
+    }
+    unsigned int herr = 0;
+    RB3_CUDA_TRY(cudaMemcpyAsync(&herr, errb, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("merge: segment seeds and walks disagree (flags %u); dst unchanged", herr);
+        return RB3_E_CUDA;
+    }
+    int64_t Cw[SIGMA + 1];
+    for (int a = 0; a <= SIGMA; ++a) Cw[a] = R.p->C[a];
+    RB3_TRY(finalize_counts(R.p, st));
+    for (int a = 0; a <= SIGMA; ++a)
+        if (R.p->C[a] != Cw[a]) {
+            set_error("merge: merged counts differ from the inputs' (symbol %d)", a);
+            return RB3_E_CUDA;
+        }
+    std::swap(*dst, *R.p);  // dst's old arrays leave with R
+    return RB3_OK;
+}
+
 int merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, const unsigned int *walk_err,
                 cudaStream_t st) {
     RB3_TRY(merge_check(dst, src));
     if (src->n == 0) return RB3_OK;
     const int64_t n1 = dst->n, n2 = src->n, nM = n1 + n2;
-    // output layout: D of dst (or of src when dst is empty)
-    int D = n1 ? dst->D : src->D;
+    // output layout: D of dst (or of src when a plain dst is empty)
+    int D = n1 || dst->rle ? dst->D : src->D;
     int log2D = ilog2(D), bb = block_bytes_for(D);
     int64_t nbM = nM / D + 1;
     int64_t ntiles = (nbM * D + MT - 1) / MT;
@@ -1404,8 +1478,6 @@ int merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, const 
     else
         RB3_CUDA_TRY(cudaMemsetAsync(errb.p, 0, sizeof(unsigned int), st));
     RB3_TRY(kst.alloc(sizeof(int64_t) * (ntiles + 2), st));
-    RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
-    RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
     OccView V1 = occ_view(dst), V2 = occ_view(src);
     const int64_t m1 = dst->m, m2 = src->m;
     if (!walk_err) {
@@ -1419,6 +1491,9 @@ int merge_apply(rb3_index *dst, const rb3_index *src, const int64_t *pos, const 
             return RB3_E_INVAL;
         }
     }
+    if (dst->rle) return merge_apply_rle(dst, src, pos, errb.as<unsigned int>(), kst.as<int64_t>(), ntiles, st);
+    RB3_TRY(tbase.alloc(sizeof(int64_t) * SIGMA * (ntiles + 1), st));
+    RB3_TRY(Mb.alloc((size_t)nbM * bb, st));
     {
         Phase ph("merge.scatter", st);
         RB3_LAUNCH(k_tile_starts, nb_for(n2 + 1, 256), 256, 0, st, pos, n2, ntiles, kst.as<int64_t>());

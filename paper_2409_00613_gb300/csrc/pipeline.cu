@@ -236,15 +236,7 @@ RB3_EXPORT int rb3_append_batches(rb3_index *dst, const uint8_t *seq, const int6
         ends.swap(cut);
         n_batches = (int64_t)ends.size();
     }
-    if (dst->rle) {  // appended to a plain copy, re-encoded once at the end
-        rb3_index *P = nullptr;
-        RB3_TRY(rle_plain_copy(dst, st, &P));
-        int r = append_batches(P, seq, lens.data(), n_seq, ends.data(), n_batches, opts, st);
-        if (r == RB3_OK) r = rle_recompress_into(dst, P, dst->D, st);
-        cudaStreamSynchronize(st);
-        rb3_index_free(P);
-        return r;
-    }
+    // a run-length dst takes each batch as it is (its spans rewritten per merge)
     RB3_TRY(append_batches(dst, seq, lens.data(), n_seq, ends.data(), n_batches, opts, st));
     RB3_CUDA_TRY(cudaStreamSynchronize(st));
     return RB3_OK;

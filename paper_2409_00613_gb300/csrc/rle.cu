@@ -10,14 +10,73 @@
 // with one or two extra length bytes for long runs; format in common.cuh),
 // not the paper's Elias-delta bit code: a byte code decodes with plain shifts
 // and needs no bit-level cursor on the GPU.  The index is built from a finished
-// plain index and is read-only: every query (backward search, SMEM search,
-// locate, export) runs on it through the same kernels, with the rank primitives
-// of the run-length layout.
+// plain index, and grows by merges: the walk ranks its spans, and the merged
+// spans are written from its old runs and the new batch's symbols at their
+// merged rows (the BWT's dynamic form, kept static between merges).  Every
+// query (backward search, SMEM search, locate, export) runs on it through the
+// same kernels, with the rank primitives of the run-length layout.
 #include "common.cuh"
 
 namespace rb3 {
 
 static inline unsigned nb_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Mark j of a span of slen symbols: the run holding offset (j + 1) * slen / 3.
+__host__ __device__ __forceinline__ int64_t rle_mark_target(int j, int64_t slen) { return (j + 1) * slen / 3; }
+
+// Encoder of one span's runs, fed (symbol, count) pieces in row order: a piece
+// of the pending run's symbol extends it, so the runs are maximal.  WRITE = false
+// counts bytes and runs only; WRITE = true also writes the run bytes from p and
+// the decode marks into the header words w[8..15].
+template <bool WRITE> struct SpanEnc {
+    uint8_t *p0 = nullptr, *p = nullptr;
+    uint32_t *w = nullptr;
+    int64_t slen = 0, at = 0;  // the span's symbols; offset of the pending run
+    int j = 0;                 // next mark
+    uint32_t cnt[SIGMA] = {0, 0, 0, 0, 0, 0};
+    uint64_t bytes = 0, runs = 0;
+    int cur = -1;
+    int64_t len = 0;
+    __device__ __forceinline__ void put(int a, int64_t t) {
+        if (t <= 0) return;
+        if (a == cur) {
+            len += t;
+            return;
+        }
+        flush();
+        cur = a;
+        len = t;
+    }
+    __device__ __forceinline__ void flush() {
+        if (len == 0) return;
+        const int64_t e = at + len;
+        if constexpr (WRITE) {
+            while (j < RLE_MARKS && rle_mark_target(j, slen) < e) {  // this run holds mark j's offset
+                w[8 + 4 * j] = (uint32_t)at | (cnt[1] << 16);
+                w[9 + 4 * j] = cnt[2] | (cnt[3] << 16);
+                w[10 + 4 * j] = cnt[4] | (cnt[5] << 16);
+                w[11 + 4 * j] = (uint32_t)(p - p0);
+                ++j;
+            }
+            if (len < RLE_BASE1) {
+                *p++ = (uint8_t)((cur << 5) | (len - 1));
+            } else if (len < RLE_BASE2) {
+                *p++ = (uint8_t)((cur << 5) | RLE_F1);
+                *p++ = (uint8_t)(len - RLE_BASE1);
+            } else {
+                const int64_t x = len - RLE_BASE2;
+                *p++ = (uint8_t)((cur << 5) | RLE_F2);
+                *p++ = (uint8_t)(x & 0xFF);
+                *p++ = (uint8_t)(x >> 8);
+            }
+        }
+        bytes += (uint64_t)rle_run_bytes(len);
+        ++runs;
+        cnt[cur] += (uint32_t)len;
+        at = e;
+        len = 0;
+    }
+};
 
 // One thread per span: runs of codes[s0, s1) and the bytes they take.
 __global__ void k_rle_size(const uint8_t *__restrict__ codes, int64_t n, int log2S, int64_t nspans,
@@ -25,22 +84,19 @@ __global__ void k_rle_size(const uint8_t *__restrict__ codes, int64_t n, int log
     const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (sp >= nspans) return;
     const int64_t s0 = sp << log2S, s1 = s0 + ((int64_t)1 << log2S) < n ? s0 + ((int64_t)1 << log2S) : n;
-    uint64_t nb = 0, nr = 0;
+    SpanEnc<false> enc;
     int64_t i = s0;
     while (i < s1) {
         const uint8_t a = codes[i];
         int64_t j = i + 1;
         while (j < s1 && codes[j] == a) ++j;
-        nb += rle_run_bytes(j - i);
-        ++nr;
+        enc.put(a, j - i);
         i = j;
     }
-    bytes[sp] = nb;
-    runs[sp] = nr;
+    enc.flush();
+    bytes[sp] = enc.bytes;
+    runs[sp] = enc.runs;
 }
-
-// Mark j of a span of slen symbols: the run holding offset (j + 1) * slen / 3.
-__host__ __device__ __forceinline__ int64_t rle_mark_target(int j, int64_t slen) { return (j + 1) * slen / 3; }
 
 // One thread per span: header (ranks at the span start from the plain index,
 // minus the gbase of their 2^32 range; where the runs begin; the marks) and runs.
@@ -61,38 +117,19 @@ __global__ void k_rle_write(const uint8_t *__restrict__ codes, OccView src, int 
     w[6] = (uint32_t)(off[sp] >> 32);
     w[7] = (uint32_t)runs[sp];
     for (int k = 8; k < 16; ++k) w[k] = 0;
-    uint8_t *const p0 = payload + off[sp];
-    uint8_t *p = p0;
-    uint32_t cnt[SIGMA] = {0, 0, 0, 0, 0, 0};
-    const int64_t slen = s1 - s0;
-    int j = 0;  // next mark to place
+    SpanEnc<true> enc;
+    enc.p0 = enc.p = payload + off[sp];
+    enc.w = w;
+    enc.slen = s1 - s0;
     int64_t i = s0;
     while (i < s1) {
         const uint8_t a = codes[i];
         int64_t e = i + 1;
         while (e < s1 && codes[e] == a) ++e;
-        const int64_t len = e - i;
-        while (j < RLE_MARKS && rle_mark_target(j, slen) < e - s0) {  // this run holds mark j's offset
-            w[8 + 4 * j] = (uint32_t)(i - s0) | (cnt[1] << 16);
-            w[9 + 4 * j] = cnt[2] | (cnt[3] << 16);
-            w[10 + 4 * j] = cnt[4] | (cnt[5] << 16);
-            w[11 + 4 * j] = (uint32_t)(p - p0);
-            ++j;
-        }
-        if (len < RLE_BASE1) {
-            *p++ = (uint8_t)((a << 5) | (len - 1));
-        } else if (len < RLE_BASE2) {
-            *p++ = (uint8_t)((a << 5) | RLE_F1);
-            *p++ = (uint8_t)(len - RLE_BASE1);
-        } else {
-            const int64_t x = len - RLE_BASE2;
-            *p++ = (uint8_t)((a << 5) | RLE_F2);
-            *p++ = (uint8_t)(x & 0xFF);
-            *p++ = (uint8_t)(x >> 8);
-        }
-        cnt[a] += (uint32_t)len;
+        enc.put(a, e - i);
         i = e;
     }
+    enc.flush();
     uint4 *h = reinterpret_cast<uint4 *>(hdr + sp * RLE_HDR_BYTES);
     for (int k = 0; k < 4; ++k) h[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
 }
@@ -136,6 +173,132 @@ __global__ void k_rle_occ(OccView V, int64_t nspans, int64_t *__restrict__ occ) 
     rle_start(V, sp, 0, r, &pos, acc);
     r[0] = (sp << V.log2D) - (r[1] + r[2] + r[3] + r[4] + r[5]);
     for (int a = 0; a < SIGMA; ++a) occ[sp * SIGMA + a] = r[a];
+}
+
+// ---- merge into a run-length index -------------------------------------------
+// The merged BWT of a run-length B1 and a plain B2 at the rows pos (increasing)
+// is written span by span, without a plain copy: output span sp holds merged
+// rows [r0, r1), of which pos[a0, a1) are B2's, a0 = |{pos < r0}|, and the rest
+// are B1's rows from o0 = r0 - a0 on, in order.  One thread per output span
+// reads B1's runs from o0 and puts B2's symbols between them.
+
+__device__ __forceinline__ int64_t lower_bound_i64(const int64_t *__restrict__ a, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Sequential reader of a run-length B's runs from a row on, across spans.
+struct RunCursor {
+    int64_t sp, s0, slen, pos;  // span, its first row, its symbols, offset after the current run
+    RunRd rd;
+    int sym = 0;
+    int64_t left = 0;  // rows of the current run not yet taken
+    __device__ __forceinline__ void open_span(const OccView &v, int64_t s, int64_t o) {
+        sp = s;
+        s0 = s << v.log2D;
+        slen = v.n - s0 < ((int64_t)1 << v.log2D) ? v.n - s0 : ((int64_t)1 << v.log2D);
+        int64_t base[SIGMA];
+        uint64_t acc[2];
+        rd.init(rle_start(v, s, o, base, &pos, acc));
+    }
+    // the run holding row l < n, with the rows of it from l on
+    __device__ __forceinline__ void open(const OccView &v, int64_t l) {
+        open_span(v, l >> v.log2D, l - ((l >> v.log2D) << v.log2D));
+        left = 0;
+        while (left == 0 && pos < slen) {
+            int64_t len;
+            rd.run(&sym, &len);
+            pos += len;
+            if (s0 + pos > l) left = s0 + pos - l;
+        }
+    }
+    // the next run (the caller takes rows only below n)
+    __device__ __forceinline__ void next(const OccView &v) {
+        if (pos >= slen) open_span(v, sp + 1, 0);
+        int64_t len;
+        rd.run(&sym, &len);
+        pos += len;
+        left = len;
+    }
+};
+
+template <bool WRITE>
+__global__ void k_rle_merge(OccView V1, OccView V2, const uint8_t *__restrict__ codes2,
+                            const int64_t *__restrict__ pos, int64_t n2, int64_t nM, int64_t nspans,
+                            const uint64_t *__restrict__ off, uint64_t *__restrict__ bytes,
+                            uint64_t *__restrict__ runs, const int64_t *__restrict__ gbase,
+                            uint8_t *__restrict__ hdr, uint8_t *__restrict__ payload) {
+    const int64_t sp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sp >= nspans) return;
+    const int log2S = V1.log2D;
+    const int64_t r0 = sp << log2S;
+    const int64_t r1 = r0 + ((int64_t)1 << log2S) < nM ? r0 + ((int64_t)1 << log2S) : nM;
+    const int64_t a0 = lower_bound_i64(pos, n2, r0);
+    SpanEnc<WRITE> enc;
+    enc.slen = r1 > r0 ? r1 - r0 : 0;
+    uint32_t w[16];
+    if constexpr (WRITE) {
+        // ranks at the span start: B1's below o0 plus B2's below a0
+        int64_t q1[SIGMA], q2[SIGMA];
+        rank_all_any(V1, r0 - a0, q1);
+        rank_all_any(V2, a0, q2);
+        const int64_t *g = gbase ? gbase + 5 * (r0 >> GSPAN_LOG2) : nullptr;
+        for (int a = 1; a < SIGMA; ++a) w[a - 1] = (uint32_t)(q1[a] + q2[a] - (g ? g[a - 1] : 0));
+        w[5] = (uint32_t)off[sp];
+        w[6] = (uint32_t)(off[sp] >> 32);
+        w[7] = (uint32_t)runs[sp];
+        for (int k = 8; k < 16; ++k) w[k] = 0;
+        enc.p0 = enc.p = payload + off[sp];
+        enc.w = w;
+    }
+    RunCursor old;
+    bool opened = false;
+    int64_t a = a0, r = r0;
+    while (r < r1) {
+        const int64_t nx = a < n2 && pos[a] < r1 ? pos[a] : r1;  // the next B2 row (or the span end)
+        while (r < nx) {  // B1's rows up to it: old row r - a
+            if (!opened) {
+                old.open(V1, r - a);
+                opened = true;
+            } else if (old.left == 0) {
+                old.next(V1);
+            }
+            const int64_t t = old.left < nx - r ? old.left : nx - r;
+            enc.put(old.sym, t);
+            old.left -= t;
+            r += t;
+        }
+        if (nx < r1) {
+            enc.put(codes2[a], 1);
+            ++a;
+            ++r;
+        }
+    }
+    enc.flush();
+    if constexpr (WRITE) {
+        uint4 *h = reinterpret_cast<uint4 *>(hdr + sp * RLE_HDR_BYTES);
+        for (int k = 0; k < 4; ++k) h[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    } else {
+        bytes[sp] = enc.bytes;
+        runs[sp] = enc.runs;
+    }
+}
+
+// gbase[5 g + a - 1] = rank(a, g * 2^32) of the merged BWT.
+__global__ void k_rle_merge_gbase(OccView V1, OccView V2, const int64_t *__restrict__ pos, int64_t n2, int64_t rows,
+                                  int64_t *__restrict__ gbase) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= rows) return;
+    const int64_t R = g << GSPAN_LOG2, a = lower_bound_i64(pos, n2, R);
+    int64_t q1[SIGMA], q2[SIGMA];
+    rank_all_any(V1, R - a, q1);
+    rank_all_any(V2, a, q2);
+    for (int c = 1; c < SIGMA; ++c) gbase[5 * g + c - 1] = q1[c] + q2[c];
 }
 
 // Consistency of a run-length image read from a file, every read bounds-checked:
@@ -381,6 +544,64 @@ static int decompress_impl(const rb3_index *x, cudaStream_t st, rb3_index *P) {
     return RB3_OK;
 }
 
+// The run-length arrays of dst merged with src at rows pos (src plain; the
+// span, strand mode and everything but the sampled suffix array): out's n, m,
+// C, layout fields, gbase, blocks (headers) and payload.
+int rle_merge_arrays(const rb3_index *dst, const rb3_index *src, const int64_t *pos, cudaStream_t st,
+                     rb3_index *out) {
+    const int64_t n2 = src->n, nM = dst->n + n2;
+    out->n = nM;
+    out->m = dst->m + src->m;
+    for (int a = 0; a < 7; ++a) out->C[a] = dst->C[a] + src->C[a];
+    out->rle = 1;
+    out->D = dst->D;
+    out->log2D = dst->log2D;
+    out->block_bytes = RLE_HDR_BYTES;
+    out->single_strand = src->single_strand;
+    out->nblocks = nM / dst->D + 1;
+    out->device = dst->device;
+    const int64_t ns = out->nblocks;
+    const OccView V1 = occ_view(dst), V2 = occ_view(src);
+    DevBuf codes2, bytes, runs, off;
+    RB3_TRY(codes2.alloc((size_t)(n2 > 0 ? n2 : 1), st));
+    RB3_TRY(bytes.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(runs.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(off.alloc(sizeof(uint64_t) * ns, st));
+    RB3_TRY(export_impl(src, codes2.as<uint8_t>(), nullptr, st));
+    if (nM >> GSPAN_LOG2) {
+        const int64_t rows = gbase_rows(nM);
+        RB3_TRY(dev_alloc((void **)&out->gbase, sizeof(int64_t) * 5 * rows, st));
+        RB3_LAUNCH(k_rle_merge_gbase, nb_for(rows, 64), 64, 0, st, V1, V2, pos, n2, rows, out->gbase);
+    }
+    {
+        Phase ph("merge.rle_size", st);
+        RB3_LAUNCH(k_rle_merge<false>, nb_for(ns, 128), 128, 0, st, V1, V2, codes2.as<uint8_t>(), pos, n2, nM, ns,
+                   (const uint64_t *)nullptr, bytes.as<uint64_t>(), runs.as<uint64_t>(), (const int64_t *)nullptr,
+                   (uint8_t *)nullptr, (uint8_t *)nullptr);
+    }
+    RB3_TRY(scan_u64(bytes.as<uint64_t>(), off.as<uint64_t>(), ns, false, st));
+    uint64_t tail[4];
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[0], off.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[1], bytes.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_TRY(scan_u64(runs.as<uint64_t>(), bytes.as<uint64_t>(), ns, false, st));  // total runs
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[2], bytes.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaMemcpyAsync(&tail[3], runs.as<uint64_t>() + ns - 1, 8, cudaMemcpyDeviceToHost, st));
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));
+    out->payload_bytes = (int64_t)(tail[0] + tail[1]);
+    out->runs = (int64_t)(tail[2] + tail[3]);
+    RB3_TRY(dev_alloc((void **)&out->blocks, (size_t)ns * RLE_HDR_BYTES, st));
+    RB3_TRY(dev_alloc((void **)&out->payload, (size_t)out->payload_bytes + 16, st));
+    RB3_CUDA_TRY(cudaMemsetAsync(out->payload + out->payload_bytes, 0, 16, st));
+    {
+        Phase ph("merge.rle_write", st);
+        RB3_LAUNCH(k_rle_merge<true>, nb_for(ns, 128), 128, 0, st, V1, V2, codes2.as<uint8_t>(), pos, n2, nM, ns,
+                   off.as<uint64_t>(), (uint64_t *)nullptr, runs.as<uint64_t>(), out->gbase, out->blocks,
+                   out->payload);
+    }
+    // the merged image passes the same checks as one read from a file
+    return rle_check_impl(out, st);
+}
+
 // Owns a temporary index.
 struct TmpIndex {
     rb3_index *p = nullptr;
@@ -389,64 +610,14 @@ struct TmpIndex {
     }
 };
 
-// dst <- x's contents; dst's old arrays are freed with x's shell.
-static void install(rb3_index *dst, rb3_index *x) {
-    std::swap(*dst, *x);
-    rb3_index_free(x);
-}
-
 int merge_any(rb3_index *dst, const rb3_index *src, const rb3_opts &o, cudaStream_t st) {
-    if (!dst->rle && !src->rle) return merge_impl(dst, src, o, st);
+    if (!src->rle) return merge_impl(dst, src, o, st);  // a run-length dst is merged into as it is
     RB3_CHECK_ARG(dst != src, "dst and src must differ");
-    TmpIndex P, Q;
-    rb3_index *d = dst;
-    const rb3_index *s = src;
-    if (src->rle) {  // the walk reads B2's LF (no build data): a plain copy of it
-        Q.p = new rb3_index();
-        RB3_TRY(decompress_impl(src, st, Q.p));
-        s = Q.p;
-    }
-    if (dst->rle) {
-        P.p = new rb3_index();
-        RB3_TRY(decompress_impl(dst, st, P.p));
-        d = P.p;
-    }
-    RB3_TRY(merge_impl(d, s, o, st));
-    if (dst->rle) {
-        rb3_index *R = new rb3_index();
-        const int r = compress_impl(P.p, dst->D, st, R);
-        if (r != RB3_OK) {
-            cudaStreamSynchronize(st);
-            rb3_index_free(R);
-            return r;
-        }
-        install(dst, R);
-    }
-    return RB3_OK;
-}
-
-int rle_plain_copy(const rb3_index *x, cudaStream_t st, rb3_index **out) {
-    rb3_index *P = new rb3_index();
-    const int r = decompress_impl(x, st, P);
-    if (r != RB3_OK) {
-        cudaStreamSynchronize(st);
-        rb3_index_free(P);
-        return r;
-    }
-    *out = P;
-    return RB3_OK;
-}
-
-int rle_recompress_into(rb3_index *dst, const rb3_index *plain, int span, cudaStream_t st) {
-    rb3_index *R = new rb3_index();
-    const int r = compress_impl(plain, span, st, R);
-    if (r != RB3_OK) {
-        cudaStreamSynchronize(st);
-        rb3_index_free(R);
-        return r;
-    }
-    install(dst, R);
-    return RB3_OK;
+    // the walk reads B2's LF (a run-length index has no build data): a plain copy of it
+    TmpIndex Q;
+    Q.p = new rb3_index();
+    RB3_TRY(decompress_impl(src, st, Q.p));
+    return merge_impl(dst, Q.p, o, st);
 }
 
 }  // namespace rb3

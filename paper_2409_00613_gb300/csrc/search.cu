@@ -19,6 +19,8 @@
 // if P[x0-1, e) occurs fewer than s_min times (then f(x0) > f(x0-1)).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "smem.cuh"
 
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(256) k_smem_steps(OccView V, const uint8_t *__
                                                     int64_t chunk, int ell, int64_t smin,
                                                     unsigned long long *__restrict__ next,
                                                     rb3_smem *__restrict__ out, int64_t cap,
-                                                    unsigned long long *__restrict__ count) {
+                                                    unsigned long long *__restrict__ count,
+                                                    const HotEnt *__restrict__ hot, int hotK) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     EmitAppend em{out, cap, count};
@@ -186,6 +189,32 @@ __global__ void __launch_bounds__(256) k_smem_steps(OccView V, const uint8_t *__
             break;
         }
         if (phase == SM_ITEM || phase == SM_DONE) continue;
+        // A backward loop that starts from the whole index (B1, B2) takes its
+        // first symbols from the hot-level table: the M symbols P[j-M+1, j]
+        // (at most hotK, no N, and leaving the loop's last symbol to the step
+        // below) in one read, when their interval still occurs >= smin times --
+        // then every shorter one does too, so the loop would have taken all M.
+        if (hotK > 0 && (phase == SM_B1 || phase == SM_B2) && x.s == V.n) {
+            const int64_t room = phase == SM_B1 ? j - i : j - i - 1;
+            const int M = room < hotK ? (int)room : hotK;
+            uint32_t w = 0;
+            int t = 0;
+            for (; t < M; ++t) {
+                const int c = P[j - t];
+                if (c < 1 || c > 4) break;
+                w |= (uint32_t)(c - 1) << (2 * t);
+            }
+            if (t >= 2) {
+                const longlong2 *h = reinterpret_cast<const longlong2 *>(hot + hot_off(t) + w);
+                const longlong2 a = __ldg(h), b = __ldg(h + 1);
+                if (b.x >= smin) {
+                    x = BiInt{a.x, a.y, b.x};
+                    j -= t;
+                    n_ext += (uint32_t)t;
+                    ++n_reads;
+                }
+            }
+        }
         // one extension per lane
         const int64_t at = phase == SM_CHK ? x0 - 1 : j;
         {
@@ -330,6 +359,96 @@ int backward_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *
     return RB3_OK;
 }
 
+// ---- hot-level table ----------------------------------------------------------
+// Level L from level L - 1: the string of digits w is its first symbol w >> 2(L-1)
+// put before the string w mod 4^(L-1), so its interval is one BackwardExt of that
+// string's (for L = 1, of the whole index).  One thread per string.
+template <int NS>
+__global__ void k_hot_level(OccView V, HotEnt *__restrict__ tab, int L) {
+    const int64_t nw = int64_t(1) << (2 * L);
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    BiInt x = {0, 0, V.n};
+    if (L > 1) {
+        const HotEnt &p = tab[hot_off(L - 1) + (w & ((nw >> 2) - 1))];
+        x = BiInt{p.k, p.kp, p.s};
+    }
+    const BiInt y = backward_ext<NS>(V, x, (int)(w >> (2 * (L - 1))) + 1);
+    tab[hot_off(L) + w] = HotEnt{y.k, y.kp, y.s, 0};
+}
+
+namespace {
+std::mutex g_hot_mu;  // one builder at a time (server slots search from several threads)
+const void *rank_arrays(const rb3_index *idx) { return idx->rle ? (const void *)idx->payload : idx->blocks; }
+}  // namespace
+
+void free_hot(rb3_index *x) {
+    std::lock_guard<std::mutex> lk(g_hot_mu);
+    if (x->hot) cudaFree(x->hot);
+    for (void *p : x->hot_old) cudaFree(p);
+    x->hot_old.clear();
+    x->hot = nullptr;
+    x->hot_k = 0;
+    x->hot_n = -1;
+    x->hot_src = nullptr;
+}
+
+// A table of depth K also serves every smaller depth (level L's place does not
+// depend on K), so a deeper table is kept.
+int hot_table(const rb3_index *idx, int K, cudaStream_t st, const HotEnt **out) {
+    std::lock_guard<std::mutex> lk(g_hot_mu);
+    const bool fresh = idx->hot && idx->hot_n == idx->n && idx->hot_src == rank_arrays(idx);
+    if (fresh && idx->hot_k >= K) {
+        *out = static_cast<const HotEnt *>(idx->hot);
+        return RB3_OK;
+    }
+    if (idx->hot) {
+        if (fresh) {
+            idx->hot_old.push_back(idx->hot);  // shallower: other streams may still read it
+        } else {
+            // the index changed since (a merge), and no search runs beside a merge
+            RB3_CUDA_TRY(cudaStreamSynchronize(st));
+            cudaFree(idx->hot);
+        }
+        idx->hot = nullptr;
+        idx->hot_k = 0;
+    }
+    // plain cudaMalloc: the table outlives the stream it is built on
+    struct Guard {
+        void *p = nullptr;
+        ~Guard() {
+            if (p) cudaFree(p);
+        }
+    } g;
+    const size_t bytes = sizeof(HotEnt) * (size_t)hot_off(K + 1);
+    RB3_CUDA_TRY(cudaMalloc(&g.p, bytes));
+    const OccView V = occ_view(idx);
+    for (int L = 1; L <= K; ++L) {
+        const int64_t nw = int64_t(1) << (2 * L);
+        RB3_WITH_NS(idx->D,
+                    RB3_LAUNCH(k_hot_level<NS>, nb_for(nw, 256), 256, 0, st, V, static_cast<HotEnt *>(g.p), L));
+    }
+    RB3_CUDA_TRY(cudaStreamSynchronize(st));  // other streams may read it as soon as it is published
+    idx->hot = g.p;
+    g.p = nullptr;
+    idx->hot_k = K;
+    idx->hot_n = idx->n;
+    idx->hot_src = rank_arrays(idx);
+    *out = static_cast<const HotEnt *>(idx->hot);
+    return RB3_OK;
+}
+
+int hot_depth_for(const rb3_index *idx, const rb3_opts &o, int64_t nq, int64_t total_q) {
+    int K = o.hot_depth;
+    if (K == 0) K = (int)tuned_hot_depth(idx, nq, total_q);
+    if (K == 0) {
+        K = idx->n > 1 ? ilog2(idx->n) / 2 - 3 : 0;
+        if (K > 10) K = 10;
+    }
+    if (K < 2) return 0;  // a table of single symbols saves no step
+    return K > HOT_MAX ? HOT_MAX : K;
+}
+
 int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, const int64_t *qoff_host,
                     int64_t nq, int64_t total_q, int32_t min_len, int64_t min_occ, const rb3_opts &o,
                     rb3_smem *out_dev, int64_t cap, int64_t *n_out, cudaStream_t st, bool codes_checked) {
@@ -341,6 +460,9 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
     if (chunk <= 0) chunk = 256;
     const bool plain = o.search_form == 1;
     const bool loops = o.search_form == 2;  // chunked, each lane running FindSMEM1's loops
+    const HotEnt *hot = nullptr;
+    int hotK = plain || loops ? 0 : hot_depth_for(idx, o, nq, total_q);
+    if (hotK > 0) RB3_TRY(hot_table(idx, hotK, st, &hot));
     std::vector<int64_t> item_off;
     int64_t nitems = nq;
     if (!plain) {
@@ -386,7 +508,7 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
                 else
                     RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_steps<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff,
                                                    nq, items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ,
-                                                   d_next, raw.as<rb3_smem>(), scap, d_count));
+                                                   d_next, raw.as<rb3_smem>(), scap, d_count, hot, hotK));
             }
         }
         RB3_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));

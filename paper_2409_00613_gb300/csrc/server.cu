@@ -69,6 +69,7 @@ static void server_worker(rb3_server *S) {
     rb3_opts so;
     rb3_opts_default(&so);
     so.search_form = (int32_t)S->o.search_form;
+    so.hot_depth = (int32_t)S->o.hot_depth;
     for (;;) {
         std::vector<rb3_server::Req> batch;
         {
@@ -203,6 +204,15 @@ RB3_EXPORT int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o,
     RB3_CHECK_ARG(opt.slots >= 1 && opt.slots <= 64, "slots must be in [1, 64]");
     RB3_CHECK_ARG(opt.max_batch_bases >= 1 && opt.max_batch_requests >= 1, "batch limits must be >= 1");
     RB3_CHECK_ARG(opt.search_form >= 0 && opt.search_form <= 2, "search_form must be 0, 1 or 2");
+    RB3_CHECK_ARG(opt.hot_depth >= -1 && opt.hot_depth <= HOT_MAX, "hot_depth must be -1..12");
+    if (opt.search_form == 0) {  // the hot-level table now, not in the first micro-batch
+        rb3_opts so;
+        rb3_opts_default(&so);
+        so.hot_depth = (int32_t)opt.hot_depth;
+        const int K = hot_depth_for(idx, so, 0, 0);
+        const HotEnt *tab = nullptr;
+        if (K > 0) RB3_TRY(hot_table(idx, K, 0, &tab));
+    }
     rb3_server *S = new rb3_server();
     S->idx = idx;
     S->o = opt;

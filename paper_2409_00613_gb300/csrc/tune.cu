@@ -1,8 +1,9 @@
 // Autotuner.  The merge's segment length trades seed work against walk
 // parallelism, its seed cap trades seed work against candidate walks and
-// second walks of unconverged segments, and the SMEM search's chunk length
-// trades load balance against the chunks' extra first steps; the best values
-// depend on the inputs' shape.
+// second walks of unconverged segments, the SMEM search's chunk length trades
+// load balance against the chunks' extra first steps, and its hot-level depth
+// trades table bytes (32 B x 4^K / 0.75) against the extensions a table read
+// replaces; the best values depend on the inputs' shape.
 // rb3_tune_merge / rb3_tune_search time candidates on the caller's own inputs
 // (the merge's walk phase runs into scratch, so the index is not modified) and
 // remember the winner per input shape: device, Occ interval, strand mode and
@@ -87,6 +88,12 @@ int64_t tuned_seed_cap(const rb3_index *dst, const rb3_index *src) {
 
 int64_t tuned_chunk_len(const rb3_index *idx, int64_t nq, int64_t total_q) {
     return lookup(search_key(idx, nq, total_q));
+}
+
+int64_t tuned_hot_depth(const rb3_index *idx, int64_t nq, int64_t total_q) {
+    Key k = search_key(idx, nq, total_q);
+    std::get<0>(k) = 3;
+    return lookup(k);
 }
 
 static int time_ms(cudaStream_t st, float *ms, const std::function<int()> &fn) {
@@ -188,6 +195,32 @@ int tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, con
     store(search_key(idx, nq, total_q), bestC);
     best->search_form = 0;
     best->chunk_len = bestC;
+    // then the hot-level table's depth at that chunk length (each table is
+    // built by an untimed call first; -1 = none)
+    if (base.hot_depth == 0) {
+        o.chunk_len = bestC;
+        int bestK = -1;
+        float bestkt = 1e30f;
+        for (int K : {-1, 6, 8, 10}) {
+            o.hot_depth = K;
+            RB3_TRY(mem_search_impl(idx, q, qoff, qoff_host, nq, total_q, min_len, min_occ, o, out.as<rb3_smem>(),
+                                    cap, &n, st));
+            float t = 0.f;
+            RB3_TRY(time_ms(st, &t, [&] {
+                return mem_search_impl(idx, q, qoff, qoff_host, nq, total_q, min_len, min_occ, o,
+                                       out.as<rb3_smem>(), cap, &n, st);
+            }));
+            if (t < bestkt) {
+                bestkt = t;
+                bestK = K;
+            }
+        }
+        Key k = search_key(idx, nq, total_q);
+        std::get<0>(k) = 3;
+        store(k, bestK);
+        best->hot_depth = bestK;
+        bestt = bestkt;
+    }
     if (best_ms) *best_ms = bestt;
     return RB3_OK;
 }
@@ -309,7 +342,7 @@ RB3_EXPORT int rb3_tune_merge(const rb3_index *dst, const rb3_index *src, const 
                               double *best_ms, void *stream) {
     set_error("%s", "");
     RB3_CHECK_ARG(dst && src && best, "NULL argument");
-    RB3_CHECK_ARG(!dst->rle && !src->rle, "merge tuning needs plain-layout indexes");
+    RB3_CHECK_ARG(!src->rle, "the batch merged in must be a plain index");
     rb3_opts o;
     rb3_opts_default(&o);
     if (base) o = *base;

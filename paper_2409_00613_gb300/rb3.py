@@ -28,13 +28,14 @@ class rb3_opts(ctypes.Structure):
                 ("seg_len", ctypes.c_int64), ("seed_cap", ctypes.c_int64),
                 ("merge_form", ctypes.c_int32), ("search_form", ctypes.c_int32),
                 ("chunk_len", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
-                ("sa_sample", ctypes.c_int32), ("batch_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("sa_sample", ctypes.c_int32), ("batch_mb", ctypes.c_int32), ("hot_depth", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class rb3_server_opts(ctypes.Structure):
     _fields_ = [("min_len", ctypes.c_int32), ("slots", ctypes.c_int32), ("min_occ", ctypes.c_int64),
                 ("max_batch_bases", ctypes.c_int64), ("max_batch_requests", ctypes.c_int64),
-                ("search_form", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("search_form", ctypes.c_int64), ("hot_depth", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 COMPLETION_DTYPE = np.dtype([("req_id", "<i8"), ("tag", "<i8"), ("n_smem", "<i8"), ("status", "<i4"),

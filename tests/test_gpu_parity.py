@@ -201,6 +201,55 @@ def test_smem_vs_oracle(chunk, ell, smin, D):
         assert np.array_equal(smem_rows(recs, n), want), (form, chunk, ell, smin)
 
 
+@pytest.mark.parametrize("layout", [32, 128, "rle512"])
+def test_smem_hot_levels_vs_oracle(layout):
+    """The hot-level table (depth -1 = none, 2, 3, 7, 12): a backward loop that
+    starts from the whole index takes its first symbols from the table; the
+    records equal the oracle's, the algorithmic extension count is the same at
+    every depth and the rank-block reads fall."""
+    S = synth.pangenome(seed=36, founder_len=4000, n_hap=6, batch=3)
+    B = ref_bwt(S)
+    D = 32 if layout == "rle512" else layout
+    idx = build(S, 0, 3, occ_interval=D)
+    rb.rb3_merge(idx, build(S, 3, 6, occ_interval=D))
+    if layout == "rle512":
+        idx = rb.rb3_index_compress(idx, 512)
+    Q = synth.mem_queries(S, seed=37, nq=400, median=90, lo=1, hi=700, sub=0.02)
+    g = synth.rng(38)
+    q = Q.q.copy()
+    nmask = g.random(len(q)) < 0.01  # N inside the looked-up windows
+    q[nmask] = 5
+    dq, doff = torch.from_numpy(q).to(DEV), torch.from_numpy(Q.qoff).to(DEV)
+    for ell, smin in ((1, 1), (4, 1), (12, 2), (31, 1)):
+        want = oracle.smem(B, q, Q.qoff, ell, smin)
+        stats = {}
+        for K in (-1, 2, 3, 7, 12):
+            rb.rb3_search_stats(reset=True)
+            recs, n = rb.rb3_mem_search_opts(idx, dq, doff, ell, smin, {"hot_depth": K, "chunk_len": 64})
+            stats[K] = rb.rb3_search_stats()
+            assert np.array_equal(smem_rows(recs, n), want), (layout, ell, smin, K)
+        assert len({v["extensions"] for v in stats.values()}) == 1, stats
+        if ell >= 12:
+            assert stats[7]["block_reads"] < stats[-1]["block_reads"], stats
+    with pytest.raises(rb.RB3Error) as e:
+        rb.rb3_mem_search_opts(idx, dq, doff, 31, 1, {"hot_depth": 13})
+    assert e.value.code == rb.RB3_E_INVAL
+
+
+def test_hot_table_follows_merges():
+    """A table built for an index is rebuilt after a merge changes it."""
+    S = synth.pangenome(seed=39, founder_len=3000, n_hap=6, batch=3)
+    idx = build(S, 0, 3)
+    Q = synth.mem_queries(S, seed=40, nq=200, median=90, lo=31, hi=400, sub=0.01)
+    dq, doff = torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV)
+    recs, n = rb.rb3_mem_search_opts(idx, dq, doff, 31, 1, {"hot_depth": 8})
+    assert np.array_equal(smem_rows(recs, n), oracle.smem(ref_bwt(S, 0, 3), Q.q, Q.qoff, 31, 1))
+    rb.rb3_merge(idx, build(S, 3, 6))
+    for K in (8, 5, 9):  # same depth after the merge, a shallower one, a deeper one
+        recs, n = rb.rb3_mem_search_opts(idx, dq, doff, 31, 1, {"hot_depth": K})
+        assert np.array_equal(smem_rows(recs, n), oracle.smem(ref_bwt(S), Q.q, Q.qoff, 31, 1)), K
+
+
 def test_smem_capacity_and_single_strand_rejected():
     S = synth.pangenome(seed=33, founder_len=2000, n_hap=3, batch=3)
     idx = build(S)
@@ -372,7 +421,8 @@ def test_autotuner_choices_keep_results():
     q, qoff = torch.from_numpy(Q.q).to(DEV), torch.from_numpy(Q.qoff).to(DEV)
     best, ms = rb.rb3_tune_search(idx, q, qoff, 31, 1)
     assert best.chunk_len in (64, 128, 256, 512, 1024, 4096)
-    recs, n = rb.rb3_mem_search(idx, q, qoff, 31, 1)
+    assert best.hot_depth in (-1, 6, 8, 10)
+    recs, n = rb.rb3_mem_search(idx, q, qoff, 31, 1)  # the remembered chunk length and depth
     assert np.array_equal(smem_rows(recs, n), oracle.smem(want, Q.q, Q.qoff, 31, 1))
 
 

@@ -154,7 +154,12 @@ def test_rle_locate_save_load_and_refusals(tmp_path):
     with pytest.raises(rb.RB3Error) as e:
         rb.rb3_index_compress(R)
     assert e.value.code == rb.RB3_E_INVAL
-    for call in (lambda: rb.rb3_tune_merge(R, build(S, 0, 1)), lambda: rb.rb3_tune_merge(idx, R)):
+    # merge tuning takes a run-length dst (the walk ranks its spans), not a run-length src
+    best, ms = rb.rb3_tune_merge(R, build(S, 0, 1))
+    assert best.seg_len >= 256 and ms > 0
+    check_rle(R, B, 1024)  # not modified
+    for call in (lambda: rb.rb3_tune_merge(idx, R),
+                 lambda: rb.rb3_merge_positions(idx, R, pos=torch.zeros(len(B), dtype=torch.int64, device=DEV))):
         with pytest.raises(rb.RB3Error) as e:
             call()
         assert e.value.code == rb.RB3_E_INVAL
@@ -166,9 +171,9 @@ def test_rle_locate_save_load_and_refusals(tmp_path):
 @pytest.mark.parametrize("span", [512, 2048])
 def test_rle_merges_and_appends(span):
     """Merges with a run-length input on either side, and appends to a
-    run-length index (through a plain copy, re-encoded at the same span): the
-    result against the oracle's BWT of the concatenation, the sampled suffix
-    array carried along, the inputs unchanged."""
+    run-length index (merged into directly, its spans rewritten): the result
+    against the oracle's BWT of the concatenation, the sampled suffix array
+    carried along, the inputs unchanged."""
     S = synth.pangenome(seed=77, founder_len=5_000, n_hap=8, batch=2)
     T_all = oracle.concat(S.seq, S.lens, True)
     B_all = oracle.bwt(T_all)
@@ -200,6 +205,73 @@ def test_rle_merges_and_appends(span):
     rows = np.arange(len(T_all), dtype=np.int64)
     assert rb.rb3_index_info(A)["sa_sample"] == 4
     assert np.array_equal(rb.rb3_locate(A, rows), oracle.locate(T_all, oracle.suffix_array(T_all), rows))
+
+
+def _image(idx, path):
+    rb.rb3_index_save(idx, path)
+    return open(path, "rb").read()
+
+
+@pytest.mark.parametrize("span", [512, 2048, 16384])
+@pytest.mark.parametrize("form", [0, 1, 3])
+def test_rle_merge_image_equals_compressed_plain_merge(tmp_path, span, form):
+    """A merge into a run-length index writes, byte for byte, the image that
+    compressing the plain merge gives (span headers, marks, runs, sampled
+    suffix array), and its BWT is the oracle's; single strand too."""
+    S = synth.pangenome(seed=78, founder_len=7_000, n_hap=6, batch=2)
+    for both in (True, False):
+        opts = {"sa_sample": 8, "single_strand": 0 if both else 1}
+        P = build(S, 0, 2, **opts)
+        R = rb.rb3_index_compress(build(S, 0, 2, **opts), span)
+        for a, b in ((2, 3), (3, 6)):
+            o = {"merge_form": form, "seg_len": 512, "seed_cap": 256 if form != 3 else 0}
+            rb.rb3_merge_opts(P, build(S, a, b, **opts), o)
+            rb.rb3_merge_opts(R, build(S, a, b, **opts), o)
+            sub = S.subset(0, b)
+            B = oracle.bwt(oracle.concat(sub.seq, sub.lens, both))
+            assert np.array_equal(rb.rb3_export(R), B), (span, form, both, b)
+            want = _image(rb.rb3_index_compress(P, span), str(tmp_path / "c.rb3"))
+            assert _image(R, str(tmp_path / "m.rb3")) == want, (span, form, both, b)
+
+
+def test_rle_merge_edges_and_parts():
+    """Merges into an empty run-length index, of an empty batch, of content the
+    index already holds (an exact duplicate), and the merge in parts (two
+    position arrays summed, then applied) into a run-length dst; the merge
+    holds no plain copy of dst (device peak below one byte per indexed symbol)."""
+    S = synth.pangenome(seed=79, founder_len=20_000, n_hap=6, batch=2)
+    span = 1024
+    E = rb.rb3_index_compress(rb.rb3_index_empty(), span)
+    rb.rb3_merge(E, build(S, 0, 2))
+    check_rle(E, ref(S, 0, 2), span)
+    rb.rb3_merge(E, rb.rb3_build_batch(np.zeros(0, np.uint8), np.zeros(0, np.int64)))
+    check_rle(E, ref(S, 0, 2), span)
+    dup = build(S, 1, 2)  # haplotype 1 again
+    rb.rb3_merge(E, dup)
+    seq = np.concatenate([S.seq[:S.offsets[2]], S.seq[S.offsets[1]:S.offsets[2]]])
+    lens = np.concatenate([S.lens[:2], S.lens[1:2]])
+    check_rle(E, oracle.bwt(oracle.concat(seq, lens, True)), span)
+    # in parts: each part's positions, summed, then applied to a run-length dst
+    R = rb.rb3_index_compress(build(S, 0, 4), span)
+    src = build(S, 4, 6)
+    owner = rb.rb3_merge_partition(S.lens[4:6], 2)
+    n2 = rb.rb3_index_info(src)["n"]
+    total = torch.zeros(n2, dtype=torch.int64, device=DEV)
+    for part in range(2):
+        pos = torch.empty(n2, dtype=torch.int64, device=DEV)
+        rb.rb3_merge_positions(R, src, owner=owner, part=part, pos=pos)
+        total += pos
+    n1 = rb.rb3_index_info(R)["n"]
+    torch.cuda.synchronize()
+    base = rb.rb3_device_peak(reset=True)  # in use now: dst, src and its build data
+    rb.rb3_merge_apply(R, src, total)
+    torch.cuda.synchronize()
+    peak = rb.rb3_device_peak() - base
+    check_rle(R, ref(S, 0, 6), span)
+    # what the merge added at its peak: the merged runs and headers, the batch's
+    # symbols (1 B each), span counts and offsets -- never a copy of dst's n1
+    # symbols (a plain copy, the merged plain index and its codes: 3 n1 + 2 n2)
+    assert peak < n1 + 2 * n2, (peak, n1, n2)
 
 
 def test_rle_server_round_trip():
