@@ -203,16 +203,38 @@ def test_occ32_index_past_2_to_32():
     for p in parts:
         p.free()
     # the run-length copy keeps the span bases: the same intervals.  Merged with
-    # an empty index (expanded to a plain copy and re-encoded): the same again;
-    # merged with one empty string (two new sentinels, which sort before every
-    # letter): every interval moves up by two
+    # an empty index: the same again; merged with one empty string (two new
+    # sentinels, which sort before every letter): every interval moves up by two
     R = rb.rb3_index_compress(idx, 2048)
     assert rb.rb3_index_info(R)["run_length"]
     assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got)
     rb.rb3_merge(R, rb.rb3_index_empty(opts))
     assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got)
-    rb.rb3_merge(R, rb.rb3_build_batch(np.zeros(0, np.uint8), np.zeros(1, np.int64), opts=opts))
+    empty_string = rb.rb3_build_batch(np.zeros(0, np.uint8), np.zeros(1, np.int64), opts=opts)
+    rb.rb3_merge(R, empty_string)
     assert rb.rb3_index_info(R)["n"] == info["n"] + 2
     assert np.array_equal(rb.rb3_backward_search(R, q, qoff), got + 2)
+    # three 5 kb windows merged into the run-length index directly (its walk
+    # ranks spans on both sides of 2^32, its span bases are rewritten) and into
+    # the plain one: the run-length result is the compressed plain result --
+    # the BWT, every span header's ranks (span bases added) and the run count
+    rb.rb3_merge(idx, empty_string)
+    g2 = synth.rng(4343)
+    starts = g2.integers(0, len(S.seq) - 5000, size=3)
+    sseq = np.concatenate([S.seq[s:s + 5000] for s in starts]).astype(np.uint8)
+    for x in (idx, R):
+        rb.rb3_merge(x, rb.rb3_build_batch(torch.from_numpy(sseq).to(DEV), np.full(3, 5000, np.int64), opts=opts))
+    R2 = rb.rb3_index_compress(idx, 2048)
+    n = info["n"] + 2 + 2 * 15000
+    assert rb.rb3_index_info(R)["n"] == n
+    codes = [torch.empty(n, dtype=torch.uint8, device=DEV) for _ in range(2)]
+    occ = [torch.empty((n // 2048 + 1, 6), dtype=torch.int64, device=DEV) for _ in range(2)]
+    for x, c, o in zip((R, R2), codes, occ):
+        rb.rb3_export(x, codes=c, occ=o)
+    torch.cuda.synchronize()
+    assert torch.equal(codes[0], codes[1]) and torch.equal(occ[0], occ[1])
+    assert rb.rb3_index_bytes(R) == rb.rb3_index_bytes(R2)
+    del codes, occ
+    R2.free()
     R.free()
     idx.free()
