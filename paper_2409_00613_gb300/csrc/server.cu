@@ -65,7 +65,8 @@ static void server_worker(rb3_server *S) {
     int64_t qcap = budget;
     dev_alloc((void **)&d_q, (size_t)qcap, st);
     dev_alloc((void **)&d_off, sizeof(int64_t) * (size_t)(S->o.max_batch_requests + 1), st);
-    std::vector<rb3_smem> h_out;
+    rb3_smem *h_out = nullptr;  // pinned: a pageable copy would go through the driver's staging
+    int64_t h_out_cap = 0;
     rb3_opts so;
     rb3_opts_default(&so);
     so.search_form = (int32_t)S->o.search_form;
@@ -130,8 +131,17 @@ static void server_worker(rb3_server *S) {
             }
         }
         if (r == RB3_OK) {
-            h_out.resize((size_t)n);
-            if (n && cudaMemcpyAsync(h_out.data(), d_out, sizeof(rb3_smem) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            if (n > h_out_cap) {
+                int64_t want = n > 2 * h_out_cap ? n : 2 * h_out_cap;  // grows geometrically
+                if (want < 65536) want = 65536;
+                cudaFreeHost(h_out);
+                h_out = nullptr;
+                h_out_cap = 0;
+                if (cudaMallocHost(&h_out, sizeof(rb3_smem) * (size_t)want) == cudaSuccess) h_out_cap = want;
+                else r = cuda_fail(cudaGetLastError(), "server: result buffer", __FILE__, __LINE__);
+            }
+            if (r == RB3_OK && n &&
+                cudaMemcpyAsync(h_out, d_out, sizeof(rb3_smem) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "server: copy results", __FILE__, __LINE__);
             if (r == RB3_OK && cudaStreamSynchronize(st) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "server: sync", __FILE__, __LINE__);
@@ -145,7 +155,7 @@ static void server_worker(rb3_server *S) {
                 const int64_t qi = h_out[i].qid;
                 int64_t j = i + 1;
                 while (j < n && h_out[j].qid == qi) ++j;
-                per[qi].assign(h_out.begin() + i, h_out.begin() + j);
+                per[qi].assign(h_out + i, h_out + j);
                 for (auto &x : per[qi]) x.qid = 0;
                 i = j;
             }
@@ -176,6 +186,7 @@ static void server_worker(rb3_server *S) {
     cudaStreamSynchronize(st);
     cudaFreeHost(h_q);
     cudaFreeHost(h_off);
+    cudaFreeHost(h_out);
     cudaStreamDestroy(st);
 }
 
@@ -222,8 +233,9 @@ RB3_EXPORT int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o,
     return RB3_OK;
 }
 
-RB3_EXPORT int rb3_server_submit(rb3_server *S, const uint8_t *q, int64_t len, int64_t tag, int64_t *req_id) {
-    RB3_CHECK_ARG(S && (len == 0 || q) && len >= 0, "bad argument");
+// A request of the query q[0, len), its symbols checked (A,C,G,T,N codes).
+static int make_req(const uint8_t *q, int64_t len, int64_t tag, rb3_server::Req *r) {
+    RB3_CHECK_ARG((len == 0 || q) && len >= 0, "bad argument");
     RB3_CHECK_ARG(len < (int64_t(1) << 31), "query longer than 2^31 - 1");
     unsigned bad = 0;  // branch-free, so the compiler vectorizes the check
     for (int64_t i = 0; i < len; ++i) bad |= (unsigned)((uint8_t)(q[i] - 1u) > 4u);
@@ -231,10 +243,16 @@ RB3_EXPORT int rb3_server_submit(rb3_server *S, const uint8_t *q, int64_t len, i
         set_error("query symbol outside 1..5 (A,C,G,T,N codes)");
         return RB3_E_INVAL;
     }
+    r->tag = tag;
+    r->q.assign(q, q + len);
+    r->t_submit = now_ns();
+    return RB3_OK;
+}
+
+RB3_EXPORT int rb3_server_submit(rb3_server *S, const uint8_t *q, int64_t len, int64_t tag, int64_t *req_id) {
+    RB3_CHECK_ARG(S != nullptr, "bad argument");
     rb3_server::Req r;
-    r.tag = tag;
-    r.q.assign(q, q + len);
-    r.t_submit = now_ns();
+    RB3_TRY(make_req(q, len, tag, &r));
     {
         std::lock_guard<std::mutex> lk(S->mu);
         r.id = S->next_id++;
@@ -301,13 +319,34 @@ RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t 
     const int64_t t0 = now_ns() + 2000000;
     std::atomic<int> sub_err{RB3_OK};
     std::thread submitter([&] {
-        for (int64_t i = 0; i < n && sub_err.load() == RB3_OK; ++i) {
+        // every request due by now is copied outside the lock and queued under
+        // one lock with one wake-up (as many clients submitting at once would)
+        std::vector<rb3_server::Req> due;
+        for (int64_t i = 0; i < n && sub_err.load() == RB3_OK;) {
             const int64_t target = t0 + arrival_ns[i];
             for (int64_t now = now_ns(); now < target; now = now_ns())
                 if (target - now > 60000) std::this_thread::sleep_for(std::chrono::nanoseconds(target - now - 40000));
-            int64_t id = 0;
-            const int r = rb3_server_submit(S, q + qoff[i], qoff[i + 1] - qoff[i], i, &id);
-            if (r != RB3_OK) sub_err.store(r);
+            const int64_t now = now_ns();
+            due.clear();
+            int64_t j = i;
+            for (; j < n && t0 + arrival_ns[j] <= now && j - i < 4096; ++j) {
+                due.emplace_back();
+                const int r = make_req(q + qoff[j], qoff[j + 1] - qoff[j], j, &due.back());
+                if (r != RB3_OK) {
+                    sub_err.store(r);
+                    due.pop_back();
+                    break;
+                }
+            }
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (auto &r : due) {
+                    r.id = S->next_id++;
+                    S->pending.push_back(std::move(r));
+                }
+            }
+            S->cv_work.notify_all();
+            i = j;
         }
     });
     int64_t got = 0;

@@ -205,14 +205,16 @@ int tune_search(const rb3_index *idx, const uint8_t *q, const int64_t *qoff, con
             o.hot_depth = K;
             RB3_TRY(mem_search_impl(idx, q, qoff, qoff_host, nq, total_q, min_len, min_occ, o, out.as<rb3_smem>(),
                                     cap, &n, st));
-            float t = 0.f;
-            RB3_TRY(time_ms(st, &t, [&] {
-                return mem_search_impl(idx, q, qoff, qoff_host, nq, total_q, min_len, min_occ, o,
-                                       out.as<rb3_smem>(), cap, &n, st);
-            }));
-            if (t < bestkt) {
-                bestkt = t;
-                bestK = K;
+            for (int rep = 0; rep < 2; ++rep) {  // the better of two timings (the gaps are a few %)
+                float t = 0.f;
+                RB3_TRY(time_ms(st, &t, [&] {
+                    return mem_search_impl(idx, q, qoff, qoff_host, nq, total_q, min_len, min_occ, o,
+                                           out.as<rb3_smem>(), cap, &n, st);
+                }));
+                if (t < bestkt) {
+                    bestkt = t;
+                    bestK = K;
+                }
             }
         }
         Key k = search_key(idx, nq, total_q);

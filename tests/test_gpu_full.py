@@ -225,7 +225,7 @@ def test_occ32_index_past_2_to_32():
     for x in (idx, R):
         rb.rb3_merge(x, rb.rb3_build_batch(torch.from_numpy(sseq).to(DEV), np.full(3, 5000, np.int64), opts=opts))
     R2 = rb.rb3_index_compress(idx, 2048)
-    n = info["n"] + 2 + 2 * 15000
+    n = info["n"] + 2 + 2 * (15000 + 3)  # both strands, each string with its sentinel
     assert rb.rb3_index_info(R)["n"] == n
     codes = [torch.empty(n, dtype=torch.uint8, device=DEV) for _ in range(2)]
     occ = [torch.empty((n // 2048 + 1, 6), dtype=torch.int64, device=DEV) for _ in range(2)]
