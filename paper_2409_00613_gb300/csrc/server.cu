@@ -65,8 +65,7 @@ static void server_worker(rb3_server *S) {
     int64_t qcap = budget;
     dev_alloc((void **)&d_q, (size_t)qcap, st);
     dev_alloc((void **)&d_off, sizeof(int64_t) * (size_t)(S->o.max_batch_requests + 1), st);
-    rb3_smem *h_out = nullptr;  // pinned: a pageable copy would go through the driver's staging
-    int64_t h_out_cap = 0;
+    std::vector<rb3_smem> h_out;
     rb3_opts so;
     rb3_opts_default(&so);
     so.search_form = (int32_t)S->o.search_form;
@@ -131,17 +130,8 @@ static void server_worker(rb3_server *S) {
             }
         }
         if (r == RB3_OK) {
-            if (n > h_out_cap) {
-                int64_t want = n > 2 * h_out_cap ? n : 2 * h_out_cap;  // grows geometrically
-                if (want < 65536) want = 65536;
-                cudaFreeHost(h_out);
-                h_out = nullptr;
-                h_out_cap = 0;
-                if (cudaMallocHost(&h_out, sizeof(rb3_smem) * (size_t)want) == cudaSuccess) h_out_cap = want;
-                else r = cuda_fail(cudaGetLastError(), "server: result buffer", __FILE__, __LINE__);
-            }
-            if (r == RB3_OK && n &&
-                cudaMemcpyAsync(h_out, d_out, sizeof(rb3_smem) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            h_out.resize((size_t)n);
+            if (n && cudaMemcpyAsync(h_out.data(), d_out, sizeof(rb3_smem) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "server: copy results", __FILE__, __LINE__);
             if (r == RB3_OK && cudaStreamSynchronize(st) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "server: sync", __FILE__, __LINE__);
@@ -155,7 +145,7 @@ static void server_worker(rb3_server *S) {
                 const int64_t qi = h_out[i].qid;
                 int64_t j = i + 1;
                 while (j < n && h_out[j].qid == qi) ++j;
-                per[qi].assign(h_out + i, h_out + j);
+                per[qi].assign(h_out.begin() + i, h_out.begin() + j);
                 for (auto &x : per[qi]) x.qid = 0;
                 i = j;
             }
@@ -186,7 +176,6 @@ static void server_worker(rb3_server *S) {
     cudaStreamSynchronize(st);
     cudaFreeHost(h_q);
     cudaFreeHost(h_off);
-    cudaFreeHost(h_out);
     cudaStreamDestroy(st);
 }
 
