@@ -827,8 +827,13 @@ def _serve_trace(rb, srv, arr, Q):
     done, batch = rb.rb3_server_replay(srv, Q.q, Q.qoff, arr)
     lat = (done - arr) * 1e3
     bp = int(Q.qoff[-1])
+    ws = rb.rb3_server_stats(srv)
+    busy = max(1, ws["gather_ns"] + ws["search_ns"] + ws["publish_ns"])
     return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "Mbp_per_s": round(bp / float(done.max()) / 1e6, 1), "mean_batch": round(float(batch.mean()), 2)}
+            "Mbp_per_s": round(bp / float(done.max()) / 1e6, 1), "mean_batch": round(float(batch.mean()), 2),
+            "slot_time": {"gather": round(ws["gather_ns"] / busy, 3), "search": round(ws["search_ns"] / busy, 3),
+                          "publish": round(ws["publish_ns"] / busy, 3),
+                          "search_ms_per_batch": round(ws["search_ns"] / 1e6 / max(1, ws["batches"]), 3)}}
 
 
 SERVE_RATES = (2000, 5000, 10000, 20000, 50000, 100000, 200000, 500000, 1000000)

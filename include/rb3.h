@@ -341,6 +341,13 @@ int rb3_server_poll(rb3_server *s, rb3_completion *out, int64_t cap, int64_t *n,
 /* Copies a completed request's SMEMs (start-ordered) and releases them. */
 int rb3_server_take(rb3_server *s, int64_t req_id, rb3_smem *out, int64_t cap, int64_t *n);
 int64_t rb3_server_batches(rb3_server *s);
+/* Where the slots' time went since the server was created (tracing; summed over
+ * slots): out[0] micro-batches, out[1] requests, out[2] query bases, out[3] ns
+ * gathering the requests' queries into a slot's pinned buffer, out[4] ns from
+ * there to the records on the host (query and offset copies, the search, the
+ * records' copy back, the stream synchronized), out[5] ns splitting the
+ * records by request and publishing the completions. */
+int rb3_server_stats(rb3_server *s, int64_t out[6]);
 /* Open-loop load generator on native threads: submits query i (q[qoff[i] ..
  * qoff[i+1]), host memory) at t0 + arrival_ns[i] (non-decreasing, relative to
  * a start t0 a few ms after the call), collects every completion and drops its

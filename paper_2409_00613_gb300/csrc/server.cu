@@ -40,6 +40,11 @@ struct rb3_server {
     int first_error = RB3_OK;
     std::string error_msg;
     std::atomic<int64_t> batches{0};
+    // worker time (rb3_server_stats): requests and bases taken, ns gathering
+    // queries into the slot's pinned buffer, ns in the micro-batch's search
+    // (copies in, search, records back, synchronized), ns splitting records and
+    // publishing completions
+    std::atomic<int64_t> st_requests{0}, st_bases{0}, st_gather_ns{0}, st_search_ns{0}, st_publish_ns{0};
 };
 
 namespace rb3 {
@@ -85,6 +90,7 @@ static void server_worker(rb3_server *S) {
                 S->pending.pop_front();
             }
         }
+        const int64_t t_take = now_ns();
         // concatenate (a request longer than the budget gets its own buffer)
         int64_t total = 0;
         for (auto &r : batch) total += (int64_t)r.q.size();
@@ -100,6 +106,7 @@ static void server_worker(rb3_server *S) {
             memcpy(hq + h_off[i], batch[i].q.data(), batch[i].q.size());
             h_off[i + 1] = h_off[i] + (int64_t)batch[i].q.size();
         }
+        const int64_t t_gathered = now_ns();
         int r = RB3_OK;
         if (total > qcap) {
             dev_free(d_q, st);
@@ -169,6 +176,11 @@ static void server_worker(rb3_server *S) {
             }
         }
         S->cv_done.notify_all();
+        S->st_requests.fetch_add(nq);
+        S->st_bases.fetch_add(total);
+        S->st_gather_ns.fetch_add(t_gathered - t_take);
+        S->st_search_ns.fetch_add(t_done - t_gathered);
+        S->st_publish_ns.fetch_add(now_ns() - t_done);
     }
     dev_free(d_q, st);
     dev_free(d_off, st);
@@ -289,6 +301,17 @@ RB3_EXPORT int rb3_server_take(rb3_server *S, int64_t req_id, rb3_smem *out, int
 }
 
 RB3_EXPORT int64_t rb3_server_batches(rb3_server *S) { return S ? S->batches.load() : 0; }
+
+RB3_EXPORT int rb3_server_stats(rb3_server *S, int64_t out[6]) {
+    RB3_CHECK_ARG(S && out, "NULL argument");
+    out[0] = S->batches.load();
+    out[1] = S->st_requests.load();
+    out[2] = S->st_bases.load();
+    out[3] = S->st_gather_ns.load();
+    out[4] = S->st_search_ns.load();
+    out[5] = S->st_publish_ns.load();
+    return RB3_OK;
+}
 
 // Open-loop replay of an arrival trace from native threads: a submitter thread
 // submits request i at t0 + arrival_ns[i] (sleeping until shortly before, then

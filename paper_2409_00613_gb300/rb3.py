@@ -113,6 +113,7 @@ def lib():
             "rb3_server_take": (ctypes.c_int, [_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)]),
             "rb3_server_replay": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
             "rb3_server_batches": (_i64, [_vp]),
+            "rb3_server_stats": (ctypes.c_int, [_vp, _vp]),
             "rb3_server_destroy": (None, [_vp]),
             "rb3_probe_random_gather": (ctypes.c_int, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double),
                                                        ctypes.POINTER(ctypes.c_double), _vp]),
@@ -602,6 +603,15 @@ def rb3_server_replay(srv: Server, q, qoff, arrival_s):
 
 def rb3_server_batches(srv: Server) -> int:
     return int(lib().rb3_server_batches(srv.handle))
+
+
+def rb3_server_stats(srv: Server) -> dict:
+    """Slot time since creation (see include/rb3.h): batches, requests, bases and
+    ns gathering / searching / publishing, summed over slots."""
+    v = (_i64 * 6)()
+    _check(lib().rb3_server_stats(srv.handle, v))
+    return {"batches": v[0], "requests": v[1], "bases": v[2], "gather_ns": v[3], "search_ns": v[4],
+            "publish_ns": v[5]}
 
 
 def rb3_server_destroy(srv: Server):

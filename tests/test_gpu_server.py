@@ -107,8 +107,13 @@ def test_server_replay_open_loop():
         arr = np.cumsum(synth.rng(5).exponential(1.0 / rate, size=Q.nq))
         srv = rb.rb3_server_create(idx, slots=4)
         done, batch = rb.rb3_server_replay(srv, Q.q, Q.qoff, arr)
+        st = rb.rb3_server_stats(srv)
+        nb = rb.rb3_server_batches(srv)
         srv.close()
         assert (done >= arr).all() and (batch >= 1).all()
+        # the slots' accounts: every request and base once, in the batches run
+        assert st["batches"] == nb and st["requests"] == Q.nq and st["bases"] == int(Q.qoff[-1])
+        assert min(st["gather_ns"], st["search_ns"], st["publish_ns"]) >= 0 and st["search_ns"] > 0
         if rate > 1e6:
             assert batch.max() > 1
     with pytest.raises(rb.RB3Error):
