@@ -316,7 +316,7 @@ typedef struct {
     int32_t min_len;            /* SMEM length threshold (default 31) */
     int32_t slots;              /* micro-batches in flight (default 4) */
     int64_t min_occ;            /* occurrence threshold (default 1) */
-    int64_t max_batch_bases;    /* query bases per micro-batch (default 8 Mi) */
+    int64_t max_batch_bases;    /* query bases per micro-batch (default 32 Mi) */
     int64_t max_batch_requests; /* requests per micro-batch (default 4096; 1 = no batching) */
     int64_t search_form;        /* rb3_opts.search_form of the micro-batches' search (default 0) */
     int64_t hot_depth;          /* rb3_opts.hot_depth of the micro-batches' search (default 0); the
@@ -348,7 +348,8 @@ int64_t rb3_server_batches(rb3_server *s);
  * records' copy back, the stream synchronized), out[5] ns splitting the
  * records by request and publishing the completions. */
 int rb3_server_stats(rb3_server *s, int64_t out[6]);
-/* Open-loop load generator on native threads: submits query i (q[qoff[i] ..
+/* Open-loop load generator on native threads (four submitting, as several
+ * clients would, and the caller's collecting): submits query i (q[qoff[i] ..
  * qoff[i+1]), host memory) at t0 + arrival_ns[i] (non-decreasing, relative to
  * a start t0 a few ms after the call), collects every completion and drops its
  * records; done_ns[i] = its completion time - t0 (latency = done_ns[i] -

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "wait.cuh"
 
 namespace rb3 {
 
@@ -67,6 +68,14 @@ int dev_alloc(void **p, size_t bytes, cudaStream_t st) {
 
 void dev_free(void *p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
+}
+
+int wait_stream_blocking(cudaStream_t st) {
+    thread_local cudaEvent_t ev = nullptr;  // released with the context
+    if (!ev) RB3_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming));
+    RB3_CUDA_TRY(cudaEventRecord(ev, st));
+    RB3_CUDA_TRY(cudaEventSynchronize(ev));
+    return RB3_OK;
 }
 
 int DevBuf::alloc(size_t nbytes, cudaStream_t s) {

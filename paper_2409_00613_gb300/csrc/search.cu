@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "wait.cuh"
 #include "smem.cuh"
 
 namespace cg = cooperative_groups;
@@ -505,14 +506,16 @@ int mem_search_impl(const rb3_index *idx, const uint8_t *q, const int64_t *qoff,
                     RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_chunked<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff,
                                                    nq, items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ,
                                                    d_next, raw.as<rb3_smem>(), scap, d_count));
-                else
-                    RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_steps<NS>, nb_for(threads, 256), 256, 0, st, V, q, qoff,
+                else  // one-warp CTAs: a warp's registers go back to the SM as soon as its lanes run out
+                      // of chunks, not when the CTA's slowest warp does (micro-batches of other
+                      // streams then get the SM)
+                    RB3_WITH_NS(idx->D, RB3_LAUNCH(k_smem_steps<NS>, nb_for(threads, 32), 32, 0, st, V, q, qoff,
                                                    nq, items.as<int64_t>(), nitems, chunk, (int)min_len, min_occ,
                                                    d_next, raw.as<rb3_smem>(), scap, d_count, hot, hotK));
             }
         }
         RB3_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st));
-        RB3_CUDA_TRY(cudaStreamSynchronize(st));
+        RB3_TRY(wait_stream_blocking(st));  // the search takes milliseconds: sleep, do not spin
         if ((int64_t)count <= scap || (int64_t)count > cap) break;
         scap = (int64_t)count;  // rerun with room for every record
     }

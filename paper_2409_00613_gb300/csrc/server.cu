@@ -20,6 +20,7 @@
 #include <thread>
 
 #include "common.cuh"
+#include "wait.cuh"
 
 struct rb3_server {
     const rb3_index *idx = nullptr;
@@ -45,6 +46,10 @@ struct rb3_server {
     // (copies in, search, records back, synchronized), ns splitting records and
     // publishing completions
     std::atomic<int64_t> st_requests{0}, st_bases{0}, st_gather_ns{0}, st_search_ns{0}, st_publish_ns{0};
+    // slots whose stream and buffers are set up (rb3_server_create waits for
+    // all of them), and the first setup failure
+    int ready = 0;
+    int setup_error = RB3_OK;
 };
 
 namespace rb3 {
@@ -68,8 +73,19 @@ static void server_worker(rb3_server *S) {
     rb3_smem *d_out = nullptr;
     int64_t out_cap = 0;
     int64_t qcap = budget;
-    dev_alloc((void **)&d_q, (size_t)qcap, st);
-    dev_alloc((void **)&d_off, sizeof(int64_t) * (size_t)(S->o.max_batch_requests + 1), st);
+    int setup = st ? RB3_OK : RB3_E_CUDA;
+    if (setup == RB3_OK) setup = h_q && h_off ? RB3_OK : RB3_E_NOMEM;
+    if (setup == RB3_OK) setup = dev_alloc((void **)&d_q, (size_t)qcap, st);
+    if (setup == RB3_OK)
+        setup = dev_alloc((void **)&d_off, sizeof(int64_t) * (size_t)(S->o.max_batch_requests + 1), st);
+    if (setup == RB3_OK && cudaStreamSynchronize(st) != cudaSuccess) setup = RB3_E_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->ready;
+        if (setup != RB3_OK && S->setup_error == RB3_OK) S->setup_error = setup;
+        if (setup != RB3_OK) S->stop = true;  // the server is not started; the other slots leave too
+    }
+    S->cv_done.notify_all();
     std::vector<rb3_smem> h_out;
     rb3_opts so;
     rb3_opts_default(&so);
@@ -140,8 +156,7 @@ static void server_worker(rb3_server *S) {
             h_out.resize((size_t)n);
             if (n && cudaMemcpyAsync(h_out.data(), d_out, sizeof(rb3_smem) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 r = cuda_fail(cudaGetLastError(), "server: copy results", __FILE__, __LINE__);
-            if (r == RB3_OK && cudaStreamSynchronize(st) != cudaSuccess)
-                r = cuda_fail(cudaGetLastError(), "server: sync", __FILE__, __LINE__);
+            if (r == RB3_OK) r = wait_stream_blocking(st);  // slots sleep while their batch runs
         }
         const int64_t t_done = now_ns();
         S->batches.fetch_add(1);
@@ -188,7 +203,7 @@ static void server_worker(rb3_server *S) {
     cudaStreamSynchronize(st);
     cudaFreeHost(h_q);
     cudaFreeHost(h_off);
-    cudaStreamDestroy(st);
+    if (st) cudaStreamDestroy(st);
 }
 
 }  // namespace rb3
@@ -201,7 +216,7 @@ RB3_EXPORT void rb3_server_opts_default(rb3_server_opts *o) {
     o->min_len = 31;
     o->min_occ = 1;
     o->slots = 4;
-    o->max_batch_bases = 8 << 20;
+    o->max_batch_bases = 32 << 20;
     o->max_batch_requests = 4096;
 }
 
@@ -230,6 +245,16 @@ RB3_EXPORT int rb3_server_create(const rb3_index *idx, const rb3_server_opts *o,
     S->o = opt;
     cudaGetDevice(&S->dev);
     for (int i = 0; i < opt.slots; ++i) S->workers.emplace_back(server_worker, S);
+    {  // every slot's stream and buffers exist before the first request arrives
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_done.wait(lk, [&] { return S->ready == opt.slots; });
+    }
+    if (S->setup_error != RB3_OK) {
+        const int e = S->setup_error;
+        rb3_server_destroy(S);
+        set_error("server: a slot's stream or buffers could not be set up");
+        return e;
+    }
     *out = S;
     return RB3_OK;
 }
@@ -313,11 +338,11 @@ RB3_EXPORT int rb3_server_stats(rb3_server *S, int64_t out[6]) {
     return RB3_OK;
 }
 
-// Open-loop replay of an arrival trace from native threads: a submitter thread
-// submits request i at t0 + arrival_ns[i] (sleeping until shortly before, then
-// spinning), while the calling thread collects the completions and drops their
-// records; done_ns[i] = completion time - t0 (CLOCK_MONOTONIC), batch[i] =
-// size of its micro-batch.
+// Open-loop replay of an arrival trace from native threads: four submitting
+// threads queue request i at t0 + arrival_ns[i] (sleeping until shortly
+// before, then spinning), while the calling thread collects the completions and
+// drops their records; done_ns[i] = completion time - t0 (CLOCK_MONOTONIC),
+// batch[i] = size of its micro-batch.
 RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t *qoff, int64_t n,
                                  const int64_t *arrival_ns, int64_t *done_ns, int32_t *batch) {
     set_error("%s", "");
@@ -330,18 +355,21 @@ RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t 
     RB3_CHECK_ARG(n == 0 || qoff[n] == qoff[0] || q, "q is NULL");
     const int64_t t0 = now_ns() + 2000000;
     std::atomic<int> sub_err{RB3_OK};
-    std::thread submitter([&] {
-        // every request due by now is copied outside the lock and queued under
-        // one lock with one wake-up (as many clients submitting at once would)
+    // several submitting threads (as several clients would be), thread t taking
+    // requests t, t + T, t + 2T, ...: each copies and checks every one of its
+    // requests due by now outside the lock, then queues them under one lock
+    // with one wake-up
+    constexpr int T = 4;
+    auto submit_part = [&](int t) {
         std::vector<rb3_server::Req> due;
-        for (int64_t i = 0; i < n && sub_err.load() == RB3_OK;) {
+        for (int64_t i = t; i < n && sub_err.load() == RB3_OK;) {
             const int64_t target = t0 + arrival_ns[i];
             for (int64_t now = now_ns(); now < target; now = now_ns())
                 if (target - now > 60000) std::this_thread::sleep_for(std::chrono::nanoseconds(target - now - 40000));
             const int64_t now = now_ns();
             due.clear();
             int64_t j = i;
-            for (; j < n && t0 + arrival_ns[j] <= now && j - i < 4096; ++j) {
+            for (; j < n && t0 + arrival_ns[j] <= now && (int64_t)due.size() < 4096; j += T) {
                 due.emplace_back();
                 const int r = make_req(q + qoff[j], qoff[j + 1] - qoff[j], j, &due.back());
                 if (r != RB3_OK) {
@@ -360,7 +388,9 @@ RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t 
             S->cv_work.notify_all();
             i = j;
         }
-    });
+    };
+    std::vector<std::thread> submitters;
+    for (int t = 0; t < T; ++t) submitters.emplace_back(submit_part, t);
     int64_t got = 0;
     int status = RB3_OK;
     std::vector<rb3_completion> c(4096);
@@ -379,7 +409,7 @@ RB3_EXPORT int rb3_server_replay(rb3_server *S, const uint8_t *q, const int64_t 
             ++got;
         }
     }
-    submitter.join();
+    for (auto &th : submitters) th.join();
     if (status == RB3_OK && sub_err.load() != RB3_OK) status = sub_err.load();
     return status;
 }
