@@ -44,8 +44,8 @@ constexpr int BW_MAXN = 2 * BW_NP;    // the SA intervals of P$'s substrings: be
 constexpr int BW_HASH = 8192;         // node hash slots (a power of two, twice the nodes)
 constexpr int BW_THREADS = 256;
 constexpr int BW_PER = BW_NP / BW_THREADS;
-constexpr int BW_CAP_S = 256, BW_WARPS_S = 6;  // cell tables, as the linear-query kernel
-constexpr int BW_CAP_L = 2048, BW_WARPS_L = 2;
+constexpr int BW_CAP_S = 256, BW_WARPS_S = 1;  // cell tables, as the linear-query kernel
+constexpr int BW_CAP_L = 2048, BW_WARPS_L = 1;
 static_assert(dv_warp_bytes(BW_CAP_S) % 16 == 0 && dv_warp_bytes(BW_CAP_L) % 16 == 0, "table alignment");
 
 // edges of a query with np = |P| + 1: at most one per node and symbol
